@@ -1,0 +1,381 @@
+"""FP64 CPU oracle of the object-centric 2DGS rasterizer — TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this module.  The product path (the CUDA library and
+its Python binding) never imports, calls or falls back to it.
+
+What it computes is the plain definition of the method, written in FP64
+PyTorch CPU ops so that reverse-mode autograd gives the exact adjoint of the
+same procedure with its discrete decisions (skip, stop, clamp, min branch,
+normal flip) held fixed:
+
+* per pixel, every non-culled surfel is a candidate; candidates are taken in
+  ascending centre depth, ties by ascending index (front-to-back order,
+  Sec. 4.3 "rendered in front-to-back order");
+* the ray through the pixel centre meets the surfel plane at (u, v), found as
+  the crossing of the two homogeneous pixel planes pulled back through the
+  surfel's 3x3 splat-to-pixel matrix (2DGS ray-splat intersection, prior work
+  the paper builds on, Sec. 3.2 and Sec. 5.1);
+* rho = min(u^2 + v^2, |x - c|^2 / sigma_f^2) with sigma_f^2 = 1/2 px^2
+  (screen-space low-pass filter), alpha = min(0.99, o exp(-rho/2));
+  a candidate is skipped if rho > 9 or alpha < 1/255, and compositing stops
+  at the first candidate for which T (1 - alpha) < 1e-4, which is not
+  blended (Sec. 4.3: rendering ends once the pixel reaches an opacity close
+  to 1, or the candidates are exhausted);
+* blending weight w = alpha T; colour C = sum w rgb, accumulated opacity
+  A = sum w (the A_i of Eq. 1), depth D = sum w z, normal N = sum w n;
+* background loss L_b = (1/(h w)) sum A (1 - M) (Eq. 1);
+* contribution score of a surfel = max blending weight over all pixels of
+  all views; the surfel is "used" (visible, not occluded) iff the score is
+  > 0 (Sec. 4.3), and the keep-set at threshold tau is {score > tau}.
+
+Readings of points the paper leaves to prior work (documented with the
+project's design notes): culling of a surfel whose 3-sigma square reaches
+the near plane; depth z = camera depth of the ray-plane hit when the surfel
+term wins the min, else the centre depth; normals flipped to face the
+camera; SH colour max(0, sum c_lm Y_lm(d) + 0.5) with the real SH basis with
+Condon-Shortley phase.  Parity of these readings against the paper itself is
+unpinned: the paper does not fix them.
+
+Inputs are numpy arrays (see ``synthetic.py`` for the layout).
+"""
+from __future__ import annotations
+
+import math
+from typing import Optional
+
+import numpy as np
+import torch
+
+DT = torch.float64
+
+SIGMA_F2 = 0.5          # low-pass filter variance, px^2 (sigma_f = sqrt(2)/2 px)
+RHO_CUT = 9.0           # support cut-off, rho <= 9 (3 sigma)
+ALPHA_MIN = 1.0 / 255.0  # skip candidates below this opacity
+ALPHA_MAX = 0.99        # opacity clamp
+T_EPS = 1e-4            # stop once the transmittance would fall below this
+
+FRAGILE_REL = 1e-5      # relative margin for flagging decisions FP32 may take differently
+
+
+# ----------------------------------------------------------------------------- helpers
+def _t(a) -> torch.Tensor:
+    return torch.as_tensor(np.asarray(a, dtype=np.float64), dtype=DT)
+
+
+def quat_to_rotmat(q: torch.Tensor) -> torch.Tensor:
+    """Rotation matrix of unit quaternions q = (w, x, y, z) (Hamilton convention), [N,3,3]."""
+    w, x, y, z = q.unbind(-1)
+    r00 = 1 - 2 * (y * y + z * z)
+    r01 = 2 * (x * y - w * z)
+    r02 = 2 * (x * z + w * y)
+    r10 = 2 * (x * y + w * z)
+    r11 = 1 - 2 * (x * x + z * z)
+    r12 = 2 * (y * z - w * x)
+    r20 = 2 * (x * z - w * y)
+    r21 = 2 * (y * z + w * x)
+    r22 = 1 - 2 * (x * x + y * y)
+    return torch.stack([torch.stack([r00, r01, r02], -1),
+                        torch.stack([r10, r11, r12], -1),
+                        torch.stack([r20, r21, r22], -1)], -2)
+
+
+def sh_basis(d: torch.Tensor, degree: int) -> torch.Tensor:
+    """Real spherical harmonics of unit directions d [N,3], degrees 0..degree, [N,(deg+1)^2].
+
+    Basis: for m > 0, sqrt(2) Re Y_l^m; for m < 0, sqrt(2) Im Y_l^|m|; Y_l^0 for
+    m = 0, where Y_l^m are the complex orthonormal harmonics with the
+    Condon-Shortley phase.  Order within a degree: m = -l .. l.
+    """
+    x, y, z = d.unbind(-1)
+    pi = math.pi
+    out = [torch.full_like(x, 0.5 / math.sqrt(pi))]
+    if degree >= 1:
+        k1 = math.sqrt(3.0 / (4.0 * pi))
+        out += [-k1 * y, k1 * z, -k1 * x]
+    if degree >= 2:
+        k2a = 0.5 * math.sqrt(15.0 / pi)
+        k2b = 0.25 * math.sqrt(5.0 / pi)
+        k2c = 0.25 * math.sqrt(15.0 / pi)
+        out += [k2a * x * y, -k2a * y * z, k2b * (2 * z * z - x * x - y * y),
+                -k2a * x * z, k2c * (x * x - y * y)]
+    if degree >= 3:
+        k3a = math.sqrt(70.0 / pi) / 8.0
+        k3b = 0.5 * math.sqrt(105.0 / pi)
+        k3c = math.sqrt(42.0 / pi) / 8.0
+        k3d = 0.25 * math.sqrt(7.0 / pi)
+        k3e = 0.25 * math.sqrt(105.0 / pi)
+        out += [-k3a * y * (3 * x * x - y * y),
+                k3b * x * y * z,
+                -k3c * y * (4 * z * z - x * x - y * y),
+                k3d * z * (2 * z * z - 3 * x * x - 3 * y * y),
+                -k3c * x * (4 * z * z - x * x - y * y),
+                k3e * z * (x * x - y * y),
+                -k3a * x * (x * x - 3 * y * y)]
+    if degree > 3:
+        raise ValueError("SH degree must be 0..3")
+    return torch.stack(out, -1)
+
+
+def camera_tensors(cam: dict):
+    vm = _t(cam["viewmat"])
+    K = _t([[cam["fx"], 0.0, cam["cx"]], [0.0, cam["fy"], cam["cy"]], [0.0, 0.0, 1.0]])
+    return vm[:3, :3], vm[:3, 3], K
+
+
+def param_tensors(g: dict, requires_grad: bool = False) -> dict:
+    out = {k: _t(g[k]).requires_grad_(requires_grad) for k in ("xyz", "quat", "scale", "opacity", "sh")}
+    return out
+
+
+# ----------------------------------------------------------------------------- projection
+def project(p: dict, cam: dict, sh_degree: int) -> dict:
+    """Per-surfel, per-view quantities (differentiable w.r.t. the parameters in ``p``).
+
+    The surfel is P(u,v) = x + s_u t_u u + s_v t_v v, with t_u, t_v the first
+    two columns of the rotation of the normalised quaternion.  Its 3x3
+    splat-to-pixel matrix is T = K [R s_u t_u, R s_v t_v, R x + t], so that
+    (x z, y z, z)^T = T (u, v, 1)^T for the image point of P(u,v).
+    """
+    r_cw, t_cw, K = camera_tensors(cam)
+    q = p["quat"] / p["quat"].norm(dim=-1, keepdim=True)
+    rot = quat_to_rotmat(q)
+    t_u, t_v = rot[..., 0], rot[..., 1]
+    su, sv = p["scale"][:, 0:1], p["scale"][:, 1:2]
+    U = (su * t_u) @ r_cw.T             # camera-frame tangent axes (scaled)
+    V = (sv * t_v) @ r_cw.T
+    pc = p["xyz"] @ r_cw.T + t_cw       # camera-frame centre
+    Hc = torch.stack([U, V, pc], dim=-1)  # [N,3,3], columns act on (u, v, 1)
+    T = K @ Hc
+    z_c = pc[:, 2]
+    # cull a surfel whose 3-sigma square has a corner at or behind the near plane
+    z_min = z_c - 3.0 * (U[:, 2].abs() + V[:, 2].abs())
+    culled = (z_min <= cam["near"]).detach()
+    # camera-frame normal, flipped to face the camera
+    n_cam = torch.linalg.cross(t_u, t_v) @ r_cw.T
+    facing = ((n_cam * pc).sum(-1) > 0).detach()
+    n_cam = torch.where(facing[:, None], -n_cam, n_cam)
+    # view-dependent colour
+    campos = -(r_cw.T @ t_cw)
+    d = p["xyz"] - campos
+    d = d / d.norm(dim=-1, keepdim=True)
+    basis = sh_basis(d, sh_degree)                         # [N,K]
+    rgb_raw = (basis[:, :, None] * p["sh"]).sum(1) + 0.5   # [N,3]
+    rgb = rgb_raw.clamp(min=0.0)
+    return dict(T=T, z_c=z_c, culled=culled, normal=n_cam, rgb=rgb, rgb_raw=rgb_raw,
+                opacity=p["opacity"], cull_margin=(z_min - cam["near"]).detach())
+
+
+def depth_order(z_c: torch.Tensor) -> torch.Tensor:
+    """Front-to-back order: ascending centre depth, ties by ascending index."""
+    return torch.sort(z_c.detach(), stable=True).indices
+
+
+# ----------------------------------------------------------------------------- candidates
+def candidate_mask(T: torch.Tensor, scale: torch.Tensor, cam: dict, xs: torch.Tensor,
+                   ys: torch.Tensor) -> torch.Tensor:
+    """Conservative candidate test [B,n]: False only where rho > 9 is certain.
+
+    rho <= 9 needs either u^2 + v^2 <= 9, whose hit point lies within
+    3 max(s_u, s_v) of the centre so the pixel ray passes that close to it, or
+    |x - c|^2 <= 9 sigma_f^2.  Dropping the other candidates cannot change a
+    result: they are skipped by the support test anyway.
+    """
+    with torch.no_grad():
+        pc_x = (T[:, 0, 2] - cam["cx"] * T[:, 2, 2]) / cam["fx"]
+        pc_y = (T[:, 1, 2] - cam["cy"] * T[:, 2, 2]) / cam["fy"]
+        pc = torch.stack([pc_x, pc_y, T[:, 2, 2]], -1)               # camera-frame centre
+        r = 3.0 * scale.max(dim=-1).values
+        dx = (xs - cam["cx"]) / cam["fx"]
+        dy = (ys - cam["cy"]) / cam["fy"]
+        dirs = torch.stack([dx, dy, torch.ones_like(dx)], -1)
+        dirs = dirs / dirs.norm(dim=-1, keepdim=True)                 # [B,3]
+        proj = dirs @ pc.T                                            # [B,n]
+        dist2 = (pc * pc).sum(-1)[None, :] - proj * proj
+        near_ray = dist2 <= (r * r)[None, :] * (1 + 1e-6) + 1e-12
+        cx = T[:, 0, 2] / T[:, 2, 2]
+        cy = T[:, 1, 2] / T[:, 2, 2]
+        fd2 = (xs[:, None] - cx[None, :]) ** 2 + (ys[:, None] - cy[None, :]) ** 2
+        near_c = fd2 <= RHO_CUT * SIGMA_F2 * (1 + 1e-6)
+        return near_ray | near_c
+
+
+# ----------------------------------------------------------------------------- compositing
+def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
+    """Front-to-back compositing of the candidates (columns, already in depth order)
+    for the pixel centres (xs, ys) (rows).  Returns per-pixel outputs and the
+    per-candidate blending weights."""
+    B = xs.shape[0]
+    n = T.shape[0]
+    if n == 0:
+        z = torch.zeros(B, dtype=DT)
+        return dict(rgb=torch.zeros(B, 3, dtype=DT), alpha=z, depth=z.clone(),
+                    normal=torch.zeros(B, 3, dtype=DT), t_final=torch.ones(B, dtype=DT),
+                    n_blended=torch.zeros(B, dtype=torch.int64),
+                    fragile=torch.zeros(B, dtype=torch.bool),
+                    fragile_grad=torch.zeros(B, dtype=torch.bool), w=torch.zeros(B, 0, dtype=DT))
+    # homogeneous pixel planes h_x = (-1, 0, x), h_y = (0, -1, y) pulled back to (u, v, 1)
+    row0, row1, row2 = T[:, 0, :], T[:, 1, :], T[:, 2, :]
+    h_u = -row0[None] + xs[:, None, None] * row2[None]   # [B,n,3]
+    h_v = -row1[None] + ys[:, None, None] * row2[None]
+    cr = torch.linalg.cross(h_u, h_v)
+    degenerate = (cr[..., 2] == 0).detach()
+    w_h = torch.where(degenerate, torch.ones_like(cr[..., 2]), cr[..., 2])
+    u = cr[..., 0] / w_h
+    v = cr[..., 1] / w_h
+    rho3 = torch.where(degenerate, torch.full_like(u, math.inf), u * u + v * v)
+    cx = row0[:, 2] / row2[:, 2]
+    cy = row1[:, 2] / row2[:, 2]
+    rho2 = ((xs[:, None] - cx[None]) ** 2 + (ys[:, None] - cy[None]) ** 2) / SIGMA_F2
+    rho = torch.minimum(rho3, rho2)
+    alpha_raw = opacity[None] * torch.exp(-0.5 * rho)
+    alpha = alpha_raw.clamp(max=ALPHA_MAX)
+    valid = ((rho <= RHO_CUT) & (alpha >= ALPHA_MIN)).detach()
+    use_hit = (rho3 <= rho2).detach()
+    z_hit = row2[None, :, 0] * u + row2[None, :, 1] * v + row2[None, :, 2]
+    z = torch.where(use_hit, z_hit, z_c[None].expand(B, n))
+    a = torch.where(valid, alpha, torch.zeros_like(alpha))
+    one_minus = 1.0 - a
+    t_incl = torch.cumprod(one_minus, dim=1)
+    blended = (valid & (t_incl.detach() >= T_EPS))
+    ones = torch.ones(B, 1, dtype=DT)
+    t_excl = torch.cat([ones, t_incl[:, :-1]], dim=1)
+    w = torch.where(blended, a * t_excl, torch.zeros_like(a))
+    out = dict(
+        rgb=w @ rgb, alpha=w.sum(1), depth=(w * z).sum(1), normal=w @ normal,
+        t_final=torch.where(blended, one_minus, torch.ones_like(a)).prod(1),
+        n_blended=blended.sum(1), w=w)
+    # decisions that a float32 evaluation may take the other way
+    with torch.no_grad():
+        e = FRAGILE_REL
+        a_at_cut = (opacity * math.exp(-0.5 * RHO_CUT)).clamp(max=ALPHA_MAX)
+        f_cut = ((rho - RHO_CUT).abs() <= e * RHO_CUT) & (a_at_cut[None] >= ALPHA_MIN * (1 - e))
+        f_amin = ((alpha_raw - ALPHA_MIN).abs() <= e * ALPHA_MIN) & (rho <= RHO_CUT * (1 + e))
+        f_stop = valid & ((t_incl - T_EPS).abs() <= e * T_EPS)
+        f_branch = blended & ((rho3 - rho2).abs() <= e * torch.maximum(rho3.clamp(max=1e30), rho2))
+        fragile = (f_cut | f_amin | f_stop | f_branch).any(1)
+        f_clamp = blended & ((alpha_raw - ALPHA_MAX).abs() <= e)
+        f_grad = f_clamp
+        if rgb_raw is not None:
+            g_col = (rgb_raw.abs() <= e).any(-1)
+            f_grad = f_grad | (blended & g_col[None])
+        out["fragile"] = fragile
+        out["fragile_grad"] = fragile | f_grad.any(1)
+    return out
+
+
+# ----------------------------------------------------------------------------- render
+def pixel_centres(cam: dict, pixels: Optional[np.ndarray]):
+    W, H = cam["width"], cam["height"]
+    if pixels is None:
+        pixels = np.arange(W * H)
+    pixels = np.asarray(pixels, np.int64)
+    xs = _t(pixels % W + 0.5)
+    ys = _t(pixels // W + 0.5)
+    return pixels, xs, ys
+
+
+def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optional[dict] = None,
+           prefilter: bool = True, chunk: int = 256) -> dict:
+    """Render one view at the given flat pixel indices (row-major, default all).
+
+    Returns numpy FP64 arrays: rgb [P,3], alpha [P], depth [P], normal [P,3],
+    t_final [P], n_blended [P], fragile [P], fragile_grad [P], and score [N]
+    (max blending weight of each surfel over these pixels).  If ``d_out`` holds
+    cotangents (rgb, alpha, depth, normal) for these pixels, also returns
+    ``grads``: d(sum <d_out, out>)/d(xyz, quat, scale, opacity, sh).
+    """
+    need_grad = d_out is not None
+    params = param_tensors(g, requires_grad=need_grad)
+    N = params["xyz"].shape[0]
+    pixels, xs_all, ys_all = pixel_centres(cam, pixels)
+    P = len(pixels)
+    proj = project(params, cam, g["sh_degree"])
+    alive = torch.nonzero(~proj["culled"]).flatten()
+    order = alive[depth_order(proj["z_c"][alive])]          # front-to-back candidate list
+    keys = ("T", "z_c", "normal", "rgb", "opacity")
+    base = {k: proj[k].detach() for k in keys}
+    acc = {k: torch.zeros_like(base[k]) for k in keys} if need_grad else None
+    res = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), depth=np.zeros(P), normal=np.zeros((P, 3)),
+               t_final=np.ones(P), n_blended=np.zeros(P, np.int64), fragile=np.zeros(P, bool),
+               fragile_grad=np.zeros(P, bool))
+    score = torch.zeros(N, dtype=DT)
+    if need_grad:
+        dts = {k: _t(d_out[k]) for k in ("rgb", "alpha", "depth", "normal")}
+    scale_d = params["scale"].detach()
+    rgb_raw = proj["rgb_raw"].detach()
+    for s in range(0, P, chunk):
+        e = min(P, s + chunk)
+        xs, ys = xs_all[s:e], ys_all[s:e]
+        cols = order
+        if prefilter and len(order) > 0:
+            m = candidate_mask(base["T"][order], scale_d[order], cam, xs, ys)
+            cols = order[m.any(0)]
+        sub = {k: base[k][cols].clone().requires_grad_(need_grad) for k in keys}
+        out = composite(sub["T"], sub["z_c"], sub["normal"], sub["rgb"], sub["opacity"], xs, ys,
+                        rgb_raw=rgb_raw[cols])
+        for k in ("rgb", "alpha", "depth", "normal", "t_final", "n_blended", "fragile", "fragile_grad"):
+            res[k][s:e] = out[k].detach().numpy()
+        if len(cols):
+            score[cols] = torch.maximum(score[cols], out["w"].detach().max(0).values)
+        if need_grad and len(cols):
+            loss = ((out["rgb"] * dts["rgb"][s:e]).sum() + (out["alpha"] * dts["alpha"][s:e]).sum()
+                    + (out["depth"] * dts["depth"][s:e]).sum() + (out["normal"] * dts["normal"][s:e]).sum())
+            gs = torch.autograd.grad(loss, [sub[k] for k in keys], allow_unused=True)
+            for k, gk in zip(keys, gs):
+                if gk is not None:
+                    acc[k].index_add_(0, cols, gk)
+    res["score"] = score.numpy()
+    res["cull_margin"] = proj["cull_margin"].numpy()
+    if need_grad:
+        torch.autograd.backward([proj[k] for k in keys], [acc[k] for k in keys])
+        res["grads"] = {k: (params[k].grad.numpy() if params[k].grad is not None
+                            else np.zeros(params[k].shape)) for k in params}
+    return res
+
+
+def render_views(g: dict, cams: list, d_outs: Optional[list] = None, pixels: Optional[list] = None,
+                 prefilter: bool = True) -> list:
+    """``render`` over several views; gradients (if requested) are per view."""
+    out = []
+    for i, cam in enumerate(cams):
+        out.append(render(g, cam, None if pixels is None else pixels[i],
+                          None if d_outs is None else d_outs[i], prefilter=prefilter))
+    return out
+
+
+# ----------------------------------------------------------------------------- paper's additions
+def background_loss(alpha: np.ndarray, mask: np.ndarray) -> float:
+    """L_b = (1 / (h w)) sum A (1 - M) over one view (Eq. 1); alpha and mask are [h,w]."""
+    a = np.asarray(alpha, np.float64)
+    m = np.asarray(mask, np.float64)
+    return float(np.sum(a * (1.0 - m)) / a.size)
+
+
+def background_loss_grad(mask: np.ndarray, gamma: float) -> np.ndarray:
+    """d(gamma L_b)/dA = gamma (1 - M) / (h w) (Eq. 1 weighted as in Eq. 3)."""
+    m = np.asarray(mask, np.float64)
+    return gamma * (1.0 - m) / m.size
+
+
+def contribution_score(g: dict, cams: list, prefilter: bool = True) -> np.ndarray:
+    """Max blending weight of every surfel over all pixels of all views (Sec. 4.3)."""
+    score = np.zeros(len(g["opacity"]))
+    for cam in cams:
+        score = np.maximum(score, render(g, cam, prefilter=prefilter)["score"])
+    return score
+
+
+def keep_set(score: np.ndarray, tau: float, borderline: float = 1e-6):
+    """Keep-set {score > tau} and the indices whose score lies within ``borderline`` of tau."""
+    s = np.asarray(score, np.float64)
+    keep = s > tau
+    near = np.nonzero(np.abs(s - tau) <= borderline)[0]
+    return keep, near
+
+
+def prune(g: dict, keep: np.ndarray) -> dict:
+    """Keep the surfels flagged in ``keep``, in their original order."""
+    out = {k: np.asarray(g[k])[keep] for k in ("xyz", "quat", "scale", "opacity", "sh")}
+    out["sh_degree"] = g["sh_degree"]
+    return out

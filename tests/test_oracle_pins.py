@@ -1,0 +1,376 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test fixes a plausible mistake in the oracle: a wrong rotation or SH
+sign (library routines), a wrong intersection (closed forms and an
+independent world-space ray-plane solve), a wrong compositing order,
+termination or cut-off (hand-computed stacks), a wrong adjoint (central
+finite differences), and a wrong loss or pruning rule (hand sums).
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+from scipy.spatial.transform import Rotation
+from scipy import special
+
+import oracle
+import synthetic
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SQ2PI = 2.0 * math.sqrt(math.pi)
+
+
+def surfels(xyz, quat, scale, opacity, rgb):
+    """Degree-0 surfels whose rendered colour is exactly ``rgb``."""
+    xyz = np.asarray(xyz, np.float64).reshape(-1, 3)
+    n = len(xyz)
+    return dict(xyz=xyz, quat=np.asarray(quat, np.float64).reshape(n, 4),
+                scale=np.asarray(scale, np.float64).reshape(n, 2),
+                opacity=np.asarray(opacity, np.float64).reshape(n),
+                sh=((np.asarray(rgb, np.float64).reshape(n, 1, 3) - 0.5) * SQ2PI), sh_degree=0)
+
+
+# rotation about +x by 90 deg maps the surfel normal +z to -y: facing a camera on the -y axis
+Q_FACE = [math.cos(math.pi / 4), math.sin(math.pi / 4), 0.0, 0.0]
+
+
+def cam65(width=65, height=65):
+    return synthetic.make_camera((0.0, -3.0, 0.0), width, height)
+
+
+def pix(cam, ix, iy):
+    return np.array([iy * cam["width"] + ix])
+
+
+# ----------------------------------------------------------------------------- library pins
+def test_quaternion_matches_scipy():
+    rng = np.random.default_rng(0)
+    q = rng.normal(size=(64, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    ours = oracle.quat_to_rotmat(torch.tensor(q)).numpy()
+    ref = Rotation.from_quat(q, scalar_first=True).as_matrix()
+    np.testing.assert_allclose(ours, ref, atol=1e-13)
+
+
+def test_sh_basis_matches_scipy_complex_harmonics():
+    rng = np.random.default_rng(1)
+    d = rng.normal(size=(50, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    theta = np.arccos(d[:, 2])
+    phi = np.arctan2(d[:, 1], d[:, 0])
+    ours = oracle.sh_basis(torch.tensor(d), 3).numpy()
+    col = 0
+    for l in range(4):
+        for m in range(-l, l + 1):
+            y = special.sph_harm_y(l, abs(m), theta, phi)
+            if m > 0:
+                ref = math.sqrt(2.0) * y.real
+            elif m < 0:
+                ref = math.sqrt(2.0) * y.imag
+            else:
+                ref = y.real
+            np.testing.assert_allclose(ours[:, col], ref, atol=1e-13, err_msg=f"l={l} m={m}")
+            col += 1
+
+
+# ----------------------------------------------------------------------------- closed forms
+def test_fronto_parallel_centre_hit():
+    cam = cam65()
+    rgb = [0.2, 0.7, 0.4]
+    g = surfels([0, 0, 0], Q_FACE, [0.1, 0.1], 0.6, rgb)
+    r = oracle.render(g, cam, pix(cam, 32, 32))
+    np.testing.assert_allclose(r["alpha"], [0.6], atol=1e-14)
+    np.testing.assert_allclose(r["rgb"][0], 0.6 * np.array(rgb), atol=1e-14)
+    np.testing.assert_allclose(r["depth"], [0.6 * 3.0], atol=1e-13)
+    np.testing.assert_allclose(r["normal"][0], [0.0, 0.0, -0.6], atol=1e-14)
+    np.testing.assert_allclose(r["t_final"], [0.4], atol=1e-14)
+
+
+def test_opacity_clamp_at_centre():
+    cam = cam65()
+    g = surfels([0, 0, 0], Q_FACE, [0.1, 0.1], 1.0, [1, 1, 1])
+    r = oracle.render(g, cam, pix(cam, 32, 32))
+    np.testing.assert_allclose(r["alpha"], [0.99], atol=1e-14)
+
+
+@pytest.mark.parametrize("s,dx,branch", [(0.2, 3, "surfel"), (0.1, 2, "surfel"), (0.005, 1, "filter")])
+def test_fronto_parallel_falloff(s, dx, branch):
+    """Ray through pixel offset dx meets the plane z = 3 at X = dx z / f: u = X / s."""
+    cam = cam65()
+    o = 0.8
+    g = surfels([0, 0, 0], Q_FACE, [s, s], o, [0.5, 0.5, 0.5])
+    r = oracle.render(g, cam, pix(cam, 32 + dx, 32))
+    rho3 = (dx * 3.0 / (cam["fx"] * s)) ** 2
+    rho2 = 2.0 * dx * dx
+    rho = min(rho3, rho2)
+    assert (rho3 <= rho2) == (branch == "surfel")
+    a = o * math.exp(-0.5 * rho)
+    np.testing.assert_allclose(r["alpha"], [a], rtol=1e-12)
+    np.testing.assert_allclose(r["depth"], [a * 3.0], rtol=1e-12)
+
+
+def test_oblique_surfel_matches_ray_plane_intersection():
+    """Tilted surfel: depth and (u, v) from the textbook ray-plane intersection."""
+    cam = synthetic.make_camera((0.0, -3.0, 0.0), 48, 40)
+    rng = np.random.default_rng(5)
+    q = Rotation.from_euler("xyz", [70, 25, 10], degrees=True).as_quat(scalar_first=True)
+    s = np.array([0.35, 0.2])
+    o = 0.7
+    centre = np.array([0.05, 0.1, -0.04])
+    g = surfels(centre, q, s, o, [0.3, 0.3, 0.3])
+    R = Rotation.from_quat(q, scalar_first=True).as_matrix()
+    vm = cam["viewmat"]
+    r_cw, t_cw = vm[:3, :3], vm[:3, 3]
+    p = r_cw @ centre + t_cw
+    U, V = r_cw @ (s[0] * R[:, 0]), r_cw @ (s[1] * R[:, 1])
+    n = np.cross(U, V)
+    px = np.arange(48 * 40)
+    r = oracle.render(g, cam, px, prefilter=False)
+    for k, pidx in enumerate(px):
+        x, y = pidx % 48 + 0.5, pidx // 48 + 0.5
+        d = np.array([(x - cam["cx"]) / cam["fx"], (y - cam["cy"]) / cam["fy"], 1.0])
+        t = n @ p / (n @ d)                 # camera depth of the hit (d has unit z)
+        X = t * d
+        u = (X - p) @ U / (U @ U)
+        v = (X - p) @ V / (V @ V)
+        rho3 = u * u + v * v
+        c = np.array([cam["fx"] * p[0] / p[2] + cam["cx"], cam["fy"] * p[1] / p[2] + cam["cy"]])
+        rho2 = ((x - c[0]) ** 2 + (y - c[1]) ** 2) * 2.0
+        rho = min(rho3, rho2)
+        a = min(0.99, o * math.exp(-0.5 * rho))
+        if rho > 9 or a < 1 / 255:
+            a = 0.0
+        z = t if rho3 <= rho2 else p[2]
+        np.testing.assert_allclose(r["alpha"][k], a, atol=1e-12)
+        np.testing.assert_allclose(r["depth"][k], a * z, atol=1e-11)
+    assert (r["alpha"] > 0).sum() > 100
+
+
+def test_two_splat_ordering_and_swap():
+    cam = cam65()
+    c1, c2 = np.array([1.0, 0.2, 0.1]), np.array([0.1, 0.3, 0.9])
+    o1, o2 = 0.6, 0.7
+    # surfel 0 at depth 2 (world y = -1), surfel 1 at depth 3 (y = 0)
+    g = surfels([[0, -1, 0], [0, 0, 0]], [Q_FACE, Q_FACE], [[0.3, 0.3]] * 2, [o1, o2], [c1, c2])
+    r = oracle.render(g, cam, pix(cam, 32, 32))
+    np.testing.assert_allclose(r["rgb"][0], o1 * c1 + (1 - o1) * o2 * c2, atol=1e-14)
+    np.testing.assert_allclose(r["depth"], [o1 * 2.0 + (1 - o1) * o2 * 3.0], atol=1e-13)
+    g2 = surfels([[0, 0, 0], [0, -1, 0]], [Q_FACE, Q_FACE], [[0.3, 0.3]] * 2, [o1, o2], [c1, c2])
+    r2 = oracle.render(g2, cam, pix(cam, 32, 32))
+    np.testing.assert_allclose(r2["rgb"][0], o2 * c2 + (1 - o2) * o1 * c1, atol=1e-14)
+    # equal depth: ties resolve to ascending index
+    g3 = surfels([[0, 0, 0], [0, 0, 0]], [Q_FACE, Q_FACE], [[0.3, 0.3]] * 2, [o1, o2], [c1, c2])
+    r3 = oracle.render(g3, cam, pix(cam, 32, 32))
+    np.testing.assert_allclose(r3["rgb"][0], o1 * c1 + (1 - o1) * o2 * c2, atol=1e-14)
+
+
+@pytest.mark.parametrize("o,expect", [(0.95, 3), (0.8, 5), (0.5, 13)])
+def test_termination_blends_closed_form_count(o, expect):
+    """A stack of equal surfels blends k = floor(log 1e-4 / log(1 - o)) of them."""
+    cam = cam65()
+    m = 20
+    xyz = [[0, -1.0 + 0.02 * i, 0] for i in range(m)]
+    g = surfels(xyz, [Q_FACE] * m, [[0.4, 0.4]] * m, [o] * m, [[0.5, 0.5, 0.5]] * m)
+    r = oracle.render(g, cam, pix(cam, 32, 32))
+    k = math.floor(math.log(1e-4) / math.log(1 - o))
+    assert k == expect
+    assert r["n_blended"][0] == k
+    np.testing.assert_allclose(r["t_final"], [(1 - o) ** k], rtol=1e-12)
+    np.testing.assert_allclose(r["alpha"], [1 - (1 - o) ** k], rtol=1e-12)
+
+
+@pytest.mark.parametrize("rho_target,blended", [(8.9, True), (9.1, False)])
+def test_support_cutoff(rho_target, blended):
+    cam = cam65()
+    dx = 4
+    s = dx * 3.0 / (cam["fx"] * math.sqrt(rho_target))   # rho3 = rho_target < rho2 = 32
+    g = surfels([0, 0, 0], Q_FACE, [s, s], 0.9, [0.5, 0.5, 0.5])
+    r = oracle.render(g, cam, pix(cam, 32 + dx, 32))
+    expect = 0.9 * math.exp(-0.5 * rho_target) if blended else 0.0
+    np.testing.assert_allclose(r["alpha"], [expect], rtol=1e-10, atol=1e-15)
+
+
+@pytest.mark.parametrize("factor,blended", [(1.01, True), (0.99, False)])
+def test_alpha_floor(factor, blended):
+    cam = cam65()
+    dx, s = 3, 0.15
+    rho = (dx * 3.0 / (cam["fx"] * s)) ** 2
+    o = factor * (1 / 255) / math.exp(-0.5 * rho)
+    g = surfels([0, 0, 0], Q_FACE, [s, s], o, [0.5, 0.5, 0.5])
+    r = oracle.render(g, cam, pix(cam, 32 + dx, 32))
+    np.testing.assert_allclose(r["alpha"], [factor / 255 if blended else 0.0], rtol=1e-10, atol=1e-15)
+
+
+def test_near_plane_cull():
+    """A surfel whose 3-sigma square crosses the near plane is not rendered."""
+    cam = cam65()
+    # camera at y=-3 looks along +y; a surfel at depth 0.5 tilted so its square spans depth +-0.4
+    q = Rotation.from_euler("x", 45, degrees=True).as_quat(scalar_first=True)
+    g = surfels([0, -2.5, 0], q, [0.2, 0.2], 0.9, [1, 1, 1])
+    r = oracle.render(g, cam)
+    assert r["alpha"].max() == 0.0
+    assert r["cull_margin"][0] < 0
+
+
+# ----------------------------------------------------------------------------- invariants
+def test_weights_plus_final_transmittance_is_one():
+    sc = synthetic.small_scene(11, 300, 40, 33, degree=1)
+    r = oracle.render(sc["gaussians"], sc["cameras"][0])
+    np.testing.assert_allclose(r["alpha"] + r["t_final"], 1.0, atol=1e-12)
+    assert r["alpha"].max() > 0.5
+
+
+def test_prefilter_is_exact():
+    sc = synthetic.small_scene(12, 400, 37, 29, degree=2)
+    a = oracle.render(sc["gaussians"], sc["cameras"][0], prefilter=True, chunk=97)
+    b = oracle.render(sc["gaussians"], sc["cameras"][0], prefilter=False, chunk=1000)
+    for k in ("rgb", "alpha", "depth", "normal", "t_final"):
+        np.testing.assert_allclose(a[k], b[k], atol=1e-13, err_msg=k)
+    np.testing.assert_array_equal(a["n_blended"], b["n_blended"])
+    np.testing.assert_array_equal(a["score"], b["score"])
+
+
+def _brute_force(g, cam):
+    """Independent per-pixel loop: world-space ray-plane solve, explicit projection."""
+    vm = cam["viewmat"]
+    r_cw, t_cw = vm[:3, :3], vm[:3, 3]
+    origin = -r_cw.T @ t_cw
+    q = g["quat"] / np.linalg.norm(g["quat"], axis=1, keepdims=True)
+    Rs = Rotation.from_quat(q, scalar_first=True).as_matrix()
+    n = len(q)
+    W, H = cam["width"], cam["height"]
+    out = np.zeros((H * W, 8))
+    zc = np.array([(r_cw @ g["xyz"][i] + t_cw)[2] for i in range(n)])
+    order = sorted(range(n), key=lambda i: (zc[i], i))
+    deg = g["sh_degree"]
+    for pidx in range(H * W):
+        x, y = pidx % W + 0.5, pidx // W + 0.5
+        d_cam = np.array([(x - cam["cx"]) / cam["fx"], (y - cam["cy"]) / cam["fy"], 1.0])
+        d_w = r_cw.T @ d_cam
+        T = 1.0
+        acc = np.zeros(8)
+        for i in order:
+            p = g["xyz"][i]
+            tu, tv, tw = Rs[i][:, 0], Rs[i][:, 1], Rs[i][:, 2]
+            su, sv = g["scale"][i]
+            pc = r_cw @ p + t_cw
+            zmin = pc[2] - 3 * (abs((r_cw @ (su * tu))[2]) + abs((r_cw @ (sv * tv))[2]))
+            if zmin <= cam["near"]:
+                continue
+            A = np.stack([d_w, -su * tu, -sv * tv], axis=1)
+            try:
+                t, u, v = np.linalg.solve(A, p - origin)
+                rho3 = u * u + v * v
+            except np.linalg.LinAlgError:
+                rho3 = math.inf
+            c = np.array([cam["fx"] * pc[0] / pc[2] + cam["cx"], cam["fy"] * pc[1] / pc[2] + cam["cy"]])
+            rho2 = ((x - c[0]) ** 2 + (y - c[1]) ** 2) / 0.5
+            rho = min(rho3, rho2)
+            a = min(0.99, g["opacity"][i] * math.exp(-0.5 * rho))
+            if rho > 9 or a < 1 / 255:
+                continue
+            if T * (1 - a) < 1e-4:
+                break
+            w = a * T
+            z = (r_cw @ (origin + t * d_w) + t_cw)[2] if rho3 <= rho2 else pc[2]
+            nc = r_cw @ tw
+            if nc @ pc > 0:
+                nc = -nc
+            dirv = (p - origin) / np.linalg.norm(p - origin)
+            basis = oracle.sh_basis(torch.tensor(dirv[None]), deg).numpy()[0]
+            rgb = np.maximum(basis @ g["sh"][i] + 0.5, 0.0)
+            acc += w * np.concatenate([rgb, [1.0, z], nc])
+            T *= 1 - a
+        out[pidx] = acc
+    return out
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_brute_force_tiny_scene(seed):
+    sc = synthetic.small_scene(seed, 8, 16, 16, degree=1, scale_range=(0.2, 0.6))
+    g, cam = sc["gaussians"], sc["cameras"][0]
+    g = {k: (np.asarray(v, np.float64) if k != "sh_degree" else v) for k, v in g.items()}
+    r = oracle.render(g, cam, prefilter=False)
+    bf = _brute_force(g, cam)
+    np.testing.assert_allclose(r["rgb"], bf[:, 0:3], atol=1e-11)
+    np.testing.assert_allclose(r["alpha"], bf[:, 3], atol=1e-11)
+    np.testing.assert_allclose(r["depth"], bf[:, 4], atol=1e-10)
+    np.testing.assert_allclose(r["normal"], bf[:, 5:8], atol=1e-11)
+    assert r["alpha"].max() > 0.3
+
+
+# ----------------------------------------------------------------------------- adjoint
+def _loss(g, cam, d_out, px):
+    r = oracle.render(g, cam, px, prefilter=False)
+    return (np.sum(r["rgb"] * d_out["rgb"]) + np.sum(r["alpha"] * d_out["alpha"])
+            + np.sum(r["depth"] * d_out["depth"]) + np.sum(r["normal"] * d_out["normal"])), r
+
+
+def test_adjoint_matches_central_differences():
+    sc = synthetic.small_scene(31, 6, 12, 10, degree=2, scale_range=(0.25, 0.6))
+    g = {k: (np.asarray(v, np.float64).copy() if k != "sh_degree" else v) for k, v in sc["gaussians"].items()}
+    cam = sc["cameras"][0]
+    px = np.arange(12 * 10)
+    rng = np.random.default_rng(3)
+    d_out = dict(rgb=rng.normal(size=(len(px), 3)), alpha=rng.normal(size=len(px)),
+                 depth=rng.normal(size=len(px)), normal=rng.normal(size=(len(px), 3)))
+    r = oracle.render(g, cam, px, d_out=d_out, prefilter=False)
+    grads = r["grads"]
+    base_sig = r["n_blended"]
+    checked = 0
+    for key in ("xyz", "quat", "scale", "opacity", "sh"):
+        flat = g[key].reshape(-1)
+        gflat = grads[key].reshape(-1)
+        for j in range(flat.size):
+            x0 = flat[j]
+            h = 1e-6 * max(1.0, abs(x0))
+            flat[j] = x0 + h
+            lp, rp = _loss(g, cam, d_out, px)
+            flat[j] = x0 - h
+            lm, rm = _loss(g, cam, d_out, px)
+            flat[j] = x0
+            if not (np.array_equal(rp["n_blended"], base_sig) and np.array_equal(rm["n_blended"], base_sig)):
+                continue  # a discrete decision flipped: the derivative is not defined there
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - gflat[j]) <= 1e-6 * max(1.0, abs(fd)), (key, j, fd, gflat[j])
+            checked += 1
+    assert checked > 100
+
+
+# ----------------------------------------------------------------------------- background loss and pruning
+def test_background_loss_hand_sum():
+    with open(os.path.join(GOLDEN, "background_loss_4x4.json")) as f:
+        case = json.load(f)
+    a = np.array(case["alpha"])
+    m = np.array(case["mask"])
+    assert oracle.background_loss(a, m) == pytest.approx(case["loss"], abs=1e-15)
+    np.testing.assert_allclose(oracle.background_loss_grad(m, 0.5), 0.5 * (1 - m) / 16, atol=0)
+
+
+def test_hidden_surfel_scores_zero_and_lone_surfel_scores_opacity():
+    cam = cam65()
+    m = 6
+    x_lone = 22.0 * 3.0 / cam["fx"]   # projects exactly onto the centre of pixel (54, 32)
+    # an opaque stack in front (0.95 each): every pixel the hidden surfel reaches terminates first
+    xyz = [[0, -1.0 + 0.02 * i, 0] for i in range(m)] + [[0, 0.5, 0], [x_lone, 0, 0]]
+    scales = [[0.2, 0.2]] * m + [[0.05, 0.05], [0.02, 0.02]]
+    g = surfels(xyz, [Q_FACE] * (m + 2), scales, [0.95] * m + [0.9, 0.7], [[0.5, 0.5, 0.5]] * (m + 2))
+    score = oracle.contribution_score(g, [cam])
+    assert score[m] == 0.0                              # hidden behind the stack
+    assert score[m + 1] == pytest.approx(0.7, abs=1e-9)  # lone surfel, hit at its centre
+    assert score[0] == pytest.approx(0.95, abs=1e-9)
+    keep, near = oracle.keep_set(score, 0.0)
+    assert not keep[m] and keep[m + 1] and keep[0]
+    keep, near = oracle.keep_set(np.array([0.01, 0.0100000005, 0.02]), 0.01)
+    np.testing.assert_array_equal(keep, [False, True, True])
+    np.testing.assert_array_equal(near, [0, 1])
+
+
+def test_lone_surfel_exact_score_at_centre_pixel():
+    cam = cam65()
+    g = surfels([0, 0, 0], Q_FACE, [0.1, 0.1], 0.42, [0.5, 0.5, 0.5])
+    score = oracle.contribution_score(g, [cam])
+    assert score[0] == pytest.approx(0.42, abs=1e-14)
