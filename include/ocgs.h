@@ -1,0 +1,212 @@
+/*
+ * ocgs.h — C ABI of the GB300-native object-centric 2D Gaussian Splatting rasterizer.
+ *
+ * The library implements the data-parallel hot path of "Object-Centric 2D
+ * Gaussian Splatting" (Rogge & Stricker, arXiv 2501.08174): the differentiable
+ * tile-based 2DGS rasterizer it extends (Sec. 3.2, Sec. 5.1), the background
+ * loss on accumulated opacity (Sec. 4.2, Eq. 1) and the occlusion-aware
+ * pruning that records which Gaussians take part in alpha blending
+ * (Sec. 4.3).  One process drives one GPU; every call is asynchronous on the
+ * context's CUDA stream unless stated otherwise.
+ *
+ * Conventions shared by every call
+ *  - Pointers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them and never writes outside the stated extents.
+ *    Pointers named "host" are ordinary host memory read during the call.
+ *  - Parameter arrays are float32, one array per attribute, row-major:
+ *      xyz [n,3], quat [n,4] = (w,x,y,z) (any non-zero norm; normalised inside),
+ *      scale [n,2] = (s_u, s_v) > 0, opacity [n] in (0,1], sh [n,(deg+1)^2,3].
+ *    These are the activated values; exp/sigmoid activations are the caller's.
+ *  - Images of several views are concatenated: view v occupies pixels
+ *    [off_v, off_v + W_v*H_v) with off_v = sum_{u<v} W_u*H_u, row-major inside
+ *    a view.  rgb and normal are [P,3], alpha and depth are [P].
+ *  - Cameras are pinhole, world->camera, OpenCV axes (+z forward, +y down);
+ *    pixel (i,j) has its centre at (i+0.5, j+0.5).
+ *  - Return value: OCGS_OK or an error code; on error ocgs_last_error() gives
+ *    a one-line reason.  Argument errors are detected before any launch.
+ *    Errors found on the device (non-finite parameters, a capacity overflow)
+ *    are reported by the next call that synchronises (ocgs_render, ocgs_prune,
+ *    ocgs_sync).  There is no CPU fallback: without a CUDA device every call
+ *    returns OCGS_ERR_CUDA.
+ */
+#ifndef OCGS_H
+#define OCGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define OCGS_ABI_VERSION 1
+
+typedef enum {
+  OCGS_OK = 0,
+  OCGS_ERR_ARG = 1,        /* invalid argument (null pointer, bad size, bad degree) */
+  OCGS_ERR_OOM = 2,        /* device allocation failed */
+  OCGS_ERR_CUDA = 3,       /* a CUDA runtime call or kernel launch failed */
+  OCGS_ERR_TIMEOUT = 4,    /* a bounded device wait gave up */
+  OCGS_ERR_NONFINITE = 5,  /* a parameter was NaN/Inf; that Gaussian was not rendered */
+  OCGS_ERR_CAPACITY = 6,   /* more (tile, Gaussian) pairs than 2^31-1 in one call */
+  OCGS_ERR_STATE = 7       /* forward state missing, released or from another context */
+} ocgs_status;
+
+typedef struct ocgs_ctx ocgs_ctx;
+typedef struct ocgs_fwd_state ocgs_fwd_state;
+
+/* Read-only Gaussian parameters (device, caller-owned). n may be 0. */
+typedef struct {
+  const float* xyz;
+  const float* quat;
+  const float* scale;
+  const float* opacity;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree; /* 0..3 */
+  int32_t reserved;
+} ocgs_gaussians;
+
+/* Writable arrays in the parameter layout (device, caller-owned): gradients
+ * (accumulated with +=) or the destination of a pruning compaction. */
+typedef struct {
+  float* xyz;
+  float* quat;
+  float* scale;
+  float* opacity;
+  float* sh;
+} ocgs_gaussians_out;
+
+/* Pinhole camera (host). viewmat is row-major world->camera [R t; 0 0 0 1]. */
+typedef struct {
+  float viewmat[16];
+  float fx, fy, cx, cy;
+  int32_t width, height;  /* 1..16384 each */
+  float near_plane;       /* > 0; a Gaussian whose 3-sigma square reaches it is culled */
+  int32_t reserved;
+} ocgs_camera;
+
+/* Per-pixel images (device, caller-owned). As render output every pointer
+ * must be non-null.  As backward cotangents any pointer may be NULL (zero). */
+typedef struct {
+  float* rgb;     /* [P,3] C = sum w rgb */
+  float* alpha;   /* [P]   A = sum w, the accumulated opacity of Eq. 1 */
+  float* depth;   /* [P]   D = sum w z  (not normalised by A) */
+  float* normal;  /* [P,3] N = sum w n  (camera frame, not normalised) */
+} ocgs_image;
+
+/* Launch options.  None of them changes a result: the support test is exact
+ * and the screen bounds are conservative, so tiles only reshape the work. */
+typedef struct {
+  int32_t tile_w;      /* 8, 16 or 32 */
+  int32_t tile_h;      /* 8 or 16; tile_w*tile_h in {64,128,256} */
+  int32_t persistent;  /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
+  int32_t reserved;
+} ocgs_options;
+
+/* Counters of the last ocgs_render / ocgs_accumulate_contribution. */
+typedef struct {
+  int64_t n_gaussians;    /* N */
+  int64_t n_views;        /* V */
+  int64_t n_pixels;       /* P, all views */
+  int64_t n_visible;      /* (view, Gaussian) records with at least one tile */
+  int64_t n_pairs;        /* K, (tile, Gaussian) pairs over all views */
+  int64_t n_tiles;        /* tiles over all views */
+  int32_t tile_w, tile_h;
+} ocgs_stats;
+
+const char* ocgs_status_str(ocgs_status s);
+const char* ocgs_last_error(const ocgs_ctx* ctx);
+int32_t ocgs_abi_version(void);
+
+/* Create a context on `device` that issues work on `stream` (a cudaStream_t;
+ * NULL = the legacy default stream).  The context owns its scratch memory
+ * (stream-ordered pool allocations) and frees it in ocgs_destroy. */
+ocgs_status ocgs_create(ocgs_ctx** ctx, int32_t device, void* stream);
+ocgs_status ocgs_destroy(ocgs_ctx* ctx);
+ocgs_status ocgs_set_stream(ocgs_ctx* ctx, void* stream);
+ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* opts);
+ocgs_status ocgs_get_options(const ocgs_ctx* ctx, ocgs_options* opts);
+ocgs_status ocgs_get_stats(const ocgs_ctx* ctx, ocgs_stats* stats);
+/* Wait for the context stream and report device-side errors. */
+ocgs_status ocgs_sync(ocgs_ctx* ctx);
+
+/*
+ * ocgs_render — forward rasterization of n_views views in one batched pass
+ * (surfel projection, tile binning with a key sort, front-to-back alpha
+ * compositing; Sec. 3.2 and Sec. 4.3 "rendered in front-to-back order ...
+ * terminated once ... a threshold opacity close to 1").
+ *   gaussians  device parameters (see above)
+ *   cams       host [n_views] cameras, n_views >= 1
+ *   out        device images, P = sum W*H pixels; fully overwritten
+ *   score      device [n] or NULL. When given, score[i] = max(score[i], w) over
+ *              every pixel where Gaussian i was blended with weight w (the
+ *              "used during the color accumulation step" record of Sec. 4.3
+ *              and Sec. 5.1). The caller zeroes it before the first view.
+ *   state      NULL, or receives an opaque forward state for
+ *              ocgs_render_backward; release it with ocgs_state_release.
+ * Synchronises once to size the pair buffers.
+ */
+ocgs_status ocgs_render(ocgs_ctx* ctx, const ocgs_gaussians* gaussians, const ocgs_camera* cams,
+                        int32_t n_views, const ocgs_image* out, float* score,
+                        ocgs_fwd_state** state);
+
+/*
+ * ocgs_render_backward — gradients of a scalar loss through ocgs_render
+ * (the backpropagation step of Sec. 3.2).  d_out holds dL/d(rgb, alpha, depth,
+ * normal) per pixel (NULL planes are zero).  The gradients with respect to
+ * xyz, quat (through the normalisation), scale, opacity and sh are ADDED to
+ * d_params (device, caller-zeroed).  The parameters in `gaussians` must be the
+ * ones the forward used.  The state stays valid for further backward calls.
+ */
+ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* state,
+                                 const ocgs_gaussians* gaussians, const ocgs_image* d_out,
+                                 const ocgs_gaussians_out* d_params);
+
+ocgs_status ocgs_state_release(ocgs_ctx* ctx, ocgs_fwd_state* state);
+
+/*
+ * ocgs_background_loss — L_b = (1/(h*w)) * sum A*(1-M) per view (Eq. 1).
+ *   alpha   device [P] accumulated opacity (render output)
+ *   mask    device [P] uint8, 1 on the object, 0 on the background
+ *   cams    host [n_views] (only width/height are read)
+ *   loss    device [n_views] float64, overwritten with the unweighted L_b
+ *   d_alpha device [P] or NULL: d_alpha += gamma*(1-M)/(h*w), the gradient of
+ *           gamma*L_b (gamma = 0.5 in Sec. 5.1, weight of Eq. 3)
+ * Deterministic (fixed-order FP64 reduction).
+ */
+ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_t* mask,
+                                 const ocgs_camera* cams, int32_t n_views, float gamma,
+                                 double* loss, float* d_alpha);
+
+/*
+ * ocgs_accumulate_contribution — the occlusion-aware pruning sweep (Sec. 4.3,
+ * Sec. 5.1): a forward pass over n_views views that only records, for every
+ * Gaussian, score[i] = max(score[i], max blending weight over all pixels).
+ * A Gaussian that is never blended (outside every frustum, or behind pixels
+ * that reached the termination opacity first) keeps score 0.
+ *   score  device [n], max-accumulated; the caller zeroes it once per sweep.
+ */
+ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* gaussians,
+                                         const ocgs_camera* cams, int32_t n_views, float* score);
+
+/*
+ * ocgs_prune — keep-set {i : score[i] > threshold} (threshold 0 reproduces
+ * the paper's "never used in blending" rule of Sec. 4.3) and stream
+ * compaction of the parameters in their original order.
+ *   in          device parameters, n Gaussians
+ *   out         device arrays with room for n Gaussians (must not alias in)
+ *   n_kept      host, receives the number kept
+ *   borderline  device [borderline_cap] int64 or NULL: indices i with
+ *               |score[i] - threshold| <= 1e-6, ascending
+ *   n_borderline host, receives how many such indices exist (may exceed cap)
+ * Synchronises.
+ */
+ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold,
+                       const ocgs_gaussians* in, const ocgs_gaussians_out* out, int64_t* n_kept,
+                       int64_t* borderline, int64_t borderline_cap, int64_t* n_borderline);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OCGS_H */

@@ -1,0 +1,272 @@
+"""PyTorch binding of libocgs: argument marshalling only.
+
+Every function here validates tensors, passes their device pointers and the
+current CUDA stream to the C ABI of ``include/ocgs.h`` and returns torch
+tensors.  All arithmetic of the method runs in the library's CUDA kernels;
+nothing here computes a rasterizer result, and nothing falls back to the CPU.
+
+Parameter layout (float32, CUDA, contiguous): xyz [N,3], quat [N,4] (w,x,y,z),
+scale [N,2], opacity [N], sh [N,(deg+1)^2,3].  Cameras are dicts with a
+4x4 world->camera ``viewmat`` (OpenCV axes), ``fx, fy, cx, cy``, ``width``,
+``height`` and ``near``.  Images of several views are concatenated in view
+order: rgb [P,3], alpha [P], depth [P], normal [P,3].
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _lib
+
+PARAM_KEYS = ("xyz", "quat", "scale", "opacity", "sh")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _check_param(name: str, t: torch.Tensor, shape_tail, device) -> None:
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, expected {device}")
+    if tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected [N,{','.join(map(str, shape_tail))}]")
+
+
+def sh_degree_of(sh: torch.Tensor) -> int:
+    k = sh.shape[1]
+    deg = int(round(k ** 0.5)) - 1
+    if (deg + 1) ** 2 != k or not 0 <= deg <= 3:
+        raise ValueError(f"sh must be [N,(deg+1)^2,3] with deg 0..3, got {tuple(sh.shape)}")
+    return deg
+
+
+def gaussians_struct(g: dict, device) -> _lib.Gaussians:
+    n = g["xyz"].shape[0]
+    deg = sh_degree_of(g["sh"])
+    for key, tail in (("xyz", (3,)), ("quat", (4,)), ("scale", (2,)), ("opacity", ()),
+                      ("sh", ((deg + 1) ** 2, 3))):
+        _check_param(key, g[key], tail, device)
+        if g[key].shape[0] != n:
+            raise ValueError(f"{key} has {g[key].shape[0]} rows, expected {n}")
+    return _lib.Gaussians(_ptr(g["xyz"]), _ptr(g["quat"]), _ptr(g["scale"]), _ptr(g["opacity"]),
+                          _ptr(g["sh"]), n, deg, 0)
+
+
+def camera_array(cameras: Sequence[dict]):
+    arr = (_lib.Camera * len(cameras))()
+    for i, cam in enumerate(cameras):
+        vm = np.asarray(cam["viewmat"], np.float64).reshape(16)
+        c = arr[i]
+        for k in range(16):
+            c.viewmat[k] = float(vm[k])
+        c.fx, c.fy, c.cx, c.cy = float(cam["fx"]), float(cam["fy"]), float(cam["cx"]), float(cam["cy"])
+        c.width, c.height = int(cam["width"]), int(cam["height"])
+        c.near_plane = float(cam.get("near", 0.2))
+    return arr
+
+
+def n_pixels(cameras: Sequence[dict]) -> int:
+    return int(sum(int(c["width"]) * int(c["height"]) for c in cameras))
+
+
+def pixel_offsets(cameras: Sequence[dict]) -> list:
+    off = [0]
+    for c in cameras:
+        off.append(off[-1] + int(c["width"]) * int(c["height"]))
+    return off
+
+
+class ForwardState:
+    """Opaque forward state of one ``render`` call (owned by its Rasterizer)."""
+
+    def __init__(self, rast: "Rasterizer", handle: C.c_void_p, n: int, deg: int, cameras):
+        self._rast = rast
+        self.handle = handle
+        self.n = n
+        self.sh_degree = deg
+        self.cameras = list(cameras)
+
+    def release(self) -> None:
+        if self.handle:
+            self._rast._call("ocgs_state_release", self._rast._ctx, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
+class Rasterizer:
+    """One libocgs context on one CUDA device."""
+
+    def __init__(self, device=None, tile=(16, 16), persistent: bool = False):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device) \
+            if not isinstance(device, torch.device) else device
+        ctx = C.c_void_p()
+        st = self.lib.ocgs_create(C.byref(ctx), self.device.index, None)
+        if st != _lib.OK:
+            raise _lib.OcgsError(st, "ocgs_create failed (is a CUDA device present?)")
+        self._ctx = ctx
+        self.set_options(tile=tile, persistent=persistent)
+
+    # -- plumbing
+    def _call(self, name: str, *args) -> int:
+        st = getattr(self.lib, name)(*args)
+        if st != _lib.OK:
+            raise _lib.OcgsError(st, self.lib.ocgs_last_error(self._ctx).decode())
+        return st
+
+    def _bind_stream(self) -> None:
+        s = torch.cuda.current_stream(self.device).cuda_stream
+        self.lib.ocgs_set_stream(self._ctx, C.c_void_p(s))
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            self.lib.ocgs_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, tile=(16, 16), persistent: bool = False) -> None:
+        o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), 0)
+        self._call("ocgs_set_options", self._ctx, C.byref(o))
+        self.tile = (int(tile[0]), int(tile[1]))
+        self.persistent = bool(persistent)
+
+    def stats(self) -> dict:
+        s = _lib.Stats()
+        self._call("ocgs_get_stats", self._ctx, C.byref(s))
+        return {k: getattr(s, k) for k, _ in _lib.Stats._fields_}
+
+    def sync(self) -> None:
+        self._call("ocgs_sync", self._ctx)
+
+    # -- the method
+    def render(self, gaussians: dict, cameras: Sequence[dict], score: Optional[torch.Tensor] = None,
+               keep_state: bool = True, out: Optional[dict] = None):
+        """Forward rasterization of all ``cameras`` in one batched pass.
+
+        Returns ({rgb, alpha, depth, normal}, ForwardState or None).  When
+        ``score`` [N] is given it is max-accumulated with each Gaussian's
+        largest blending weight."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        cams = camera_array(cameras)
+        P = n_pixels(cameras)
+        if out is None:
+            f32 = dict(dtype=torch.float32, device=self.device)
+            out = dict(rgb=torch.empty(P, 3, **f32), alpha=torch.empty(P, **f32),
+                       depth=torch.empty(P, **f32), normal=torch.empty(P, 3, **f32))
+        img = _lib.Image(_ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["normal"]))
+        if score is not None:
+            _check_param("score", score, (), self.device)
+        handle = C.c_void_p()
+        st = self.lib.ocgs_render(self._ctx, C.byref(gs), cams, len(cameras), C.byref(img), _ptr(score),
+                                  C.byref(handle) if keep_state else None)
+        if st != _lib.OK:
+            msg = self.lib.ocgs_last_error(self._ctx).decode()
+            if handle:
+                self.lib.ocgs_state_release(self._ctx, handle)
+            raise _lib.OcgsError(st, msg)
+        state = ForwardState(self, handle, gs.n, gs.sh_degree, cameras) if keep_state else None
+        return out, state
+
+    def render_backward(self, state: ForwardState, gaussians: dict, d_out: dict,
+                        grads: Optional[dict] = None) -> dict:
+        """Gradients of sum <d_out, out> w.r.t. the parameters (added into ``grads``)."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        if grads is None:
+            grads = {k: torch.zeros_like(gaussians[k]) for k in PARAM_KEYS}
+        img = _lib.Image(_ptr(d_out.get("rgb")), _ptr(d_out.get("alpha")), _ptr(d_out.get("depth")),
+                         _ptr(d_out.get("normal")))
+        for k, v in d_out.items():
+            if v is not None and (not v.is_cuda or v.dtype != torch.float32 or not v.is_contiguous()):
+                raise ValueError(f"d_out[{k}] must be a contiguous float32 CUDA tensor")
+        go = _lib.GaussiansOut(*[_ptr(grads[k]) for k in PARAM_KEYS])
+        self._call("ocgs_render_backward", self._ctx, state.handle, C.byref(gs), C.byref(img), C.byref(go))
+        return grads
+
+    def background_loss(self, alpha: torch.Tensor, mask: torch.Tensor, cameras: Sequence[dict],
+                        gamma: float = 0.5, d_alpha: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Per-view L_b (Eq. 1) as a float64 tensor; adds gamma dL_b/dA into ``d_alpha``."""
+        self._bind_stream()
+        if mask.dtype != torch.uint8 or not mask.is_cuda or not mask.is_contiguous():
+            raise ValueError("mask must be a contiguous uint8 CUDA tensor")
+        if not alpha.is_cuda or alpha.dtype != torch.float32 or not alpha.is_contiguous():
+            raise ValueError("alpha must be a contiguous float32 CUDA tensor")
+        P = n_pixels(cameras)
+        if alpha.numel() != P or mask.numel() != P:
+            raise ValueError(f"alpha and mask must hold {P} pixels")
+        loss = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_background_loss", self._ctx, _ptr(alpha), _ptr(mask), camera_array(cameras),
+                   len(cameras), float(gamma), _ptr(loss), _ptr(d_alpha))
+        return loss
+
+    def accumulate_contribution(self, gaussians: dict, cameras: Sequence[dict],
+                                score: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Pruning sweep (Sec. 4.3): max blending weight of every Gaussian over all views."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        if score is None:
+            score = torch.zeros(gs.n, dtype=torch.float32, device=self.device)
+        _check_param("score", score, (), self.device)
+        self._call("ocgs_accumulate_contribution", self._ctx, C.byref(gs), camera_array(cameras),
+                   len(cameras), _ptr(score))
+        return score
+
+    def prune(self, gaussians: dict, score: torch.Tensor, threshold: float, borderline_cap: int = 4096):
+        """Keep {score > threshold}; returns (kept parameters, borderline indices)."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        _check_param("score", score, (), self.device)
+        out = {k: torch.empty_like(gaussians[k]) for k in PARAM_KEYS}
+        go = _lib.GaussiansOut(*[_ptr(out[k]) for k in PARAM_KEYS])
+        border = torch.empty(max(1, borderline_cap), dtype=torch.int64, device=self.device)
+        n_kept = C.c_int64()
+        n_border = C.c_int64()
+        self._call("ocgs_prune", self._ctx, _ptr(score), float(threshold), C.byref(gs), C.byref(go),
+                   C.byref(n_kept), _ptr(border), int(borderline_cap), C.byref(n_border))
+        kept = {k: v[: n_kept.value] for k, v in out.items()}
+        return kept, border[: min(n_border.value, borderline_cap)], n_border.value
+
+
+class RenderFunction(torch.autograd.Function):
+    """Differentiable render of a list of views through libocgs."""
+
+    @staticmethod
+    def forward(ctx, rast: Rasterizer, cameras, xyz, quat, scale, opacity, sh):
+        g = dict(xyz=xyz.detach(), quat=quat.detach(), scale=scale.detach(), opacity=opacity.detach(),
+                 sh=sh.detach())
+        out, state = rast.render(g, cameras)
+        ctx.rast = rast
+        ctx.state = state
+        ctx.g = g
+        return out["rgb"], out["alpha"], out["depth"], out["normal"]
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_alpha, g_depth, g_normal):
+        d_out = {k: (None if v is None else v.contiguous()) for k, v in
+                 (("rgb", g_rgb), ("alpha", g_alpha), ("depth", g_depth), ("normal", g_normal))}
+        grads = ctx.rast.render_backward(ctx.state, ctx.g, d_out)
+        ctx.state.release()
+        return (None, None) + tuple(grads[k] for k in PARAM_KEYS)
+
+
+def render(rast: Rasterizer, gaussians: dict, cameras: Sequence[dict]):
+    """Differentiable (rgb, alpha, depth, normal) of ``cameras``."""
+    return RenderFunction.apply(rast, list(cameras), *[gaussians[k] for k in PARAM_KEYS])

@@ -1,0 +1,605 @@
+// Host runtime of libocgs: the C ABI declared in include/ocgs.h.
+//
+// A context binds one device and one stream and owns a stream-ordered memory
+// pool (cudaMallocFromPoolAsync) that keeps freed blocks for reuse, so the
+// per-call buffers (records, keys, pairs) cost no driver allocation after the
+// first call of a given size.  Every call validates its arguments on the host
+// before any launch; device-side conditions (non-finite parameters) are
+// raised in a status word that the synchronising calls read back.
+#include "ocgs.h"
+#include "common.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace ocgs;
+
+struct ocgs_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaMemPool_t pool = nullptr;
+  ocgs_options opts{16, 16, 0, 0};
+  ocgs_stats stats{};
+  std::string err;
+  int* d_status = nullptr;
+  uint64_t* d_scalar = nullptr;   // [4]
+  uint64_t* h_scalar = nullptr;   // pinned [4]
+  int sm_count = 0;
+};
+
+struct ocgs_fwd_state {
+  ocgs_ctx* ctx = nullptr;
+  int V = 0;
+  int64_t N = 0;
+  int deg = 0;
+  int64_t P = 0;
+  uint32_t K = 0;
+  uint32_t n_tiles = 0;
+  int tile_w = 16, tile_h = 16;
+  int persistent = 0;
+  DevCam* d_cams = nullptr;
+  int* d_tile_prefix = nullptr;
+  RecPtrs rec{};
+  int32_t* ntiles = nullptr;
+  uint32_t* vals = nullptr;
+  uint2* ranges = nullptr;
+  float* t_final = nullptr;
+  uint32_t* last = nullptr;
+  uint32_t* tile_order = nullptr;
+  std::vector<void*> allocs;
+};
+
+namespace {
+
+const char* kStatusNames[] = {"OCGS_OK",      "OCGS_ERR_ARG",       "OCGS_ERR_OOM",      "OCGS_ERR_CUDA",
+                              "OCGS_ERR_TIMEOUT", "OCGS_ERR_NONFINITE", "OCGS_ERR_CAPACITY", "OCGS_ERR_STATE"};
+
+ocgs_status set_err(ocgs_ctx* ctx, ocgs_status s, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return s;
+}
+
+ocgs_status cuda_err(ocgs_ctx* ctx, cudaError_t e, const char* what) {
+  const ocgs_status s = (e == cudaErrorMemoryAllocation) ? OCGS_ERR_OOM : OCGS_ERR_CUDA;
+  return set_err(ctx, s, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_err(ctx, e_, #call);   \
+  } while (0)
+
+// Stream-ordered allocations of one call; freed (stream-ordered) on scope
+// exit unless handed over to a forward state.
+struct Arena {
+  ocgs_ctx* ctx;
+  std::vector<void*> ptrs;
+  explicit Arena(ocgs_ctx* c) : ctx(c) {}
+  ~Arena() {
+    for (void* p : ptrs) cudaFreeAsync(p, ctx->stream);
+  }
+  template <typename T>
+  cudaError_t alloc(T** p, size_t count) {
+    const size_t bytes = count * sizeof(T) > 0 ? count * sizeof(T) : 16;
+    void* q = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(&q, (bytes + 255) & ~(size_t)255, ctx->pool, ctx->stream);
+    if (e != cudaSuccess) return e;
+    ptrs.push_back(q);
+    *p = static_cast<T*>(q);
+    return cudaSuccess;
+  }
+  void release_to(std::vector<void*>& dst) {
+    dst.insert(dst.end(), ptrs.begin(), ptrs.end());
+    ptrs.clear();
+  }
+};
+
+bool finite_f(float x) { return std::isfinite(x); }
+
+ocgs_status check_gaussians(ocgs_ctx* ctx, const ocgs_gaussians* g) {
+  if (!g) return set_err(ctx, OCGS_ERR_ARG, "gaussians is NULL");
+  if (g->n < 0) return set_err(ctx, OCGS_ERR_ARG, "gaussians.n < 0");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return set_err(ctx, OCGS_ERR_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->xyz || !g->quat || !g->scale || !g->opacity || !g->sh))
+    return set_err(ctx, OCGS_ERR_ARG, "a Gaussian parameter pointer is NULL");
+  if (g->n > 0 && ((uintptr_t)g->quat % 16 || (uintptr_t)g->scale % 8))
+    return set_err(ctx, OCGS_ERR_ARG, "quat must be 16-byte and scale 8-byte aligned");
+  return OCGS_OK;
+}
+
+ocgs_status check_cameras(ocgs_ctx* ctx, const ocgs_camera* cams, int n_views) {
+  if (!cams) return set_err(ctx, OCGS_ERR_ARG, "cams is NULL");
+  if (n_views < 1 || n_views > 4096) return set_err(ctx, OCGS_ERR_ARG, "n_views must be 1..4096");
+  for (int v = 0; v < n_views; ++v) {
+    const ocgs_camera& c = cams[v];
+    if (c.width < 1 || c.height < 1 || c.width > 16384 || c.height > 16384)
+      return set_err(ctx, OCGS_ERR_ARG, "camera " + std::to_string(v) + ": width/height must be 1..16384");
+    if (!(c.near_plane > 0.f) || !finite_f(c.near_plane))
+      return set_err(ctx, OCGS_ERR_ARG, "camera " + std::to_string(v) + ": near_plane must be > 0");
+    if (!finite_f(c.fx) || !finite_f(c.fy) || !finite_f(c.cx) || !finite_f(c.cy) || !(c.fx > 0.f) || !(c.fy > 0.f))
+      return set_err(ctx, OCGS_ERR_ARG, "camera " + std::to_string(v) + ": bad intrinsics");
+    for (int k = 0; k < 16; ++k)
+      if (!finite_f(c.viewmat[k])) return set_err(ctx, OCGS_ERR_ARG, "camera " + std::to_string(v) + ": non-finite viewmat");
+  }
+  return OCGS_OK;
+}
+
+struct CamPlan {
+  std::vector<DevCam> cams;
+  std::vector<int> tile_prefix;  // V+1
+  int64_t P = 0;
+  int64_t tiles = 0;
+};
+
+CamPlan plan_cameras(const ocgs_camera* cams, int V, int tw, int th) {
+  CamPlan pl;
+  pl.cams.resize(V);
+  pl.tile_prefix.resize(V + 1);
+  int64_t tiles = 0, pix = 0;
+  for (int v = 0; v < V; ++v) {
+    const ocgs_camera& c = cams[v];
+    DevCam& d = pl.cams[v];
+    std::memset(&d, 0, sizeof(d));
+    for (int r = 0; r < 3; ++r) {
+      for (int k = 0; k < 3; ++k) d.R[3 * r + k] = c.viewmat[4 * r + k];
+      d.t[r] = c.viewmat[4 * r + 3];
+    }
+    // camera centre = -R^T t
+    for (int k = 0; k < 3; ++k)
+      d.campos[k] = -(d.R[k] * d.t[0] + d.R[3 + k] * d.t[1] + d.R[6 + k] * d.t[2]);
+    d.fx = c.fx; d.fy = c.fy; d.cx = c.cx; d.cy = c.cy;
+    d.near_plane = c.near_plane;
+    d.W = c.width; d.H = c.height;
+    d.tiles_x = (c.width + tw - 1) / tw;
+    d.tiles_y = (c.height + th - 1) / th;
+    d.tile_offset = (int)tiles;
+    d.pix_offset = pix;
+    pl.tile_prefix[v] = (int)tiles;
+    tiles += (int64_t)d.tiles_x * d.tiles_y;
+    pix += (int64_t)c.width * c.height;
+  }
+  pl.tile_prefix[V] = (int)tiles;
+  pl.P = pix;
+  pl.tiles = tiles;
+  return pl;
+}
+
+int bits_for(uint64_t n) {  // bits needed to represent values 0..n-1
+  int b = 0;
+  while (n > 1 && (1ull << b) < n) ++b;
+  return b;
+}
+
+ocgs_status read_status(ocgs_ctx* ctx, int* status) {
+  CK(cudaMemcpyAsync(ctx->h_scalar + 3, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  *status = *reinterpret_cast<int*>(ctx->h_scalar + 3);
+  return OCGS_OK;
+}
+
+bool valid_tile(int tw, int th) {
+  return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+}
+
+GaussPtrs gptrs(const ocgs_gaussians* g) { return GaussPtrs{g->xyz, g->quat, g->scale, g->opacity, g->sh}; }
+
+void free_state(ocgs_fwd_state* st) {
+  for (void* p : st->allocs) cudaFreeAsync(p, st->ctx->stream);
+  st->allocs.clear();
+}
+
+// The forward pipeline shared by ocgs_render and ocgs_accumulate_contribution:
+// preprocess, depth sort, duplication, tile sort, ranges, rasterization.
+ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams, int V,
+                         const ocgs_image* out, float* score, ocgs_fwd_state* st, bool keep_state) {
+  const int tw = ctx->opts.tile_w, th = ctx->opts.tile_h;
+  const int64_t N = g->n;
+  CamPlan pl = plan_cameras(cams, V, tw, th);
+  if ((uint64_t)N * (uint64_t)V >= 0xffffffffull)
+    return set_err(ctx, OCGS_ERR_CAPACITY, "n_views * n exceeds 2^32 - 1 records");
+  if (pl.tiles >= (int64_t)INT32_MAX) return set_err(ctx, OCGS_ERR_CAPACITY, "too many tiles");
+  const uint32_t VN = (uint32_t)(N * V);
+  cudaStream_t s = ctx->stream;
+  Arena keep(ctx), tmp(ctx);
+
+  st->ctx = ctx; st->V = V; st->N = N; st->deg = g->sh_degree; st->P = pl.P;
+  st->n_tiles = (uint32_t)pl.tiles; st->tile_w = tw; st->tile_h = th; st->persistent = ctx->opts.persistent;
+  CK(keep.alloc(&st->d_cams, V));
+  CK(keep.alloc(&st->d_tile_prefix, V + 1));
+  CK(cudaMemcpyAsync(st->d_cams, pl.cams.data(), sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(st->d_tile_prefix, pl.tile_prefix.data(), sizeof(int) * (V + 1), cudaMemcpyHostToDevice, s));
+  CK(keep.alloc(&st->rec.g0, VN));
+  CK(keep.alloc(&st->rec.g1, VN));
+  CK(keep.alloc(&st->rec.g2, VN));
+  CK(keep.alloc(&st->rec.a0, VN));
+  CK(keep.alloc(&st->rec.a1, VN));
+  CK(keep.alloc(&st->ntiles, VN));
+  CK(keep.alloc(&st->ranges, pl.tiles));
+  CK(keep.alloc(&st->t_final, keep_state ? pl.P : 1));
+  CK(keep.alloc(&st->last, keep_state ? pl.P : 1));
+  int4* rect;
+  uint32_t *dkey, *order, *dkey_alt, *order_alt;
+  uint64_t* counts;
+  CK(tmp.alloc(&rect, VN));
+  CK(tmp.alloc(&dkey, VN));
+  CK(tmp.alloc(&order, VN));
+  CK(tmp.alloc(&dkey_alt, VN));
+  CK(tmp.alloc(&order_alt, VN));
+  CK(tmp.alloc(&counts, VN));
+  char* scratch;
+  const size_t sbytes = std::max(radix_scratch_bytes(VN), scan_scratch_bytes(VN));
+  CK(tmp.alloc(&scratch, sbytes));
+  CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
+  CK(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * pl.tiles, s));
+
+  CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, rect, dkey,
+                       ctx->d_status, s));
+  CK(launch_iota(order, VN, s));
+  bool alt = false;
+  CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+  uint32_t* sorted = alt ? order_alt : order;
+  CK(launch_gather_counts(sorted, st->ntiles, counts, VN, s));
+  CK(scan_exclusive_u64(counts, counts, VN, ctx->d_scalar, scratch, s));
+  CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+  int status = 0;
+  ocgs_status rs = read_status(ctx, &status);
+  if (rs != OCGS_OK) return rs;
+  const uint64_t K64 = VN ? ctx->h_scalar[0] : 0;
+  if (K64 > (uint64_t)INT32_MAX)
+    return set_err(ctx, OCGS_ERR_CAPACITY, "more than 2^31-1 (tile, Gaussian) pairs; split the views");
+  const uint32_t K = (uint32_t)K64;
+  st->K = K;
+
+  uint32_t *pkey, *pval, *pkey_alt, *pval_alt;
+  CK(tmp.alloc(&pkey, K));
+  CK(keep.alloc(&pval, K));
+  CK(tmp.alloc(&pkey_alt, K));
+  CK(keep.alloc(&pval_alt, K));
+  char* pscratch;
+  CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
+  CK(launch_duplicate(sorted, counts, VN, rect, st->d_cams, N, K, pkey, pval, ctx->d_status, s));
+  const int tbits = bits_for((uint64_t)pl.tiles);
+  bool palt = false;
+  CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K, tbits, pscratch, &palt, s));
+  uint32_t* skey = palt ? pkey_alt : pkey;
+  st->vals = palt ? pval_alt : pval;
+  CK(launch_tile_ranges(skey, K, st->ranges, s));
+
+  uint32_t* queue = nullptr;
+  st->tile_order = nullptr;
+  if (st->persistent) {
+    CK(tmp.alloc(&queue, 1));
+    CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+    uint32_t *wk, *ids, *wk_alt, *ids_alt;
+    CK(tmp.alloc(&wk, pl.tiles));
+    CK(keep.alloc(&ids, pl.tiles));
+    CK(tmp.alloc(&wk_alt, pl.tiles));
+    CK(keep.alloc(&ids_alt, pl.tiles));
+    char* tscratch;
+    CK(tmp.alloc(&tscratch, radix_scratch_bytes((uint32_t)pl.tiles)));
+    CK(launch_tile_order(st->ranges, (uint32_t)pl.tiles, wk, ids, s));
+    bool talt = false;
+    CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, (uint32_t)pl.tiles, 32, tscratch, &talt, s));
+    st->tile_order = talt ? ids_alt : ids;
+  }
+
+  RasterArgs ra{};
+  ra.cams = st->d_cams;
+  ra.tile_prefix = st->d_tile_prefix;
+  ra.n_views = V;
+  ra.n_gauss = N;
+  ra.n_tiles = (uint32_t)pl.tiles;
+  ra.ranges = st->ranges;
+  ra.vals = st->vals;
+  ra.rec = st->rec;
+  if (out) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal};
+  ra.t_final = st->t_final;
+  ra.last = st->last;
+  ra.score = score;
+  ra.tile_order = st->tile_order;
+  ra.queue = queue;
+  ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 / (tw * th)) : 0;
+  CK(launch_raster_forward(ra, tw, th, out != nullptr, s));
+
+  ctx->stats.n_gaussians = N;
+  ctx->stats.n_views = V;
+  ctx->stats.n_pixels = pl.P;
+  ctx->stats.n_pairs = K;
+  ctx->stats.n_tiles = pl.tiles;
+  ctx->stats.tile_w = tw;
+  ctx->stats.tile_h = th;
+  ctx->stats.n_visible = -1;
+  if (keep_state) keep.release_to(st->allocs);
+  if (status & kStatusNonFinite)
+    return set_err(ctx, OCGS_ERR_NONFINITE, "non-finite Gaussian parameters (those Gaussians were not rendered)");
+  return OCGS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ocgs_status_str(ocgs_status s) {
+  const int i = (int)s;
+  if (i < 0 || i >= (int)(sizeof(kStatusNames) / sizeof(kStatusNames[0]))) return "OCGS_ERR_UNKNOWN";
+  return kStatusNames[i];
+}
+
+const char* ocgs_last_error(const ocgs_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+int32_t ocgs_abi_version(void) { return OCGS_ABI_VERSION; }
+
+ocgs_status ocgs_create(ocgs_ctx** out, int32_t device, void* stream) {
+  if (!out) return OCGS_ERR_ARG;
+  *out = nullptr;
+  int n_dev = 0;
+  if (cudaGetDeviceCount(&n_dev) != cudaSuccess || n_dev == 0) return OCGS_ERR_CUDA;
+  if (device < 0 || device >= n_dev) return OCGS_ERR_ARG;
+  ocgs_ctx* ctx = new ocgs_ctx();
+  ctx->device = device;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  if (cudaSetDevice(device) != cudaSuccess) { delete ctx; return OCGS_ERR_CUDA; }
+  cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  if (cudaMemPoolCreate(&ctx->pool, &props) != cudaSuccess) { delete ctx; return OCGS_ERR_CUDA; }
+  uint64_t thr = UINT64_MAX;
+  cudaMemPoolSetAttribute(ctx->pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  if (cudaMalloc(&ctx->d_status, 256) != cudaSuccess || cudaMalloc(&ctx->d_scalar, 256) != cudaSuccess ||
+      cudaHostAlloc(&ctx->h_scalar, 256, cudaHostAllocDefault) != cudaSuccess) {
+    ocgs_destroy(ctx);
+    return OCGS_ERR_OOM;
+  }
+  cudaMemset(ctx->d_status, 0, 256);
+  *out = ctx;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_destroy(ocgs_ctx* ctx) {
+  if (!ctx) return OCGS_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  if (ctx->d_scalar) cudaFree(ctx->d_scalar);
+  if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
+  if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  delete ctx;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_set_stream(ocgs_ctx* ctx, void* stream) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
+  if (!ctx || !o) return OCGS_ERR_ARG;
+  if (!valid_tile(o->tile_w, o->tile_h))
+    return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8");
+  ctx->opts = *o;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_get_options(const ocgs_ctx* ctx, ocgs_options* o) {
+  if (!ctx || !o) return OCGS_ERR_ARG;
+  *o = ctx->opts;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_get_stats(const ocgs_ctx* ctx, ocgs_stats* s) {
+  if (!ctx || !s) return OCGS_ERR_ARG;
+  *s = ctx->stats;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_sync(ocgs_ctx* ctx) {
+  if (!ctx) return OCGS_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  int status = 0;
+  ocgs_status r = read_status(ctx, &status);
+  if (r != OCGS_OK) return r;
+  CK(cudaGetLastError());
+  if (status & kStatusNonFinite) return set_err(ctx, OCGS_ERR_NONFINITE, "non-finite Gaussian parameters");
+  if (status & kStatusTimeout) return set_err(ctx, OCGS_ERR_TIMEOUT, "a bounded device wait gave up");
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_render(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams, int32_t n_views,
+                        const ocgs_image* out, float* score, ocgs_fwd_state** state) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ocgs_status r = check_gaussians(ctx, g);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  if (!out || !out->rgb || !out->alpha || !out->depth || !out->normal)
+    return set_err(ctx, OCGS_ERR_ARG, "every output image pointer must be non-NULL");
+  CK(cudaSetDevice(ctx->device));
+  if (state) *state = nullptr;
+  ocgs_fwd_state* st = new ocgs_fwd_state();
+  r = forward_pass(ctx, g, cams, n_views, out, score, st, true);
+  if (r != OCGS_OK && r != OCGS_ERR_NONFINITE) {
+    free_state(st);
+    delete st;
+    return r;
+  }
+  if (state) {
+    *state = st;
+  } else {
+    free_state(st);
+    delete st;
+  }
+  return r;
+}
+
+ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const ocgs_gaussians* g,
+                                 const ocgs_image* d_out, const ocgs_gaussians_out* d_params) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!st || st->ctx != ctx) return set_err(ctx, OCGS_ERR_STATE, "forward state missing or from another context");
+  ocgs_status r = check_gaussians(ctx, g);
+  if (r != OCGS_OK) return r;
+  if (g->n != st->N || g->sh_degree != st->deg)
+    return set_err(ctx, OCGS_ERR_ARG, "gaussians differ from the forward call (n or sh_degree)");
+  if (!d_out) return set_err(ctx, OCGS_ERR_ARG, "d_out is NULL");
+  if (!d_params || (st->N > 0 && (!d_params->xyz || !d_params->quat || !d_params->scale || !d_params->opacity ||
+                                  !d_params->sh)))
+    return set_err(ctx, OCGS_ERR_ARG, "a gradient pointer is NULL");
+  if (st->N == 0) return OCGS_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  const uint64_t VN = (uint64_t)st->N * st->V;
+  float* grad_rec;
+  CK(tmp.alloc(&grad_rec, VN * kGradStride));
+  CK(cudaMemsetAsync(grad_rec, 0, VN * kGradStride * sizeof(float), s));
+  RasterBwdArgs ba{};
+  ba.cams = st->d_cams;
+  ba.tile_prefix = st->d_tile_prefix;
+  ba.n_views = st->V;
+  ba.n_gauss = st->N;
+  ba.n_tiles = st->n_tiles;
+  ba.ranges = st->ranges;
+  ba.vals = st->vals;
+  ba.rec = st->rec;
+  ba.t_final = st->t_final;
+  ba.last = st->last;
+  ba.d_out = ImgPtrs{d_out->rgb, d_out->alpha, d_out->depth, d_out->normal};
+  ba.grad_rec = grad_rec;
+  ba.tile_order = st->tile_order;
+  uint32_t* queue = nullptr;
+  if (st->persistent) {
+    CK(tmp.alloc(&queue, 1));
+    CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+    ba.persistent_ctas = ctx->sm_count * (2048 / (st->tile_w * st->tile_h));
+  }
+  ba.queue = queue;
+  CK(launch_raster_backward(ba, st->tile_w, st->tile_h, s));
+  GaussOut go{d_params->xyz, d_params->quat, d_params->scale, d_params->opacity, d_params->sh};
+  CK(launch_preprocess_backward(gptrs(g), st->N, st->deg, st->d_cams, st->V, grad_rec, st->ntiles, go, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_state_release(ocgs_ctx* ctx, ocgs_fwd_state* st) {
+  if (!ctx || !st) return OCGS_ERR_ARG;
+  if (st->ctx != ctx) return set_err(ctx, OCGS_ERR_STATE, "state from another context");
+  cudaSetDevice(ctx->device);
+  free_state(st);
+  delete st;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_t* mask,
+                                 const ocgs_camera* cams, int32_t n_views, float gamma, double* loss,
+                                 float* d_alpha) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!alpha || !mask || !loss) return set_err(ctx, OCGS_ERR_ARG, "alpha, mask and loss must be non-NULL");
+  if (!cams || n_views < 1 || n_views > 4096) return set_err(ctx, OCGS_ERR_ARG, "bad cameras");
+  if (!std::isfinite(gamma)) return set_err(ctx, OCGS_ERR_ARG, "gamma must be finite");
+  std::vector<DevCam> dc(n_views);
+  std::vector<int> prefix(n_views + 1);
+  int64_t pix = 0;
+  int blocks = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width < 1 || cams[v].height < 1 || cams[v].width > 16384 || cams[v].height > 16384)
+      return set_err(ctx, OCGS_ERR_ARG, "camera width/height must be 1..16384");
+    std::memset(&dc[v], 0, sizeof(DevCam));
+    dc[v].W = cams[v].width;
+    dc[v].H = cams[v].height;
+    dc[v].pix_offset = pix;
+    const int64_t np = (int64_t)cams[v].width * cams[v].height;
+    prefix[v] = blocks;
+    blocks += (int)((np + kLossBlockPixels - 1) / kLossBlockPixels);
+    pix += np;
+  }
+  prefix[n_views] = blocks;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, blocks));
+  CK(cudaMemcpyAsync(d_cams, dc.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, blocks, gamma, partial, loss, d_alpha, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams,
+                                         int32_t n_views, float* score) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ocgs_status r = check_gaussians(ctx, g);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  if (!score && g->n > 0) return set_err(ctx, OCGS_ERR_ARG, "score is NULL");
+  if (g->n == 0) return OCGS_OK;
+  CK(cudaSetDevice(ctx->device));
+  // views are swept in chunks so that one chunk's pairs stay well inside the 2^31 limit
+  const int chunk = 16;
+  ocgs_status worst = OCGS_OK;
+  int64_t pairs = 0;
+  for (int v0 = 0; v0 < n_views; v0 += chunk) {
+    const int nv = std::min(chunk, n_views - v0);
+    ocgs_fwd_state st;
+    r = forward_pass(ctx, g, cams + v0, nv, nullptr, score, &st, false);
+    pairs += ctx->stats.n_pairs;
+    if (r == OCGS_ERR_NONFINITE) worst = r;
+    else if (r != OCGS_OK) return r;
+  }
+  ctx->stats.n_views = n_views;
+  ctx->stats.n_pairs = pairs;
+  return worst;
+}
+
+ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold, const ocgs_gaussians* in,
+                       const ocgs_gaussians_out* out, int64_t* n_kept, int64_t* borderline,
+                       int64_t borderline_cap, int64_t* n_borderline) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ocgs_status r = check_gaussians(ctx, in);
+  if (r != OCGS_OK) return r;
+  if (!n_kept || !n_borderline) return set_err(ctx, OCGS_ERR_ARG, "n_kept and n_borderline must be non-NULL");
+  if (!std::isfinite(threshold)) return set_err(ctx, OCGS_ERR_ARG, "threshold must be finite");
+  if (in->n > 0 && (!score || !out || !out->xyz || !out->quat || !out->scale || !out->opacity || !out->sh))
+    return set_err(ctx, OCGS_ERR_ARG, "score and every output pointer must be non-NULL");
+  if (borderline_cap < 0 || (borderline_cap > 0 && !borderline))
+    return set_err(ctx, OCGS_ERR_ARG, "bad borderline buffer");
+  if (in->n >= (int64_t)0xffffffffll) return set_err(ctx, OCGS_ERR_CAPACITY, "n too large");
+  *n_kept = 0;
+  *n_borderline = 0;
+  if (in->n == 0) return OCGS_OK;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  const uint32_t n = (uint32_t)in->n;
+  Arena tmp(ctx);
+  uint32_t *keep, *keep_pos, *border, *border_pos;
+  CK(tmp.alloc(&keep, n));
+  CK(tmp.alloc(&keep_pos, n));
+  CK(tmp.alloc(&border, n));
+  CK(tmp.alloc(&border_pos, n));
+  char* scratch;
+  CK(tmp.alloc(&scratch, scan_scratch_bytes(n)));
+  uint32_t* totals = reinterpret_cast<uint32_t*>(ctx->d_scalar);
+  CK(launch_prune_flags(score, n, threshold, keep, border, s));
+  CK(scan_exclusive_u32(keep, keep_pos, n, totals, scratch, s));
+  CK(scan_exclusive_u32(border, border_pos, n, totals + 1, scratch, s));
+  GaussOut go{out->xyz, out->quat, out->scale, out->opacity, out->sh};
+  CK(launch_prune_compact(gptrs(in), n, in->sh_degree, keep, keep_pos, border, border_pos, go,
+                          borderline_cap > 0 ? borderline : nullptr, borderline_cap, s));
+  CK(cudaMemcpyAsync(ctx->h_scalar, totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  const uint32_t* h = reinterpret_cast<const uint32_t*>(ctx->h_scalar);
+  *n_kept = h[0];
+  *n_borderline = h[1];
+  return OCGS_OK;
+}
+
+}  // extern "C"

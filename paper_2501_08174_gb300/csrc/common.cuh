@@ -1,0 +1,231 @@
+// Internal definitions shared by the CUDA translation units of libocgs.
+//
+// Record layout of one (view, Gaussian) pair, written by the preprocess kernel
+// and read by the rasterizers (structure of arrays, one float4 per array):
+//   g0 = (c_x, c_y, o, z_c)      projected centre [px], opacity, centre depth
+//   g1 = (A00, A01, A10, A11)    numerator of the ray-splat hit (u, v)
+//   g2 = (e0, e1, e2, zD)        denominator coefficients and zD = z_c * e0
+//   a0 = (r, g, b, n_x)          colour and camera-frame normal
+//   a1 = (n_y, n_z)
+// For a pixel centre x with (dx, dy) = x - c the ray-splat intersection of
+// 2DGS (planes x = const and y = const pulled back through the surfel's
+// splat-to-pixel matrix, then crossed) reduces to the projective map
+//   u = (A00 dx + A01 dy) / den,  v = (A10 dx + A11 dy) / den,
+//   den = e0 + e1 dx + e2 dy,  z_hit = zD / den,
+// which is the same intersection written about the projected centre so that
+// no large pixel coordinates cancel in float32.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ocgs {
+
+constexpr float kRhoCut = 9.0f;            // support cut-off rho <= 9 (3 sigma)
+constexpr float kAlphaMin = 1.0f / 255.0f;  // skip below this opacity
+constexpr float kAlphaMax = 0.99f;          // opacity clamp
+constexpr float kTEps = 1e-4f;              // stop when T (1 - alpha) would fall below this
+constexpr float kInvSigmaF2 = 2.0f;         // 1 / sigma_f^2 of the screen low-pass filter (sigma_f^2 = 1/2 px^2)
+
+// status bits raised on the device, read back by the host
+constexpr int kStatusNonFinite = 1;
+constexpr int kStatusCapacity = 2;
+constexpr int kStatusTimeout = 4;
+
+struct DevCam {
+  float R[9];        // world->camera rotation, row-major
+  float t[3];
+  float fx, fy, cx, cy;
+  float campos[3];   // camera centre in world coordinates
+  float near_plane;
+  int W, H;
+  int tiles_x, tiles_y;
+  int tile_offset;   // first global tile id of this view
+  int pad0;
+  long long pix_offset;  // first pixel of this view in the concatenated images
+};
+
+struct RecPtrs {
+  float4* g0;
+  float4* g1;
+  float4* g2;
+  float4* a0;
+  float2* a1;
+};
+
+struct ImgPtrs {
+  float* rgb;
+  float* alpha;
+  float* depth;
+  float* normal;
+};
+
+struct GaussPtrs {
+  const float* xyz;
+  const float* quat;
+  const float* scale;
+  const float* opacity;
+  const float* sh;
+};
+
+struct GaussOut {
+  float* xyz;
+  float* quat;
+  float* scale;
+  float* opacity;
+  float* sh;
+};
+
+// number of float slots of one record gradient (18 used, padded to 5 float4)
+constexpr int kGradStride = 20;
+enum GradSlot {
+  kGcx = 0, kGcy, kGo, kGzc, kGA00, kGA01, kGA10, kGA11, kGe0, kGe1, kGe2, kGzD,
+  kGr, kGg, kGb, kGnx, kGny, kGnz
+};
+
+// Result of evaluating one surfel at one pixel centre.  All arithmetic uses
+// explicitly rounded intrinsics so that the forward and the backward kernels
+// take bit-identical decisions (skip, clamp, branch) for the same inputs.
+struct SplatEval {
+  float dx, dy, un, vn, den, r, rho3, rho, G, oG, alpha, z;
+  bool surf;  // the surfel term rho3 <= rho2 is used (else the screen filter)
+  bool ok;    // rho <= 9 and alpha >= 1/255: the candidate is blended unless the pixel stops
+};
+
+__device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1, const float4 g2,
+                                                float px, float py) {
+  SplatEval e;
+  e.dx = __fsub_rn(px, g0.x);
+  e.dy = __fsub_rn(py, g0.y);
+  e.un = __fmaf_rn(g1.x, e.dx, __fmul_rn(g1.y, e.dy));
+  e.vn = __fmaf_rn(g1.z, e.dx, __fmul_rn(g1.w, e.dy));
+  e.den = __fmaf_rn(g2.z, e.dy, __fmaf_rn(g2.y, e.dx, g2.x));
+  const float rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
+  const float q = __fmaf_rn(e.un, e.un, __fmul_rn(e.vn, e.vn));
+  const float dd = __fmul_rn(e.den, e.den);
+  const bool in3 = (e.den != 0.0f) && (q <= __fmul_rn(kRhoCut, dd));
+  e.r = 0.0f;
+  e.rho3 = __int_as_float(0x7f800000);  // +inf
+  if (in3) {
+    e.r = __fdividef(1.0f, e.den);
+    e.rho3 = __fmul_rn(q, __fmul_rn(e.r, e.r));
+  }
+  e.surf = in3 && (e.rho3 <= rho2);
+  e.rho = e.surf ? e.rho3 : rho2;
+  e.G = 0.0f;
+  e.oG = 0.0f;
+  e.alpha = 0.0f;
+  e.z = 0.0f;
+  e.ok = false;
+  if (e.rho <= kRhoCut) {
+    e.G = __expf(__fmul_rn(-0.5f, e.rho));
+    e.oG = __fmul_rn(g0.z, e.G);
+    e.alpha = fminf(kAlphaMax, e.oG);
+    e.ok = e.alpha >= kAlphaMin;
+    e.z = e.surf ? __fmul_rn(g2.w, e.r) : g0.w;
+  }
+  return e;
+}
+
+__device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
+
+// first global tile id -> view, by binary search over V+1 prefix offsets
+__device__ __forceinline__ int view_of_tile(const int* tile_prefix, int n_views, int tile) {
+  int lo = 0, hi = n_views - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tile_prefix[mid] <= tile) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+}  // namespace ocgs
+
+// ----------------------------------------------------------------------------- host-side launch helpers
+namespace ocgs {
+
+cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams,
+                              int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
+                              int4* rect, uint32_t* depth_key, int* status, cudaStream_t s);
+
+cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
+                                       const DevCam* cams, int n_views, const float* grad_rec,
+                                       const int32_t* ntiles, GaussOut out, cudaStream_t s);
+
+// stable LSD radix sort of (key, value) 32-bit pairs on key bits [0, n_bits)
+// in ping-pong buffers; returns in *result_in_alt whether the sorted data ended
+// in the alternate buffers.  scratch must hold radix_scratch_bytes(n) bytes.
+size_t radix_scratch_bytes(uint32_t n);
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                             uint32_t n, int n_bits, void* scratch, bool* result_in_alt,
+                             cudaStream_t s);
+
+// exclusive scan of n uint64 values (in may equal out); the total is written to *d_total.
+size_t scan_scratch_bytes(uint32_t n);
+cudaError_t scan_exclusive_u64(const uint64_t* in, uint64_t* out, uint32_t n, uint64_t* d_total,
+                               void* scratch, cudaStream_t s);
+cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, uint32_t n, uint32_t* d_total,
+                               void* scratch, cudaStream_t s);
+
+cudaError_t launch_gather_counts(const uint32_t* order, const int32_t* ntiles, uint64_t* counts,
+                                 uint32_t n, cudaStream_t s);
+cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s);
+cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint32_t n_items,
+                             const int4* rect, const DevCam* cams, int64_t n_gauss, uint32_t n_pairs,
+                             uint32_t* keys, uint32_t* vals, int* status, cudaStream_t s);
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s);
+cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
+                              uint32_t* tile_ids, cudaStream_t s);
+
+struct RasterArgs {
+  const DevCam* cams;
+  const int* tile_prefix;   // [V+1]
+  int n_views;
+  int64_t n_gauss;
+  uint32_t n_tiles;
+  const uint2* ranges;
+  const uint32_t* vals;     // sorted record indices
+  RecPtrs rec;
+  ImgPtrs out;
+  float* t_final;
+  uint32_t* last;
+  float* score;
+  const uint32_t* tile_order;  // persistent: tiles in work order (NULL = natural)
+  uint32_t* queue;             // persistent: global tile counter (zeroed)
+  int persistent_ctas;         // 0 = one CTA per tile
+};
+cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, bool write_image,
+                                  cudaStream_t s);
+
+struct RasterBwdArgs {
+  const DevCam* cams;
+  const int* tile_prefix;
+  int n_views;
+  int64_t n_gauss;
+  uint32_t n_tiles;
+  const uint2* ranges;
+  const uint32_t* vals;
+  RecPtrs rec;
+  const float* t_final;
+  const uint32_t* last;
+  ImgPtrs d_out;            // cotangents, NULL planes = 0
+  float* grad_rec;          // [V*N][kGradStride], zeroed
+  const uint32_t* tile_order;
+  uint32_t* queue;
+  int persistent_ctas;
+};
+cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, cudaStream_t s);
+
+cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, const DevCam* cams,
+                                   int n_views, const int* block_prefix, int n_blocks, float gamma,
+                                   double* partial, double* loss, float* d_alpha, cudaStream_t s);
+constexpr int kLossBlockPixels = 4096;
+
+cudaError_t launch_prune_flags(const float* score, uint32_t n, float threshold, uint32_t* keep,
+                               uint32_t* border, cudaStream_t s);
+cudaError_t launch_prune_compact(const GaussPtrs& in, uint32_t n, int sh_degree, const uint32_t* keep,
+                                 const uint32_t* keep_pos, const uint32_t* border,
+                                 const uint32_t* border_pos, GaussOut out, int64_t* border_idx,
+                                 int64_t border_cap, cudaStream_t s);
+
+}  // namespace ocgs
