@@ -1,0 +1,426 @@
+#!/usr/bin/env python
+"""Throughput of the object-centric 2DGS training step on GB300.
+
+One step is one pass of the whole hot path over one batch of views:
+surfel projection, depth sort, tile binning, tile sort, front-to-back
+compositing with the per-Gaussian contribution record, the masked L1 of
+Eq. 2 and the background loss of Eq. 1 with their adjoints, the backward
+compositing, the chain rule to the parameters and the pruning keep-set with
+compaction.  The workload is 500k surfels (SH degree 3) seen by 16 views of
+uneven resolution (640x480 / 800x800 / 1024x768 / 1600x1200), synthetic and
+seeded.  The metric is pixels per second of the step (Mpix/s), batched (all
+16 views in one pass) and per view (16 passes of one view).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
+timed instead, on a bounded pixel sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "fwd+bwd Mpix/s at 500k surfels, batched vs per-view; % of HBM roofline"
+UNIT = "Mpix/s"
+GAMMA = 0.5      # background-loss weight (Sec. 5.1)
+TAU = 0.01       # pruning threshold of the sweep configuration
+# FP32 operations per evaluated (pixel, Gaussian) pair, counted from the kernels'
+# arithmetic (an FMA counts 2): support test and alpha (31) plus blending (17)
+# in the forward; the same test plus the adjoint and the warp reduction in the backward.
+FLOPS_FWD = 48
+FLOPS_BWD = 90
+
+
+def parse_args():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--n", type=int, default=500_000, help="surfels")
+    p.add_argument("--views", type=int, default=16)
+    p.add_argument("--tile", default="16x16")
+    p.add_argument("--persistent", type=int, default=0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-per-view", action="store_true")
+    p.add_argument("--cpu-sample", type=int, default=384, help="pixels of the oracle's timed sample")
+    return p.parse_args()
+
+
+def workload_name(a) -> str:
+    return (f"object-centric 2DGS training step: {a.n} surfels SH3 (70% object ball r=0.8, 30% shell r=2-4), "
+            f"{a.views} hemisphere views of uneven resolution, masked L1 + 0.5 L_b, fwd+bwd, prune tau={TAU}")
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (every 200 ms)."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, path: str):
+        self.path = path
+        self.proc = None
+        try:
+            self.fh = open(path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# ----------------------------------------------------------------------------- distributed
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------- roofline model
+def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile_passes: int, kept: int) -> dict:
+    """Minimum HBM bytes (and FP32 flops) of each stage for one step."""
+    VN = V * N
+    b = {
+        "preprocess": N * 232 + VN * (72 + 4 + 16 + 4),
+        "depth_sort": VN * 4 + 4 * VN * 20,
+        "binning": VN * 68 + K * 12 + T * 8,
+        "tile_sort": tile_passes * K * 20,
+        "raster_fwd": K * 4 + P * 40,
+        "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24),
+        "raster_bwd": VN * 80 + K * 4 + P * 40,
+        "preprocess_bwd": N * 232 * 3 + VN * 84,
+        "prune": N * 24 + kept * 232 * 2,
+    }[stage]
+    f = {"raster_fwd": E * FLOPS_FWD, "raster_bwd": E * FLOPS_BWD}.get(stage, 0)
+    return {"bytes": b, "flops": f}
+
+
+# ----------------------------------------------------------------------------- CPU oracle leg
+def oracle_sample(g_np, cam, n_pix: int, seed: int = 0):
+    rng = np.random.default_rng(seed)
+    P = cam["width"] * cam["height"]
+    pix = np.sort(rng.choice(P, size=min(n_pix, P), replace=False))
+    d_out = dict(rgb=rng.normal(size=(len(pix), 3)), alpha=rng.normal(size=len(pix)),
+                 depth=np.zeros(len(pix)), normal=np.zeros((len(pix), 3)))
+    return pix, d_out
+
+
+def time_oracle(sc, n_pix: int) -> dict:
+    import torch
+    import oracle
+    cam = sc["cameras"][0]
+    pix, d_out = oracle_sample(sc["gaussians"], cam, n_pix)
+    t0 = time.perf_counter()
+    oracle.render(sc["gaussians"], cam, pixels=pix, d_out=d_out)
+    dt = time.perf_counter() - t0
+    return {"value": len(pix) / dt / 1e6, "unit": UNIT, "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"fwd+bwd (FP64 autograd) of {len(pix)} seeded pixels of view 0 ({cam['width']}x{cam['height']}) "
+                      f"over all {len(sc['gaussians']['opacity'])} surfels; {dt:.1f} s"}
+
+
+def run_reference(a, rank: int, world: int):
+    if rank != 0:
+        return
+    import synthetic
+    import torch
+    sc = synthetic.config4(n=a.n, n_views=a.views)
+    n_pix = max(16, a.cpu_sample // 6)
+    times = []
+    for i in range(a.warmup + a.steps):
+        cam = sc["cameras"][i % len(sc["cameras"])]
+        pix, d_out = oracle_sample(sc["gaussians"], cam, n_pix, seed=i)
+        t0 = time.perf_counter()
+        import oracle
+        oracle.render(sc["gaussians"], cam, pixels=pix, d_out=d_out)
+        if i >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = n_pix / (ms / 1e3) / 1e6
+    cores = torch.get_num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name(a), "sample": f"{n_pix} pixels of one view per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"FP64 oracle fwd+bwd of {n_pix} seeded pixels of one view per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- GPU step
+class TrainingStep:
+    """One training step through the library (all arithmetic in libocgs kernels)."""
+
+    def __init__(self, rast, g, cams, target, mask, per_view: bool):
+        import torch
+        from paper_2501_08174_gb300 import pixel_offsets
+        self.rast, self.g, self.cams, self.target, self.mask = rast, g, cams, target, mask
+        self.per_view = per_view
+        self.off = pixel_offsets(cams)
+        P = self.off[-1]
+        dev = g["xyz"].device
+        self.d_rgb = torch.zeros(P, 3, device=dev)
+        self.d_alpha = torch.zeros(P, device=dev)
+        self.grads = {k: torch.zeros_like(v) for k, v in g.items()}
+        self.score = torch.zeros(g["opacity"].shape[0], device=dev)
+        self.loss = torch.zeros(2, len(cams), dtype=torch.float64, device=dev)
+        self.kept = 0
+
+    def _views(self, cams, lo, hi):
+        r = self.rast
+        out, st = r.render(self.g, cams, score=self.score)
+        tgt = self.target[lo:hi]
+        msk = self.mask[lo:hi]
+        d_rgb, d_alpha = self.d_rgb[lo:hi], self.d_alpha[lo:hi]
+        l1 = r.masked_l1(out["rgb"], tgt, msk, cams, weight=1.0, d_rgb=d_rgb)
+        lb = r.background_loss(out["alpha"], msk, cams, gamma=GAMMA, d_alpha=d_alpha)
+        r.render_backward(st, self.g, {"rgb": d_rgb, "alpha": d_alpha}, grads=self.grads)
+        st.release()
+        return l1, lb
+
+    def __call__(self):
+        self.score.zero_()
+        self.d_rgb.zero_()
+        self.d_alpha.zero_()
+        for v in self.grads.values():
+            v.zero_()
+        if self.per_view:
+            for i, cam in enumerate(self.cams):
+                l1, lb = self._views([cam], self.off[i], self.off[i + 1])
+                self.loss[0, i:i + 1].copy_(l1)
+                self.loss[1, i:i + 1].copy_(lb)
+        else:
+            l1, lb = self._views(self.cams, 0, self.off[-1])
+            self.loss[0].copy_(l1)
+            self.loss[1].copy_(lb)
+        kept, _, _ = self.rast.prune(self.g, self.score, TAU)
+        self.kept = kept["xyz"].shape[0]
+
+
+def timed(step, k: int, warmup: int, world: int, dev, sampler_path=None, gpu_index=0):
+    import torch
+    import torch.distributed as dist
+    for _ in range(warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        dist.barrier()
+    sampler = ClockSampler(gpu_index, sampler_path) if sampler_path else None
+    s = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(s)
+    for _ in range(k):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize(dev)
+    wall = time.perf_counter() - t0
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop() if sampler else None
+    ms = e0.elapsed_time(e1) / k
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, wall / k * 1e3, clocks
+
+
+def run_ours(a, rank: int, world: int, local: int):
+    import torch
+    import torch.distributed as dist
+
+    import synthetic
+    from paper_2501_08174_gb300 import Rasterizer, n_pixels
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    os.makedirs(out_dir, exist_ok=True)
+
+    sc = synthetic.config4(seed=4 + rank, n=a.n, n_views=a.views)
+    cams = sc["cameras"]
+    P = n_pixels(cams)
+    g_np = sc["gaussians"]
+    N = len(g_np["opacity"])
+    rng = np.random.default_rng(40 + rank)
+    target_np = rng.uniform(0.0, 1.0, size=(P, 3)).astype(np.float32)
+    mask_np = np.concatenate([m.reshape(-1) for m in sc["masks"]]).astype(np.uint8)
+    g = {k: torch.tensor(np.asarray(g_np[k], np.float32), device=dev) for k in ("xyz", "quat", "scale", "opacity", "sh")}
+    target = torch.tensor(target_np, device=dev)
+    mask = torch.tensor(mask_np, device=dev)
+    tw, th = (int(x) for x in a.tile.split("x"))
+    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent))
+
+    # sizes of the workload (outside the timed region)
+    _, st = rast.render(g, cams)
+    info = st.info()
+    st.release()
+    K, E, T = info["n_pairs"], info["n_evals"], info["n_tiles"]
+    tile_bits = max(1, math.ceil(math.log2(max(T, 2))))
+    tile_passes = (tile_bits + 7) // 8
+
+    # batched step, with the library's stage timers on
+    step = TrainingStep(rast, g, cams, target, mask, per_view=False)
+    for _ in range(a.warmup):
+        step()
+    rast.profile(True)
+    launches0 = rast.kernel_launches()
+    ms, wall_ms, clocks = timed(step, a.steps, 0, world, dev, os.path.join(out_dir, f"clocks_rank{rank}.csv"), local)
+    launches = rast.kernel_launches() - launches0
+    prof = rast.profile_read()
+    rast.profile(False)
+    kept = step.kept
+
+    per_view = None
+    if not a.no_per_view:
+        pstep = TrainingStep(rast, g, cams, target, mask, per_view=True)
+        pms, pwall, _ = timed(pstep, a.steps, a.warmup, world, dev)
+        per_view = {"ms_per_step": pms, "value": world * P / (pms / 1e3) / 1e6,
+                    "launch_sets": len(cams), "batched_speedup": pms / ms}
+
+    # roofline of the dominant stage and of the whole step
+    peaks = load_peaks()
+    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    stages = {}
+    step_bytes = 0
+    for name, (tot_ms, cnt) in prof.items():
+        alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept)
+        step_bytes += alg["bytes"]
+        per_ms = tot_ms / a.steps
+        stages[name] = {"ms": per_ms, "launch_sets": cnt / a.steps,
+                        "gbs": alg["bytes"] / (per_ms * 1e-3) / 1e9 if per_ms > 0 else None,
+                        "tflops": (alg["flops"] / (per_ms * 1e-3) / 1e12) if alg["flops"] and per_ms > 0 else None}
+    dom = max(stages, key=lambda k: stages[k]["ms"])
+    dstage = stages[dom]
+    per_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
+    alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept)
+    if alg["flops"]:
+        ach = alg["flops"] / (per_launch_ms * 1e-3) / 1e12
+        roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": ach / fp32_peak, "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+    else:
+        ach = alg["bytes"] / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]}
+    hbm_step = {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
+                "peak_gbs": peaks["hbm_gbs"], "frac": step_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                "mpix_s_at_roofline": P / (step_bytes / (peaks["hbm_gbs"] * 1e9)) / 1e6}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        pin = {k: v.cpu().pin_memory() for k, v in g.items()}
+        tgt_h = torch.tensor(target_np).pin_memory()
+        msk_h = torch.tensor(mask_np).pin_memory()
+        grads_h = {k: torch.empty_like(v).pin_memory() for k, v in pin.items()}
+        loss_h = torch.empty(2, len(cams), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            for k in g:
+                g[k].copy_(pin[k], non_blocking=True)
+            target.copy_(tgt_h, non_blocking=True)
+            mask.copy_(msk_h, non_blocking=True)
+            step()
+            for k in g:
+                grads_h[k].copy_(step.grads[k], non_blocking=True)
+            loss_h.copy_(step.loss, non_blocking=True)
+
+        ems, ewall, _ = timed(e2e_step, a.steps, 1, world, dev)
+        h2d = sum(v.numel() * v.element_size() for v in pin.values()) + tgt_h.numel() * 4 + msk_h.numel()
+        d2h = sum(v.numel() * v.element_size() for v in grads_h.values()) + loss_h.numel() * 8
+        e2e = {"value": world * P / (max(ems, ewall) / 1e3) / 1e6, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": max(ems, ewall)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cpu = time_oracle(sc, a.cpu_sample)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": world * P / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": workload_name(a), "mode": "batched (one pass over all views)",
+                           "n_gaussians": N, "n_views": len(cams), "pixels_per_gpu": P,
+                           "resolutions": [f"{c['width']}x{c['height']}" for c in cams],
+                           "tile": a.tile, "persistent": bool(a.persistent), "pairs": K, "evals": E,
+                           "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB algorithmic traffic per step",
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "per_view": per_view, "stages": stages, "roofline": roofline, "hbm_roofline_step": hbm_step,
+                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": int(launches),
+                "wall_ms_per_step": wall_ms, "kept_after_prune": kept}
+        print(json.dumps(line), flush=True)
+    rast.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse_args()
+    rank, world, local = dist_info()
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    run_ours(a, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -115,6 +115,26 @@ typedef struct {
   int32_t tile_w, tile_h;
 } ocgs_stats;
 
+/* Stages timed by the built-in profiler (CUDA events recorded on the context
+ * stream around each stage's launches). */
+typedef enum {
+  OCGS_STAGE_PREPROCESS = 0,      /* projection, bounds, SH colour (per Gaussian) */
+  OCGS_STAGE_DEPTH_SORT = 1,      /* radix sort of the records by centre depth */
+  OCGS_STAGE_BINNING = 2,         /* tile counts scan, duplication, tile ranges */
+  OCGS_STAGE_TILE_SORT = 3,       /* stable radix sort of the pairs by tile */
+  OCGS_STAGE_RASTER_FWD = 4,      /* front-to-back compositing (+ contribution record) */
+  OCGS_STAGE_LOSS = 5,            /* background loss and masked L1, with their adjoints */
+  OCGS_STAGE_RASTER_BWD = 6,      /* back-to-front adjoint of the compositing */
+  OCGS_STAGE_PREPROCESS_BWD = 7,  /* chain rule to the parameters */
+  OCGS_STAGE_PRUNE = 8,           /* keep-set and compaction */
+  OCGS_STAGE_COUNT = 9
+} ocgs_stage;
+
+typedef struct {
+  double ms[16];        /* summed device time per stage, milliseconds */
+  int64_t launches[16]; /* number of timed stage instances */
+} ocgs_profile;
+
 const char* ocgs_status_str(ocgs_status s);
 const char* ocgs_last_error(const ocgs_ctx* ctx);
 int32_t ocgs_abi_version(void);
@@ -134,14 +154,14 @@ ocgs_status ocgs_sync(ocgs_ctx* ctx);
 /*
  * ocgs_render — forward rasterization of n_views views in one batched pass
  * (surfel projection, tile binning with a key sort, front-to-back alpha
- * compositing; Sec. 3.2 and Sec. 4.3 "rendered in front-to-back order ...
- * terminated once ... a threshold opacity close to 1").
+ * compositing that ends a pixel once it is nearly opaque; Sec. 3.2 and
+ * Sec. 4.3).
  *   gaussians  device parameters (see above)
  *   cams       host [n_views] cameras, n_views >= 1
  *   out        device images, P = sum W*H pixels; fully overwritten
  *   score      device [n] or NULL. When given, score[i] = max(score[i], w) over
  *              every pixel where Gaussian i was blended with weight w (the
- *              "used during the color accumulation step" record of Sec. 4.3
+ *              visibility record kept during colour accumulation, Sec. 4.3
  *              and Sec. 5.1). The caller zeroes it before the first view.
  *   state      NULL, or receives an opaque forward state for
  *              ocgs_render_backward; release it with ocgs_state_release.
@@ -192,7 +212,7 @@ ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* ga
 
 /*
  * ocgs_prune — keep-set {i : score[i] > threshold} (threshold 0 reproduces
- * the paper's "never used in blending" rule of Sec. 4.3) and stream
+ * the rule of Sec. 4.3: drop what no pixel ever blended) and stream
  * compaction of the parameters in their original order.
  *   in          device parameters, n Gaussians
  *   out         device arrays with room for n Gaussians (must not alias in)
@@ -205,6 +225,42 @@ ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* ga
 ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold,
                        const ocgs_gaussians* in, const ocgs_gaussians_out* out, int64_t* n_kept,
                        int64_t* borderline, int64_t borderline_cap, int64_t* n_borderline);
+
+/*
+ * ocgs_masked_l1 — the L1 part of the masked photometric loss of Eq. 2,
+ * L_c^M = mean |I*M - R*M| over the 3*h*w colour values of each view.
+ *   rgb     device [P,3] rendered colour R
+ *   target  device [P,3] reference image I
+ *   mask    device [P] uint8 object mask M
+ *   loss    device [n_views] float64, overwritten
+ *   d_rgb   device [P,3] or NULL: d_rgb += weight * dL_c^M/dR
+ *           = weight * sign(R - I) * M / (3*h*w)
+ * Deterministic (fixed-order FP64 reduction).
+ */
+ocgs_status ocgs_masked_l1(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                           const ocgs_camera* cams, int32_t n_views, float weight, double* loss,
+                           float* d_rgb);
+
+/* Sizes of one forward state: K pairs, P pixels, and E = sum over pixels of
+ * the length of the blended prefix of the pixel's tile list (the (pixel,
+ * Gaussian) pairs that both the forward and the backward must evaluate).
+ * Synchronises. */
+typedef struct {
+  int64_t n_pairs;
+  int64_t n_pixels;
+  int64_t n_tiles;
+  int64_t n_views;
+  int64_t n_evals;
+} ocgs_state_info;
+ocgs_status ocgs_state_query(ocgs_ctx* ctx, const ocgs_fwd_state* state, ocgs_state_info* info);
+
+/* Number of CUDA kernels this library has launched in this process. */
+int64_t ocgs_kernel_launches(void);
+
+/* Built-in stage profiler: enable (1) resets the accumulators and starts
+ * recording; read synchronises the stream and returns the sums so far. */
+ocgs_status ocgs_profile_enable(ocgs_ctx* ctx, int32_t enable);
+ocgs_status ocgs_profile_read(ocgs_ctx* ctx, ocgs_profile* out);
 
 #ifdef __cplusplus
 }

@@ -10,8 +10,8 @@ same procedure with its discrete decisions (skip, stop, clamp, min branch,
 normal flip) held fixed:
 
 * per pixel, every non-culled surfel is a candidate; candidates are taken in
-  ascending centre depth, ties by ascending index (front-to-back order,
-  Sec. 4.3 "rendered in front-to-back order");
+  ascending centre depth, ties by ascending index (the front-to-back
+  compositing order of Sec. 4.3);
 * the ray through the pixel centre meets the surfel plane at (u, v), found as
   the crossing of the two homogeneous pixel planes pulled back through the
   surfel's 3x3 splat-to-pixel matrix (2DGS ray-splat intersection, prior work
@@ -309,8 +309,11 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
         xs, ys = xs_all[s:e], ys_all[s:e]
         cols = order
         if prefilter and len(order) > 0:
-            m = candidate_mask(base["T"][order], scale_d[order], cam, xs, ys)
-            cols = order[m.any(0)]
+            T_o, s_o = base["T"][order], scale_d[order]
+            hit = torch.zeros(len(order), dtype=torch.bool)
+            for r0 in range(0, e - s, 32):  # rows in small groups to bound memory
+                hit |= candidate_mask(T_o, s_o, cam, xs[r0:r0 + 32], ys[r0:r0 + 32]).any(0)
+            cols = order[hit]
         sub = {k: base[k][cols].clone().requires_grad_(need_grad) for k in keys}
         out = composite(sub["T"], sub["z_c"], sub["normal"], sub["rgb"], sub["opacity"], xs, ys,
                         rgb_raw=rgb_raw[cols])

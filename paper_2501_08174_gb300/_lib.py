@@ -43,6 +43,19 @@ class Options(C.Structure):
                 ("reserved", C.c_int32)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 16), ("launches", C.c_int64 * 16)]
+
+
+class StateInfo(C.Structure):
+    _fields_ = [("n_pairs", C.c_int64), ("n_pixels", C.c_int64), ("n_tiles", C.c_int64),
+                ("n_views", C.c_int64), ("n_evals", C.c_int64)]
+
+
+STAGES = ["preprocess", "depth_sort", "binning", "tile_sort", "raster_fwd", "loss", "raster_bwd",
+          "preprocess_bwd", "prune"]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_views", C.c_int64), ("n_pixels", C.c_int64),
                 ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_tiles", C.c_int64),
@@ -73,6 +86,12 @@ SIGNATURES = {
     "ocgs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(Gaussians),
                              C.POINTER(GaussiansOut), C.POINTER(C.c_int64), C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
+    "ocgs_masked_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
+                                 C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
+    "ocgs_state_query": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(StateInfo)]),
+    "ocgs_kernel_launches": (C.c_int64, []),
+    "ocgs_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "ocgs_profile_read": (C.c_int, [C.c_void_p, C.POINTER(Profile)]),
 }
 
 _lib = None

@@ -93,6 +93,12 @@ class ForwardState:
         self.sh_degree = deg
         self.cameras = list(cameras)
 
+    def info(self) -> dict:
+        """Pairs K, pixels P, tiles, views and E (pairs both passes evaluate). Synchronises."""
+        inf = _lib.StateInfo()
+        self._rast._call("ocgs_state_query", self._rast._ctx, self.handle, C.byref(inf))
+        return {k: getattr(inf, k) for k, _ in _lib.StateInfo._fields_}
+
     def release(self) -> None:
         if self.handle:
             self._rast._call("ocgs_state_release", self._rast._ctx, self.handle)
@@ -155,6 +161,20 @@ class Rasterizer:
     def sync(self) -> None:
         self._call("ocgs_sync", self._ctx)
 
+    def profile(self, enable: bool) -> None:
+        """Start (reset) or stop the library's per-stage CUDA-event timers."""
+        self._call("ocgs_profile_enable", self._ctx, int(bool(enable)))
+
+    def profile_read(self) -> dict:
+        """Summed device milliseconds and instance counts per stage (synchronises)."""
+        p = _lib.Profile()
+        self._call("ocgs_profile_read", self._ctx, C.byref(p))
+        return {name: (p.ms[i], p.launches[i]) for i, name in enumerate(_lib.STAGES)}
+
+    def kernel_launches(self) -> int:
+        """Kernels launched by libocgs in this process so far."""
+        return int(self.lib.ocgs_kernel_launches())
+
     # -- the method
     def render(self, gaussians: dict, cameras: Sequence[dict], score: Optional[torch.Tensor] = None,
                keep_state: bool = True, out: Optional[dict] = None):
@@ -215,6 +235,21 @@ class Rasterizer:
         loss = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
         self._call("ocgs_background_loss", self._ctx, _ptr(alpha), _ptr(mask), camera_array(cameras),
                    len(cameras), float(gamma), _ptr(loss), _ptr(d_alpha))
+        return loss
+
+    def masked_l1(self, rgb: torch.Tensor, target: torch.Tensor, mask: torch.Tensor, cameras: Sequence[dict],
+                  weight: float = 1.0, d_rgb: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Per-view masked L1 of Eq. 2 (float64 tensor); adds weight * dL/dR into ``d_rgb``."""
+        self._bind_stream()
+        P = n_pixels(cameras)
+        for name, t in (("rgb", rgb), ("target", target)):
+            if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != 3 * P:
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {P}x3 values")
+        if mask.dtype != torch.uint8 or not mask.is_cuda or not mask.is_contiguous() or mask.numel() != P:
+            raise ValueError(f"mask must be a contiguous uint8 CUDA tensor of {P} values")
+        loss = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_masked_l1", self._ctx, _ptr(rgb), _ptr(target), _ptr(mask), camera_array(cameras),
+                   len(cameras), float(weight), _ptr(loss), _ptr(d_rgb))
         return loss
 
     def accumulate_contribution(self, gaussians: dict, cameras: Sequence[dict],

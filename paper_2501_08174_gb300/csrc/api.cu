@@ -17,6 +17,8 @@
 
 using namespace ocgs;
 
+std::atomic<long long> ocgs::g_kernel_launches{0};
+
 struct ocgs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
@@ -28,6 +30,13 @@ struct ocgs_ctx {
   uint64_t* d_scalar = nullptr;   // [4]
   uint64_t* h_scalar = nullptr;   // pinned [4]
   int sm_count = 0;
+  // built-in stage profiler: event pairs recorded on the stream around each stage
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_stage;
+  size_t ev_used = 0;
+  double prof_ms[16] = {0};
+  int64_t prof_n[16] = {0};
 };
 
 struct ocgs_fwd_state {
@@ -96,6 +105,31 @@ struct Arena {
     dst.insert(dst.end(), ptrs.begin(), ptrs.end());
     ptrs.clear();
   }
+};
+
+// Records a CUDA event pair around one stage when the profiler is on.
+struct StageTimer {
+  ocgs_ctx* ctx;
+  int slot = -1;
+  StageTimer(ocgs_ctx* c, int stage) : ctx(c) {
+    if (!ctx->prof) return;
+    if (2 * ctx->ev_used + 2 > ctx->ev.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      ctx->ev.push_back(a);
+      ctx->ev.push_back(b);
+      ctx->ev_stage.push_back(0);
+    }
+    slot = (int)ctx->ev_used++;
+    ctx->ev_stage[slot] = stage;
+    cudaEventRecord(ctx->ev[2 * slot], ctx->stream);
+  }
+  void stop() {
+    if (slot >= 0) cudaEventRecord(ctx->ev[2 * slot + 1], ctx->stream);
+    slot = -1;
+  }
+  ~StageTimer() { stop(); }
 };
 
 bool finite_f(float x) { return std::isfinite(x); }
@@ -174,6 +208,36 @@ int bits_for(uint64_t n) {  // bits needed to represent values 0..n-1
   return b;
 }
 
+struct LossPlan {
+  std::vector<DevCam> cams;
+  std::vector<int> prefix;  // loss blocks per view, prefix sums
+  int blocks = 0;
+};
+
+ocgs_status plan_loss(ocgs_ctx* ctx, const ocgs_camera* cams, int n_views, LossPlan* lp) {
+  if (!cams || n_views < 1 || n_views > 4096) return set_err(ctx, OCGS_ERR_ARG, "bad cameras");
+  lp->cams.assign(n_views, DevCam{});
+  lp->prefix.assign(n_views + 1, 0);
+  int64_t pix = 0;
+  int blocks = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width < 1 || cams[v].height < 1 || cams[v].width > 16384 || cams[v].height > 16384)
+      return set_err(ctx, OCGS_ERR_ARG, "camera width/height must be 1..16384");
+    DevCam& d = lp->cams[v];
+    std::memset(&d, 0, sizeof(DevCam));
+    d.W = cams[v].width;
+    d.H = cams[v].height;
+    d.pix_offset = pix;
+    const int64_t np = (int64_t)cams[v].width * cams[v].height;
+    lp->prefix[v] = blocks;
+    blocks += (int)((np + kLossBlockPixels - 1) / kLossBlockPixels);
+    pix += np;
+  }
+  lp->prefix[n_views] = blocks;
+  lp->blocks = blocks;
+  return OCGS_OK;
+}
+
 ocgs_status read_status(ocgs_ctx* ctx, int* status) {
   CK(cudaMemcpyAsync(ctx->h_scalar + 3, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -236,14 +300,23 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(cudaMemsetAsync(ctx->d_status, 0, sizeof(int), s));
   CK(cudaMemsetAsync(st->ranges, 0, sizeof(uint2) * pl.tiles, s));
 
-  CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, rect, dkey,
-                       ctx->d_status, s));
-  CK(launch_iota(order, VN, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_PREPROCESS);
+    CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, rect, dkey,
+                         ctx->d_status, s));
+  }
   bool alt = false;
-  CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
+    CK(launch_iota(order, VN, s));
+    CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+  }
   uint32_t* sorted = alt ? order_alt : order;
-  CK(launch_gather_counts(sorted, st->ntiles, counts, VN, s));
-  CK(scan_exclusive_u64(counts, counts, VN, ctx->d_scalar, scratch, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_BINNING);
+    CK(launch_gather_counts(sorted, st->ntiles, counts, VN, s));
+    CK(scan_exclusive_u64(counts, counts, VN, ctx->d_scalar, scratch, s));
+  }
   CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   int status = 0;
   ocgs_status rs = read_status(ctx, &status);
@@ -261,13 +334,22 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(keep.alloc(&pval_alt, K));
   char* pscratch;
   CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
-  CK(launch_duplicate(sorted, counts, VN, rect, st->d_cams, N, K, pkey, pval, ctx->d_status, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_BINNING);
+    CK(launch_duplicate(sorted, counts, VN, rect, st->d_cams, N, K, pkey, pval, ctx->d_status, s));
+  }
   const int tbits = bits_for((uint64_t)pl.tiles);
   bool palt = false;
-  CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K, tbits, pscratch, &palt, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_TILE_SORT);
+    CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K, tbits, pscratch, &palt, s));
+  }
   uint32_t* skey = palt ? pkey_alt : pkey;
   st->vals = palt ? pval_alt : pval;
-  CK(launch_tile_ranges(skey, K, st->ranges, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_BINNING);
+    CK(launch_tile_ranges(skey, K, st->ranges, s));
+  }
 
   uint32_t* queue = nullptr;
   st->tile_order = nullptr;
@@ -303,7 +385,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   ra.tile_order = st->tile_order;
   ra.queue = queue;
   ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 / (tw * th)) : 0;
-  CK(launch_raster_forward(ra, tw, th, out != nullptr, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
+    CK(launch_raster_forward(ra, tw, th, out != nullptr, s));
+  }
 
   ctx->stats.n_gaussians = N;
   ctx->stats.n_views = V;
@@ -369,6 +454,7 @@ ocgs_status ocgs_destroy(ocgs_ctx* ctx) {
   if (ctx->d_scalar) cudaFree(ctx->d_scalar);
   if (ctx->h_scalar) cudaFreeHost(ctx->h_scalar);
   if (ctx->pool) cudaMemPoolDestroy(ctx->pool);
+  for (cudaEvent_t e : ctx->ev) cudaEventDestroy(e);
   delete ctx;
   return OCGS_OK;
 }
@@ -457,6 +543,7 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   const uint64_t VN = (uint64_t)st->N * st->V;
   float* grad_rec;
   CK(tmp.alloc(&grad_rec, VN * kGradStride));
+  StageTimer t_bwd(ctx, OCGS_STAGE_RASTER_BWD);
   CK(cudaMemsetAsync(grad_rec, 0, VN * kGradStride * sizeof(float), s));
   RasterBwdArgs ba{};
   ba.cams = st->d_cams;
@@ -480,8 +567,12 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   }
   ba.queue = queue;
   CK(launch_raster_backward(ba, st->tile_w, st->tile_h, s));
+  t_bwd.stop();
   GaussOut go{d_params->xyz, d_params->quat, d_params->scale, d_params->opacity, d_params->sh};
-  CK(launch_preprocess_backward(gptrs(g), st->N, st->deg, st->d_cams, st->V, grad_rec, st->ntiles, go, s));
+  {
+    StageTimer t(ctx, OCGS_STAGE_PREPROCESS_BWD);
+    CK(launch_preprocess_backward(gptrs(g), st->N, st->deg, st->d_cams, st->V, grad_rec, st->ntiles, go, s));
+  }
   return OCGS_OK;
 }
 
@@ -499,25 +590,10 @@ ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_
                                  float* d_alpha) {
   if (!ctx) return OCGS_ERR_ARG;
   if (!alpha || !mask || !loss) return set_err(ctx, OCGS_ERR_ARG, "alpha, mask and loss must be non-NULL");
-  if (!cams || n_views < 1 || n_views > 4096) return set_err(ctx, OCGS_ERR_ARG, "bad cameras");
   if (!std::isfinite(gamma)) return set_err(ctx, OCGS_ERR_ARG, "gamma must be finite");
-  std::vector<DevCam> dc(n_views);
-  std::vector<int> prefix(n_views + 1);
-  int64_t pix = 0;
-  int blocks = 0;
-  for (int v = 0; v < n_views; ++v) {
-    if (cams[v].width < 1 || cams[v].height < 1 || cams[v].width > 16384 || cams[v].height > 16384)
-      return set_err(ctx, OCGS_ERR_ARG, "camera width/height must be 1..16384");
-    std::memset(&dc[v], 0, sizeof(DevCam));
-    dc[v].W = cams[v].width;
-    dc[v].H = cams[v].height;
-    dc[v].pix_offset = pix;
-    const int64_t np = (int64_t)cams[v].width * cams[v].height;
-    prefix[v] = blocks;
-    blocks += (int)((np + kLossBlockPixels - 1) / kLossBlockPixels);
-    pix += np;
-  }
-  prefix[n_views] = blocks;
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
   CK(cudaSetDevice(ctx->device));
   cudaStream_t s = ctx->stream;
   Arena tmp(ctx);
@@ -526,10 +602,76 @@ ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_
   double* partial;
   CK(tmp.alloc(&d_cams, n_views));
   CK(tmp.alloc(&d_prefix, n_views + 1));
-  CK(tmp.alloc(&partial, blocks));
-  CK(cudaMemcpyAsync(d_cams, dc.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
-  CK(launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, blocks, gamma, partial, loss, d_alpha, s));
+  CK(tmp.alloc(&partial, lp.blocks));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, lp.blocks, gamma, partial, loss, d_alpha, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_masked_l1(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                           const ocgs_camera* cams, int32_t n_views, float weight, double* loss, float* d_rgb) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!rgb || !target || !mask || !loss) return set_err(ctx, OCGS_ERR_ARG, "rgb, target, mask and loss must be non-NULL");
+  if (!std::isfinite(weight)) return set_err(ctx, OCGS_ERR_ARG, "weight must be finite");
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, lp.blocks));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_masked_l1(rgb, target, mask, d_cams, n_views, d_prefix, lp.blocks, weight, partial, loss, d_rgb, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_state_query(ocgs_ctx* ctx, const ocgs_fwd_state* st, ocgs_state_info* info) {
+  if (!ctx || !info) return OCGS_ERR_ARG;
+  if (!st || st->ctx != ctx) return set_err(ctx, OCGS_ERR_STATE, "forward state missing or from another context");
+  CK(cudaSetDevice(ctx->device));
+  unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->d_scalar) + 2;
+  CK(launch_sum_u32(st->last, st->P, d, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->h_scalar + 2, d, sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  info->n_pairs = st->K;
+  info->n_pixels = st->P;
+  info->n_tiles = st->n_tiles;
+  info->n_views = st->V;
+  info->n_evals = (int64_t)ctx->h_scalar[2];
+  return OCGS_OK;
+}
+
+int64_t ocgs_kernel_launches(void) { return (int64_t)g_kernel_launches.load(); }
+
+ocgs_status ocgs_profile_enable(ocgs_ctx* ctx, int32_t enable) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (ctx->prof || enable) CK(cudaStreamSynchronize(ctx->stream));
+  ctx->prof = enable != 0;
+  ctx->ev_used = 0;
+  for (int i = 0; i < 16; ++i) { ctx->prof_ms[i] = 0.0; ctx->prof_n[i] = 0; }
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_profile_read(ocgs_ctx* ctx, ocgs_profile* out) {
+  if (!ctx || !out) return OCGS_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev[2 * i], ctx->ev[2 * i + 1]));
+    ctx->prof_ms[ctx->ev_stage[i]] += ms;
+    ctx->prof_n[ctx->ev_stage[i]] += 1;
+  }
+  ctx->ev_used = 0;
+  for (int i = 0; i < 16; ++i) { out->ms[i] = ctx->prof_ms[i]; out->launches[i] = ctx->prof_n[i]; }
   return OCGS_OK;
 }
 
@@ -588,12 +730,14 @@ ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold, const
   char* scratch;
   CK(tmp.alloc(&scratch, scan_scratch_bytes(n)));
   uint32_t* totals = reinterpret_cast<uint32_t*>(ctx->d_scalar);
+  StageTimer t(ctx, OCGS_STAGE_PRUNE);
   CK(launch_prune_flags(score, n, threshold, keep, border, s));
   CK(scan_exclusive_u32(keep, keep_pos, n, totals, scratch, s));
   CK(scan_exclusive_u32(border, border_pos, n, totals + 1, scratch, s));
   GaussOut go{out->xyz, out->quat, out->scale, out->opacity, out->sh};
   CK(launch_prune_compact(gptrs(in), n, in->sh_degree, keep, keep_pos, border, border_pos, go,
                           borderline_cap > 0 ? borderline : nullptr, borderline_cap, s));
+  t.stop();
   CK(cudaMemcpyAsync(ctx->h_scalar, totals, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
   const uint32_t* h = reinterpret_cast<const uint32_t*>(ctx->h_scalar);

@@ -19,6 +19,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 namespace ocgs {
 
 constexpr float kRhoCut = 9.0f;            // support cut-off rho <= 9 (3 sigma)
@@ -144,6 +146,13 @@ __device__ __forceinline__ int view_of_tile(const int* tile_prefix, int n_views,
 // ----------------------------------------------------------------------------- host-side launch helpers
 namespace ocgs {
 
+// process-wide count of kernels launched by this library (read by ocgs_kernel_launches)
+extern std::atomic<long long> g_kernel_launches;
+inline cudaError_t launched() {
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams,
                               int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
                               int4* rect, uint32_t* depth_key, int* status, cudaStream_t s);
@@ -215,11 +224,16 @@ struct RasterBwdArgs {
   int persistent_ctas;
 };
 cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, cudaStream_t s);
+// sum of the per-pixel blended-prefix lengths (the pairs both passes must evaluate)
+cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out, cudaStream_t s);
 
 cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, const DevCam* cams,
                                    int n_views, const int* block_prefix, int n_blocks, float gamma,
                                    double* partial, double* loss, float* d_alpha, cudaStream_t s);
 constexpr int kLossBlockPixels = 4096;
+cudaError_t launch_masked_l1(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams,
+                             int n_views, const int* block_prefix, int n_blocks, float weight, double* partial,
+                             double* loss, float* d_rgb, cudaStream_t s);
 
 cudaError_t launch_prune_flags(const float* score, uint32_t n, float threshold, uint32_t* keep,
                                uint32_t* border, cudaStream_t s);

@@ -436,7 +436,7 @@ cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, cons
     case 2: preprocess_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
     default: preprocess_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
@@ -451,7 +451,7 @@ cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_deg
     case 2: preprocess_bwd_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
     default: preprocess_bwd_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
   }
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace ocgs

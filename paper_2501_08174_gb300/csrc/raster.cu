@@ -9,8 +9,9 @@
 // pixel reaches an opacity close to 1), warps stop once all their pixels have
 // stopped, and the CTA stops once every pixel has.  The forward optionally
 // records, for each Gaussian, the max blending weight over the pixels where it
-// was blended (the "used during colour accumulation" record of Sec. 4.3 and
-// Sec. 5.1), with one warp max-reduction and at most one atomic per warp.
+// was blended (the per-Gaussian visibility record that Sec. 4.3 and Sec. 5.1
+// keep while colours accumulate), with one warp max-reduction and at most one
+// atomic per warp.
 //
 // The backward walks the same list back to front from each pixel's last
 // blended entry, recovering the transmittance T_i = T_{i+1} / (1 - alpha_i)
@@ -263,7 +264,7 @@ cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
   else if (img) raster_fwd_kernel<TW, TH, true, false><<<grid, TW * TH, 0, s>>>(a);
   else if (score) raster_fwd_kernel<TW, TH, false, true><<<grid, TW * TH, 0, s>>>(a);
   else return cudaSuccess;
-  return cudaGetLastError();
+  return launched();
 }
 
 template <int TW, int TH>
@@ -271,10 +272,26 @@ cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
   const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
   if (grid == 0) return cudaSuccess;
   raster_bwd_kernel<TW, TH><<<grid, TW * TH, 0, s>>>(a);
-  return cudaGetLastError();
+  return launched();
+}
+
+__global__ void sum_u32_kernel(const uint32_t* __restrict__ v, int64_t n, unsigned long long* __restrict__ out) {
+  unsigned long long acc = 0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    acc += v[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(kFull, acc, o);
+  if ((threadIdx.x & 31) == 0 && acc) atomicAdd(out, acc);
 }
 
 }  // namespace
+
+cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
+  if (e != cudaSuccess || n == 0) return e;
+  sum_u32_kernel<<<304, 256, 0, s>>>(v, n, out);
+  return launched();
+}
 
 cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, bool write_image,
                                   cudaStream_t s) {

@@ -108,17 +108,17 @@ cudaError_t scan_exclusive(const T* in, T* out, uint32_t n, T* d_total, char* sc
   const uint32_t nb = (n + kChunk - 1) / kChunk;
   if (nb == 1) {
     scan_chunk_kernel<T><<<1, kBlock, 0, s>>>(in, out, n, nullptr, d_total);
-    return cudaGetLastError();
+    return launched();
   }
   T* sums = reinterpret_cast<T*>(scratch);
   char* rest = scratch + (((size_t)nb * sizeof(T) + 255) & ~(size_t)255);
   scan_reduce_kernel<T><<<nb, kBlock, 0, s>>>(in, n, sums);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   e = scan_exclusive<T>(sums, sums, nb, nullptr, rest, s);  // in place over the block sums
   if (e != cudaSuccess) return e;
   scan_chunk_kernel<T><<<nb, kBlock, 0, s>>>(in, out, n, sums, d_total);
-  return cudaGetLastError();
+  return launched();
 }
 
 // ------------------------------------------------------------------ radix sort
@@ -316,12 +316,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     const int width = min(digit, n_bits - shift);
     const uint32_t mask = (1u << width) - 1u;
     radix_upsweep_kernel<<<nb, kBlock, 0, s>>>(kin, n, shift, mask, counts, nb);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launched();
     if (e != cudaSuccess) return e;
     e = scan_exclusive<uint32_t>(counts, counts, (mask + 1) * nb, nullptr, scan_scratch, s);
     if (e != cudaSuccess) return e;
     radix_scatter_kernel<<<nb, kBlock, 0, s>>>(kin, vin, kout, vout, n, shift, mask, counts, nb);
-    e = cudaGetLastError();
+    e = launched();
     if (e != cudaSuccess) return e;
     uint32_t* t = kin; kin = kout; kout = t;
     t = vin; vin = vout; vout = t;
@@ -334,13 +334,13 @@ cudaError_t launch_gather_counts(const uint32_t* order, const int32_t* ntiles, u
                                  uint32_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   gather_counts_kernel<<<(n + 255) / 256, 256, 0, s>>>(order, ntiles, counts, n);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   iota_kernel<<<(n + 255) / 256, 256, 0, s>>>(v, n);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint32_t n_items,
@@ -349,20 +349,20 @@ cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uin
   if (n_pairs == 0) return cudaSuccess;
   const uint32_t nb = (n_pairs + kDupPerBlock - 1) / kDupPerBlock;
   duplicate_kernel<<<nb, kBlock, 0, s>>>(order, offsets, n_items, rect, cams, n_gauss, n_pairs, keys, vals, status);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s) {
   if (n_pairs == 0) return cudaSuccess;
   tile_ranges_kernel<<<(n_pairs + 255) / 256, 256, 0, s>>>(keys, n_pairs, ranges);
-  return cudaGetLastError();
+  return launched();
 }
 
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
                               uint32_t* tile_ids, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   tile_work_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, work_key, tile_ids);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace ocgs

@@ -169,7 +169,7 @@ def test_batched_views_equal_per_view_launches(rast, dev):
 
 
 def test_contribution_score_matches_oracle(rast, dev):
-    sc = synthetic.small_scene(501, 1200, 48, 40, degree=1, n_views=3, scale_range=(0.05, 0.2))
+    sc = synthetic.small_scene(501, 3000, 48, 40, degree=1, n_views=3, scale_range=(0.08, 0.3))
     g_np = sc["gaussians"]
     score = rast.accumulate_contribution(to_device(g_np, dev), sc["cameras"]).cpu().numpy()
     refs = [oracle.render(g_np, c) for c in sc["cameras"]]
