@@ -53,7 +53,8 @@ def parse_args():
     p.add_argument("--n", type=int, default=500_000, help="surfels")
     p.add_argument("--views", type=int, default=16)
     p.add_argument("--tile", default="16x16")
-    p.add_argument("--persistent", type=int, default=0)
+    p.add_argument("--persistent", type=int, default=1)
+    p.add_argument("--ppt", type=int, default=4, help="pixels per thread")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
@@ -307,7 +308,7 @@ def run_ours(a, rank: int, world: int, local: int):
     target = torch.tensor(target_np, device=dev)
     mask = torch.tensor(mask_np, device=dev)
     tw, th = (int(x) for x in a.tile.split("x"))
-    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent))
+    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt)
 
     # sizes of the workload (outside the timed region)
     _, st = rast.render(g, cams)
@@ -401,7 +402,8 @@ def run_ours(a, rank: int, world: int, local: int):
                 "config": {"workload": workload_name(a), "mode": "batched (one pass over all views)",
                            "n_gaussians": N, "n_views": len(cams), "pixels_per_gpu": P,
                            "resolutions": [f"{c['width']}x{c['height']}" for c in cams],
-                           "tile": a.tile, "persistent": bool(a.persistent), "pairs": K, "evals": E,
+                           "tile": a.tile, "pixels_per_thread": a.ppt, "persistent": bool(a.persistent),
+                           "pairs": K, "evals": E,
                            "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB algorithmic traffic per step",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "per_view": per_view, "stages": stages, "roofline": roofline, "hbm_roofline_step": hbm_step,

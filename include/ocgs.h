@@ -98,10 +98,10 @@ typedef struct {
 /* Launch options.  None of them changes a result: the support test is exact
  * and the screen bounds are conservative, so tiles only reshape the work. */
 typedef struct {
-  int32_t tile_w;      /* 8, 16 or 32 */
-  int32_t tile_h;      /* 8 or 16; tile_w*tile_h in {64,128,256} */
-  int32_t persistent;  /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
-  int32_t reserved;
+  int32_t tile_w;             /* 8, 16 or 32 */
+  int32_t tile_h;             /* 8 or 16: 16x16, 16x8, 8x8 or 32x8 */
+  int32_t persistent;         /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
+  int32_t pixels_per_thread;  /* vertically adjacent pixels per thread: 1, 2 (0 = 2), or 4 for 16x16 */
 } ocgs_options;
 
 /* Counters of the last ocgs_render / ocgs_accumulate_contribution. */

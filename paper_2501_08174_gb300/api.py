@@ -114,7 +114,7 @@ class ForwardState:
 class Rasterizer:
     """One libocgs context on one CUDA device."""
 
-    def __init__(self, device=None, tile=(16, 16), persistent: bool = False):
+    def __init__(self, device=None, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device) \
             if not isinstance(device, torch.device) else device
@@ -123,7 +123,7 @@ class Rasterizer:
         if st != _lib.OK:
             raise _lib.OcgsError(st, "ocgs_create failed (is a CUDA device present?)")
         self._ctx = ctx
-        self.set_options(tile=tile, persistent=persistent)
+        self.set_options(tile=tile, persistent=persistent, pixels_per_thread=pixels_per_thread)
 
     # -- plumbing
     def _call(self, name: str, *args) -> int:
@@ -147,11 +147,12 @@ class Rasterizer:
         except Exception:
             pass
 
-    def set_options(self, tile=(16, 16), persistent: bool = False) -> None:
-        o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), 0)
+    def set_options(self, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2) -> None:
+        o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), int(pixels_per_thread))
         self._call("ocgs_set_options", self._ctx, C.byref(o))
         self.tile = (int(tile[0]), int(tile[1]))
         self.persistent = bool(persistent)
+        self.pixels_per_thread = int(pixels_per_thread)
 
     def stats(self) -> dict:
         s = _lib.Stats()

@@ -23,7 +23,7 @@ struct ocgs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
-  ocgs_options opts{16, 16, 0, 0};
+  ocgs_options opts{16, 16, 0, 2};
   ocgs_stats stats{};
   std::string err;
   int* d_status = nullptr;
@@ -47,7 +47,7 @@ struct ocgs_fwd_state {
   int64_t P = 0;
   uint32_t K = 0;
   uint32_t n_tiles = 0;
-  int tile_w = 16, tile_h = 16;
+  int tile_w = 16, tile_h = 16, ppt = 1;
   int persistent = 0;
   DevCam* d_cams = nullptr;
   int* d_tile_prefix = nullptr;
@@ -245,8 +245,9 @@ ocgs_status read_status(ocgs_ctx* ctx, int* status) {
   return OCGS_OK;
 }
 
-bool valid_tile(int tw, int th) {
-  return (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+bool valid_tile(int tw, int th, int ppt) {
+  const bool shape = (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
+  return shape && (ppt == 1 || ppt == 2 || (ppt == 4 && tw == 16 && th == 16));
 }
 
 GaussPtrs gptrs(const ocgs_gaussians* g) { return GaussPtrs{g->xyz, g->quat, g->scale, g->opacity, g->sh}; }
@@ -271,7 +272,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   Arena keep(ctx), tmp(ctx);
 
   st->ctx = ctx; st->V = V; st->N = N; st->deg = g->sh_degree; st->P = pl.P;
-  st->n_tiles = (uint32_t)pl.tiles; st->tile_w = tw; st->tile_h = th; st->persistent = ctx->opts.persistent;
+  st->n_tiles = (uint32_t)pl.tiles; st->tile_w = tw; st->tile_h = th; st->ppt = ctx->opts.pixels_per_thread;
+  st->persistent = ctx->opts.persistent;
   CK(keep.alloc(&st->d_cams, V));
   CK(keep.alloc(&st->d_tile_prefix, V + 1));
   CK(cudaMemcpyAsync(st->d_cams, pl.cams.data(), sizeof(DevCam) * V, cudaMemcpyHostToDevice, s));
@@ -289,6 +291,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   uint32_t *dkey, *order, *dkey_alt, *order_alt;
   uint64_t* counts;
   CK(tmp.alloc(&rect, VN));
+  uint32_t* tmask;
+  CK(tmp.alloc(&tmask, VN));
+  uint64_t* roff;
+  CK(tmp.alloc(&roff, VN));
   CK(tmp.alloc(&dkey, VN));
   CK(tmp.alloc(&order, VN));
   CK(tmp.alloc(&dkey_alt, VN));
@@ -304,6 +310,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     StageTimer t(ctx, OCGS_STAGE_PREPROCESS);
     CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, rect, dkey,
                          ctx->d_status, s));
+  }
+  {
+    StageTimer t(ctx, OCGS_STAGE_BINNING);
+    CK(launch_tile_count(st->rec, rect, st->d_cams, N, VN, tw, th, st->ntiles, tmask, dkey, s));
   }
   bool alt = false;
   {
@@ -336,7 +346,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_duplicate(sorted, counts, VN, rect, st->d_cams, N, K, pkey, pval, ctx->d_status, s));
+    CK(launch_duplicate(sorted, counts, roff, VN, st->ntiles, rect, tmask, st->rec, st->d_cams, N, tw, th, K, pkey,
+                        pval, s));
   }
   const int tbits = bits_for((uint64_t)pl.tiles);
   bool palt = false;
@@ -384,10 +395,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   ra.score = score;
   ra.tile_order = st->tile_order;
   ra.queue = queue;
-  ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 / (tw * th)) : 0;
+  ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 * st->ppt / (tw * th)) : 0;
   {
     StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-    CK(launch_raster_forward(ra, tw, th, out != nullptr, s));
+    CK(launch_raster_forward(ra, tw, th, st->ppt, out != nullptr, s));
   }
 
   ctx->stats.n_gaussians = N;
@@ -467,9 +478,11 @@ ocgs_status ocgs_set_stream(ocgs_ctx* ctx, void* stream) {
 
 ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
   if (!ctx || !o) return OCGS_ERR_ARG;
-  if (!valid_tile(o->tile_w, o->tile_h))
-    return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8");
+  const int ppt = o->pixels_per_thread == 0 ? 2 : o->pixels_per_thread;
+  if (!valid_tile(o->tile_w, o->tile_h, ppt))
+    return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8 with 1 or 2 pixels per thread (4 for 16x16)");
   ctx->opts = *o;
+  ctx->opts.pixels_per_thread = ppt;
   return OCGS_OK;
 }
 
@@ -563,10 +576,10 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   if (st->persistent) {
     CK(tmp.alloc(&queue, 1));
     CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
-    ba.persistent_ctas = ctx->sm_count * (2048 / (st->tile_w * st->tile_h));
+    ba.persistent_ctas = ctx->sm_count * (2048 * st->ppt / (st->tile_w * st->tile_h));
   }
   ba.queue = queue;
-  CK(launch_raster_backward(ba, st->tile_w, st->tile_h, s));
+  CK(launch_raster_backward(ba, st->tile_w, st->tile_h, st->ppt, s));
   t_bwd.stop();
   GaussOut go{d_params->xyz, d_params->quat, d_params->scale, d_params->opacity, d_params->sh};
   {

@@ -87,39 +87,62 @@ enum GradSlot {
 
 // Result of evaluating one surfel at one pixel centre.  All arithmetic uses
 // explicitly rounded intrinsics so that the forward and the backward kernels
-// take bit-identical decisions (skip, clamp, branch) for the same inputs.
+// take bit-identical decisions (skip, clamp, branch) for the same inputs, and
+// the value at a pixel does not depend on the tile shape or on how many
+// pixels a thread owns.
 struct SplatEval {
   float dx, dy, un, vn, den, r, rho3, rho, G, oG, alpha, z;
   bool surf;  // the surfel term rho3 <= rho2 is used (else the screen filter)
   bool ok;    // rho <= 9 and alpha >= 1/255: the candidate is blended unless the pixel stops
 };
 
+// Terms of the ray-splat map that depend only on the pixel column.
+struct SplatColumn {
+  float dx, ux, vx, ex, dx2;
+};
+
+__device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float4 g1, const float4 g2, float px) {
+  SplatColumn c;
+  c.dx = __fsub_rn(px, g0.x);
+  c.ux = __fmul_rn(g1.x, c.dx);
+  c.vx = __fmul_rn(g1.z, c.dx);
+  c.ex = __fmaf_rn(g2.y, c.dx, g2.x);
+  c.dx2 = __fmul_rn(c.dx, c.dx);
+  return c;
+}
+
+// rb: the record's support bound support_rho(o) <= 9.  Candidates with
+// rho > rb have o exp(-rho/2) < 1/255, so testing rb instead of 9 first only
+// skips work; every decision is the one the 9 cut and the 1/255 floor give.
 __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1, const float4 g2,
-                                                float px, float py) {
+                                                const SplatColumn& c, float py, float rb) {
   SplatEval e;
-  e.dx = __fsub_rn(px, g0.x);
+  e.dx = c.dx;
   e.dy = __fsub_rn(py, g0.y);
-  e.un = __fmaf_rn(g1.x, e.dx, __fmul_rn(g1.y, e.dy));
-  e.vn = __fmaf_rn(g1.z, e.dx, __fmul_rn(g1.w, e.dy));
-  e.den = __fmaf_rn(g2.z, e.dy, __fmaf_rn(g2.y, e.dx, g2.x));
-  const float rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(e.dx, e.dx, __fmul_rn(e.dy, e.dy)));
+  e.un = __fmaf_rn(g1.y, e.dy, c.ux);
+  e.vn = __fmaf_rn(g1.w, e.dy, c.vx);
+  e.den = __fmaf_rn(g2.z, e.dy, c.ex);
+  const float rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(e.dy, e.dy, c.dx2));
   const float q = __fmaf_rn(e.un, e.un, __fmul_rn(e.vn, e.vn));
   const float dd = __fmul_rn(e.den, e.den);
-  const bool in3 = (e.den != 0.0f) && (q <= __fmul_rn(kRhoCut, dd));
+  const bool in3 = (e.den != 0.0f) && (q <= __fmul_rn(rb, dd));
   e.r = 0.0f;
   e.rho3 = __int_as_float(0x7f800000);  // +inf
+  e.G = 0.0f;
+  e.oG = 0.0f;
+  e.alpha = 0.0f;
+  e.z = 0.0f;
+  e.ok = false;
+  e.surf = false;
+  e.rho = rho2;
+  if (!in3 && rho2 > rb) return e;  // outside the support
   if (in3) {
     e.r = __fdividef(1.0f, e.den);
     e.rho3 = __fmul_rn(q, __fmul_rn(e.r, e.r));
   }
   e.surf = in3 && (e.rho3 <= rho2);
   e.rho = e.surf ? e.rho3 : rho2;
-  e.G = 0.0f;
-  e.oG = 0.0f;
-  e.alpha = 0.0f;
-  e.z = 0.0f;
-  e.ok = false;
-  if (e.rho <= kRhoCut) {
+  if (e.rho <= rb) {
     e.G = __expf(__fmul_rn(-0.5f, e.rho));
     e.oG = __fmul_rn(g0.z, e.G);
     e.alpha = fminf(kAlphaMax, e.oG);
@@ -130,6 +153,89 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1
 }
 
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
+
+// Support bound in rho of a surfel of opacity o: the 3-sigma cut, tightened to
+// where o exp(-rho/2) can still reach 1/255 (with a margin, so that no pixel
+// that FP32 would blend lies outside).  Used for the screen box and tile test.
+__device__ __forceinline__ float support_rho(float o) {
+  return fminf(kRhoCut, __fadd_rn(__fmul_rn(2.0f, __logf(__fmul_rn(255.0f, o))), 1e-3f));
+}
+
+// min over t in [t0, t1] of a t^2 + b t + c  (any sign of a)
+__device__ __forceinline__ float quad_min(float a, float b, float c, float t0, float t1) {
+  const float f0 = __fmaf_rn(__fmaf_rn(a, t0, b), t0, c);
+  const float f1 = __fmaf_rn(__fmaf_rn(a, t1, b), t1, c);
+  float m = fminf(f0, f1);
+  if (a > 0.f) {
+    const float ts = __fdividef(-b, __fmul_rn(2.f, a));
+    if (ts > t0 && ts < t1) m = fminf(m, __fmaf_rn(__fmaf_rn(a, ts, b), ts, c));
+  }
+  return m;
+}
+
+// Support conic of a record grown by the test margin:
+// f(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 + 2 d dx + 2 e dy + f0 <= 0 where
+// (A00 dx + A01 dy)^2 + (A10 dx + A11 dy)^2 <= rt (e0 + e1 dx + e2 dy)^2.
+struct SupportConic {
+  float cx, cy, r2f;             // filter disc: |x - c|^2 <= r2f
+  float a, b, c, d, e, f0;
+  bool finite;
+};
+
+__device__ __forceinline__ SupportConic support_conic(const float4 g0, const float4 g1, const float4 g2, float rb) {
+  SupportConic k;
+  const float rt = __fadd_rn(__fmul_rn(rb, 1.001f), 1e-3f);
+  k.cx = g0.x;
+  k.cy = g0.y;
+  k.r2f = __fmul_rn(0.5f, rt);
+  k.a = __fsub_rn(__fmaf_rn(g1.x, g1.x, __fmul_rn(g1.z, g1.z)), __fmul_rn(rt, __fmul_rn(g2.y, g2.y)));
+  k.b = __fsub_rn(__fmaf_rn(g1.x, g1.y, __fmul_rn(g1.z, g1.w)), __fmul_rn(rt, __fmul_rn(g2.y, g2.z)));
+  k.c = __fsub_rn(__fmaf_rn(g1.y, g1.y, __fmul_rn(g1.w, g1.w)), __fmul_rn(rt, __fmul_rn(g2.z, g2.z)));
+  k.d = -__fmul_rn(rt, __fmul_rn(g2.x, g2.y));
+  k.e = -__fmul_rn(rt, __fmul_rn(g2.x, g2.z));
+  k.f0 = -__fmul_rn(rt, __fmul_rn(g2.x, g2.x));
+  k.finite = isfinite(k.a) && isfinite(k.b) && isfinite(k.c) && isfinite(k.d) && isfinite(k.e) && isfinite(k.f0);
+  return k;
+}
+
+__device__ __forceinline__ float conic_at(const SupportConic& k, float x, float y) {
+  return __fmaf_rn(__fmaf_rn(k.c, y, __fmul_rn(2.f, __fmaf_rn(k.b, x, k.e))), y,
+                   __fmaf_rn(__fmaf_rn(k.a, x, __fmul_rn(2.f, k.d)), x, k.f0));
+}
+
+// Does the support {rho <= rb} of a record reach a pixel centre inside the
+// rectangle [x0, x1] x [y0, y1] (pixel coordinates)?  Conservative: the
+// rectangle is grown by 0.02 px and rb by 0.1 % (+1e-3).  The support is the
+// union of the screen filter disc |x - c|^2 <= rb/2 and the projected surfel
+// disc (the conic above), whose minimum over the rectangle lies at a corner,
+// at its stationary point or on an edge.  The same explicitly rounded
+// arithmetic gives the same answer in every kernel that asks.
+__device__ __forceinline__ bool conic_touches(const SupportConic& k, float x0, float x1, float y0, float y1) {
+  const float X0 = __fsub_rn(x0 - 0.02f, k.cx), X1 = __fsub_rn(x1 + 0.02f, k.cx);
+  const float Y0 = __fsub_rn(y0 - 0.02f, k.cy), Y1 = __fsub_rn(y1 + 0.02f, k.cy);
+  const float qx = fminf(fmaxf(0.f, X0), X1), qy = fminf(fmaxf(0.f, Y0), Y1);
+  if (__fmaf_rn(qx, qx, __fmul_rn(qy, qy)) <= k.r2f) return true;
+  if (!k.finite) return true;
+  if (conic_at(k, X0, Y0) <= 0.f || conic_at(k, X1, Y0) <= 0.f || conic_at(k, X0, Y1) <= 0.f ||
+      conic_at(k, X1, Y1) <= 0.f)
+    return true;
+  const float det = __fsub_rn(__fmul_rn(k.a, k.c), __fmul_rn(k.b, k.b));
+  if (k.a > 0.f && det > 0.f) {
+    const float sx = __fdividef(__fsub_rn(__fmul_rn(k.b, k.e), __fmul_rn(k.c, k.d)), det);
+    const float sy = __fdividef(__fsub_rn(__fmul_rn(k.b, k.d), __fmul_rn(k.a, k.e)), det);
+    if (sx >= X0 && sx <= X1 && sy >= Y0 && sy <= Y1 && conic_at(k, sx, sy) <= 0.f) return true;
+  }
+  // edges: dy = Y fixed -> a dx^2 + 2 (b Y + d) dx + (c Y^2 + 2 e Y + f0), and likewise in dy
+  const float cy0 = __fmaf_rn(__fmaf_rn(k.c, Y0, __fmul_rn(2.f, k.e)), Y0, k.f0);
+  const float cy1 = __fmaf_rn(__fmaf_rn(k.c, Y1, __fmul_rn(2.f, k.e)), Y1, k.f0);
+  if (quad_min(k.a, __fmul_rn(2.f, __fmaf_rn(k.b, Y0, k.d)), cy0, X0, X1) <= 0.f) return true;
+  if (quad_min(k.a, __fmul_rn(2.f, __fmaf_rn(k.b, Y1, k.d)), cy1, X0, X1) <= 0.f) return true;
+  const float cx0 = __fmaf_rn(__fmaf_rn(k.a, X0, __fmul_rn(2.f, k.d)), X0, k.f0);
+  const float cx1 = __fmaf_rn(__fmaf_rn(k.a, X1, __fmul_rn(2.f, k.d)), X1, k.f0);
+  if (quad_min(k.c, __fmul_rn(2.f, __fmaf_rn(k.b, X0, k.e)), cx0, Y0, Y1) <= 0.f) return true;
+  if (quad_min(k.c, __fmul_rn(2.f, __fmaf_rn(k.b, X1, k.e)), cx1, Y0, Y1) <= 0.f) return true;
+  return false;
+}
 
 // first global tile id -> view, by binary search over V+1 prefix offsets
 __device__ __forceinline__ int view_of_tile(const int* tile_prefix, int n_views, int tile) {
@@ -179,9 +285,18 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, uint32_t n, ui
 cudaError_t launch_gather_counts(const uint32_t* order, const int32_t* ntiles, uint64_t* counts,
                                  uint32_t n, cudaStream_t s);
 cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s);
-cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint32_t n_items,
-                             const int4* rect, const DevCam* cams, int64_t n_gauss, uint32_t n_pairs,
-                             uint32_t* keys, uint32_t* vals, int* status, cudaStream_t s);
+// exact tile counts: ntiles[r] = tiles of rect[r] that conic_touches; a record
+// with none gets depth key 0xffffffff so that it sorts to the tail.  For a
+// record with at most 32 candidate tiles, tmask[r] keeps which ones.
+cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
+                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* tmask,
+                              uint32_t* depth_key, cudaStream_t s);
+// write the (tile, record) pairs: offsets are the scanned counts in depth order
+// (order), scattered to record order in roff [n_rec] first
+cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint64_t* roff, uint32_t n_rec,
+                             const int32_t* ntiles, const int4* rect, const uint32_t* tmask, const RecPtrs rec,
+                             const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs,
+                             uint32_t* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s);
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
                               uint32_t* tile_ids, cudaStream_t s);
@@ -203,7 +318,8 @@ struct RasterArgs {
   uint32_t* queue;             // persistent: global tile counter (zeroed)
   int persistent_ctas;         // 0 = one CTA per tile
 };
-cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, bool write_image,
+// ppt: pixels per thread (vertically adjacent): 1 or 2, and 4 for 16x16 tiles
+cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, int ppt, bool write_image,
                                   cudaStream_t s);
 
 struct RasterBwdArgs {
@@ -223,7 +339,7 @@ struct RasterBwdArgs {
   uint32_t* queue;
   int persistent_ctas;
 };
-cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, cudaStream_t s);
+cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, cudaStream_t s);
 // sum of the per-pixel blended-prefix lengths (the pairs both passes must evaluate)
 cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out, cudaStream_t s);
 

@@ -219,7 +219,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
   const bool bad = !finite || !(qn2 > 0.f) || !(s.x > 0.f) || !(s.y > 0.f) || !(o >= kAlphaMin);
   const Frame f = make_frame(q);
   // support bound in rho: the 3-sigma cut, tightened where o exp(-rho/2) < 1/255 anyway
-  const float rho_b = bad ? 0.f : fminf(kRhoCut, 2.0f * __logf(255.0f * o) + 1e-3f);
+  const float rho_b = bad ? 0.f : support_rho(o);
   const float kq = sqrtf(fmaxf(rho_b, 0.f));
   const float rf = sqrtf(0.5f * fmaxf(rho_b, 0.f));
 

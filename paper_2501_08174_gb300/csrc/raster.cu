@@ -1,10 +1,12 @@
 // Tile rasterizer: front-to-back compositing (forward) and its reverse-order
 // adjoint (backward).
 //
-// One CTA owns one screen tile (one thread per pixel).  The tile's sorted
-// (depth, Gaussian) list is streamed through shared memory in batches of one
-// record per thread; every thread then evaluates the batch against its pixel
-// centre.  Compositing of a pixel stops at the first blended candidate that
+// One CTA owns one screen tile; each thread owns PPT vertically adjacent
+// pixels of it.  The tile's sorted (depth, Gaussian) list is streamed through
+// shared memory in batches of one record per thread; every thread then
+// evaluates the batch against its pixel centres, so one shared-memory read of
+// a record (and, in the backward, one warp reduction of its gradient) serves
+// PPT pixels.  Compositing of a pixel stops at the first blended candidate that
 // would bring its transmittance below 1e-4 (Sec. 4.3: rendering ends once the
 // pixel reaches an opacity close to 1), warps stop once all their pixels have
 // stopped, and the CTA stops once every pixel has.  The forward optionally
@@ -16,8 +18,10 @@
 // The backward walks the same list back to front from each pixel's last
 // blended entry, recovering the transmittance T_i = T_{i+1} / (1 - alpha_i)
 // from the stored final transmittance, so nothing per (pixel, Gaussian) is
-// stored between the passes.  Per-Gaussian gradients are reduced over the warp
-// with shuffles before one atomic add per slot and warp.
+// stored between the passes.  Per-Gaussian gradients are summed over the
+// thread's pixels, reduced over the warp with a halving transpose (about 20
+// shuffles for 18 values), accumulated per tile in shared memory and added to
+// global memory with one vector atomic per 4 values, entry and tile.
 #include "common.cuh"
 
 namespace ocgs {
@@ -25,16 +29,35 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 
-template <int TW, int TH, bool IMG, bool SCORE>
-__global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(const RasterArgs a) {
-  constexpr int BS = TW * TH;
-  __shared__ float4 s_g0[BS], s_g1[BS], s_g2[BS], s_a0[BS];
-  __shared__ float2 s_a1[BS];
-  __shared__ uint32_t s_gid[BS];
+#ifdef OCGS_COUNT
+// diagnostic build only: warp iterations and evaluated (lane, pixel) pairs
+__device__ unsigned long long g_diag[8];
+#define OCGS_DIAG(slot, v) atomicAdd(&g_diag[slot], (unsigned long long)(v))
+#else
+#define OCGS_DIAG(slot, v)
+#endif
+
+// Resident warps per SM the compiler is asked to fit (caps registers per thread).
+#ifndef OCGS_FWD_WARPS
+#define OCGS_FWD_WARPS 16
+#endif
+#ifndef OCGS_BWD_WARPS
+#define OCGS_BWD_WARPS 16
+#endif
+
+template <int TW, int TH, int PPT, bool IMG, bool SCORE>
+__global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW * TH)) raster_fwd_kernel(const RasterArgs a) {
+  constexpr int NT = TW * TH / PPT;  // threads, and records per shared-memory batch
+  __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
+  __shared__ float2 s_a1[NT];
+  __shared__ uint32_t s_gid[NT];
+  __shared__ uint32_t s_best[NT];  // per-batch max blending weight bits of each entry (SCORE)
+  __shared__ float s_rb[NT];
   __shared__ uint32_t s_tile;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int lx = tid % TW, ly = tid / TW;
+  const int lx = tid % TW, ly0 = (tid / TW) * PPT;  // this thread's column and first of PPT rows
+  if (SCORE) s_best[tid] = 0u;
   for (uint32_t it = 0;; ++it) {
     uint32_t tile;
     if (a.persistent_ctas) {
@@ -52,91 +75,177 @@ __global__ void __launch_bounds__(TW * TH) raster_fwd_kernel(const RasterArgs a)
     const DevCam& cam = a.cams[v];
     const int local = (int)tile - cam.tile_offset;
     const int px = (local % cam.tiles_x) * TW + lx;
-    const int py = (local / cam.tiles_x) * TH + ly;
-    const bool inside = px < cam.W && py < cam.H;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const int py0 = (local / cam.tiles_x) * TH + ly0;
+    const float pxf = (float)px + 0.5f;
     const uint2 rg = a.ranges[tile];
     const uint32_t start = rg.x, end = rg.y;
     const int64_t gbase = (int64_t)v * a.n_gauss;
-    float T = 1.f, c0 = 0.f, c1 = 0.f, c2 = 0.f, dep = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
-    uint32_t last = 0;
-    bool done = !inside;
-    for (uint32_t b0 = start; b0 < end; b0 += BS) {
-      if (__syncthreads_count(!done) == 0) break;
-      const uint32_t k = b0 + tid;
-      if (k < end) {
-        const uint32_t idx = a.vals[k];
-        s_g0[tid] = a.rec.g0[idx];
-        s_g1[tid] = a.rec.g1[idx];
-        s_g2[tid] = a.rec.g2[idx];
+    float T[PPT], c0[PPT], c1[PPT], c2[PPT], dep[PPT], n0[PPT], n1[PPT], n2[PPT];
+    uint32_t last[PPT];
+    bool done[PPT];
+    bool alldone = true;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      T[k] = 1.f;
+      c0[k] = c1[k] = c2[k] = dep[k] = n0[k] = n1[k] = n2[k] = 0.f;
+      last[k] = 0u;
+      done[k] = !(px < cam.W && py0 + k < cam.H);
+      alldone = alldone && done[k];
+    }
+    for (uint32_t b0 = start; b0 < end; b0 += NT) {
+      if (__syncthreads_count(!alldone) == 0) break;
+      const uint32_t kk = b0 + tid;
+      if (kk < end) {
+        const uint32_t idx = a.vals[kk];
+        const float4 g0 = a.rec.g0[idx], g1 = a.rec.g1[idx], g2 = a.rec.g2[idx];
+        const float rb = support_rho(g0.z);
+        s_g0[tid] = g0;
+        s_g1[tid] = g1;
+        s_g2[tid] = g2;
         s_a0[tid] = a.rec.a0[idx];
         s_a1[tid] = a.rec.a1[idx];
+        s_rb[tid] = rb;
         if (SCORE) s_gid[tid] = (uint32_t)((int64_t)idx - gbase);
       }
       __syncthreads();
-      const int cnt = (end - b0 < (uint32_t)BS) ? (int)(end - b0) : BS;
+      const int cnt = (end - b0 < (uint32_t)NT) ? (int)(end - b0) : NT;
       for (int j = 0; j < cnt; ++j) {
-        if (__all_sync(kFull, done)) break;
-        float w = 0.f;
-        if (!done) {
-          const SplatEval e = eval_splat(s_g0[j], s_g1[j], s_g2[j], pxf, pyf);
-          if (e.ok) {
-            const float Tn = T * (1.f - e.alpha);
-            if (Tn < kTEps) {
-              done = true;
-            } else {
-              w = e.alpha * T;
-              if (IMG) {
-                const float4 ap = s_a0[j];
-                const float2 an = s_a1[j];
-                c0 += w * ap.x; c1 += w * ap.y; c2 += w * ap.z;
-                dep += w * e.z;
-                n0 += w * ap.w; n1 += w * an.x; n2 += w * an.y;
+        if ((j & 7) == 0 && __all_sync(kFull, alldone)) break;
+        float wmax = 0.f;
+#ifdef OCGS_COUNT
+        if (lane == 0) OCGS_DIAG(0, 1);
+        {
+          int act = 0;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) act += done[k] ? 0 : 1;
+          OCGS_DIAG(1, act);
+        }
+#endif
+        if (!alldone) {
+          const float4 g0 = s_g0[j], g1 = s_g1[j], g2 = s_g2[j];
+          const float rb = s_rb[j];
+          const SplatColumn col = splat_column(g0, g1, g2, pxf);
+          float4 ap = make_float4(0.f, 0.f, 0.f, 0.f);
+          float2 an = make_float2(0.f, 0.f);
+          if (IMG) {
+            ap = s_a0[j];
+            an = s_a1[j];
+          }
+          alldone = true;
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (!done[k]) {
+              const SplatEval e = eval_splat(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
+              if (e.ok) {
+                const float Tn = T[k] * (1.f - e.alpha);
+                if (Tn < kTEps) {
+                  done[k] = true;
+                } else {
+                  const float w = e.alpha * T[k];
+                  if (IMG) {
+                    c0[k] += w * ap.x;
+                    c1[k] += w * ap.y;
+                    c2[k] += w * ap.z;
+                    dep[k] += w * e.z;
+                    n0[k] += w * ap.w;
+                    n1[k] += w * an.x;
+                    n2[k] += w * an.y;
+                  }
+                  T[k] = Tn;
+                  last[k] = b0 + (uint32_t)j - start + 1u;
+                  wmax = fmaxf(wmax, w);
+                }
               }
-              T = Tn;
-              last = b0 + (uint32_t)j - start + 1u;
             }
+            alldone = alldone && done[k];
           }
         }
         if (SCORE) {
-          const unsigned m = __reduce_max_sync(kFull, __float_as_uint(w));
-          if (lane == 0 && m != 0u) atomicMax(reinterpret_cast<unsigned*>(a.score) + s_gid[j], m);
+          const unsigned m = __reduce_max_sync(kFull, __float_as_uint(wmax));
+          if (lane == 0 && m != 0u) atomicMax(&s_best[j], m);
+        }
+      }
+      if (SCORE) {
+        // one global max per entry and tile (non-negative floats order like their bits)
+        __syncthreads();
+        if (tid < cnt && s_best[tid] != 0u) {
+          atomicMax(reinterpret_cast<unsigned*>(a.score) + s_gid[tid], s_best[tid]);
+          s_best[tid] = 0u;
         }
       }
     }
-    if (IMG && inside) {
-      const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
-      a.out.rgb[3 * pix + 0] = c0;
-      a.out.rgb[3 * pix + 1] = c1;
-      a.out.rgb[3 * pix + 2] = c2;
-      a.out.alpha[pix] = 1.f - T;
-      a.out.depth[pix] = dep;
-      a.out.normal[3 * pix + 0] = n0;
-      a.out.normal[3 * pix + 1] = n1;
-      a.out.normal[3 * pix + 2] = n2;
-      a.t_final[pix] = T;
-      a.last[pix] = last;
+    if (IMG) {
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        const int py = py0 + k;
+        if (px < cam.W && py < cam.H) {
+          const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
+          a.out.rgb[3 * pix + 0] = c0[k];
+          a.out.rgb[3 * pix + 1] = c1[k];
+          a.out.rgb[3 * pix + 2] = c2[k];
+          a.out.alpha[pix] = 1.f - T[k];
+          a.out.depth[pix] = dep[k];
+          a.out.normal[3 * pix + 0] = n0[k];
+          a.out.normal[3 * pix + 1] = n1[k];
+          a.out.normal[3 * pix + 2] = n2[k];
+          a.t_final[pix] = T[k];
+          a.last[pix] = last[k];
+        }
+      }
     }
   }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// One halving step of a warp transpose-reduction: lanes with bit OFF clear keep
+// the first ceil(C/2) of their C values, the others keep the rest, and each
+// adds the partner's copy of what it keeps.  After the steps for OFF = 16..1
+// every lane holds the warp total of one slot: C + C/2 + ... shuffles in all
+// instead of 5 C for independent butterflies.
+template <int C, int OFF>
+__device__ __forceinline__ void halve(float* v, int lane, int& base, int& real) {
+  constexpr int KEEP = (C + 1) / 2;
+  const bool upper = (lane & OFF) != 0;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
+  for (int i = 0; i < KEEP; ++i) {
+    const float lo = v[i];
+    const float hi = (KEEP + i < C) ? v[KEEP + i] : 0.f;
+    const float got = __shfl_xor_sync(kFull, upper ? lo : hi, OFF);
+    v[i] = (upper ? hi : lo) + got;
+  }
+  if (upper) {
+    base += KEEP;
+    real -= KEEP;
+  } else if (real > KEEP) {
+    real = KEEP;
+  }
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(const RasterBwdArgs a) {
-  constexpr int BS = TW * TH;
+// Warp sum of 18 gradient slots; returns the slot this lane holds (or -1).
+__device__ __forceinline__ int warp_reduce18(float* v, int lane) {
+  int base = 0, real = 18;
+  halve<18, 16>(v, lane, base, real);
+  halve<9, 8>(v, lane, base, real);
+  halve<5, 4>(v, lane, base, real);
+  halve<3, 2>(v, lane, base, real);
+  halve<2, 1>(v, lane, base, real);
+  return real >= 1 ? base : -1;
+}
+
+template <int TW, int TH, int PPT>
+__global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW * TH)) raster_bwd_kernel(const RasterBwdArgs a) {
+  constexpr int NT = TW * TH / PPT;
   constexpr int NG = 18;
-  __shared__ float4 s_g0[BS], s_g1[BS], s_g2[BS], s_a0[BS];
-  __shared__ float2 s_a1[BS];
-  __shared__ uint32_t s_idx[BS];
+  __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
+  __shared__ float2 s_a1[NT];
+  __shared__ uint32_t s_idx[NT];
+  __shared__ __align__(16) float s_grad[NT * kGradStride];  // per-batch gradient sums of each entry
+  __shared__ float s_rb[NT];
   __shared__ uint32_t s_tile, s_max;
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int lx = tid % TW, ly = tid / TW;
+  const int lx = tid % TW, ly0 = (tid / TW) * PPT;
+#pragma unroll
+  for (int q = 0; q < kGradStride; ++q) s_grad[tid * kGradStride + q] = 0.f;
   for (uint32_t it = 0;; ++it) {
     uint32_t tile;
     if (a.persistent_ctas) {
@@ -154,100 +263,151 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(const RasterBwdArgs
     const DevCam& cam = a.cams[v];
     const int local = (int)tile - cam.tile_offset;
     const int px = (local % cam.tiles_x) * TW + lx;
-    const int py = (local / cam.tiles_x) * TH + ly;
-    const bool inside = px < cam.W && py < cam.H;
-    const float pxf = (float)px + 0.5f, pyf = (float)py + 0.5f;
+    const int py0 = (local / cam.tiles_x) * TH + ly0;
+    const float pxf = (float)px + 0.5f;
     const uint32_t start = a.ranges[tile].x;
-    float T = 1.f, Tf = 1.f;
-    uint32_t my_last = 0;
-    float gC0 = 0.f, gC1 = 0.f, gC2 = 0.f, gA = 0.f, gD = 0.f, gN0 = 0.f, gN1 = 0.f, gN2 = 0.f;
-    if (inside) {
-      const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
-      Tf = a.t_final[pix];
-      T = Tf;
-      my_last = a.last[pix];
-      if (a.d_out.rgb) { gC0 = a.d_out.rgb[3 * pix]; gC1 = a.d_out.rgb[3 * pix + 1]; gC2 = a.d_out.rgb[3 * pix + 2]; }
-      if (a.d_out.alpha) gA = a.d_out.alpha[pix];
-      if (a.d_out.depth) gD = a.d_out.depth[pix];
-      if (a.d_out.normal) { gN0 = a.d_out.normal[3 * pix]; gN1 = a.d_out.normal[3 * pix + 1]; gN2 = a.d_out.normal[3 * pix + 2]; }
+    float T[PPT], gAT[PPT], S[PPT];
+    float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gN0[PPT], gN1[PPT], gN2[PPT];
+    uint32_t last[PPT];
+    uint32_t thread_last = 0;
+#pragma unroll
+    for (int k = 0; k < PPT; ++k) {
+      T[k] = 1.f;
+      gAT[k] = 0.f;
+      S[k] = 0.f;  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
+      last[k] = 0u;
+      gC0[k] = gC1[k] = gC2[k] = gD[k] = gN0[k] = gN1[k] = gN2[k] = 0.f;
+      const int py = py0 + k;
+      if (px < cam.W && py < cam.H) {
+        const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
+        const float Tf = a.t_final[pix];
+        T[k] = Tf;
+        last[k] = a.last[pix];
+        if (a.d_out.rgb) {
+          gC0[k] = a.d_out.rgb[3 * pix];
+          gC1[k] = a.d_out.rgb[3 * pix + 1];
+          gC2[k] = a.d_out.rgb[3 * pix + 2];
+        }
+        if (a.d_out.alpha) gAT[k] = a.d_out.alpha[pix] * Tf;
+        if (a.d_out.depth) gD[k] = a.d_out.depth[pix];
+        if (a.d_out.normal) {
+          gN0[k] = a.d_out.normal[3 * pix];
+          gN1[k] = a.d_out.normal[3 * pix + 1];
+          gN2[k] = a.d_out.normal[3 * pix + 2];
+        }
+        thread_last = max(thread_last, last[k]);
+      }
     }
     __syncthreads();
     if (tid == 0) s_max = 0u;
     __syncthreads();
-    if (my_last) atomicMax(&s_max, my_last);
+    if (thread_last) atomicMax(&s_max, thread_last);
     __syncthreads();
     const int max_last = (int)s_max;
-    float S = 0.f;  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
-    const float gAT = gA * Tf;
-    for (int bend = max_last; bend > 0; bend -= BS) {
-      const int bstart = max(0, bend - BS);
+    const int warp_last = (int)__reduce_max_sync(kFull, thread_last);  // entries beyond it are idle for this warp
+    for (int bend = max_last; bend > 0; bend -= NT) {
+      const int bstart = max(0, bend - NT);
       __syncthreads();
       if (bstart + tid < bend) {
         const uint32_t idx = a.vals[start + (uint32_t)(bstart + tid)];
-        s_g0[tid] = a.rec.g0[idx];
-        s_g1[tid] = a.rec.g1[idx];
-        s_g2[tid] = a.rec.g2[idx];
+        const float4 g0 = a.rec.g0[idx], g1 = a.rec.g1[idx], g2 = a.rec.g2[idx];
+        const float rb = support_rho(g0.z);
+        s_g0[tid] = g0;
+        s_g1[tid] = g1;
+        s_g2[tid] = g2;
         s_a0[tid] = a.rec.a0[idx];
         s_a1[tid] = a.rec.a1[idx];
+        s_rb[tid] = rb;
         s_idx[tid] = idx;
       }
       __syncthreads();
-      for (int j = bend - 1 - bstart; j >= 0; --j) {
+      const int jtop = min(bend, warp_last) - 1 - bstart;
+      for (int j = jtop; j >= 0; --j) {
         const int jj = bstart + j;
         float gr[NG];
 #pragma unroll
         for (int q = 0; q < NG; ++q) gr[q] = 0.f;
         bool contrib = false;
-        if (jj < (int)my_last) {
-          const float4 g1 = s_g1[j], g2 = s_g2[j];
-          const SplatEval e = eval_splat(s_g0[j], g1, g2, pxf, pyf);
-          if (e.ok) {
-            contrib = true;
-            const float4 ap = s_a0[j];
-            const float2 an = s_a1[j];
-            const float inv = 1.f / (1.f - e.alpha);
-            const float Ti = T * inv;
-            const float w = e.alpha * Ti;
-            const float F = gC0 * ap.x + gC1 * ap.y + gC2 * ap.z + gD * e.z + gN0 * ap.w + gN1 * an.x +
-                            gN2 * an.y;
-            const float galpha = Ti * F - (S - gAT) * inv;
-            S += w * F;
-            T = Ti;
-            gr[kGr] = gC0 * w; gr[kGg] = gC1 * w; gr[kGb] = gC2 * w;
-            gr[kGnx] = gN0 * w; gr[kGny] = gN1 * w; gr[kGnz] = gN2 * w;
-            const float gz = gD * w;
-            const bool unclamped = e.oG < kAlphaMax;
-            const float grho = unclamped ? -0.5f * galpha * e.alpha : 0.f;
-            gr[kGo] = unclamped ? galpha * e.G : 0.f;
-            float gdx, gdy;
-            if (e.surf) {
-              const float r2 = e.r * e.r;
-              const float gun = grho * 2.f * e.un * r2;
-              const float gvn = grho * 2.f * e.vn * r2;
-              const float gden = -grho * 2.f * e.rho3 * e.r - gz * e.z * e.r;
-              gr[kGzD] = gz * e.r;
-              gdx = gun * g1.x + gvn * g1.z + gden * g2.y;
-              gdy = gun * g1.y + gvn * g1.w + gden * g2.z;
-              gr[kGA00] = gun * e.dx; gr[kGA01] = gun * e.dy;
-              gr[kGA10] = gvn * e.dx; gr[kGA11] = gvn * e.dy;
-              gr[kGe0] = gden; gr[kGe1] = gden * e.dx; gr[kGe2] = gden * e.dy;
-            } else {
-              gdx = grho * 4.f * e.dx;
-              gdy = grho * 4.f * e.dy;
-              gr[kGzc] = gz;
+#ifdef OCGS_COUNT
+        if (lane == 0) OCGS_DIAG(2, 1);
+#endif
+        if (jj < (int)thread_last) {
+          const float4 g0 = s_g0[j], g1 = s_g1[j], g2 = s_g2[j];
+          const float rb = s_rb[j];
+          const SplatColumn col = splat_column(g0, g1, g2, pxf);
+          const float4 ap = s_a0[j];
+          const float2 an = s_a1[j];
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (jj < (int)last[k]) {
+              const SplatEval e = eval_splat(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
+              if (e.ok) {
+                contrib = true;
+                const float inv = 1.f / (1.f - e.alpha);
+                const float Ti = T[k] * inv;
+                const float w = e.alpha * Ti;
+                const float F = gC0[k] * ap.x + gC1[k] * ap.y + gC2[k] * ap.z + gD[k] * e.z + gN0[k] * ap.w +
+                                gN1[k] * an.x + gN2[k] * an.y;
+                const float galpha = Ti * F - (S[k] - gAT[k]) * inv;
+                S[k] += w * F;
+                T[k] = Ti;
+                gr[kGr] += gC0[k] * w;
+                gr[kGg] += gC1[k] * w;
+                gr[kGb] += gC2[k] * w;
+                gr[kGnx] += gN0[k] * w;
+                gr[kGny] += gN1[k] * w;
+                gr[kGnz] += gN2[k] * w;
+                const float gz = gD[k] * w;
+                const bool unclamped = e.oG < kAlphaMax;
+                const float grho = unclamped ? -0.5f * galpha * e.alpha : 0.f;
+                if (unclamped) gr[kGo] += galpha * e.G;
+                float gdx, gdy;
+                if (e.surf) {
+                  const float r2 = e.r * e.r;
+                  const float gun = grho * 2.f * e.un * r2;
+                  const float gvn = grho * 2.f * e.vn * r2;
+                  const float gden = -grho * 2.f * e.rho3 * e.r - gz * e.z * e.r;
+                  gr[kGzD] += gz * e.r;
+                  gdx = gun * g1.x + gvn * g1.z + gden * g2.y;
+                  gdy = gun * g1.y + gvn * g1.w + gden * g2.z;
+                  gr[kGA00] += gun * e.dx;
+                  gr[kGA01] += gun * e.dy;
+                  gr[kGA10] += gvn * e.dx;
+                  gr[kGA11] += gvn * e.dy;
+                  gr[kGe0] += gden;
+                  gr[kGe1] += gden * e.dx;
+                  gr[kGe2] += gden * e.dy;
+                } else {
+                  gdx = grho * 4.f * e.dx;
+                  gdy = grho * 4.f * e.dy;
+                  gr[kGzc] += gz;
+                }
+                gr[kGcx] -= gdx;
+                gr[kGcy] -= gdy;
+              }
             }
-            gr[kGcx] = -gdx;
-            gr[kGcy] = -gdy;
           }
         }
         if (__any_sync(kFull, contrib)) {
+#ifdef OCGS_COUNT
+          if (lane == 0) OCGS_DIAG(3, 1);
+          OCGS_DIAG(4, contrib ? 1 : 0);
+#endif
+          const int slot = warp_reduce18(gr, lane);
+          if (slot >= 0 && gr[0] != 0.f) atomicAdd(&s_grad[j * kGradStride + slot], gr[0]);
+        }
+      }
+      // flush the batch: one vector atomic per 4 slots and entry for the whole tile
+      __syncthreads();
+      if (bstart + tid < bend) {
+        float4* row = reinterpret_cast<float4*>(&s_grad[tid * kGradStride]);
+        float4* dst = reinterpret_cast<float4*>(a.grad_rec + (size_t)s_idx[tid] * kGradStride);
 #pragma unroll
-          for (int q = 0; q < NG; ++q) gr[q] = warp_sum(gr[q]);
-          if (lane == 0) {
-            float* dst = a.grad_rec + (size_t)s_idx[j] * kGradStride;
-#pragma unroll
-            for (int q = 0; q < NG; ++q)
-              if (gr[q] != 0.f) atomicAdd(dst + q, gr[q]);
+        for (int q = 0; q < kGradStride / 4; ++q) {
+          const float4 g4 = row[q];
+          if (g4.x != 0.f || g4.y != 0.f || g4.z != 0.f || g4.w != 0.f) {
+            atomicAdd(dst + q, g4);
+            row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
           }
         }
       }
@@ -255,23 +415,24 @@ __global__ void __launch_bounds__(TW * TH) raster_bwd_kernel(const RasterBwdArgs
   }
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
   const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
   if (grid == 0) return cudaSuccess;
+  constexpr int NT = TW * TH / PPT;
   const bool score = a.score != nullptr;
-  if (img && score) raster_fwd_kernel<TW, TH, true, true><<<grid, TW * TH, 0, s>>>(a);
-  else if (img) raster_fwd_kernel<TW, TH, true, false><<<grid, TW * TH, 0, s>>>(a);
-  else if (score) raster_fwd_kernel<TW, TH, false, true><<<grid, TW * TH, 0, s>>>(a);
+  if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true><<<grid, NT, 0, s>>>(a);
+  else if (img) raster_fwd_kernel<TW, TH, PPT, true, false><<<grid, NT, 0, s>>>(a);
+  else if (score) raster_fwd_kernel<TW, TH, PPT, false, true><<<grid, NT, 0, s>>>(a);
   else return cudaSuccess;
   return launched();
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int PPT>
 cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
   const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
   if (grid == 0) return cudaSuccess;
-  raster_bwd_kernel<TW, TH><<<grid, TW * TH, 0, s>>>(a);
+  raster_bwd_kernel<TW, TH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
   return launched();
 }
 
@@ -286,6 +447,17 @@ __global__ void sum_u32_kernel(const uint32_t* __restrict__ v, int64_t n, unsign
 
 }  // namespace
 
+#ifdef OCGS_COUNT
+extern "C" int ocgs_diag_read(unsigned long long* out, int reset) {
+  cudaMemcpyFromSymbol(out, g_diag, sizeof(g_diag));
+  if (reset) {
+    unsigned long long z[8] = {0};
+    cudaMemcpyToSymbol(g_diag, z, sizeof(z));
+  }
+  return 0;
+}
+#endif
+
 cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), s);
   if (e != cudaSuccess || n == 0) return e;
@@ -293,20 +465,26 @@ cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out
   return launched();
 }
 
-cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, bool write_image,
+cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, int ppt, bool write_image,
                                   cudaStream_t s) {
-  if (tile_w == 16 && tile_h == 16) return fwd_dispatch<16, 16>(a, write_image, s);
-  if (tile_w == 16 && tile_h == 8) return fwd_dispatch<16, 8>(a, write_image, s);
-  if (tile_w == 8 && tile_h == 8) return fwd_dispatch<8, 8>(a, write_image, s);
-  if (tile_w == 32 && tile_h == 8) return fwd_dispatch<32, 8>(a, write_image, s);
+#define OCGS_FWD(W, H, K) \
+  if (tile_w == W && tile_h == H && ppt == K) return fwd_dispatch<W, H, K>(a, write_image, s);
+  OCGS_FWD(16, 16, 1) OCGS_FWD(16, 16, 2) OCGS_FWD(16, 16, 4)
+  OCGS_FWD(16, 8, 1) OCGS_FWD(16, 8, 2)
+  OCGS_FWD(8, 8, 1) OCGS_FWD(8, 8, 2)
+  OCGS_FWD(32, 8, 1) OCGS_FWD(32, 8, 2)
+#undef OCGS_FWD
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, cudaStream_t s) {
-  if (tile_w == 16 && tile_h == 16) return bwd_dispatch<16, 16>(a, s);
-  if (tile_w == 16 && tile_h == 8) return bwd_dispatch<16, 8>(a, s);
-  if (tile_w == 8 && tile_h == 8) return bwd_dispatch<8, 8>(a, s);
-  if (tile_w == 32 && tile_h == 8) return bwd_dispatch<32, 8>(a, s);
+cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, cudaStream_t s) {
+#define OCGS_BWD(W, H, K) \
+  if (tile_w == W && tile_h == H && ppt == K) return bwd_dispatch<W, H, K>(a, s);
+  OCGS_BWD(16, 16, 1) OCGS_BWD(16, 16, 2) OCGS_BWD(16, 16, 4)
+  OCGS_BWD(16, 8, 1) OCGS_BWD(16, 8, 2)
+  OCGS_BWD(8, 8, 1) OCGS_BWD(8, 8, 2)
+  OCGS_BWD(32, 8, 1) OCGS_BWD(32, 8, 2)
+#undef OCGS_BWD
   return cudaErrorInvalidValue;
 }
 

@@ -125,9 +125,10 @@ def test_tile_shapes_and_persistent_queue_give_identical_results(dev):
     g = to_device(sc["gaussians"], dev)
     cams = sc["cameras"]
     base = None
-    for tile in ((16, 16), (16, 8), (8, 8), (32, 8)):
+    combos = [(t, k) for t in ((16, 16), (16, 8), (8, 8), (32, 8)) for k in (1, 2)] + [((16, 16), 4)]
+    for tile, ppt in combos:
         for persistent in (False, True):
-            r = Rasterizer(dev, tile=tile, persistent=persistent)
+            r = Rasterizer(dev, tile=tile, persistent=persistent, pixels_per_thread=ppt)
             score = torch.zeros(len(sc["gaussians"]["opacity"]), device=dev)
             out, _ = r.render(g, cams, score=score, keep_state=False)
             torch.cuda.synchronize()
@@ -137,7 +138,7 @@ def test_tile_shapes_and_persistent_queue_give_identical_results(dev):
                 base = cur
             else:
                 for k in base:
-                    assert torch.equal(base[k], cur[k]), (tile, persistent, k)
+                    assert torch.equal(base[k], cur[k]), (tile, ppt, persistent, k)
             r.close()
 
 
