@@ -291,8 +291,6 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   uint32_t *dkey, *order, *dkey_alt, *order_alt;
   uint64_t* counts;
   CK(tmp.alloc(&rect, VN));
-  uint32_t* tmask;
-  CK(tmp.alloc(&tmask, VN));
   uint64_t* roff;
   CK(tmp.alloc(&roff, VN));
   CK(tmp.alloc(&dkey, VN));
@@ -313,7 +311,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   }
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_tile_count(st->rec, rect, st->d_cams, N, VN, tw, th, st->ntiles, tmask, dkey, s));
+    CK(launch_tile_count(st->rec, rect, st->d_cams, N, VN, tw, th, st->ntiles, dkey, s));
   }
   bool alt = false;
   {
@@ -346,8 +344,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_duplicate(sorted, counts, roff, VN, st->ntiles, rect, tmask, st->rec, st->d_cams, N, tw, th, K, pkey,
-                        pval, s));
+    CK(launch_duplicate(sorted, counts, roff, VN, st->ntiles, rect, st->rec, st->d_cams, N, tw, th, K, pkey, pval,
+                        s));
   }
   const int tbits = bits_for((uint64_t)pl.tiles);
   bool palt = false;

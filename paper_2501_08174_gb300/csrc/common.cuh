@@ -161,25 +161,18 @@ __device__ __forceinline__ float support_rho(float o) {
   return fminf(kRhoCut, __fadd_rn(__fmul_rn(2.0f, __logf(__fmul_rn(255.0f, o))), 1e-3f));
 }
 
-// min over t in [t0, t1] of a t^2 + b t + c  (any sign of a)
-__device__ __forceinline__ float quad_min(float a, float b, float c, float t0, float t1) {
-  const float f0 = __fmaf_rn(__fmaf_rn(a, t0, b), t0, c);
-  const float f1 = __fmaf_rn(__fmaf_rn(a, t1, b), t1, c);
-  float m = fminf(f0, f1);
-  if (a > 0.f) {
-    const float ts = __fdividef(-b, __fmul_rn(2.f, a));
-    if (ts > t0 && ts < t1) m = fminf(m, __fmaf_rn(__fmaf_rn(a, ts, b), ts, c));
-  }
-  return m;
-}
-
-// Support conic of a record grown by the test margin:
-// f(dx, dy) = a dx^2 + 2 b dx dy + c dy^2 + 2 d dx + 2 e dy + f0 <= 0 where
-// (A00 dx + A01 dy)^2 + (A10 dx + A11 dy)^2 <= rt (e0 + e1 dx + e2 dy)^2.
+// Screen support of a record, {rho <= rb} grown by 0.1 % (+1e-3) in rho:
+//  * the filter disc |x - c|^2 <= r2f, and
+//  * the projected surfel disc, the ellipse
+//      (A00 dx + A01 dy)^2 + (A10 dx + A11 dy)^2 <= rt (e0 + e1 dx + e2 dy)^2
+//    in (dx, dy) = x - c, written a dx^2 + 2 b dx dy + c dy^2 + 2 d dx + 2 e dy + f <= 0
+//    and, about its centre m, a u^2 + 2 b u v + c v^2 <= kappa.
 struct SupportConic {
-  float cx, cy, r2f;             // filter disc: |x - c|^2 <= r2f
-  float a, b, c, d, e, f0;
-  bool finite;
+  float cx, cy, r2f;
+  float a, b, c;
+  float mx, my, kappa, det;
+  float umax, vmax, vstar;  // x half-extent, y half-extent, v of the rightmost point
+  bool ellipse;             // a > 0, det > 0, kappa > 0 and finite
 };
 
 __device__ __forceinline__ SupportConic support_conic(const float4 g0, const float4 g1, const float4 g2, float rb) {
@@ -191,50 +184,106 @@ __device__ __forceinline__ SupportConic support_conic(const float4 g0, const flo
   k.a = __fsub_rn(__fmaf_rn(g1.x, g1.x, __fmul_rn(g1.z, g1.z)), __fmul_rn(rt, __fmul_rn(g2.y, g2.y)));
   k.b = __fsub_rn(__fmaf_rn(g1.x, g1.y, __fmul_rn(g1.z, g1.w)), __fmul_rn(rt, __fmul_rn(g2.y, g2.z)));
   k.c = __fsub_rn(__fmaf_rn(g1.y, g1.y, __fmul_rn(g1.w, g1.w)), __fmul_rn(rt, __fmul_rn(g2.z, g2.z)));
-  k.d = -__fmul_rn(rt, __fmul_rn(g2.x, g2.y));
-  k.e = -__fmul_rn(rt, __fmul_rn(g2.x, g2.z));
-  k.f0 = -__fmul_rn(rt, __fmul_rn(g2.x, g2.x));
-  k.finite = isfinite(k.a) && isfinite(k.b) && isfinite(k.c) && isfinite(k.d) && isfinite(k.e) && isfinite(k.f0);
+  const float d = -__fmul_rn(rt, __fmul_rn(g2.x, g2.y));
+  const float e = -__fmul_rn(rt, __fmul_rn(g2.x, g2.z));
+  const float f = -__fmul_rn(rt, __fmul_rn(g2.x, g2.x));
+  k.det = __fsub_rn(__fmul_rn(k.a, k.c), __fmul_rn(k.b, k.b));
+  k.mx = __fdiv_rn(__fsub_rn(__fmul_rn(k.b, e), __fmul_rn(k.c, d)), k.det);
+  k.my = __fdiv_rn(__fsub_rn(__fmul_rn(k.b, d), __fmul_rn(k.a, e)), k.det);
+  k.kappa = -__fmaf_rn(e, k.my, __fmaf_rn(d, k.mx, f));
+  k.ellipse = k.a > 0.f && k.det > 0.f && k.kappa > 0.f && isfinite(k.mx) && isfinite(k.my) &&
+              isfinite(k.kappa) && isfinite(k.det);
+  k.umax = k.vmax = k.vstar = 0.f;
+  if (k.ellipse) {
+    k.umax = __fsqrt_rn(__fdiv_rn(__fmul_rn(k.kappa, k.c), k.det));
+    k.vmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(k.kappa, k.a), k.det));
+    k.vstar = __fdiv_rn(-__fmul_rn(k.b, k.umax), k.c);
+  }
   return k;
 }
 
-__device__ __forceinline__ float conic_at(const SupportConic& k, float x, float y) {
-  return __fmaf_rn(__fmaf_rn(k.c, y, __fmul_rn(2.f, __fmaf_rn(k.b, x, k.e))), y,
-                   __fmaf_rn(__fmaf_rn(k.a, x, __fmul_rn(2.f, k.d)), x, k.f0));
+// The x extent (absolute pixel coordinates) of the support within the band
+// y in [y0, y1]: up to two intervals [lo0, hi0] (ellipse) and [lo1, hi1]
+// (filter disc); an empty interval has lo > hi.  Each end carries a margin of
+// 0.02 px plus 2e-6 of its magnitude for the FP32 roots.
+struct RowSpan {
+  float lo0, hi0, lo1, hi1;
+};
+
+__device__ __forceinline__ float ellipse_u(const SupportConic& k, float v, float sgn) {
+  const float disc = fmaxf(0.f, __fsub_rn(__fmul_rn(k.a, k.kappa), __fmul_rn(k.det, __fmul_rn(v, v))));
+  return __fdiv_rn(__fmaf_rn(sgn, __fsqrt_rn(disc), -__fmul_rn(k.b, v)), k.a);
 }
 
-// Does the support {rho <= rb} of a record reach a pixel centre inside the
-// rectangle [x0, x1] x [y0, y1] (pixel coordinates)?  Conservative: the
-// rectangle is grown by 0.02 px and rb by 0.1 % (+1e-3).  The support is the
-// union of the screen filter disc |x - c|^2 <= rb/2 and the projected surfel
-// disc (the conic above), whose minimum over the rectangle lies at a corner,
-// at its stationary point or on an edge.  The same explicitly rounded
-// arithmetic gives the same answer in every kernel that asks.
-__device__ __forceinline__ bool conic_touches(const SupportConic& k, float x0, float x1, float y0, float y1) {
-  const float X0 = __fsub_rn(x0 - 0.02f, k.cx), X1 = __fsub_rn(x1 + 0.02f, k.cx);
-  const float Y0 = __fsub_rn(y0 - 0.02f, k.cy), Y1 = __fsub_rn(y1 + 0.02f, k.cy);
-  const float qx = fminf(fmaxf(0.f, X0), X1), qy = fminf(fmaxf(0.f, Y0), Y1);
-  if (__fmaf_rn(qx, qx, __fmul_rn(qy, qy)) <= k.r2f) return true;
-  if (!k.finite) return true;
-  if (conic_at(k, X0, Y0) <= 0.f || conic_at(k, X1, Y0) <= 0.f || conic_at(k, X0, Y1) <= 0.f ||
-      conic_at(k, X1, Y1) <= 0.f)
-    return true;
-  const float det = __fsub_rn(__fmul_rn(k.a, k.c), __fmul_rn(k.b, k.b));
-  if (k.a > 0.f && det > 0.f) {
-    const float sx = __fdividef(__fsub_rn(__fmul_rn(k.b, k.e), __fmul_rn(k.c, k.d)), det);
-    const float sy = __fdividef(__fsub_rn(__fmul_rn(k.b, k.d), __fmul_rn(k.a, k.e)), det);
-    if (sx >= X0 && sx <= X1 && sy >= Y0 && sy <= Y1 && conic_at(k, sx, sy) <= 0.f) return true;
+__device__ __forceinline__ RowSpan support_row_span(const SupportConic& k, float y0, float y1, float full_lo,
+                                                    float full_hi) {
+  RowSpan s;
+  s.lo0 = 1.f; s.hi0 = 0.f; s.lo1 = 1.f; s.hi1 = 0.f;
+  const float Y0 = __fsub_rn(y0, k.cy) - 0.02f, Y1 = __fsub_rn(y1, k.cy) + 0.02f;
+  if (k.ellipse) {
+    const float vlo = fmaxf(__fsub_rn(Y0, k.my), -k.vmax), vhi = fminf(__fsub_rn(Y1, k.my), k.vmax);
+    if (vlo <= vhi) {
+      const float hi = (k.vstar >= vlo && k.vstar <= vhi) ? k.umax
+                                                          : fmaxf(ellipse_u(k, vlo, 1.f), ellipse_u(k, vhi, 1.f));
+      const float lo = (-k.vstar >= vlo && -k.vstar <= vhi) ? -k.umax
+                                                            : fminf(ellipse_u(k, vlo, -1.f), ellipse_u(k, vhi, -1.f));
+      const float xl = __fadd_rn(__fadd_rn(k.cx, k.mx), lo), xh = __fadd_rn(__fadd_rn(k.cx, k.mx), hi);
+      s.lo0 = xl - (0.02f + 2e-6f * fabsf(xl));
+      s.hi0 = xh + (0.02f + 2e-6f * fabsf(xh));
+    }
+  } else {
+    s.lo0 = full_lo;  // not a proper ellipse in FP32: keep the whole candidate row
+    s.hi0 = full_hi;
   }
-  // edges: dy = Y fixed -> a dx^2 + 2 (b Y + d) dx + (c Y^2 + 2 e Y + f0), and likewise in dy
-  const float cy0 = __fmaf_rn(__fmaf_rn(k.c, Y0, __fmul_rn(2.f, k.e)), Y0, k.f0);
-  const float cy1 = __fmaf_rn(__fmaf_rn(k.c, Y1, __fmul_rn(2.f, k.e)), Y1, k.f0);
-  if (quad_min(k.a, __fmul_rn(2.f, __fmaf_rn(k.b, Y0, k.d)), cy0, X0, X1) <= 0.f) return true;
-  if (quad_min(k.a, __fmul_rn(2.f, __fmaf_rn(k.b, Y1, k.d)), cy1, X0, X1) <= 0.f) return true;
-  const float cx0 = __fmaf_rn(__fmaf_rn(k.a, X0, __fmul_rn(2.f, k.d)), X0, k.f0);
-  const float cx1 = __fmaf_rn(__fmaf_rn(k.a, X1, __fmul_rn(2.f, k.d)), X1, k.f0);
-  if (quad_min(k.c, __fmul_rn(2.f, __fmaf_rn(k.b, X0, k.e)), cx0, Y0, Y1) <= 0.f) return true;
-  if (quad_min(k.c, __fmul_rn(2.f, __fmaf_rn(k.b, X1, k.e)), cx1, Y0, Y1) <= 0.f) return true;
-  return false;
+  const float yc = fminf(fmaxf(0.f, Y0), Y1);
+  const float rem = __fsub_rn(k.r2f, __fmul_rn(yc, yc));
+  if (rem >= 0.f) {
+    const float hw = __fsqrt_rn(rem);
+    const float xl = __fsub_rn(k.cx, hw), xh = __fadd_rn(k.cx, hw);
+    s.lo1 = xl - (0.02f + 2e-6f * fabsf(xl));
+    s.hi1 = xh + (0.02f + 2e-6f * fabsf(xh));
+  }
+  return s;
+}
+
+// Tiles [t0, t1] of a row whose pixel-centre columns i (centre i + 0.5) meet
+// [lo, hi], clipped to the candidate tiles [c0, c1]; t0 > t1 if none.
+__device__ __forceinline__ void span_tiles(float lo, float hi, int tw, int W, int c0, int c1, int* t0, int* t1) {
+  *t0 = 1;
+  *t1 = 0;
+  if (!(lo <= hi)) return;
+  const float ilo = fmaxf(ceilf(lo - 0.5f), 0.f), ihi = fminf(floorf(hi - 0.5f), (float)(W - 1));
+  if (ilo > ihi) return;
+  *t0 = max((int)ilo / tw, c0);
+  *t1 = min((int)ihi / tw, c1);
+}
+
+// Tile runs of one row of a record's candidate rectangle: the union of the
+// runs of the two intervals, as at most two disjoint runs in increasing order.
+struct RowRuns {
+  int a0, a1, b0, b1;  // run a = [a0, a1], run b = [b0, b1] (empty if start > end)
+};
+
+__device__ __forceinline__ RowRuns row_runs(const SupportConic& k, int ty, int tw, int th, int W, int H,
+                                            const int4 rc) {
+  const float y0 = (float)(ty * th) + 0.5f;
+  const float y1 = (float)(min((ty + 1) * th, H) - 1) + 0.5f;
+  const float full_lo = (float)(rc.x * tw) + 0.5f, full_hi = (float)(min((rc.z + 1) * tw, W) - 1) + 0.5f;
+  const RowSpan sp = support_row_span(k, y0, y1, full_lo, full_hi);
+  int p0, p1, q0, q1;
+  span_tiles(sp.lo0, sp.hi0, tw, W, rc.x, rc.z, &p0, &p1);
+  span_tiles(sp.lo1, sp.hi1, tw, W, rc.x, rc.z, &q0, &q1);
+  RowRuns r;
+  if (p0 > p1) { p0 = q0; p1 = q1; q0 = 1; q1 = 0; }
+  if (q0 > q1) {
+    r.a0 = p0; r.a1 = p1; r.b0 = 1; r.b1 = 0;
+  } else if (q0 > p1 + 1 || p0 > q1 + 1) {  // disjoint: order them
+    if (p0 < q0) { r.a0 = p0; r.a1 = p1; r.b0 = q0; r.b1 = q1; }
+    else { r.a0 = q0; r.a1 = q1; r.b0 = p0; r.b1 = p1; }
+  } else {  // overlapping or adjacent: merge
+    r.a0 = min(p0, q0); r.a1 = max(p1, q1); r.b0 = 1; r.b1 = 0;
+  }
+  return r;
 }
 
 // first global tile id -> view, by binary search over V+1 prefix offsets
@@ -285,18 +334,18 @@ cudaError_t scan_exclusive_u32(const uint32_t* in, uint32_t* out, uint32_t n, ui
 cudaError_t launch_gather_counts(const uint32_t* order, const int32_t* ntiles, uint64_t* counts,
                                  uint32_t n, cudaStream_t s);
 cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s);
-// exact tile counts: ntiles[r] = tiles of rect[r] that conic_touches; a record
-// with none gets depth key 0xffffffff so that it sorts to the tail.  For a
-// record with at most 32 candidate tiles, tmask[r] keeps which ones.
+// exact tile counts: ntiles[r] = tiles of rect[r] the record's support reaches
+// (row_runs); a record with none gets depth key 0xffffffff so that it sorts to
+// the tail
 cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
-                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* tmask,
-                              uint32_t* depth_key, cudaStream_t s);
+                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* depth_key,
+                              cudaStream_t s);
 // write the (tile, record) pairs: offsets are the scanned counts in depth order
 // (order), scattered to record order in roff [n_rec] first
 cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint64_t* roff, uint32_t n_rec,
-                             const int32_t* ntiles, const int4* rect, const uint32_t* tmask, const RecPtrs rec,
-                             const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs,
-                             uint32_t* keys, uint32_t* vals, cudaStream_t s);
+                             const int32_t* ntiles, const int4* rect, const RecPtrs rec, const DevCam* cams,
+                             int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs, uint32_t* keys,
+                             uint32_t* vals, cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s);
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
                               uint32_t* tile_ids, cudaStream_t s);

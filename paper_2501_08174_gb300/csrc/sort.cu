@@ -276,106 +276,33 @@ __global__ void iota_kernel(uint32_t* v, uint32_t n) {
   if (i < n) v[i] = i;
 }
 
-// Pixel-centre rectangle of tile (tx, ty) of a view, clipped to the image.
-__device__ __forceinline__ void tile_rect(const DevCam& cam, int tw, int th, int tx, int ty, float* x0, float* x1,
-                                          float* y0, float* y1) {
-  *x0 = (float)(tx * tw) + 0.5f;
-  *x1 = (float)(min((tx + 1) * tw, cam.W) - 1) + 0.5f;
-  *y0 = (float)(ty * th) + 0.5f;
-  *y1 = (float)(min((ty + 1) * th, cam.H) - 1) + 0.5f;
+constexpr int kThreads = 256;
+constexpr int kSmallRows = 4;   // a lane handles a record with at most this many candidate rows alone
+constexpr int kSmallTiles = 64; // ... and at most this many tiles to write
+
+__device__ __forceinline__ int row_count(const RowRuns& rr) {
+  return max(0, rr.a1 - rr.a0 + 1) + max(0, rr.b1 - rr.b0 + 1);
 }
 
-constexpr int kWarpsPerBlock = 8;
-constexpr int kSmallRect = 32;  // records with at most this many candidate tiles keep a bit mask
-
-// The (record, candidate tile) items of the 32 records of a warp are walked as
-// one flat list, 32 items per step, so that a record with many candidate
-// tiles does not leave the other lanes idle.  Items of one record occupy
-// consecutive lanes of a step (a "segment"); the first lane of each segment
-// accounts for the whole segment, so no two lanes update the same record.
-struct WarpItems {
-  int incl[32];  // inclusive prefix of the candidate counts
-  int4 rc[32];
-  int view[32];
-};
-
-__device__ __forceinline__ int item_record(const int* incl, int q) {
-  int lo = 0, hi = 31;
-  while (lo < hi) {
-    const int mid = (lo + hi) >> 1;
-    if (incl[mid] > q) hi = mid; else lo = mid + 1;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ unsigned lanes_le(int lane) { return lane == 31 ? kFull : ((2u << lane) - 1u); }
-
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) tile_count_kernel(
-    const RecPtrs rec, const int4* __restrict__ rect, const DevCam* __restrict__ cams, int64_t n_gauss,
-    uint32_t n_rec, int tw, int th, int32_t* __restrict__ ntiles, uint32_t* __restrict__ tmask,
-    uint32_t* __restrict__ depth_key) {
-  __shared__ WarpItems s_it[kWarpsPerBlock];
-  __shared__ SupportConic s_k[kWarpsPerBlock][32];
-  __shared__ int s_cnt[kWarpsPerBlock][32];
-  __shared__ uint32_t s_bits[kWarpsPerBlock][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t r = (blockIdx.x * kWarpsPerBlock + warp) * 32u + lane;
-  int4 rc = make_int4(0, 0, -1, -1);
-  if (r < n_rec) rc = rect[r];
-  const int n = (rc.z < rc.x) ? 0 : (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-  if (n > 0) {
+// Exact tile count of each record: one thread per record, one closed-form
+// coverage computation per candidate tile row.
+__global__ void __launch_bounds__(kThreads) tile_count_kernel(const RecPtrs rec, const int4* __restrict__ rect,
+                                                              const DevCam* __restrict__ cams, int64_t n_gauss,
+                                                              uint32_t n_rec, int tw, int th,
+                                                              int32_t* __restrict__ ntiles,
+                                                              uint32_t* __restrict__ depth_key) {
+  const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
+  if (r >= n_rec) return;
+  const int4 rc = rect[r];
+  int cnt = 0;
+  if (rc.z >= rc.x) {
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
     const float4 g0 = rec.g0[r];
-    s_k[warp][lane] = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
+    const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
+    for (int ty = rc.y; ty <= rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, rc));
   }
-  WarpItems& it = s_it[warp];
-  it.rc[lane] = rc;
-  it.view[lane] = (int)(r / (uint64_t)n_gauss);
-  s_cnt[warp][lane] = 0;
-  s_bits[warp][lane] = 0u;
-  int incl = n;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += t;
-  }
-  it.incl[lane] = incl;
-  const int total = __shfl_sync(kFull, incl, 31);
-  __syncwarp();
-  for (int q0 = 0; q0 < total; q0 += 32) {
-    const int q = q0 + lane;
-    const bool valid = q < total;
-    int ri = 0, t = 0;
-    bool hit = false;
-    if (valid) {
-      ri = item_record(it.incl, q);
-      const int4 c = it.rc[ri];
-      const int w = c.z - c.x + 1;
-      t = q - (it.incl[ri] - w * (c.w - c.y + 1));
-      const DevCam& cam = cams[it.view[ri]];
-      float x0, x1, y0, y1;
-      tile_rect(cam, tw, th, c.x + t % w, c.y + t / w, &x0, &x1, &y0, &y1);
-      hit = conic_touches(s_k[warp][ri], x0, x1, y0, y1);
-    }
-    const bool head = valid && (t == 0 || lane == 0);
-    const unsigned heads = __ballot_sync(kFull, head);
-    const unsigned hitm = __ballot_sync(kFull, hit);
-    if (head) {
-      const unsigned later = heads & ~lanes_le(lane);
-      const int end = later ? __ffs(later) - 1 : 32;
-      const unsigned seg = (end == 32 ? kFull : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
-      const unsigned sh = hitm & seg;
-      s_cnt[warp][ri] += __popc(sh);
-      const int4 c = it.rc[ri];
-      if ((c.z - c.x + 1) * (c.w - c.y + 1) <= kSmallRect) s_bits[warp][ri] |= (sh >> lane) << t;
-    }
-    __syncwarp();
-  }
-  if (r < n_rec) {
-    const int cnt = s_cnt[warp][lane];
-    ntiles[r] = cnt;
-    tmask[r] = s_bits[warp][lane];
-    if (cnt == 0) depth_key[r] = 0xffffffffu;
-  }
+  ntiles[r] = cnt;
+  if (cnt == 0) depth_key[r] = 0xffffffffu;
 }
 
 // roff[order[i]] = offsets[i]: each record's first pair slot, in record order.
@@ -385,91 +312,80 @@ __global__ void scatter_offsets_kernel(const uint32_t* __restrict__ order, const
   if (i < n) roff[order[i]] = offsets[i];
 }
 
-// Same flat walk as the count, in record order: a small record takes its hits
-// from the count-pass mask, a large one repeats the test.  The k-th kept tile
-// of a record goes to roff[record] + k (kept tiles in rectangle order).
-__global__ void __launch_bounds__(32 * kWarpsPerBlock) duplicate_kernel(
+__device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
+                                               uint64_t stop, uint32_t* __restrict__ keys,
+                                               uint32_t* __restrict__ vals) {
+  for (int tx = rr.a0; tx <= rr.a1; ++tx, ++pos)
+    if (pos < stop) { keys[pos] = rowbase + tx; vals[pos] = r; }
+  for (int tx = rr.b0; tx <= rr.b1; ++tx, ++pos)
+    if (pos < stop) { keys[pos] = rowbase + tx; vals[pos] = r; }
+  return pos;
+}
+
+// The same rows again, in record order, writing each record's tiles from its
+// first pair slot (rows in order, tiles left to right).  Small records are
+// written by their lane; the rows of large ones are shared out over the warp,
+// with a warp scan of the row counts for the positions.
+__global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const uint64_t* __restrict__ roff, const int32_t* __restrict__ ntiles, uint32_t n_rec,
-    const int4* __restrict__ rect, const uint32_t* __restrict__ tmask, const RecPtrs rec,
-    const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th, uint32_t n_pairs, uint32_t* __restrict__ keys,
-    uint32_t* __restrict__ vals) {
-  __shared__ WarpItems s_it[kWarpsPerBlock];
-  __shared__ SupportConic s_k[kWarpsPerBlock][32];
-  __shared__ uint64_t s_o[kWarpsPerBlock][32];
-  __shared__ uint32_t s_bits[kWarpsPerBlock][32];
-  __shared__ uint32_t s_run[kWarpsPerBlock][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const unsigned lt = (1u << lane) - 1u;
-  const uint32_t r = (blockIdx.x * kWarpsPerBlock + warp) * 32u + lane;
+    const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams, int64_t n_gauss, int tw,
+    int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
+  int cnt = 0;
   int4 rc = make_int4(0, 0, -1, -1);
-  int n = 0;
-  if (r < n_rec && ntiles[r] > 0) {
-    rc = rect[r];
-    n = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-    s_o[warp][lane] = roff[r];
-    if (n <= kSmallRect) {
-      s_bits[warp][lane] = tmask[r];
-    } else {
-      const float4 g0 = rec.g0[r];
-      s_k[warp][lane] = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
+  uint64_t o = 0;
+  if (r < n_rec) {
+    cnt = ntiles[r];
+    if (cnt > 0) {
+      rc = rect[r];
+      o = roff[r];
     }
   }
-  WarpItems& it = s_it[warp];
-  it.rc[lane] = rc;
-  it.view[lane] = (int)(r / (uint64_t)n_gauss);
-  s_run[warp][lane] = 0u;
-  int incl = n;
+  const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows && cnt <= kSmallTiles;
+  if (small) {
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const float4 g0 = rec.g0[r];
+    const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
+    const uint64_t stop = min(o + (uint64_t)cnt, (uint64_t)n_pairs);
+    uint64_t pos = o;
+    for (int ty = rc.y; ty <= rc.w; ++ty) {
+      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
+      pos = write_runs(rr, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), r, pos, stop, keys, vals);
+    }
+  }
+  unsigned big = __ballot_sync(kFull, cnt > 0 && !small);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1u;
+    const uint32_t rr = __shfl_sync(kFull, r, src);
+    const uint64_t oo = __shfl_sync(kFull, o, src);
+    const int bcnt = __shfl_sync(kFull, cnt, src);
+    const int4 bc = rect[rr];
+    const DevCam& cam = cams[rr / (uint64_t)n_gauss];
+    const float4 g0 = rec.g0[rr];
+    const SupportConic k = support_conic(g0, rec.g1[rr], rec.g2[rr], support_rho(g0.z));
+    const uint64_t stop = min(oo + (uint64_t)bcnt, (uint64_t)n_pairs);
+    uint64_t base = oo;
+    for (int row0 = bc.y; row0 <= bc.w; row0 += 32) {
+      const int ty = row0 + lane;
+      RowRuns runs{1, 0, 1, 0};
+      int c = 0;
+      if (ty <= bc.w) {
+        runs = row_runs(k, ty, tw, th, cam.W, cam.H, bc);
+        c = row_count(runs);
+      }
+      int incl = c;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += t;
-  }
-  it.incl[lane] = incl;
-  const int total = __shfl_sync(kFull, incl, 31);
-  const uint32_t rbase = r - lane;
-  __syncwarp();
-  for (int q0 = 0; q0 < total; q0 += 32) {
-    const int q = q0 + lane;
-    const bool valid = q < total;
-    int ri = 0, t = 0, tx = 0, ty = 0;
-    bool hit = false;
-    const DevCam* cam = cams;
-    if (valid) {
-      ri = item_record(it.incl, q);
-      const int4 c = it.rc[ri];
-      const int w = c.z - c.x + 1;
-      const int nr = w * (c.w - c.y + 1);
-      t = q - (it.incl[ri] - nr);
-      tx = c.x + t % w;
-      ty = c.y + t / w;
-      cam = &cams[it.view[ri]];
-      if (nr <= kSmallRect) {
-        hit = (s_bits[warp][ri] >> t) & 1u;
-      } else {
-        float x0, x1, y0, y1;
-        tile_rect(*cam, tw, th, tx, ty, &x0, &x1, &y0, &y1);
-        hit = conic_touches(s_k[warp][ri], x0, x1, y0, y1);
+      for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        const int t = __shfl_up_sync(kFull, incl, s2);
+        if (lane >= s2) incl += t;
       }
+      if (c > 0)
+        write_runs(runs, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), rr, base + (uint64_t)(incl - c), stop,
+                   keys, vals);
+      base += (uint64_t)__shfl_sync(kFull, incl, 31);
     }
-    const bool head = valid && (t == 0 || lane == 0);
-    const unsigned heads = __ballot_sync(kFull, head);
-    const unsigned hitm = __ballot_sync(kFull, hit);
-    const int h = 31 - __clz(heads & lanes_le(lane));  // first lane of this lane's segment
-    if (hit) {
-      const uint64_t pos = s_o[warp][ri] + s_run[warp][ri] + __popc(hitm & lt & ~((1u << h) - 1u));
-      if (pos < n_pairs) {
-        keys[pos] = (uint32_t)(cam->tile_offset + ty * cam->tiles_x + tx);
-        vals[pos] = rbase + (uint32_t)ri;
-      }
-    }
-    __syncwarp();
-    if (head) {
-      const unsigned later = heads & ~lanes_le(lane);
-      const int end = later ? __ffs(later) - 1 : 32;
-      const unsigned seg = (end == 32 ? kFull : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
-      s_run[warp][ri] += __popc(hitm & seg);
-    }
-    __syncwarp();
   }
 }
 
@@ -556,26 +472,25 @@ cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s) {
 }
 
 cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
-                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* tmask,
-                              uint32_t* depth_key, cudaStream_t s) {
+                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* depth_key,
+                              cudaStream_t s) {
   if (n_rec == 0) return cudaSuccess;
-  const uint32_t per_block = 32u * kWarpsPerBlock;
-  tile_count_kernel<<<(n_rec + per_block - 1) / per_block, 32 * kWarpsPerBlock, 0, s>>>(
-      rec, rect, cams, n_gauss, n_rec, tile_w, tile_h, ntiles, tmask, depth_key);
+  tile_count_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(rec, rect, cams, n_gauss, n_rec, tile_w,
+                                                                           tile_h, ntiles, depth_key);
   return launched();
 }
 
 cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint64_t* roff, uint32_t n_rec,
-                             const int32_t* ntiles, const int4* rect, const uint32_t* tmask, const RecPtrs rec,
-                             const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs,
-                             uint32_t* keys, uint32_t* vals, cudaStream_t s) {
+                             const int32_t* ntiles, const int4* rect, const RecPtrs rec, const DevCam* cams,
+                             int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs, uint32_t* keys,
+                             uint32_t* vals, cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
   scatter_offsets_kernel<<<(n_rec + 255) / 256, 256, 0, s>>>(order, offsets, n_rec, roff);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
-  const uint32_t per_block = 32u * kWarpsPerBlock;
-  duplicate_kernel<<<(n_rec + per_block - 1) / per_block, 32 * kWarpsPerBlock, 0, s>>>(
-      roff, ntiles, n_rec, rect, tmask, rec, cams, n_gauss, tile_w, tile_h, n_pairs, keys, vals);
+  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(roff, ntiles, n_rec, rect, rec, cams,
+                                                                          n_gauss, tile_w, tile_h, n_pairs, keys,
+                                                                          vals);
   return launched();
 }
 
