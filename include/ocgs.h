@@ -200,6 +200,34 @@ ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_
                                  double* loss, float* d_alpha);
 
 /*
+ * ocgs_background_loss_noalloc — the same background loss and adjoint as
+ * ocgs_background_loss, for callers that must not allocate device memory:
+ * code whose device memory is all held by another allocator (a framework's
+ * caching pool that reserves the GPU up front), or a loop with a latency
+ * budget that cannot afford cudaMalloc/cudaFree, which may synchronise the
+ * device and take unbounded time.  The paper has no counterpart; it is an
+ * interface convenience of this library.
+ *   alpha, mask, cams, n_views, gamma, loss, d_alpha  as in ocgs_background_loss
+ *   stream   the cudaStream_t to run on (NULL = legacy default stream); the
+ *            current device is used
+ * It needs no context and allocates nothing: its scratch (per-block partial
+ * sums, view table, block prefix) is one fixed static device array of
+ * 643,076 bytes that every GPU loading this library holds until the process exits.
+ * Limits: at most 1024 views and 65536 blocks of 4096 pixels
+ * (268,435,456 pixels) per call; larger requests return OCGS_ERR_CAPACITY,
+ * other bad arguments OCGS_ERR_ARG, before any device work.  The first call
+ * on a device looks up the array's device address (cudaGetSymbolAddress),
+ * so make that first call before any stream capture.  Every call shares the
+ * one array and leaves its contents behind; each call overwrites all it
+ * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
+ * (different streams) race on it.  Errors are returned only (there is no
+ * context for ocgs_last_error).
+ */
+ocgs_status ocgs_background_loss_noalloc(const float* alpha, const uint8_t* mask, const ocgs_camera* cams,
+                                         int32_t n_views, float gamma, double* loss, float* d_alpha,
+                                         void* stream);
+
+/*
  * ocgs_accumulate_contribution — the occlusion-aware pruning sweep (Sec. 4.3,
  * Sec. 5.1): a forward pass over n_views views that only records, for every
  * Gaussian, score[i] = max(score[i], max blending weight over all pixels).

@@ -81,6 +81,8 @@ SIGNATURES = {
     "ocgs_state_release": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ocgs_background_loss": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
                                        C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
+    "ocgs_background_loss_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Camera), C.c_int32, C.c_float,
+                                               C.c_void_p, C.c_void_p, C.c_void_p]),
     "ocgs_accumulate_contribution": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera),
                                                C.c_int32, C.c_void_p]),
     "ocgs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(Gaussians),

@@ -1,6 +1,11 @@
 // Background loss (Eq. 1) with its fused adjoint, and the pruning keep-set
 // compaction (Sec. 4.3).
 #include "common.cuh"
+#include "ocgs.h"
+
+#include <cmath>
+#include <cstring>
+#include <mutex>
 
 namespace ocgs {
 namespace {
@@ -172,3 +177,90 @@ cudaError_t launch_prune_compact(const GaussPtrs& in, uint32_t n, int sh_degree,
 }
 
 }  // namespace ocgs
+
+// ----------------------------------------------------------------------------- allocation-free background loss
+//
+// ocgs_background_loss_noalloc computes exactly what ocgs_background_loss
+// computes, with the same kernels, but needs no context and allocates no
+// device memory: its scratch (the per-block FP64 partial sums, the view table
+// and the block prefix) lives in one file-scope device array of fixed size,
+// which every GPU that loads this library holds until the process exits.
+// Host code cannot hand that array to a kernel by name (in host code the name
+// is only a stand-in), so the first call on each device, with that device
+// current, looks its device address up with cudaGetSymbolAddress and keeps it.
+namespace {
+
+constexpr int kNoAllocMaxViews = 1024;
+constexpr int kNoAllocMaxBlocks = 65536;  // 65536 blocks x 4096 pixels = 268,435,456 pixels per call
+constexpr size_t kNoAllocPartialBytes = sizeof(double) * kNoAllocMaxBlocks;
+constexpr size_t kNoAllocCamOffset = kNoAllocPartialBytes;
+constexpr size_t kNoAllocCamBytes = ((sizeof(ocgs::DevCam) * kNoAllocMaxViews) + 255) & ~(size_t)255;
+constexpr size_t kNoAllocPrefixOffset = kNoAllocCamOffset + kNoAllocCamBytes;
+constexpr size_t kNoAllocBytes = kNoAllocPrefixOffset + sizeof(int) * (kNoAllocMaxViews + 1);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
+// host staging of the view table and prefix (reused under the mutex)
+ocgs::DevCam g_noalloc_cams[kNoAllocMaxViews];
+int g_noalloc_prefix[kNoAllocMaxViews + 1];
+
+}  // namespace
+
+extern "C" ocgs_status ocgs_background_loss_noalloc(const float* alpha, const uint8_t* mask,
+                                                    const ocgs_camera* cams, int32_t n_views, float gamma,
+                                                    double* loss, float* d_alpha, void* stream) {
+  if (!alpha || !mask || !loss || !cams) return OCGS_ERR_ARG;
+  if (n_views < 1 || n_views > kNoAllocMaxViews) return OCGS_ERR_ARG;
+  if (!std::isfinite(gamma)) return OCGS_ERR_ARG;
+  int64_t blocks = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (cams[v].width < 1 || cams[v].height < 1 || cams[v].width > 16384 || cams[v].height > 16384)
+      return OCGS_ERR_ARG;
+    const int64_t np = (int64_t)cams[v].width * cams[v].height;
+    blocks += (np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels;
+  }
+  if (blocks > kNoAllocMaxBlocks) return OCGS_ERR_CAPACITY;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return OCGS_ERR_CUDA;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return OCGS_ERR_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OCGS_ERR_CUDA;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  }
+  unsigned char* base = g_noalloc_addr[dev];
+  int64_t pix = 0;
+  int acc = 0;
+  for (int v = 0; v < n_views; ++v) {
+    ocgs::DevCam& d = g_noalloc_cams[v];
+    std::memset(&d, 0, sizeof(d));
+    d.W = cams[v].width;
+    d.H = cams[v].height;
+    d.pix_offset = pix;
+    g_noalloc_prefix[v] = acc;
+    const int64_t np = (int64_t)d.W * d.H;
+    acc += (int)((np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels);
+    pix += np;
+  }
+  g_noalloc_prefix[n_views] = acc;
+  ocgs::DevCam* d_cams = reinterpret_cast<ocgs::DevCam*>(base + kNoAllocCamOffset);
+  int* d_prefix = reinterpret_cast<int*>(base + kNoAllocPrefixOffset);
+  double* d_partial = reinterpret_cast<double*>(base);
+  // copies from pageable host memory return once the data is staged, so the
+  // host tables may be refilled by the next call
+  if (cudaMemcpyAsync(d_cams, g_noalloc_cams, sizeof(ocgs::DevCam) * n_views, cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return OCGS_ERR_CUDA;
+  if (cudaMemcpyAsync(d_prefix, g_noalloc_prefix, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s) !=
+      cudaSuccess)
+    return OCGS_ERR_CUDA;
+  if (ocgs::launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, acc, gamma, d_partial, loss, d_alpha,
+                                   s) != cudaSuccess)
+    return OCGS_ERR_CUDA;
+  return OCGS_OK;
+}
