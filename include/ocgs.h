@@ -101,7 +101,7 @@ typedef struct {
   int32_t tile_w;             /* 8, 16 or 32 */
   int32_t tile_h;             /* 8 or 16: 16x16, 16x8, 8x8 or 32x8 */
   int32_t persistent;         /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
-  int32_t pixels_per_thread;  /* vertically adjacent pixels per thread: 1, 2 (0 = 2), or 4 for 16x16 */
+  int32_t pixels_per_thread;  /* vertically adjacent pixels per thread: 1, 2 (0 = 2), or 4 for 16x16 and 16x8 */
 } ocgs_options;
 
 /* Counters of the last ocgs_render / ocgs_accumulate_contribution. */
@@ -239,6 +239,28 @@ ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* ga
                                          const ocgs_camera* cams, int32_t n_views, float* score);
 
 /*
+ * ocgs_contribution_graph_create — the pruning sweep of
+ * ocgs_accumulate_contribution (score zeroed, then max-accumulated over all
+ * n_views views, 16 views per chunk) captured once as one CUDA graph, so
+ * that a periodic sweep (every 100 or 600 iterations in Sec. 5.1) costs one
+ * graph launch and no host synchronisation.  The graph reads the parameter
+ * arrays and writes score through the pointers given here: keep them alive
+ * and in place; their contents may change between launches.  Creation runs
+ * the sweep once to measure the largest chunk's (tile, Gaussian) pair count
+ * and sizes the pair buffers to headroom (>= 1) times it.  A launch whose
+ * pairs exceed that capacity leaves score incomplete and makes the next
+ * ocgs_sync return OCGS_ERR_CAPACITY: re-create the graph then.  The graph
+ * uses the context's options at creation.  Synchronises.
+ */
+typedef struct ocgs_graph ocgs_graph;
+ocgs_status ocgs_contribution_graph_create(ocgs_ctx* ctx, const ocgs_gaussians* gaussians,
+                                           const ocgs_camera* cams, int32_t n_views, float* score,
+                                           float headroom, ocgs_graph** graph);
+/* Launch the captured sweep on the context stream (asynchronous). */
+ocgs_status ocgs_graph_launch(ocgs_ctx* ctx, ocgs_graph* graph);
+ocgs_status ocgs_graph_destroy(ocgs_ctx* ctx, ocgs_graph* graph);
+
+/*
  * ocgs_prune — keep-set {i : score[i] > threshold} (threshold 0 reproduces
  * the rule of Sec. 4.3: drop what no pixel ever blended) and stream
  * compaction of the parameters in their original order.
@@ -284,6 +306,29 @@ ocgs_status ocgs_state_query(ocgs_ctx* ctx, const ocgs_fwd_state* state, ocgs_st
 
 /* Number of CUDA kernels this library has launched in this process. */
 int64_t ocgs_kernel_launches(void);
+
+/* Result of ocgs_autotune. */
+typedef struct {
+  ocgs_options best;     /* chosen options (also set on the context) */
+  double best_ms;        /* forward + backward time of the chosen options, ms */
+  int32_t n_tried;       /* candidates timed (0 when taken from the cache) */
+  int32_t from_cache;    /* 1: read from the cache file */
+} ocgs_tune_result;
+
+/*
+ * ocgs_autotune — pick the launch options (tile shape, pixels per thread,
+ * persistent queue) that make one forward + backward of this workload
+ * fastest on this GPU, and set them on the context.  Options never change a
+ * result (see ocgs_options), only the time.  Each candidate runs once
+ * untimed and twice timed (CUDA events on the context stream); the
+ * cotangent is dL/dA = 1.  cache_path (host string or NULL) names a text
+ * file of earlier choices keyed by GPU, SM count, SH degree, views and
+ * power-of-two buckets of Gaussians and pixels; a hit skips the timing, a
+ * miss appends a line.  Synchronises; allocates its buffers from the context
+ * pool for the duration of the call.
+ */
+ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* gaussians, const ocgs_camera* cams,
+                          int32_t n_views, const char* cache_path, ocgs_tune_result* result);
 
 /* Built-in stage profiler: enable (1) resets the accumulators and starts
  * recording; read synchronises the stream and returns the sums so far. */

@@ -56,6 +56,10 @@ STAGES = ["preprocess", "depth_sort", "binning", "tile_sort", "raster_fwd", "los
           "preprocess_bwd", "prune"]
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("best", Options), ("best_ms", C.c_double), ("n_tried", C.c_int32), ("from_cache", C.c_int32)]
+
+
 class Stats(C.Structure):
     _fields_ = [("n_gaussians", C.c_int64), ("n_views", C.c_int64), ("n_pixels", C.c_int64),
                 ("n_visible", C.c_int64), ("n_pairs", C.c_int64), ("n_tiles", C.c_int64),
@@ -90,6 +94,12 @@ SIGNATURES = {
                              C.POINTER(C.c_int64)]),
     "ocgs_masked_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
                                  C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
+    "ocgs_autotune": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32, C.c_char_p,
+                                C.POINTER(TuneResult)]),
+    "ocgs_contribution_graph_create": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32,
+                                                 C.c_void_p, C.c_float, C.POINTER(C.c_void_p)]),
+    "ocgs_graph_launch": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "ocgs_graph_destroy": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ocgs_state_query": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(StateInfo)]),
     "ocgs_kernel_launches": (C.c_int64, []),
     "ocgs_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),

@@ -111,6 +111,32 @@ class ForwardState:
             pass
 
 
+class ContributionGraph:
+    """The pruning sweep captured as one CUDA graph (see ocgs_contribution_graph_create)."""
+
+    def __init__(self, rast: "Rasterizer", handle: C.c_void_p, score: torch.Tensor, keep_alive):
+        self._rast = rast
+        self.handle = handle
+        self.score = score
+        self._keep = keep_alive  # parameter tensors the graph reads
+
+    def launch(self) -> torch.Tensor:
+        self._rast._bind_stream()
+        self._rast._call("ocgs_graph_launch", self._rast._ctx, self.handle)
+        return self.score
+
+    def close(self) -> None:
+        if self.handle:
+            self._rast._call("ocgs_graph_destroy", self._rast._ctx, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Rasterizer:
     """One libocgs context on one CUDA device."""
 
@@ -153,6 +179,20 @@ class Rasterizer:
         self.tile = (int(tile[0]), int(tile[1]))
         self.persistent = bool(persistent)
         self.pixels_per_thread = int(pixels_per_thread)
+
+    def autotune(self, gaussians: dict, cameras: Sequence[dict], cache_path: Optional[str] = None) -> dict:
+        """Time the launch-option candidates on this workload and keep the fastest (see ocgs_autotune)."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        res = _lib.TuneResult()
+        self._call("ocgs_autotune", self._ctx, C.byref(gs), camera_array(cameras), len(cameras),
+                   None if cache_path is None else str(cache_path).encode(), C.byref(res))
+        b = res.best
+        self.tile = (b.tile_w, b.tile_h)
+        self.persistent = bool(b.persistent)
+        self.pixels_per_thread = b.pixels_per_thread
+        return {"tile": self.tile, "pixels_per_thread": b.pixels_per_thread, "persistent": bool(b.persistent),
+                "ms": res.best_ms, "n_tried": res.n_tried, "from_cache": bool(res.from_cache)}
 
     def stats(self) -> dict:
         s = _lib.Stats()
@@ -264,6 +304,19 @@ class Rasterizer:
         self._call("ocgs_accumulate_contribution", self._ctx, C.byref(gs), camera_array(cameras),
                    len(cameras), _ptr(score))
         return score
+
+    def contribution_graph(self, gaussians: dict, cameras: Sequence[dict], score: Optional[torch.Tensor] = None,
+                           headroom: float = 1.25) -> ContributionGraph:
+        """Capture the pruning sweep over ``cameras`` once; ``.launch()`` replays it."""
+        self._bind_stream()
+        gs = gaussians_struct(gaussians, self.device)
+        if score is None:
+            score = torch.zeros(gs.n, dtype=torch.float32, device=self.device)
+        _check_param("score", score, (), self.device)
+        handle = C.c_void_p()
+        self._call("ocgs_contribution_graph_create", self._ctx, C.byref(gs), camera_array(cameras), len(cameras),
+                   _ptr(score), float(headroom), C.byref(handle))
+        return ContributionGraph(self, handle, score, [gaussians[k] for k in PARAM_KEYS])
 
     def prune(self, gaussians: dict, score: torch.Tensor, threshold: float, borderline_cap: int = 4096):
         """Keep {score > threshold}; returns (kept parameters, borderline indices)."""

@@ -12,6 +12,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -247,7 +249,7 @@ ocgs_status read_status(ocgs_ctx* ctx, int* status) {
 
 bool valid_tile(int tw, int th, int ppt) {
   const bool shape = (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
-  return shape && (ppt == 1 || ppt == 2 || (ppt == 4 && tw == 16 && th == 16));
+  return shape && (ppt == 1 || ppt == 2 || (ppt == 4 && tw == 16 && (th == 16 || th == 8)));
 }
 
 GaussPtrs gptrs(const ocgs_gaussians* g) { return GaussPtrs{g->xyz, g->quat, g->scale, g->opacity, g->sh}; }
@@ -413,6 +415,99 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   return OCGS_OK;
 }
 
+// Buffers of one pruning-sweep chunk with a fixed pair capacity: everything a
+// forward pass needs, allocated once, so that the pass can be enqueued without
+// allocation, host copy or host synchronisation (and hence captured).
+struct SweepWs {
+  RecPtrs rec{};
+  int32_t* ntiles = nullptr;
+  uint2* ranges = nullptr;
+  int4* rect = nullptr;
+  uint32_t *dkey = nullptr, *order = nullptr, *dkey_alt = nullptr, *order_alt = nullptr;
+  uint64_t *counts = nullptr, *roff = nullptr, *total = nullptr;
+  uint32_t* n32 = nullptr;
+  char *scratch = nullptr, *pscratch = nullptr, *tscratch = nullptr;
+  uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
+  uint32_t *queue = nullptr, *wk = nullptr, *ids = nullptr, *wk_alt = nullptr, *ids_alt = nullptr;
+  float* t_final = nullptr;
+  uint32_t* last = nullptr;
+  uint32_t vn_max = 0, cap = 0;
+  int64_t tiles_max = 0;
+};
+
+cudaError_t alloc_sweep_ws(Arena& a, SweepWs& w, uint32_t vn_max, int64_t tiles_max, uint32_t cap) {
+  w.vn_max = vn_max;
+  w.tiles_max = tiles_max;
+  w.cap = cap;
+  cudaError_t e = cudaSuccess;
+#define OCGS_A(ptr, n) if (e == cudaSuccess) e = a.alloc(&(ptr), (size_t)(n))
+  OCGS_A(w.rec.g0, vn_max); OCGS_A(w.rec.g1, vn_max); OCGS_A(w.rec.g2, vn_max);
+  OCGS_A(w.rec.a0, vn_max); OCGS_A(w.rec.a1, vn_max);
+  OCGS_A(w.ntiles, vn_max); OCGS_A(w.ranges, tiles_max); OCGS_A(w.rect, vn_max);
+  OCGS_A(w.dkey, vn_max); OCGS_A(w.order, vn_max); OCGS_A(w.dkey_alt, vn_max); OCGS_A(w.order_alt, vn_max);
+  OCGS_A(w.counts, vn_max); OCGS_A(w.roff, vn_max); OCGS_A(w.total, 1); OCGS_A(w.n32, 1);
+  OCGS_A(w.scratch, std::max(radix_scratch_bytes(vn_max), scan_scratch_bytes(vn_max)));
+  OCGS_A(w.pkey, cap); OCGS_A(w.pval, cap); OCGS_A(w.pkey_alt, cap); OCGS_A(w.pval_alt, cap);
+  OCGS_A(w.pscratch, radix_scratch_bytes(cap));
+  OCGS_A(w.queue, 1); OCGS_A(w.wk, tiles_max); OCGS_A(w.ids, tiles_max); OCGS_A(w.wk_alt, tiles_max);
+  OCGS_A(w.ids_alt, tiles_max); OCGS_A(w.tscratch, radix_scratch_bytes((uint32_t)tiles_max));
+  OCGS_A(w.t_final, 1); OCGS_A(w.last, 1);
+#undef OCGS_A
+  return e;
+}
+
+// One chunk of the pruning sweep (V <= 16 views) in capacity mode: the pair
+// count stays on the device (clamped to w.cap; an overflow raises the status
+// word's capacity bit and the result must then be discarded).
+ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, const DevCam* d_cams,
+                                const int* d_prefix, int64_t n_tiles, SweepWs& w, float* score, cudaStream_t s) {
+  const int tw = ctx->opts.tile_w, th = ctx->opts.tile_h, ppt = ctx->opts.pixels_per_thread;
+  const int64_t N = g->n;
+  const uint32_t VN = (uint32_t)(N * V);
+  CK(cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * n_tiles, s));
+  CK(launch_preprocess(gptrs(g), N, g->sh_degree, d_cams, V, tw, th, w.rec, w.ntiles, w.rect, w.dkey, ctx->d_status,
+                       s));
+  CK(launch_tile_count(w.rec, w.rect, d_cams, N, VN, tw, th, w.ntiles, w.dkey, s));
+  CK(launch_iota(w.order, VN, s));
+  bool alt = false;
+  CK(radix_sort_pairs(w.dkey, w.order, w.dkey_alt, w.order_alt, VN, 32, w.scratch, &alt, s));
+  uint32_t* sorted = alt ? w.order_alt : w.order;
+  CK(launch_gather_counts(sorted, w.ntiles, w.counts, VN, s));
+  CK(scan_exclusive_u64(w.counts, w.counts, VN, w.total, w.scratch, s));
+  CK(launch_clamp_count(w.total, w.cap, w.n32, ctx->d_status, s));
+  CK(launch_duplicate(sorted, w.counts, w.roff, VN, w.ntiles, w.rect, w.rec, d_cams, N, tw, th, w.cap, w.pkey,
+                      w.pval, s));
+  bool palt = false;
+  CK(radix_sort_pairs(w.pkey, w.pval, w.pkey_alt, w.pval_alt, w.cap, bits_for((uint64_t)n_tiles), w.pscratch, &palt,
+                      s, w.n32));
+  uint32_t* skey = palt ? w.pkey_alt : w.pkey;
+  uint32_t* svals = palt ? w.pval_alt : w.pval;
+  CK(launch_tile_ranges(skey, w.cap, w.ranges, s, w.n32));
+  RasterArgs ra{};
+  ra.cams = d_cams;
+  ra.tile_prefix = d_prefix;
+  ra.n_views = V;
+  ra.n_gauss = N;
+  ra.n_tiles = (uint32_t)n_tiles;
+  ra.ranges = w.ranges;
+  ra.vals = svals;
+  ra.rec = w.rec;
+  ra.t_final = w.t_final;
+  ra.last = w.last;
+  ra.score = score;
+  if (ctx->opts.persistent) {
+    CK(cudaMemsetAsync(w.queue, 0, sizeof(uint32_t), s));
+    CK(launch_tile_order(w.ranges, (uint32_t)n_tiles, w.wk, w.ids, s));
+    bool talt = false;
+    CK(radix_sort_pairs(w.wk, w.ids, w.wk_alt, w.ids_alt, (uint32_t)n_tiles, 32, w.tscratch, &talt, s));
+    ra.tile_order = talt ? w.ids_alt : w.ids;
+    ra.queue = w.queue;
+    ra.persistent_ctas = ctx->sm_count * (2048 * ppt / (tw * th));
+  }
+  CK(launch_raster_forward(ra, tw, th, ppt, false, s));
+  return OCGS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -478,7 +573,7 @@ ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
   if (!ctx || !o) return OCGS_ERR_ARG;
   const int ppt = o->pixels_per_thread == 0 ? 2 : o->pixels_per_thread;
   if (!valid_tile(o->tile_w, o->tile_h, ppt))
-    return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8 with 1 or 2 pixels per thread (4 for 16x16)");
+    return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8 with 1 or 2 pixels per thread (4 for 16x16 and 16x8)");
   ctx->opts = *o;
   ctx->opts.pixels_per_thread = ppt;
   return OCGS_OK;
@@ -503,6 +598,8 @@ ocgs_status ocgs_sync(ocgs_ctx* ctx) {
   ocgs_status r = read_status(ctx, &status);
   if (r != OCGS_OK) return r;
   CK(cudaGetLastError());
+  if (status & kStatusCapacity)
+    return set_err(ctx, OCGS_ERR_CAPACITY, "more (tile, Gaussian) pairs than a captured graph's capacity; re-create it");
   if (status & kStatusNonFinite) return set_err(ctx, OCGS_ERR_NONFINITE, "non-finite Gaussian parameters");
   if (status & kStatusTimeout) return set_err(ctx, OCGS_ERR_TIMEOUT, "a bounded device wait gave up");
   return OCGS_OK;
@@ -758,3 +855,239 @@ ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold, const
 }
 
 }  // extern "C"
+
+// ----------------------------------------------------------------------------- autotuner
+namespace {
+
+int log2_bucket(int64_t x) {
+  int b = 0;
+  while (x > 1) { x >>= 1; ++b; }
+  return b;
+}
+
+std::string tune_key(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams, int V) {
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, ctx->device);
+  int64_t pix = 0;
+  for (int v = 0; v < V; ++v) pix += (int64_t)cams[v].width * cams[v].height;
+  std::ostringstream os;
+  std::string name(prop.name);
+  for (char& c : name) if (c == ' ') c = '_';
+  os << name << "/sm" << prop.multiProcessorCount << "/deg" << g->sh_degree << "/v" << V << "/n2^"
+     << log2_bucket(g->n) << "/p2^" << log2_bucket(pix);
+  return os.str();
+}
+
+}  // namespace
+
+extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams,
+                                     int32_t n_views, const char* cache_path, ocgs_tune_result* result) {
+  if (!ctx || !result) return OCGS_ERR_ARG;
+  ocgs_status r = check_gaussians(ctx, g);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  CK(cudaSetDevice(ctx->device));
+  std::memset(result, 0, sizeof(*result));
+  const std::string key = tune_key(ctx, g, cams, n_views);
+  if (cache_path) {
+    std::ifstream in(cache_path);
+    std::string line;
+    while (std::getline(in, line)) {
+      std::istringstream ls(line);
+      std::string k;
+      ocgs_options o{};
+      double ms = 0.0;
+      if ((ls >> k >> o.tile_w >> o.tile_h >> o.pixels_per_thread >> o.persistent >> ms) && k == key &&
+          ocgs_set_options(ctx, &o) == OCGS_OK) {
+        result->best = ctx->opts;
+        result->best_ms = ms;
+        result->from_cache = 1;
+      }
+    }
+    if (result->from_cache) return OCGS_OK;
+  }
+  // buffers for the timed passes
+  int64_t P = 0;
+  for (int v = 0; v < n_views; ++v) P += (int64_t)cams[v].width * cams[v].height;
+  const int64_t N = g->n;
+  const int64_t K3 = 3 * (int64_t)(g->sh_degree + 1) * (g->sh_degree + 1);
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  float *img, *ones, *grad;
+  CK(tmp.alloc(&img, (size_t)P * 8));
+  CK(tmp.alloc(&ones, (size_t)P));
+  CK(tmp.alloc(&grad, (size_t)N * (10 + K3)));
+  std::vector<float> h_ones(1 << 16, 1.0f);
+  for (int64_t off = 0; off < P; off += (int64_t)h_ones.size()) {
+    const int64_t n = std::min<int64_t>((int64_t)h_ones.size(), P - off);
+    CK(cudaMemcpyAsync(ones + off, h_ones.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  }
+  const ocgs_image out{img, img + 3 * P, img + 4 * P, img + 5 * P};
+  const ocgs_image d_out{nullptr, ones, nullptr, nullptr};
+  const ocgs_gaussians_out dp{grad, grad + 3 * N, grad + 7 * N, grad + 9 * N, grad + 10 * N};
+  const int shapes[][3] = {{16, 16, 4}, {16, 16, 2}, {16, 8, 4}, {16, 8, 2}, {8, 8, 2}, {32, 8, 2}, {16, 16, 1}};
+  const ocgs_options saved = ctx->opts;
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  double best = 1e30;
+  ocgs_options best_opts = saved;
+  ocgs_status status = OCGS_OK;
+  for (const auto& sh : shapes) {
+    for (int pers = 0; pers <= 1; ++pers) {
+      ocgs_options o{sh[0], sh[1], pers, sh[2]};
+      if (ocgs_set_options(ctx, &o) != OCGS_OK) continue;
+      double ms_sum = 0.0;
+      for (int rep = 0; rep < 3 && status == OCGS_OK; ++rep) {
+        if (rep == 1) cudaEventRecord(e0, s);
+        ocgs_fwd_state* st = nullptr;
+        status = ocgs_render(ctx, g, cams, n_views, &out, nullptr, &st);
+        if (status == OCGS_ERR_NONFINITE) status = OCGS_OK;
+        if (status == OCGS_OK) status = ocgs_render_backward(ctx, st, g, &d_out, &dp);
+        if (st) ocgs_state_release(ctx, st);
+      }
+      if (status != OCGS_OK) break;
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms_sum = ms / 2.0;
+      result->n_tried++;
+      if (ms_sum < best) {
+        best = ms_sum;
+        best_opts = ctx->opts;
+      }
+    }
+    if (status != OCGS_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->prof = prof;
+  if (status != OCGS_OK) {
+    ctx->opts = saved;
+    return status;
+  }
+  ctx->opts = best_opts;
+  result->best = best_opts;
+  result->best_ms = best;
+  if (cache_path) {
+    std::ofstream outf(cache_path, std::ios::app);
+    outf << key << " " << best_opts.tile_w << " " << best_opts.tile_h << " " << best_opts.pixels_per_thread << " "
+         << best_opts.persistent << " " << best << "\n";
+  }
+  return OCGS_OK;
+}
+
+// ----------------------------------------------------------------------------- captured pruning sweep
+struct ocgs_graph {
+  ocgs_ctx* ctx = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<void*> allocs;
+  int64_t n_kernels = 0;
+};
+
+extern "C" ocgs_status ocgs_contribution_graph_create(ocgs_ctx* ctx, const ocgs_gaussians* g,
+                                                      const ocgs_camera* cams, int32_t n_views, float* score,
+                                                      float headroom, ocgs_graph** out) {
+  if (!ctx || !out) return OCGS_ERR_ARG;
+  *out = nullptr;
+  ocgs_status r = check_gaussians(ctx, g);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  if (!score || g->n == 0) return set_err(ctx, OCGS_ERR_ARG, "score must be non-NULL and n > 0");
+  if (!(headroom >= 1.f) || !std::isfinite(headroom)) return set_err(ctx, OCGS_ERR_ARG, "headroom must be >= 1");
+  CK(cudaSetDevice(ctx->device));
+  const int chunk = 16;
+  const int tw = ctx->opts.tile_w, th = ctx->opts.tile_h;
+  // measure the pair count of every chunk with the eager path
+  uint64_t kmax = 0;
+  int64_t tiles_max = 0;
+  std::vector<CamPlan> plans;
+  for (int v0 = 0; v0 < n_views; v0 += chunk) {
+    const int nv = std::min(chunk, n_views - v0);
+    ocgs_fwd_state st;
+    r = forward_pass(ctx, g, cams + v0, nv, nullptr, nullptr, &st, false);
+    if (r != OCGS_OK && r != OCGS_ERR_NONFINITE) return r;
+    kmax = std::max<uint64_t>(kmax, (uint64_t)ctx->stats.n_pairs);
+    plans.push_back(plan_cameras(cams + v0, nv, tw, th));
+    tiles_max = std::max<int64_t>(tiles_max, plans.back().tiles);
+  }
+  const double capd = (double)kmax * (double)headroom + 4096.0;
+  if (capd > (double)INT32_MAX) return set_err(ctx, OCGS_ERR_CAPACITY, "pair capacity above 2^31-1");
+  const uint32_t cap = (uint32_t)capd;
+  ocgs_graph* gr = new ocgs_graph();
+  gr->ctx = ctx;
+  Arena a(ctx);
+  SweepWs w;
+  cudaError_t e = alloc_sweep_ws(a, w, (uint32_t)(g->n * std::min(chunk, n_views)), tiles_max, cap);
+  std::vector<DevCam*> dc(plans.size());
+  std::vector<int*> dp(plans.size());
+  for (size_t c = 0; c < plans.size() && e == cudaSuccess; ++c) {
+    const int nv = (int)plans[c].cams.size();
+    e = a.alloc(&dc[c], nv);
+    if (e == cudaSuccess) e = a.alloc(&dp[c], nv + 1);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dc[c], plans[c].cams.data(), sizeof(DevCam) * nv, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(dp[c], plans[c].tile_prefix.data(), sizeof(int) * (nv + 1), cudaMemcpyHostToDevice,
+                          ctx->stream);
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e != cudaSuccess) {
+    delete gr;
+    return cuda_err(ctx, e, "graph workspace");
+  }
+  // capture on a private stream (the context stream may be the legacy default stream)
+  cudaStream_t cs;
+  CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const bool prof = ctx->prof;
+  ctx->prof = false;
+  const long long launches0 = g_kernel_launches.load();
+  r = OCGS_OK;
+  e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    e = cudaMemsetAsync(ctx->d_status, 0, sizeof(int), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(score, 0, sizeof(float) * g->n, cs);
+    for (size_t c = 0; c < plans.size() && e == cudaSuccess && r == OCGS_OK; ++c)
+      r = enqueue_sweep_chunk(ctx, g, (int)plans[c].cams.size(), dc[c], dp[c], plans[c].tiles, w, score, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &gr->graph);
+    if (e == cudaSuccess) e = e2;
+  }
+  ctx->prof = prof;
+  gr->n_kernels = g_kernel_launches.load() - launches0;
+  g_kernel_launches -= gr->n_kernels;  // counted when launched, not when captured
+  cudaStreamDestroy(cs);
+  if (e == cudaSuccess && r == OCGS_OK) e = cudaGraphInstantiate(&gr->exec, gr->graph, 0);
+  if (e != cudaSuccess || r != OCGS_OK) {
+    if (gr->graph) cudaGraphDestroy(gr->graph);
+    delete gr;
+    return r != OCGS_OK ? r : cuda_err(ctx, e, "graph capture");
+  }
+  a.release_to(gr->allocs);
+  *out = gr;
+  return OCGS_OK;
+}
+
+extern "C" ocgs_status ocgs_graph_launch(ocgs_ctx* ctx, ocgs_graph* gr) {
+  if (!ctx || !gr || gr->ctx != ctx) return OCGS_ERR_ARG;
+  CK(cudaSetDevice(ctx->device));
+  CK(cudaGraphLaunch(gr->exec, ctx->stream));
+  g_kernel_launches += gr->n_kernels;
+  return OCGS_OK;
+}
+
+extern "C" ocgs_status ocgs_graph_destroy(ocgs_ctx* ctx, ocgs_graph* gr) {
+  if (!ctx || !gr || gr->ctx != ctx) return OCGS_ERR_ARG;
+  cudaSetDevice(ctx->device);
+  cudaStreamSynchronize(ctx->stream);
+  if (gr->exec) cudaGraphExecDestroy(gr->exec);
+  if (gr->graph) cudaGraphDestroy(gr->graph);
+  for (void* p : gr->allocs) cudaFreeAsync(p, ctx->stream);
+  delete gr;
+  return OCGS_OK;
+}

@@ -161,6 +161,10 @@ __device__ __forceinline__ float support_rho(float o) {
   return fminf(kRhoCut, __fadd_rn(__fmul_rn(2.0f, __logf(__fmul_rn(255.0f, o))), 1e-3f));
 }
 
+// sqrt from the approximate reciprocal square root (the coverage test below
+// carries margins far above its error; every caller uses the same function).
+__device__ __forceinline__ float fast_sqrt(float x) { return x > 0.f ? __fmul_rn(x, rsqrtf(x)) : 0.f; }
+
 // Screen support of a record, {rho <= rb} grown by 0.1 % (+1e-3) in rho:
 //  * the filter disc |x - c|^2 <= r2f, and
 //  * the projected surfel disc, the ellipse
@@ -188,16 +192,16 @@ __device__ __forceinline__ SupportConic support_conic(const float4 g0, const flo
   const float e = -__fmul_rn(rt, __fmul_rn(g2.x, g2.z));
   const float f = -__fmul_rn(rt, __fmul_rn(g2.x, g2.x));
   k.det = __fsub_rn(__fmul_rn(k.a, k.c), __fmul_rn(k.b, k.b));
-  k.mx = __fdiv_rn(__fsub_rn(__fmul_rn(k.b, e), __fmul_rn(k.c, d)), k.det);
-  k.my = __fdiv_rn(__fsub_rn(__fmul_rn(k.b, d), __fmul_rn(k.a, e)), k.det);
+  k.mx = __fdividef(__fsub_rn(__fmul_rn(k.b, e), __fmul_rn(k.c, d)), k.det);
+  k.my = __fdividef(__fsub_rn(__fmul_rn(k.b, d), __fmul_rn(k.a, e)), k.det);
   k.kappa = -__fmaf_rn(e, k.my, __fmaf_rn(d, k.mx, f));
   k.ellipse = k.a > 0.f && k.det > 0.f && k.kappa > 0.f && isfinite(k.mx) && isfinite(k.my) &&
               isfinite(k.kappa) && isfinite(k.det);
   k.umax = k.vmax = k.vstar = 0.f;
   if (k.ellipse) {
-    k.umax = __fsqrt_rn(__fdiv_rn(__fmul_rn(k.kappa, k.c), k.det));
-    k.vmax = __fsqrt_rn(__fdiv_rn(__fmul_rn(k.kappa, k.a), k.det));
-    k.vstar = __fdiv_rn(-__fmul_rn(k.b, k.umax), k.c);
+    k.umax = fast_sqrt(__fdividef(__fmul_rn(k.kappa, k.c), k.det));
+    k.vmax = fast_sqrt(__fdividef(__fmul_rn(k.kappa, k.a), k.det));
+    k.vstar = __fdividef(-__fmul_rn(k.b, k.umax), k.c);
   }
   return k;
 }
@@ -212,7 +216,7 @@ struct RowSpan {
 
 __device__ __forceinline__ float ellipse_u(const SupportConic& k, float v, float sgn) {
   const float disc = fmaxf(0.f, __fsub_rn(__fmul_rn(k.a, k.kappa), __fmul_rn(k.det, __fmul_rn(v, v))));
-  return __fdiv_rn(__fmaf_rn(sgn, __fsqrt_rn(disc), -__fmul_rn(k.b, v)), k.a);
+  return __fdividef(__fmaf_rn(sgn, fast_sqrt(disc), -__fmul_rn(k.b, v)), k.a);
 }
 
 __device__ __forceinline__ RowSpan support_row_span(const SupportConic& k, float y0, float y1, float full_lo,
@@ -238,7 +242,7 @@ __device__ __forceinline__ RowSpan support_row_span(const SupportConic& k, float
   const float yc = fminf(fmaxf(0.f, Y0), Y1);
   const float rem = __fsub_rn(k.r2f, __fmul_rn(yc, yc));
   if (rem >= 0.f) {
-    const float hw = __fsqrt_rn(rem);
+    const float hw = fast_sqrt(rem);
     const float xl = __fsub_rn(k.cx, hw), xh = __fadd_rn(k.cx, hw);
     s.lo1 = xl - (0.02f + 2e-6f * fabsf(xl));
     s.hi1 = xh + (0.02f + 2e-6f * fabsf(xh));
@@ -320,9 +324,11 @@ cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_deg
 // in ping-pong buffers; returns in *result_in_alt whether the sorted data ended
 // in the alternate buffers.  scratch must hold radix_scratch_bytes(n) bytes.
 size_t radix_scratch_bytes(uint32_t n);
+// d_n (optional): device-side item count, read by the kernels and clamped to n
+// (n sizes the launch: a capacity)
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              uint32_t n, int n_bits, void* scratch, bool* result_in_alt,
-                             cudaStream_t s);
+                             cudaStream_t s, const uint32_t* d_n = nullptr);
 
 // exclusive scan of n uint64 values (in may equal out); the total is written to *d_total.
 size_t scan_scratch_bytes(uint32_t n);
@@ -346,7 +352,10 @@ cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uin
                              const int32_t* ntiles, const int4* rect, const RecPtrs rec, const DevCam* cams,
                              int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs, uint32_t* keys,
                              uint32_t* vals, cudaStream_t s);
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s);
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s,
+                               const uint32_t* d_n = nullptr);
+// n32 = min(*total, cap); raises kStatusCapacity when *total > cap
+cudaError_t launch_clamp_count(const uint64_t* total, uint32_t cap, uint32_t* n32, int* status, cudaStream_t s);
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
                               uint32_t* tile_ids, cudaStream_t s);
 

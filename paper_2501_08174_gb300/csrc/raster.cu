@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               const SplatEval e = eval_splat(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
               if (e.ok) {
                 contrib = true;
-                const float inv = 1.f / (1.f - e.alpha);
+                const float inv = __fdividef(1.f, 1.f - e.alpha);
                 const float Ti = T[k] * inv;
                 const float w = e.alpha * Ti;
                 const float F = gC0[k] * ap.x + gC1[k] * ap.y + gC2[k] * ap.z + gD[k] * e.z + gN0[k] * ap.w +
@@ -470,7 +470,7 @@ cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, i
 #define OCGS_FWD(W, H, K) \
   if (tile_w == W && tile_h == H && ppt == K) return fwd_dispatch<W, H, K>(a, write_image, s);
   OCGS_FWD(16, 16, 1) OCGS_FWD(16, 16, 2) OCGS_FWD(16, 16, 4)
-  OCGS_FWD(16, 8, 1) OCGS_FWD(16, 8, 2)
+  OCGS_FWD(16, 8, 1) OCGS_FWD(16, 8, 2) OCGS_FWD(16, 8, 4)
   OCGS_FWD(8, 8, 1) OCGS_FWD(8, 8, 2)
   OCGS_FWD(32, 8, 1) OCGS_FWD(32, 8, 2)
 #undef OCGS_FWD
@@ -481,7 +481,7 @@ cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_
 #define OCGS_BWD(W, H, K) \
   if (tile_w == W && tile_h == H && ppt == K) return bwd_dispatch<W, H, K>(a, s);
   OCGS_BWD(16, 16, 1) OCGS_BWD(16, 16, 2) OCGS_BWD(16, 16, 4)
-  OCGS_BWD(16, 8, 1) OCGS_BWD(16, 8, 2)
+  OCGS_BWD(16, 8, 1) OCGS_BWD(16, 8, 2) OCGS_BWD(16, 8, 4)
   OCGS_BWD(8, 8, 1) OCGS_BWD(8, 8, 2)
   OCGS_BWD(32, 8, 1) OCGS_BWD(32, 8, 2)
 #undef OCGS_BWD

@@ -139,11 +139,11 @@ __device__ __forceinline__ unsigned digit_peers(uint32_t d, int bits) {
 __global__ void __launch_bounds__(kBlock) radix_upsweep_kernel(const uint32_t* __restrict__ keys,
                                                                uint32_t n, int shift, uint32_t mask,
                                                                uint32_t* __restrict__ counts,
-                                                               uint32_t n_blocks) {
+                                                               uint32_t n_blocks, const uint32_t* __restrict__ d_n) {
   constexpr int NW = kBlock / 32;
   __shared__ uint32_t whist[NW][kMaxRadix + 1];
+  if (d_n) n = min(n, *d_n);  // device-side count (capacity launches)
   const int R = (int)mask + 1;
-  const int bits = __popc(mask) + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int i = lane; i <= R; i += 32) whist[warp][i] = 0;
   __syncwarp();
@@ -157,10 +157,7 @@ __global__ void __launch_bounds__(kBlock) radix_upsweep_kernel(const uint32_t* _
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t k = wbase + j * 32 + lane;
-    const uint32_t d = k < n ? ((key[j] >> shift) & mask) : (uint32_t)R;
-    const unsigned peers = digit_peers(d, bits);
-    if (lane == __ffs(peers) - 1) whist[warp][d] += __popc(peers);
-    __syncwarp();
+    if (k < n) atomicAdd(&whist[warp][(key[j] >> shift) & mask], 1u);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < R; i += kBlock) {
@@ -183,8 +180,9 @@ __global__ void __launch_bounds__(kBlock) radix_scatter_kernel(const uint32_t* _
                                                                uint32_t* __restrict__ vals_out,
                                                                uint32_t n, int shift, uint32_t mask,
                                                                const uint32_t* __restrict__ offsets,
-                                                               uint32_t n_blocks) {
+                                                               uint32_t n_blocks, const uint32_t* __restrict__ d_n) {
   constexpr int NW = kBlock / 32;
+  if (d_n) n = min(n, *d_n);  // device-side count (capacity launches)
   __shared__ uint32_t whist[NW][kMaxRadix + 1];
   __shared__ uint32_t dstart[kMaxRadix];
   __shared__ uint32_t gbase[kMaxRadix];
@@ -243,7 +241,8 @@ __global__ void __launch_bounds__(kBlock) radix_scatter_kernel(const uint32_t* _
   for (int w = 0; w < warp; ++w) carry += wsum[w];
   if (threadIdx.x < R) dstart[threadIdx.x] = carry + inc - tot;
   __syncthreads();
-  const uint32_t n_here = (n - blockIdx.x * kChunk < (uint32_t)kChunk) ? n - blockIdx.x * kChunk : (uint32_t)kChunk;
+  const uint32_t n_here = (blockIdx.x * kChunk >= n) ? 0u
+                          : ((n - blockIdx.x * kChunk < (uint32_t)kChunk) ? n - blockIdx.x * kChunk : (uint32_t)kChunk);
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
     const uint32_t k = wbase + j * 32 + lane;
@@ -323,15 +322,23 @@ __device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowba
 }
 
 // The same rows again, in record order, writing each record's tiles from its
-// first pair slot (rows in order, tiles left to right).  Small records are
-// written by their lane; the rows of large ones are shared out over the warp,
-// with a warp scan of the row counts for the positions.
+// first pair slot (rows in order, tiles left to right).  Each lane computes
+// the row runs of its record when it is small; the warp then writes all the
+// small records' tiles as one flat list, 32 tiles per step, so the stores are
+// balanced over the lanes and contiguous within a record.  The rows of a
+// large record are shared out over the warp, with a warp scan of the row
+// counts for the positions.
+constexpr int kWarpsPerBlock = kThreads / 32;
+
 __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const uint64_t* __restrict__ roff, const int32_t* __restrict__ ntiles, uint32_t n_rec,
     const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams, int64_t n_gauss, int tw,
     int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
+  __shared__ int4 s_runs[kWarpsPerBlock][32][kSmallRows];
+  __shared__ int s_incl[kWarpsPerBlock][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
+  const uint32_t rbase = r - lane;
   int cnt = 0;
   int4 rc = make_int4(0, 0, -1, -1);
   uint64_t o = 0;
@@ -347,11 +354,50 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
     const float4 g0 = rec.g0[r];
     const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
-    const uint64_t stop = min(o + (uint64_t)cnt, (uint64_t)n_pairs);
-    uint64_t pos = o;
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      pos = write_runs(rr, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), r, pos, stop, keys, vals);
+      s_runs[warp][lane][ty - rc.y] = make_int4(rr.a0, rr.a1, rr.b0, rr.b1);
+    }
+  }
+  // flat walk over the small records' tiles
+  const int scnt = small ? cnt : 0;
+  int incl = scnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += t;
+  }
+  s_incl[warp][lane] = incl;
+  const int total = __shfl_sync(kFull, incl, 31);
+  __syncwarp();
+  for (int q0 = 0; q0 < total; q0 += 32) {
+    const int q = q0 + lane;
+    if (q < total) {
+      int lo = 0, hi = 31;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_incl[warp][mid] > q) hi = mid; else lo = mid + 1;
+      }
+      const int ri = lo;
+      const uint32_t rr = rbase + (uint32_t)ri;
+      const int excl = ri > 0 ? s_incl[warp][ri - 1] : 0;  // tiles of the warp's earlier small records
+      int kth = q - excl;
+      const int4 bc = rect[rr];
+      const DevCam& cam = cams[rr / (uint64_t)n_gauss];
+      int tx = -1, ty = bc.y;
+      for (int row = 0; row <= bc.w - bc.y; ++row) {
+        const int4 ru = s_runs[warp][ri][row];
+        const int la = max(0, ru.y - ru.x + 1), lb = max(0, ru.w - ru.z + 1);
+        if (kth < la) { tx = ru.x + kth; ty = bc.y + row; break; }
+        kth -= la;
+        if (kth < lb) { tx = ru.z + kth; ty = bc.y + row; break; }
+        kth -= lb;
+      }
+      const uint64_t pos = roff[rr] + (uint64_t)(q - excl);
+      if (tx >= 0 && pos < n_pairs) {
+        keys[pos] = (uint32_t)(cam.tile_offset + ty * cam.tiles_x + tx);
+        vals[pos] = rr;
+      }
     }
   }
   unsigned big = __ballot_sync(kFull, cnt > 0 && !small);
@@ -375,21 +421,23 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
         runs = row_runs(k, ty, tw, th, cam.W, cam.H, bc);
         c = row_count(runs);
       }
-      int incl = c;
+      int inc = c;
 #pragma unroll
       for (int s2 = 1; s2 < 32; s2 <<= 1) {
-        const int t = __shfl_up_sync(kFull, incl, s2);
-        if (lane >= s2) incl += t;
+        const int t = __shfl_up_sync(kFull, inc, s2);
+        if (lane >= s2) inc += t;
       }
       if (c > 0)
-        write_runs(runs, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), rr, base + (uint64_t)(incl - c), stop,
-                   keys, vals);
-      base += (uint64_t)__shfl_sync(kFull, incl, 31);
+        write_runs(runs, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), rr, base + (uint64_t)(inc - c), stop, keys,
+                   vals);
+      base += (uint64_t)__shfl_sync(kFull, inc, 31);
     }
   }
 }
 
-__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint2* __restrict__ ranges) {
+__global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint2* __restrict__ ranges,
+                                   const uint32_t* __restrict__ d_n) {
+  if (d_n) n = min(n, *d_n);
   const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   const uint32_t t = keys[k];
@@ -429,7 +477,8 @@ size_t radix_scratch_bytes(uint32_t n) {
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                             uint32_t n, int n_bits, void* scratch, bool* result_in_alt, cudaStream_t s) {
+                             uint32_t n, int n_bits, void* scratch, bool* result_in_alt, cudaStream_t s,
+                             const uint32_t* d_n) {
   *result_in_alt = false;
   if (n <= 1 || n_bits <= 0) return cudaSuccess;
   const uint32_t nb = (n + kChunk - 1) / kChunk;
@@ -443,12 +492,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     const int shift = p * digit;
     const int width = min(digit, n_bits - shift);
     const uint32_t mask = (1u << width) - 1u;
-    radix_upsweep_kernel<<<nb, kBlock, 0, s>>>(kin, n, shift, mask, counts, nb);
+    radix_upsweep_kernel<<<nb, kBlock, 0, s>>>(kin, n, shift, mask, counts, nb, d_n);
     cudaError_t e = launched();
     if (e != cudaSuccess) return e;
     e = scan_exclusive<uint32_t>(counts, counts, (mask + 1) * nb, nullptr, scan_scratch, s);
     if (e != cudaSuccess) return e;
-    radix_scatter_kernel<<<nb, kBlock, 0, s>>>(kin, vin, kout, vout, n, shift, mask, counts, nb);
+    radix_scatter_kernel<<<nb, kBlock, 0, s>>>(kin, vin, kout, vout, n, shift, mask, counts, nb, d_n);
     e = launched();
     if (e != cudaSuccess) return e;
     uint32_t* t = kin; kin = kout; kout = t;
@@ -494,9 +543,10 @@ cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uin
   return launched();
 }
 
-cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s) {
+cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s,
+                               const uint32_t* d_n) {
   if (n_pairs == 0) return cudaSuccess;
-  tile_ranges_kernel<<<(n_pairs + 255) / 256, 256, 0, s>>>(keys, n_pairs, ranges);
+  tile_ranges_kernel<<<(n_pairs + 255) / 256, 256, 0, s>>>(keys, n_pairs, ranges, d_n);
   return launched();
 }
 
@@ -504,6 +554,23 @@ cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* w
                               uint32_t* tile_ids, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   tile_work_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, work_key, tile_ids);
+  return launched();
+}
+
+}  // namespace ocgs
+
+namespace ocgs {
+namespace {
+__global__ void clamp_count_kernel(const uint64_t* __restrict__ total, uint32_t cap, uint32_t* __restrict__ n32,
+                                   int* __restrict__ status) {
+  const uint64_t t = *total;
+  *n32 = (uint32_t)(t < (uint64_t)cap ? t : (uint64_t)cap);
+  if (t > (uint64_t)cap) atomicOr(status, kStatusCapacity);
+}
+}  // namespace
+
+cudaError_t launch_clamp_count(const uint64_t* total, uint32_t cap, uint32_t* n32, int* status, cudaStream_t s) {
+  clamp_count_kernel<<<1, 1, 0, s>>>(total, cap, n32, status);
   return launched();
 }
 

@@ -261,3 +261,56 @@ def test_surfel_behind_camera_and_edge_on(rast, dev):
     errs = forward_errors(gpu_at(out, np.arange(41 * 41)), ref, ok)
     assert max(errs.values()) <= FWD_TOL, errs
     assert ref["alpha"].max() > 0.1
+
+
+def test_autotune_picks_valid_options_and_caches_them(dev, tmp_path):
+    from paper_2501_08174_gb300 import Rasterizer
+    sc = synthetic.small_scene(801, 1200, 96, 80, degree=2, n_views=2)
+    g = to_device(sc["gaussians"], dev)
+    r = Rasterizer(dev)
+    before, _ = r.render(g, sc["cameras"], keep_state=False)
+    before = {k: v.clone() for k, v in before.items()}
+    cache = tmp_path / "tune.txt"
+    res = r.autotune(g, sc["cameras"], cache_path=cache)
+    assert res["n_tried"] >= 10 and not res["from_cache"] and res["ms"] > 0
+    after, _ = r.render(g, sc["cameras"], keep_state=False)
+    torch.cuda.synchronize()
+    for k in OUT_KEYS:  # options change the time, never the result
+        assert torch.equal(before[k], after[k]), k
+    r2 = Rasterizer(dev)
+    res2 = r2.autotune(g, sc["cameras"], cache_path=cache)
+    assert res2["from_cache"] and res2["tile"] == res["tile"] and res2["pixels_per_thread"] == res["pixels_per_thread"]
+    r.close()
+    r2.close()
+
+
+def test_captured_sweep_equals_eager_sweep_and_reports_overflow(dev):
+    from paper_2501_08174_gb300 import OcgsError, Rasterizer
+    sc = synthetic.small_scene(901, 3000, 64, 48, degree=1, n_views=20, scale_range=(0.05, 0.2))
+    g = to_device(sc["gaussians"], dev)
+    cams = sc["cameras"]
+    for opts in (dict(), dict(tile=(16, 8), persistent=False, pixels_per_thread=2)):
+        r = Rasterizer(dev, **opts)
+        eager = r.accumulate_contribution(g, cams).clone()
+        graph = r.contribution_graph(g, cams, headroom=1.0)
+        got = graph.launch()
+        r.sync()
+        assert torch.equal(got, eager)
+        got.fill_(7.0)  # the graph zeroes the score itself
+        graph.launch()
+        r.sync()
+        assert torch.equal(got, eager)
+        # parameters change in place between launches: the graph sees the new values
+        g["opacity"].mul_(0.5)
+        graph.launch()
+        r.sync()
+        assert torch.equal(graph.score, r.accumulate_contribution(g, cams))
+        g["opacity"].mul_(2.0)
+        # larger surfels need more pairs than the capacity: reported, not faulted
+        g["scale"].mul_(3.0)
+        graph.launch()
+        with pytest.raises(OcgsError, match="CAPACITY"):
+            r.sync()
+        g["scale"].div_(3.0)
+        graph.close()
+        r.close()
