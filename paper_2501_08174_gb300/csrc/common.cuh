@@ -114,18 +114,39 @@ __device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float
 // rb: the record's support bound support_rho(o) <= 9.  Candidates with
 // rho > rb have o exp(-rho/2) < 1/255, so testing rb instead of 9 first only
 // skips work; every decision is the one the 9 cut and the 1/255 floor give.
-__device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1, const float4 g2,
+//
+// The evaluation is split in two so that a thread can run the cheap support
+// test of all its pixels as straight-line code and finish only the pixels
+// that pass: splat_head (support test) and splat_tail (rho, alpha, depth).
+struct SplatHead {
+  float dy, un, vn, den, rho2, q, dd;
+  bool in3;   // rho3 <= rb
+  bool pass;  // rho3 <= rb or rho2 <= rb
+};
+
+__device__ __forceinline__ SplatHead splat_head(const float4 g0, const float4 g1, const float4 g2,
                                                 const SplatColumn& c, float py, float rb) {
+  SplatHead h;
+  h.dy = __fsub_rn(py, g0.y);
+  h.un = __fmaf_rn(g1.y, h.dy, c.ux);
+  h.vn = __fmaf_rn(g1.w, h.dy, c.vx);
+  h.den = __fmaf_rn(g2.z, h.dy, c.ex);
+  h.rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(h.dy, h.dy, c.dx2));
+  h.q = __fmaf_rn(h.un, h.un, __fmul_rn(h.vn, h.vn));
+  h.dd = __fmul_rn(h.den, h.den);
+  h.in3 = (h.den != 0.0f) && (h.q <= __fmul_rn(rb, h.dd));
+  h.pass = h.in3 || (h.rho2 <= rb);
+  return h;
+}
+
+__device__ __forceinline__ SplatEval splat_tail(const float4 g0, const float4 g2, const SplatColumn& c,
+                                                const SplatHead& h, float rb) {
   SplatEval e;
   e.dx = c.dx;
-  e.dy = __fsub_rn(py, g0.y);
-  e.un = __fmaf_rn(g1.y, e.dy, c.ux);
-  e.vn = __fmaf_rn(g1.w, e.dy, c.vx);
-  e.den = __fmaf_rn(g2.z, e.dy, c.ex);
-  const float rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(e.dy, e.dy, c.dx2));
-  const float q = __fmaf_rn(e.un, e.un, __fmul_rn(e.vn, e.vn));
-  const float dd = __fmul_rn(e.den, e.den);
-  const bool in3 = (e.den != 0.0f) && (q <= __fmul_rn(rb, dd));
+  e.dy = h.dy;
+  e.un = h.un;
+  e.vn = h.vn;
+  e.den = h.den;
   e.r = 0.0f;
   e.rho3 = __int_as_float(0x7f800000);  // +inf
   e.G = 0.0f;
@@ -134,14 +155,14 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1
   e.z = 0.0f;
   e.ok = false;
   e.surf = false;
-  e.rho = rho2;
-  if (!in3 && rho2 > rb) return e;  // outside the support
-  if (in3) {
-    e.r = __fdividef(1.0f, e.den);
-    e.rho3 = __fmul_rn(q, __fmul_rn(e.r, e.r));
+  e.rho = h.rho2;
+  if (!h.pass) return e;  // outside the support
+  if (h.in3) {
+    e.r = __fdividef(1.0f, h.den);
+    e.rho3 = __fmul_rn(h.q, __fmul_rn(e.r, e.r));
   }
-  e.surf = in3 && (e.rho3 <= rho2);
-  e.rho = e.surf ? e.rho3 : rho2;
+  e.surf = h.in3 && (e.rho3 <= h.rho2);
+  e.rho = e.surf ? e.rho3 : h.rho2;
   if (e.rho <= rb) {
     e.G = __expf(__fmul_rn(-0.5f, e.rho));
     e.oG = __fmul_rn(g0.z, e.G);
@@ -150,6 +171,11 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1
     e.z = e.surf ? __fmul_rn(g2.w, e.r) : g0.w;
   }
   return e;
+}
+
+__device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1, const float4 g2,
+                                                const SplatColumn& c, float py, float rb) {
+  return splat_tail(g0, g2, c, splat_head(g0, g1, g2, c, py, rb), rb);
 }
 
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }

@@ -337,10 +337,18 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
           const SplatColumn col = splat_column(g0, g1, g2, pxf);
           const float4 ap = s_a0[j];
           const float2 an = s_a1[j];
+          SplatHead hd[PPT];
+          bool any = false;
 #pragma unroll
           for (int k = 0; k < PPT; ++k) {
-            if (jj < (int)last[k]) {
-              const SplatEval e = eval_splat(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
+            hd[k] = splat_head(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
+            hd[k].pass = hd[k].pass && jj < (int)last[k];
+            any = any || hd[k].pass;
+          }
+#pragma unroll
+          for (int k = 0; k < PPT; ++k) {
+            if (any && hd[k].pass) {
+              const SplatEval e = splat_tail(g0, g2, col, hd[k], rb);
               if (e.ok) {
                 contrib = true;
                 const float inv = __fdividef(1.f, 1.f - e.alpha);

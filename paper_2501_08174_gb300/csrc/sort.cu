@@ -276,8 +276,7 @@ __global__ void iota_kernel(uint32_t* v, uint32_t n) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kSmallRows = 4;   // a lane handles a record with at most this many candidate rows alone
-constexpr int kSmallTiles = 64; // ... and at most this many tiles to write
+constexpr int kSmallRows = 16;  // a lane handles a record with at most this many candidate rows alone
 
 __device__ __forceinline__ int row_count(const RowRuns& rr) {
   return max(0, rr.a1 - rr.a0 + 1) + max(0, rr.b1 - rr.b0 + 1);
@@ -334,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const uint64_t* __restrict__ roff, const int32_t* __restrict__ ntiles, uint32_t n_rec,
     const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams, int64_t n_gauss, int tw,
     int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  __shared__ int4 s_runs[kWarpsPerBlock][32][kSmallRows];
+  __shared__ short4 s_runs[kWarpsPerBlock][32][kSmallRows];  // tile runs of each row (tile indices < 2^15)
   __shared__ int s_incl[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
@@ -349,14 +348,14 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
       o = roff[r];
     }
   }
-  const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows && cnt <= kSmallTiles;
+  const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
     const float4 g0 = rec.g0[r];
     const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      s_runs[warp][lane][ty - rc.y] = make_int4(rr.a0, rr.a1, rr.b0, rr.b1);
+      s_runs[warp][lane][ty - rc.y] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
     }
   }
   // flat walk over the small records' tiles
@@ -386,8 +385,8 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
       const DevCam& cam = cams[rr / (uint64_t)n_gauss];
       int tx = -1, ty = bc.y;
       for (int row = 0; row <= bc.w - bc.y; ++row) {
-        const int4 ru = s_runs[warp][ri][row];
-        const int la = max(0, ru.y - ru.x + 1), lb = max(0, ru.w - ru.z + 1);
+        const short4 ru = s_runs[warp][ri][row];
+        const int la = max(0, (int)ru.y - (int)ru.x + 1), lb = max(0, (int)ru.w - (int)ru.z + 1);
         if (kth < la) { tx = ru.x + kth; ty = bc.y + row; break; }
         kth -= la;
         if (kth < lb) { tx = ru.z + kth; ty = bc.y + row; break; }
