@@ -22,6 +22,7 @@ import argparse
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -123,6 +124,10 @@ def dist_info():
     return rank, world, local
 
 
+def workload_args(a) -> str:
+    return f"--n {a.n} --views {a.views} --tile {a.tile} --persistent {a.persistent} --ppt {a.ppt}"
+
+
 def load_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -130,6 +135,44 @@ def load_peaks() -> dict:
             d = json.load(f)
         return {"hbm_gbs": d["hbm_gbs"], "sm_max_mhz": d.get("sm_max_mhz", 2070.0), "source": "measured"}
     return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0, "source": "fallback"}
+
+
+# ----------------------------------------------------------------------------- measured DRAM traffic
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_500k_16views.md")
+
+
+def sources_digest() -> str:
+    """sha256 (first 16 hex digits) over the kernel sources and their build flags."""
+    import hashlib
+    pkg = os.path.join(ROOT, "paper_2501_08174_gb300")
+    csrc = os.path.join(pkg, "csrc")
+    files = sorted(os.path.join(csrc, f) for f in os.listdir(csrc) if f.endswith((".cu", ".cuh")))
+    files.append(os.path.join(pkg, "build.py"))
+    h = hashlib.sha256()
+    for path in files:
+        h.update(os.path.relpath(path, ROOT).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str, workload_args: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the ncu summary in profiles/.
+
+    The summary records the source digest and the bench arguments it was captured
+    with; a capture of other sources or another workload gives None."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    text = open(TRAFFIC_FILE).read()
+    dig = re.search(r"^sources-sha256: *(\w+)", text, re.M)
+    wl = re.search(r"^workload-args: *(.+?) *$", text, re.M)
+    if not dig or not wl or dig.group(1) != sources_digest() or wl.group(1) != workload_args:
+        return None
+    row = re.search(r"^\| *" + re.escape(kernel) + r" *\|([^\n]*)$", text, re.M)
+    if not row:
+        return None
+    cells = [c.strip() for c in row.group(1).split("|") if c.strip()]
+    return int(cells[2])  # columns: read, write, read + write, ...
 
 
 # ----------------------------------------------------------------------------- roofline model
@@ -141,9 +184,9 @@ def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile
         "depth_sort": VN * 4 + 4 * VN * 20,
         "binning": VN * 68 + K * 12 + T * 8,
         "tile_sort": tile_passes * K * 20,
-        "raster_fwd": K * 4 + P * 40,
+        "raster_fwd": VN * 72 + K * 4 + P * 40,
         "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24),
-        "raster_bwd": VN * 80 + K * 4 + P * 40,
+        "raster_bwd": VN * (72 + 80) + K * 4 + P * 40,
         "preprocess_bwd": N * 232 * 3 + VN * 84,
         "prune": N * 24 + kept * 232 * 2,
     }[stage]
@@ -353,15 +396,20 @@ def run_ours(a, rank: int, world: int, local: int):
     dstage = stages[dom]
     per_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
     alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept)
+    stage_kernel = {"raster_fwd": "raster_fwd_kernel", "raster_bwd": "raster_bwd_kernel",
+                    "preprocess": "preprocess_kernel", "preprocess_bwd": "preprocess_bwd_kernel"}
+    traffic = None
+    if dom in stage_kernel:
+        traffic = measured_traffic(stage_kernel[dom], workload_args(a))
     if alg["flops"]:
         ach = alg["flops"] / (per_launch_ms * 1e-3) / 1e12
         roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
-                    "frac": ach / fp32_peak, "traffic": None,
+                    "frac": ach / fp32_peak, "traffic": traffic,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
     else:
         ach = alg["bytes"] / (per_launch_ms * 1e-3) / 1e9
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                    "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": peaks["source"]}
+                    "frac": ach / peaks["hbm_gbs"], "traffic": traffic, "peak_source": peaks["source"]}
     hbm_step = {"bytes_per_step": step_bytes, "achieved_gbs": step_bytes / (ms * 1e-3) / 1e9,
                 "peak_gbs": peaks["hbm_gbs"], "frac": step_bytes / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
                 "mpix_s_at_roofline": P / (step_bytes / (peaks["hbm_gbs"] * 1e9)) / 1e6}
