@@ -178,6 +178,71 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1
   return splat_tail(g0, g2, c, splat_head(g0, g1, g2, c, py, rb), rb);
 }
 
+// ----------------------------------------------------------------------------- two pixels at once
+// The same evaluation for two pixels of one column (rows py.x and py.y) on the
+// packed FP32x2 pipes of sm_100+: every lane of __ffma2_rn / __fmul2_rn /
+// __fadd2_rn rounds as the scalar operation does, so a pair gives the two scalar
+// results bit for bit with half the issued instructions.  All lanes are
+// evaluated; the flags say which results count.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+__device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
+__device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
+  if (i) v.y = x;
+  else v.x = x;
+}
+
+struct SplatHead2 {
+  float2 dy, un, vn, den, rho2, q;
+  bool in3[2];
+  bool pass[2];
+};
+
+__device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
+                                                  const SplatColumn& c, float2 py, float rb) {
+  SplatHead2 h;
+  h.dy = __fadd2_rn(py, bc2(-g0.y));
+  h.un = __ffma2_rn(bc2(g1.y), h.dy, bc2(c.ux));
+  h.vn = __ffma2_rn(bc2(g1.w), h.dy, bc2(c.vx));
+  h.den = __ffma2_rn(bc2(g2.z), h.dy, bc2(c.ex));
+  h.rho2 = __fmul2_rn(bc2(kInvSigmaF2), __ffma2_rn(h.dy, h.dy, bc2(c.dx2)));
+  h.q = __ffma2_rn(h.un, h.un, __fmul2_rn(h.vn, h.vn));
+  const float2 lim = __fmul2_rn(bc2(rb), __fmul2_rn(h.den, h.den));
+  h.in3[0] = (h.den.x != 0.0f) && (h.q.x <= lim.x);
+  h.in3[1] = (h.den.y != 0.0f) && (h.q.y <= lim.y);
+  h.pass[0] = h.in3[0] || (h.rho2.x <= rb);
+  h.pass[1] = h.in3[1] || (h.rho2.y <= rb);
+  return h;
+}
+
+struct SplatEval2 {
+  float2 r, rho3;  // 1 / den and the surfel rho where the surfel term won, else 0
+  float2 G, oG, alpha, z;
+  bool surf[2];
+  bool ok[2];  // pass, rho <= rb and alpha >= 1/255
+};
+
+__device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
+  SplatEval2 e;
+  const float2 r = make_float2(h.in3[0] ? __fdividef(1.0f, h.den.x) : 0.0f, h.in3[1] ? __fdividef(1.0f, h.den.y) : 0.0f);
+  const float2 r3 = __fmul2_rn(h.q, __fmul2_rn(r, r));
+  e.surf[0] = h.in3[0] && (r3.x <= h.rho2.x);
+  e.surf[1] = h.in3[1] && (r3.y <= h.rho2.y);
+  // zero where the filter term won, so that masked products stay finite
+  e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
+  e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
+  const float2 rho = make_float2(e.surf[0] ? r3.x : h.rho2.x, e.surf[1] ? r3.y : h.rho2.y);
+  const float2 ex = __fmul2_rn(bc2(-0.5f), rho);
+  e.G = make_float2(__expf(ex.x), __expf(ex.y));
+  e.oG = __fmul2_rn(bc2(g0.z), e.G);
+  e.alpha = make_float2(fminf(kAlphaMax, e.oG.x), fminf(kAlphaMax, e.oG.y));
+  e.ok[0] = h.pass[0] && (rho.x <= rb) && (e.alpha.x >= kAlphaMin);
+  e.ok[1] = h.pass[1] && (rho.y <= rb) && (e.alpha.y >= kAlphaMin);
+  const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
+  e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);
+  return e;
+}
+
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
 
 // Support bound in rho of a surfel of opacity o: the 3-sigma cut, tightened to

@@ -80,16 +80,22 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
     const uint2 rg = a.ranges[tile];
     const uint32_t start = rg.x, end = rg.y;
     const int64_t gbase = (int64_t)v * a.n_gauss;
-    float T[PPT], c0[PPT], c1[PPT], c2[PPT], dep[PPT], n0[PPT], n1[PPT], n2[PPT];
-    uint32_t last[PPT];
-    bool done[PPT];
+    // pixel k of this thread is lane (k & 1) of pair k / 2; an odd PPT leaves a
+    // dummy lane that starts done
+    constexpr int NP = (PPT + 1) / 2;
+    float2 T[NP], c0[NP], c1[NP], c2[NP], dep[NP], n0[NP], n1[NP], n2[NP];
+    uint32_t last[2 * NP];
+    bool done[2 * NP];
     bool alldone = true;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      T[k] = 1.f;
-      c0[k] = c1[k] = c2[k] = dep[k] = n0[k] = n1[k] = n2[k] = 0.f;
+    for (int p = 0; p < NP; ++p) {
+      T[p] = bc2(1.f);
+      c0[p] = c1[p] = c2[p] = dep[p] = n0[p] = n1[p] = n2[p] = bc2(0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) {
       last[k] = 0u;
-      done[k] = !(px < cam.W && py0 + k < cam.H);
+      done[k] = !(k < PPT && px < cam.W && py0 + k < cam.H);
       alldone = alldone && done[k];
     }
     for (uint32_t b0 = start; b0 < end; b0 += NT) {
@@ -117,7 +123,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
         {
           int act = 0;
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) act += done[k] ? 0 : 1;
+          for (int k = 0; k < 2 * NP; ++k) act += done[k] ? 0 : 1;
           OCGS_DIAG(1, act);
         }
 #endif
@@ -131,34 +137,42 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             ap = s_a0[j];
             an = s_a1[j];
           }
+          const uint32_t pos = b0 + (uint32_t)j - start + 1u;
+#pragma unroll
+          for (int p = 0; p < NP; ++p) {
+            const int k0 = 2 * p, k1 = 2 * p + 1;
+            if (done[k0] && done[k1]) continue;
+            const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
+            SplatHead2 h = splat_head2(g0, g1, g2, col, py, rb);
+            h.pass[0] = h.pass[0] && !done[k0];
+            h.pass[1] = h.pass[1] && !done[k1];
+            if (!(h.pass[0] || h.pass[1])) continue;
+            const SplatEval2 e = splat_tail2(g0, g2, h, rb);
+            const float2 Tn = __fmul2_rn(T[p], __fadd2_rn(bc2(1.f), neg2(e.alpha)));
+            const float2 w = __fmul2_rn(e.alpha, T[p]);
+            // an entry that would take T below kTEps ends the pixel unblended
+            const bool end0 = e.ok[0] && Tn.x < kTEps, end1 = e.ok[1] && Tn.y < kTEps;
+            const bool bl0 = e.ok[0] && !end0, bl1 = e.ok[1] && !end1;
+            done[k0] = done[k0] || end0;
+            done[k1] = done[k1] || end1;
+            const float2 wm = make_float2(bl0 ? w.x : 0.f, bl1 ? w.y : 0.f);
+            if (IMG) {
+              c0[p] = __ffma2_rn(wm, bc2(ap.x), c0[p]);
+              c1[p] = __ffma2_rn(wm, bc2(ap.y), c1[p]);
+              c2[p] = __ffma2_rn(wm, bc2(ap.z), c2[p]);
+              dep[p] = __ffma2_rn(wm, e.z, dep[p]);
+              n0[p] = __ffma2_rn(wm, bc2(ap.w), n0[p]);
+              n1[p] = __ffma2_rn(wm, bc2(an.x), n1[p]);
+              n2[p] = __ffma2_rn(wm, bc2(an.y), n2[p]);
+            }
+            T[p] = make_float2(bl0 ? Tn.x : T[p].x, bl1 ? Tn.y : T[p].y);
+            if (bl0) last[k0] = pos;
+            if (bl1) last[k1] = pos;
+            wmax = fmaxf(wmax, fmaxf(wm.x, wm.y));
+          }
           alldone = true;
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (!done[k]) {
-              const SplatEval e = eval_splat(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
-              if (e.ok) {
-                const float Tn = T[k] * (1.f - e.alpha);
-                if (Tn < kTEps) {
-                  done[k] = true;
-                } else {
-                  const float w = e.alpha * T[k];
-                  if (IMG) {
-                    c0[k] += w * ap.x;
-                    c1[k] += w * ap.y;
-                    c2[k] += w * ap.z;
-                    dep[k] += w * e.z;
-                    n0[k] += w * ap.w;
-                    n1[k] += w * an.x;
-                    n2[k] += w * an.y;
-                  }
-                  T[k] = Tn;
-                  last[k] = b0 + (uint32_t)j - start + 1u;
-                  wmax = fmaxf(wmax, w);
-                }
-              }
-            }
-            alldone = alldone && done[k];
-          }
+          for (int k = 0; k < 2 * NP; ++k) alldone = alldone && done[k];
         }
         if (SCORE) {
           const unsigned m = __reduce_max_sync(kFull, __float_as_uint(wmax));
@@ -178,17 +192,19 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
         const int py = py0 + k;
+        const int p = k >> 1, i = k & 1;
         if (px < cam.W && py < cam.H) {
           const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
-          a.out.rgb[3 * pix + 0] = c0[k];
-          a.out.rgb[3 * pix + 1] = c1[k];
-          a.out.rgb[3 * pix + 2] = c2[k];
-          a.out.alpha[pix] = 1.f - T[k];
-          a.out.depth[pix] = dep[k];
-          a.out.normal[3 * pix + 0] = n0[k];
-          a.out.normal[3 * pix + 1] = n1[k];
-          a.out.normal[3 * pix + 2] = n2[k];
-          a.t_final[pix] = T[k];
+          const float Tk = lane2(T[p], i);
+          a.out.rgb[3 * pix + 0] = lane2(c0[p], i);
+          a.out.rgb[3 * pix + 1] = lane2(c1[p], i);
+          a.out.rgb[3 * pix + 2] = lane2(c2[p], i);
+          a.out.alpha[pix] = 1.f - Tk;
+          a.out.depth[pix] = lane2(dep[p], i);
+          a.out.normal[3 * pix + 0] = lane2(n0[p], i);
+          a.out.normal[3 * pix + 1] = lane2(n1[p], i);
+          a.out.normal[3 * pix + 2] = lane2(n2[p], i);
+          a.t_final[pix] = Tk;
           a.last[pix] = last[k];
         }
       }
@@ -266,34 +282,40 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
     const int py0 = (local / cam.tiles_x) * TH + ly0;
     const float pxf = (float)px + 0.5f;
     const uint32_t start = a.ranges[tile].x;
-    float T[PPT], gAT[PPT], S[PPT];
-    float gC0[PPT], gC1[PPT], gC2[PPT], gD[PPT], gN0[PPT], gN1[PPT], gN2[PPT];
-    uint32_t last[PPT];
+    // pixel k of this thread is lane (k & 1) of pair k / 2 (an odd PPT leaves an idle lane)
+    constexpr int NP = (PPT + 1) / 2;
+    float2 T[NP], gAT[NP], S[NP];
+    float2 gC0[NP], gC1[NP], gC2[NP], gD[NP], gN0[NP], gN1[NP], gN2[NP];
+    uint32_t last[2 * NP];
     uint32_t thread_last = 0;
 #pragma unroll
-    for (int k = 0; k < PPT; ++k) {
-      T[k] = 1.f;
-      gAT[k] = 0.f;
-      S[k] = 0.f;  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
+    for (int p = 0; p < NP; ++p) {
+      T[p] = bc2(1.f);
+      gAT[p] = bc2(0.f);
+      S[p] = bc2(0.f);  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
+      gC0[p] = gC1[p] = gC2[p] = gD[p] = gN0[p] = gN1[p] = gN2[p] = bc2(0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) {
       last[k] = 0u;
-      gC0[k] = gC1[k] = gC2[k] = gD[k] = gN0[k] = gN1[k] = gN2[k] = 0.f;
       const int py = py0 + k;
-      if (px < cam.W && py < cam.H) {
+      const int p = k >> 1, i = k & 1;
+      if (k < PPT && px < cam.W && py < cam.H) {
         const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
         const float Tf = a.t_final[pix];
-        T[k] = Tf;
+        set_lane2(T[p], i, Tf);
         last[k] = a.last[pix];
         if (a.d_out.rgb) {
-          gC0[k] = a.d_out.rgb[3 * pix];
-          gC1[k] = a.d_out.rgb[3 * pix + 1];
-          gC2[k] = a.d_out.rgb[3 * pix + 2];
+          set_lane2(gC0[p], i, a.d_out.rgb[3 * pix]);
+          set_lane2(gC1[p], i, a.d_out.rgb[3 * pix + 1]);
+          set_lane2(gC2[p], i, a.d_out.rgb[3 * pix + 2]);
         }
-        if (a.d_out.alpha) gAT[k] = a.d_out.alpha[pix] * Tf;
-        if (a.d_out.depth) gD[k] = a.d_out.depth[pix];
+        if (a.d_out.alpha) set_lane2(gAT[p], i, a.d_out.alpha[pix] * Tf);
+        if (a.d_out.depth) set_lane2(gD[p], i, a.d_out.depth[pix]);
         if (a.d_out.normal) {
-          gN0[k] = a.d_out.normal[3 * pix];
-          gN1[k] = a.d_out.normal[3 * pix + 1];
-          gN2[k] = a.d_out.normal[3 * pix + 2];
+          set_lane2(gN0[p], i, a.d_out.normal[3 * pix]);
+          set_lane2(gN1[p], i, a.d_out.normal[3 * pix + 1]);
+          set_lane2(gN2[p], i, a.d_out.normal[3 * pix + 2]);
         }
         thread_last = max(thread_last, last[k]);
       }
@@ -335,65 +357,90 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
           const float4 g0 = s_g0[j], g1 = s_g1[j], g2 = s_g2[j];
           const float rb = s_rb[j];
           const SplatColumn col = splat_column(g0, g1, g2, pxf);
-          const float4 ap = s_a0[j];
-          const float2 an = s_a1[j];
-          SplatHead hd[PPT];
+          SplatHead2 hd[NP];
           bool any = false;
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            hd[k] = splat_head(g0, g1, g2, col, (float)(py0 + k) + 0.5f, rb);
-            hd[k].pass = hd[k].pass && jj < (int)last[k];
-            any = any || hd[k].pass;
+          for (int p = 0; p < NP; ++p) {
+            const float2 py = make_float2((float)(py0 + 2 * p) + 0.5f, (float)(py0 + 2 * p + 1) + 0.5f);
+            hd[p] = splat_head2(g0, g1, g2, col, py, rb);
+            hd[p].pass[0] = hd[p].pass[0] && jj < (int)last[2 * p];
+            hd[p].pass[1] = hd[p].pass[1] && jj < (int)last[2 * p + 1];
+            any = any || hd[p].pass[0] || hd[p].pass[1];
           }
+          if (any) {
+            const float4 ap = s_a0[j];
+            const float2 an = s_a1[j];
+            const float2 dx = bc2(col.dx);
+            float2 acc[NG];  // this thread's sums, one lane per pixel of a pair
 #pragma unroll
-          for (int k = 0; k < PPT; ++k) {
-            if (any && hd[k].pass) {
-              const SplatEval e = splat_tail(g0, g2, col, hd[k], rb);
-              if (e.ok) {
-                contrib = true;
-                const float inv = __fdividef(1.f, 1.f - e.alpha);
-                const float Ti = T[k] * inv;
-                const float w = e.alpha * Ti;
-                const float F = gC0[k] * ap.x + gC1[k] * ap.y + gC2[k] * ap.z + gD[k] * e.z + gN0[k] * ap.w +
-                                gN1[k] * an.x + gN2[k] * an.y;
-                const float galpha = Ti * F - (S[k] - gAT[k]) * inv;
-                S[k] += w * F;
-                T[k] = Ti;
-                gr[kGr] += gC0[k] * w;
-                gr[kGg] += gC1[k] * w;
-                gr[kGb] += gC2[k] * w;
-                gr[kGnx] += gN0[k] * w;
-                gr[kGny] += gN1[k] * w;
-                gr[kGnz] += gN2[k] * w;
-                const float gz = gD[k] * w;
-                const bool unclamped = e.oG < kAlphaMax;
-                const float grho = unclamped ? -0.5f * galpha * e.alpha : 0.f;
-                if (unclamped) gr[kGo] += galpha * e.G;
-                float gdx, gdy;
-                if (e.surf) {
-                  const float r2 = e.r * e.r;
-                  const float gun = grho * 2.f * e.un * r2;
-                  const float gvn = grho * 2.f * e.vn * r2;
-                  const float gden = -grho * 2.f * e.rho3 * e.r - gz * e.z * e.r;
-                  gr[kGzD] += gz * e.r;
-                  gdx = gun * g1.x + gvn * g1.z + gden * g2.y;
-                  gdy = gun * g1.y + gvn * g1.w + gden * g2.z;
-                  gr[kGA00] += gun * e.dx;
-                  gr[kGA01] += gun * e.dy;
-                  gr[kGA10] += gvn * e.dx;
-                  gr[kGA11] += gvn * e.dy;
-                  gr[kGe0] += gden;
-                  gr[kGe1] += gden * e.dx;
-                  gr[kGe2] += gden * e.dy;
-                } else {
-                  gdx = grho * 4.f * e.dx;
-                  gdy = grho * 4.f * e.dy;
-                  gr[kGzc] += gz;
-                }
-                gr[kGcx] -= gdx;
-                gr[kGcy] -= gdy;
-              }
+            for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
+#pragma unroll
+            for (int p = 0; p < NP; ++p) {
+              if (!(hd[p].pass[0] || hd[p].pass[1])) continue;
+              const SplatEval2 e = splat_tail2(g0, g2, hd[p], rb);
+              const bool ok0 = e.ok[0], ok1 = e.ok[1];
+              if (!(ok0 || ok1)) continue;
+              contrib = true;
+              // undo the entry: T before it, its weight, and dL/dalpha (lanes that did
+              // not blend get zero weight and zero dL/dalpha, which zeroes every term)
+              const float2 om = __fadd2_rn(bc2(1.f), neg2(e.alpha));
+              const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+              const float2 Ti = __fmul2_rn(T[p], inv);
+              const float2 w = __fmul2_rn(e.alpha, Ti);
+              float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
+              F = __ffma2_rn(gC1[p], bc2(ap.y), F);
+              F = __ffma2_rn(gC2[p], bc2(ap.z), F);
+              F = __ffma2_rn(gD[p], e.z, F);
+              F = __ffma2_rn(gN0[p], bc2(ap.w), F);
+              F = __ffma2_rn(gN1[p], bc2(an.x), F);
+              F = __ffma2_rn(gN2[p], bc2(an.y), F);
+              const float2 galpha = __ffma2_rn(Ti, F, neg2(__fmul2_rn(__fadd2_rn(S[p], neg2(gAT[p])), inv)));
+              const float2 wm = make_float2(ok0 ? w.x : 0.f, ok1 ? w.y : 0.f);
+              const float2 ga = make_float2(ok0 ? galpha.x : 0.f, ok1 ? galpha.y : 0.f);
+              S[p] = __ffma2_rn(wm, F, S[p]);
+              T[p] = make_float2(ok0 ? Ti.x : T[p].x, ok1 ? Ti.y : T[p].y);
+              acc[kGr] = __ffma2_rn(gC0[p], wm, acc[kGr]);
+              acc[kGg] = __ffma2_rn(gC1[p], wm, acc[kGg]);
+              acc[kGb] = __ffma2_rn(gC2[p], wm, acc[kGb]);
+              acc[kGnx] = __ffma2_rn(gN0[p], wm, acc[kGnx]);
+              acc[kGny] = __ffma2_rn(gN1[p], wm, acc[kGny]);
+              acc[kGnz] = __ffma2_rn(gN2[p], wm, acc[kGnz]);
+              const float2 gz = __fmul2_rn(gD[p], wm);
+              // alpha = o G below the 0.99 clamp; at the clamp nothing flows to rho or o
+              const bool un0 = e.oG.x < kAlphaMax, un1 = e.oG.y < kAlphaMax;
+              const float2 grr = __fmul2_rn(__fmul2_rn(bc2(-0.5f), ga), e.alpha);
+              const float2 grho = make_float2(un0 ? grr.x : 0.f, un1 ? grr.y : 0.f);
+              const float2 gop = __fmul2_rn(ga, e.G);
+              acc[kGo] = __fadd2_rn(acc[kGo], make_float2(un0 ? gop.x : 0.f, un1 ? gop.y : 0.f));
+              // rho and depth came from the surfel's (u, v) where it won the min, from the
+              // screen-space filter elsewhere: split the cotangents between the two
+              const bool s0 = e.surf[0], s1 = e.surf[1];
+              const float2 grs = make_float2(s0 ? grho.x : 0.f, s1 ? grho.y : 0.f);
+              const float2 gzs = make_float2(s0 ? gz.x : 0.f, s1 ? gz.y : 0.f);
+              const float2 grf = make_float2(s0 ? 0.f : grho.x, s1 ? 0.f : grho.y);
+              const float2 gzf = make_float2(s0 ? 0.f : gz.x, s1 ? 0.f : gz.y);
+              const float2 r2 = __fmul2_rn(e.r, e.r);
+              const float2 gs2 = __fmul2_rn(grs, bc2(2.f));
+              const float2 gun = __fmul2_rn(__fmul2_rn(gs2, hd[p].un), r2);
+              const float2 gvn = __fmul2_rn(__fmul2_rn(gs2, hd[p].vn), r2);
+              const float2 gden = __ffma2_rn(neg2(__fmul2_rn(gzs, e.z)), e.r, neg2(__fmul2_rn(__fmul2_rn(gs2, e.rho3), e.r)));
+              acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+              const float2 gdxs = __ffma2_rn(gden, bc2(g2.y), __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
+              const float2 gdys = __ffma2_rn(gden, bc2(g2.z), __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
+              acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
+              acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
+              acc[kGA10] = __ffma2_rn(gvn, dx, acc[kGA10]);
+              acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
+              acc[kGe0] = __fadd2_rn(acc[kGe0], gden);
+              acc[kGe1] = __ffma2_rn(gden, dx, acc[kGe1]);
+              acc[kGe2] = __ffma2_rn(gden, hd[p].dy, acc[kGe2]);
+              const float2 gf4 = __fmul2_rn(grf, bc2(4.f));
+              acc[kGzc] = __fadd2_rn(acc[kGzc], gzf);
+              acc[kGcx] = __fadd2_rn(acc[kGcx], neg2(__ffma2_rn(gf4, dx, gdxs)));
+              acc[kGcy] = __fadd2_rn(acc[kGcy], neg2(__ffma2_rn(gf4, hd[p].dy, gdys)));
             }
+#pragma unroll
+            for (int q = 0; q < NG; ++q) gr[q] = __fadd_rn(acc[q].x, acc[q].y);
           }
         }
         if (__any_sync(kFull, contrib)) {
