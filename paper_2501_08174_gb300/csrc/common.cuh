@@ -185,7 +185,6 @@ __device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1
 // results bit for bit with half the issued instructions.  All lanes are
 // evaluated; the flags say which results count.
 __device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
-__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
 __device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
 __device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
   if (i) v.y = x;
@@ -222,15 +221,22 @@ struct SplatEval2 {
   bool ok[2];  // pass, rho <= rb and alpha >= 1/255
 };
 
+// FINITE: r and rho3 are zeroed where the filter term won, so that products
+// the backward masks with zero stay finite (the forward only reads z there).
+template <bool FINITE>
 __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
   SplatEval2 e;
   const float2 r = make_float2(h.in3[0] ? __fdividef(1.0f, h.den.x) : 0.0f, h.in3[1] ? __fdividef(1.0f, h.den.y) : 0.0f);
   const float2 r3 = __fmul2_rn(h.q, __fmul2_rn(r, r));
   e.surf[0] = h.in3[0] && (r3.x <= h.rho2.x);
   e.surf[1] = h.in3[1] && (r3.y <= h.rho2.y);
-  // zero where the filter term won, so that masked products stay finite
-  e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
-  e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
+  if (FINITE) {
+    e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
+    e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
+  } else {
+    e.r = r;
+    e.rho3 = r3;
+  }
   const float2 rho = make_float2(e.surf[0] ? r3.x : h.rho2.x, e.surf[1] ? r3.y : h.rho2.y);
   const float2 ex = __fmul2_rn(bc2(-0.5f), rho);
   e.G = make_float2(__expf(ex.x), __expf(ex.y));

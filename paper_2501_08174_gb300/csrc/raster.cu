@@ -39,7 +39,7 @@ __device__ unsigned long long g_diag[8];
 
 // Resident warps per SM the compiler is asked to fit (caps registers per thread).
 #ifndef OCGS_FWD_WARPS
-#define OCGS_FWD_WARPS 16
+#define OCGS_FWD_WARPS 20
 #endif
 #ifndef OCGS_BWD_WARPS
 #define OCGS_BWD_WARPS 16
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             h.pass[0] = h.pass[0] && !done[k0];
             h.pass[1] = h.pass[1] && !done[k1];
             if (!(h.pass[0] || h.pass[1])) continue;
-            const SplatEval2 e = splat_tail2(g0, g2, h, rb);
-            const float2 Tn = __fmul2_rn(T[p], __fadd2_rn(bc2(1.f), neg2(e.alpha)));
+            const SplatEval2 e = splat_tail2<false>(g0, g2, h, rb);
+            const float2 Tn = __fmul2_rn(T[p], __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
             const float2 w = __fmul2_rn(e.alpha, T[p]);
             // an entry that would take T below kTEps ends the pixel unblended
             const bool end0 = e.ok[0] && Tn.x < kTEps, end1 = e.ok[1] && Tn.y < kTEps;
@@ -371,19 +371,20 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
             const float4 ap = s_a0[j];
             const float2 an = s_a1[j];
             const float2 dx = bc2(col.dx);
+            const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
             float2 acc[NG];  // this thread's sums, one lane per pixel of a pair
 #pragma unroll
             for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
               if (!(hd[p].pass[0] || hd[p].pass[1])) continue;
-              const SplatEval2 e = splat_tail2(g0, g2, hd[p], rb);
+              const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb);
               const bool ok0 = e.ok[0], ok1 = e.ok[1];
               if (!(ok0 || ok1)) continue;
               contrib = true;
               // undo the entry: T before it, its weight, and dL/dalpha (lanes that did
               // not blend get zero weight and zero dL/dalpha, which zeroes every term)
-              const float2 om = __fadd2_rn(bc2(1.f), neg2(e.alpha));
+              const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
               const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
               const float2 Ti = __fmul2_rn(T[p], inv);
               const float2 w = __fmul2_rn(e.alpha, Ti);
@@ -394,7 +395,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               F = __ffma2_rn(gN0[p], bc2(ap.w), F);
               F = __ffma2_rn(gN1[p], bc2(an.x), F);
               F = __ffma2_rn(gN2[p], bc2(an.y), F);
-              const float2 galpha = __ffma2_rn(Ti, F, neg2(__fmul2_rn(__fadd2_rn(S[p], neg2(gAT[p])), inv)));
+              // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
+              const float2 galpha = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
               const float2 wm = make_float2(ok0 ? w.x : 0.f, ok1 ? w.y : 0.f);
               const float2 ga = make_float2(ok0 ? galpha.x : 0.f, ok1 ? galpha.y : 0.f);
               S[p] = __ffma2_rn(wm, F, S[p]);
@@ -417,36 +419,45 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               const bool s0 = e.surf[0], s1 = e.surf[1];
               const float2 grs = make_float2(s0 ? grho.x : 0.f, s1 ? grho.y : 0.f);
               const float2 gzs = make_float2(s0 ? gz.x : 0.f, s1 ? gz.y : 0.f);
-              const float2 grf = make_float2(s0 ? 0.f : grho.x, s1 ? 0.f : grho.y);
-              const float2 gzf = make_float2(s0 ? 0.f : gz.x, s1 ? 0.f : gz.y);
+              const float2 grf = __ffma2_rn(grs, bc2(-1.f), grho);  // grho where the filter won, else 0
+              const float2 gzf = __ffma2_rn(gzs, bc2(-1.f), gz);
               const float2 r2 = __fmul2_rn(e.r, e.r);
               const float2 gs2 = __fmul2_rn(grs, bc2(2.f));
               const float2 gun = __fmul2_rn(__fmul2_rn(gs2, hd[p].un), r2);
               const float2 gvn = __fmul2_rn(__fmul2_rn(gs2, hd[p].vn), r2);
-              const float2 gden = __ffma2_rn(neg2(__fmul2_rn(gzs, e.z)), e.r, neg2(__fmul2_rn(__fmul2_rn(gs2, e.rho3), e.r)));
+              // -dL/dden = (2 grho rho3 + gz z) / den; the e slots and c slots below
+              // accumulate negated and are flipped when the lanes are summed
+              const float2 ngden = __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r);
               acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
-              const float2 gdxs = __ffma2_rn(gden, bc2(g2.y), __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
-              const float2 gdys = __ffma2_rn(gden, bc2(g2.z), __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
+              const float2 gdxs = __ffma2_rn(ngden, ng2y, __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
+              const float2 gdys = __ffma2_rn(ngden, ng2z, __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
               acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
               acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
               acc[kGA10] = __ffma2_rn(gvn, dx, acc[kGA10]);
               acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
-              acc[kGe0] = __fadd2_rn(acc[kGe0], gden);
-              acc[kGe1] = __ffma2_rn(gden, dx, acc[kGe1]);
-              acc[kGe2] = __ffma2_rn(gden, hd[p].dy, acc[kGe2]);
+              acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
+              acc[kGe1] = __ffma2_rn(ngden, dx, acc[kGe1]);
+              acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
               const float2 gf4 = __fmul2_rn(grf, bc2(4.f));
               acc[kGzc] = __fadd2_rn(acc[kGzc], gzf);
-              acc[kGcx] = __fadd2_rn(acc[kGcx], neg2(__ffma2_rn(gf4, dx, gdxs)));
-              acc[kGcy] = __fadd2_rn(acc[kGcy], neg2(__ffma2_rn(gf4, hd[p].dy, gdys)));
+              acc[kGcx] = __fadd2_rn(acc[kGcx], __ffma2_rn(gf4, dx, gdxs));
+              acc[kGcy] = __fadd2_rn(acc[kGcy], __ffma2_rn(gf4, hd[p].dy, gdys));
             }
 #pragma unroll
-            for (int q = 0; q < NG; ++q) gr[q] = __fadd_rn(acc[q].x, acc[q].y);
+            for (int q = 0; q < NG; ++q) {
+              const bool negated = q == kGcx || q == kGcy || q == kGe0 || q == kGe1 || q == kGe2;
+              gr[q] = negated ? -__fadd_rn(acc[q].x, acc[q].y) : __fadd_rn(acc[q].x, acc[q].y);
+            }
           }
         }
         if (__any_sync(kFull, contrib)) {
 #ifdef OCGS_COUNT
           if (lane == 0) OCGS_DIAG(3, 1);
           OCGS_DIAG(4, contrib ? 1 : 0);
+          {
+            const int nc = __popc(__ballot_sync(kFull, contrib));
+            if (lane == 0) OCGS_DIAG(nc == 1 ? 5 : (nc <= 8 ? 6 : (nc >= 24 ? 7 : 0)), nc == 1 || nc <= 8 || nc >= 24 ? 1 : 0);
+          }
 #endif
           const int slot = warp_reduce18(gr, lane);
           if (slot >= 0 && gr[0] != 0.f) atomicAdd(&s_grad[j * kGradStride + slot], gr[0]);
