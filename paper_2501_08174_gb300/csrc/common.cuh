@@ -80,10 +80,14 @@ struct GaussOut {
 
 // number of float slots of one record gradient (18 used, padded to 5 float4)
 constexpr int kGradStride = 20;
+// The first kGradSlotsRGB slots are the ones a loss on colour and opacity alone
+// reaches; the depth and normal cotangents add the last five.
 enum GradSlot {
-  kGcx = 0, kGcy, kGo, kGzc, kGA00, kGA01, kGA10, kGA11, kGe0, kGe1, kGe2, kGzD,
-  kGr, kGg, kGb, kGnx, kGny, kGnz
+  kGcx = 0, kGcy, kGo, kGA00, kGA01, kGA10, kGA11, kGe0, kGe1, kGe2, kGr, kGg, kGb,
+  kGzc, kGzD, kGnx, kGny, kGnz
 };
+constexpr int kGradSlotsRGB = 13;
+constexpr int kGradSlots = 18;
 
 // Result of evaluating one surfel at one pixel centre.  All arithmetic uses
 // explicitly rounded intrinsics so that the forward and the backward kernels

@@ -314,14 +314,21 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
     if (ntiles[idx] == 0) continue;
     const DevCam& cam = cams[v];
     const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + idx * kGradStride);
-    const float4 q0 = gr4[0], q1 = gr4[1], q2 = gr4[2], q3 = gr4[3], q4 = gr4[4];
-    // slots: cx cy o zc | A00 A01 A10 A11 | e0 e1 e2 zD | r g b nx | ny nz - -
-    const float g_cx = q0.x, g_cy = q0.y, g_o = q0.z, g_zc = q0.w;
-    const float gA00 = q1.x, gA01 = q1.y, gA10 = q1.z, gA11 = q1.w;
-    float ge0 = q2.x;
-    const float ge1 = q2.y, ge2 = q2.z, gzD = q2.w;
-    const float grgb[3] = {q3.x, q3.y, q3.z};
-    const float gn[3] = {q3.w, q4.x, q4.y};
+    float gq[kGradStride];
+#pragma unroll
+    for (int q = 0; q < kGradStride / 4; ++q) {
+      const float4 t = gr4[q];
+      gq[4 * q] = t.x;
+      gq[4 * q + 1] = t.y;
+      gq[4 * q + 2] = t.z;
+      gq[4 * q + 3] = t.w;
+    }
+    const float g_cx = gq[kGcx], g_cy = gq[kGcy], g_o = gq[kGo], g_zc = gq[kGzc];
+    const float gA00 = gq[kGA00], gA01 = gq[kGA01], gA10 = gq[kGA10], gA11 = gq[kGA11];
+    float ge0 = gq[kGe0];
+    const float ge1 = gq[kGe1], ge2 = gq[kGe2], gzD = gq[kGzD];
+    const float grgb[3] = {gq[kGr], gq[kGg], gq[kGb]};
+    const float gn[3] = {gq[kGnx], gq[kGny], gq[kGnz]};
     go += g_o;
 
     ViewGeom G;

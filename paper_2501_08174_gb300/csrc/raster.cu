@@ -236,21 +236,34 @@ __device__ __forceinline__ void halve(float* v, int lane, int& base, int& real) 
   }
 }
 
-// Warp sum of 18 gradient slots; returns the slot this lane holds (or -1).
-__device__ __forceinline__ int warp_reduce18(float* v, int lane) {
-  int base = 0, real = 18;
-  halve<18, 16>(v, lane, base, real);
-  halve<9, 8>(v, lane, base, real);
-  halve<5, 4>(v, lane, base, real);
-  halve<3, 2>(v, lane, base, real);
-  halve<2, 1>(v, lane, base, real);
+// Warp sum of C gradient slots (18, or 13 without depth and normal cotangents);
+// returns the slot this lane holds (or -1).
+template <int C>
+__device__ __forceinline__ int warp_reduce(float* v, int lane) {
+  static_assert(C == 18 || C == 13, "slot count");
+  int base = 0, real = C;
+  if (C == 18) {
+    halve<18, 16>(v, lane, base, real);
+    halve<9, 8>(v, lane, base, real);
+    halve<5, 4>(v, lane, base, real);
+    halve<3, 2>(v, lane, base, real);
+    halve<2, 1>(v, lane, base, real);
+  } else {
+    halve<13, 16>(v, lane, base, real);
+    halve<7, 8>(v, lane, base, real);
+    halve<4, 4>(v, lane, base, real);
+    halve<2, 2>(v, lane, base, real);
+    halve<1, 1>(v, lane, base, real);
+  }
   return real >= 1 ? base : -1;
 }
 
-template <int TW, int TH, int PPT>
+// GEO: a depth or normal cotangent is given; without one the depth and normal
+// terms of the adjoint are zero and are not evaluated (13 slots instead of 18).
+template <int TW, int TH, int PPT, bool GEO>
 __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW * TH)) raster_bwd_kernel(const RasterBwdArgs a) {
   constexpr int NT = TW * TH / PPT;
-  constexpr int NG = 18;
+  constexpr int NG = GEO ? kGradSlots : kGradSlotsRGB;
   __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
   __shared__ float2 s_a1[NT];
   __shared__ uint32_t s_idx[NT];
@@ -311,8 +324,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
           set_lane2(gC2[p], i, a.d_out.rgb[3 * pix + 2]);
         }
         if (a.d_out.alpha) set_lane2(gAT[p], i, a.d_out.alpha[pix] * Tf);
-        if (a.d_out.depth) set_lane2(gD[p], i, a.d_out.depth[pix]);
-        if (a.d_out.normal) {
+        if (GEO && a.d_out.depth) set_lane2(gD[p], i, a.d_out.depth[pix]);
+        if (GEO && a.d_out.normal) {
           set_lane2(gN0[p], i, a.d_out.normal[3 * pix]);
           set_lane2(gN1[p], i, a.d_out.normal[3 * pix + 1]);
           set_lane2(gN2[p], i, a.d_out.normal[3 * pix + 2]);
@@ -346,7 +359,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
       const int jtop = min(bend, warp_last) - 1 - bstart;
       for (int j = jtop; j >= 0; --j) {
         const int jj = bstart + j;
-        float gr[NG];
+        float gr[kGradSlots];
 #pragma unroll
         for (int q = 0; q < NG; ++q) gr[q] = 0.f;
         bool contrib = false;
@@ -372,7 +385,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
             const float2 an = s_a1[j];
             const float2 dx = bc2(col.dx);
             const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
-            float2 acc[NG];  // this thread's sums, one lane per pixel of a pair
+            float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
 #pragma unroll
             for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
 #pragma unroll
@@ -391,10 +404,12 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
               F = __ffma2_rn(gC1[p], bc2(ap.y), F);
               F = __ffma2_rn(gC2[p], bc2(ap.z), F);
-              F = __ffma2_rn(gD[p], e.z, F);
-              F = __ffma2_rn(gN0[p], bc2(ap.w), F);
-              F = __ffma2_rn(gN1[p], bc2(an.x), F);
-              F = __ffma2_rn(gN2[p], bc2(an.y), F);
+              if (GEO) {
+                F = __ffma2_rn(gD[p], e.z, F);
+                F = __ffma2_rn(gN0[p], bc2(ap.w), F);
+                F = __ffma2_rn(gN1[p], bc2(an.x), F);
+                F = __ffma2_rn(gN2[p], bc2(an.y), F);
+              }
               // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
               const float2 galpha = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
               const float2 wm = make_float2(ok0 ? w.x : 0.f, ok1 ? w.y : 0.f);
@@ -404,10 +419,11 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               acc[kGr] = __ffma2_rn(gC0[p], wm, acc[kGr]);
               acc[kGg] = __ffma2_rn(gC1[p], wm, acc[kGg]);
               acc[kGb] = __ffma2_rn(gC2[p], wm, acc[kGb]);
-              acc[kGnx] = __ffma2_rn(gN0[p], wm, acc[kGnx]);
-              acc[kGny] = __ffma2_rn(gN1[p], wm, acc[kGny]);
-              acc[kGnz] = __ffma2_rn(gN2[p], wm, acc[kGnz]);
-              const float2 gz = __fmul2_rn(gD[p], wm);
+              if (GEO) {
+                acc[kGnx] = __ffma2_rn(gN0[p], wm, acc[kGnx]);
+                acc[kGny] = __ffma2_rn(gN1[p], wm, acc[kGny]);
+                acc[kGnz] = __ffma2_rn(gN2[p], wm, acc[kGnz]);
+              }
               // alpha = o G below the 0.99 clamp; at the clamp nothing flows to rho or o
               const bool un0 = e.oG.x < kAlphaMax, un1 = e.oG.y < kAlphaMax;
               const float2 grr = __fmul2_rn(__fmul2_rn(bc2(-0.5f), ga), e.alpha);
@@ -418,17 +434,22 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               // screen-space filter elsewhere: split the cotangents between the two
               const bool s0 = e.surf[0], s1 = e.surf[1];
               const float2 grs = make_float2(s0 ? grho.x : 0.f, s1 ? grho.y : 0.f);
-              const float2 gzs = make_float2(s0 ? gz.x : 0.f, s1 ? gz.y : 0.f);
               const float2 grf = __ffma2_rn(grs, bc2(-1.f), grho);  // grho where the filter won, else 0
-              const float2 gzf = __ffma2_rn(gzs, bc2(-1.f), gz);
+              float2 gzs = bc2(0.f);
+              if (GEO) {
+                const float2 gz = __fmul2_rn(gD[p], wm);
+                gzs = make_float2(s0 ? gz.x : 0.f, s1 ? gz.y : 0.f);
+                acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
+                acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+              }
               const float2 r2 = __fmul2_rn(e.r, e.r);
               const float2 gs2 = __fmul2_rn(grs, bc2(2.f));
               const float2 gun = __fmul2_rn(__fmul2_rn(gs2, hd[p].un), r2);
               const float2 gvn = __fmul2_rn(__fmul2_rn(gs2, hd[p].vn), r2);
               // -dL/dden = (2 grho rho3 + gz z) / den; the e slots and c slots below
               // accumulate negated and are flipped when the lanes are summed
-              const float2 ngden = __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r);
-              acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+              const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
+                                       : __fmul2_rn(__fmul2_rn(gs2, e.rho3), e.r);
               const float2 gdxs = __ffma2_rn(ngden, ng2y, __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
               const float2 gdys = __ffma2_rn(ngden, ng2z, __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
               acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
@@ -439,7 +460,6 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               acc[kGe1] = __ffma2_rn(ngden, dx, acc[kGe1]);
               acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
               const float2 gf4 = __fmul2_rn(grf, bc2(4.f));
-              acc[kGzc] = __fadd2_rn(acc[kGzc], gzf);
               acc[kGcx] = __fadd2_rn(acc[kGcx], __ffma2_rn(gf4, dx, gdxs));
               acc[kGcy] = __fadd2_rn(acc[kGcy], __ffma2_rn(gf4, hd[p].dy, gdys));
             }
@@ -459,7 +479,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
             if (lane == 0) OCGS_DIAG(nc == 1 ? 5 : (nc <= 8 ? 6 : (nc >= 24 ? 7 : 0)), nc == 1 || nc <= 8 || nc >= 24 ? 1 : 0);
           }
 #endif
-          const int slot = warp_reduce18(gr, lane);
+          const int slot = warp_reduce<NG>(gr, lane);
           if (slot >= 0 && gr[0] != 0.f) atomicAdd(&s_grad[j * kGradStride + slot], gr[0]);
         }
       }
@@ -498,7 +518,8 @@ template <int TW, int TH, int PPT>
 cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
   const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
   if (grid == 0) return cudaSuccess;
-  raster_bwd_kernel<TW, TH, PPT><<<grid, TW * TH / PPT, 0, s>>>(a);
+  if (a.d_out.depth || a.d_out.normal) raster_bwd_kernel<TW, TH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
+  else raster_bwd_kernel<TW, TH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
   return launched();
 }
 
