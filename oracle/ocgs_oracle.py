@@ -27,7 +27,9 @@ normal flip) held fixed:
 * background loss L_b = (1/(h w)) sum A (1 - M) (Eq. 1);
 * contribution score of a surfel = max blending weight over all pixels of
   all views; the surfel is "used" (visible, not occluded) iff the score is
-  > 0 (Sec. 4.3), and the keep-set at threshold tau is {score > tau}.
+  > 0 (Sec. 4.3), and the keep-set at threshold tau is {score > tau};
+* one Adam update of the parameters (the optimiser of the training Sec. 5.1
+  keeps; Kingma & Ba, 2015, Algorithm 1).
 
 Readings of points the paper leaves to prior work (documented with the
 project's design notes): culling of a surfel whose 3-sigma square reaches
@@ -382,3 +384,25 @@ def prune(g: dict, keep: np.ndarray) -> dict:
     out = {k: np.asarray(g[k])[keep] for k in ("xyz", "quat", "scale", "opacity", "sh")}
     out["sh_degree"] = g["sh_degree"]
     return out
+
+
+def adam_step(params: dict, grads: dict, m: dict, v: dict, lr, step: int,
+              beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15):
+    """One Adam update in FP64 (Kingma & Ba, 2015, Algorithm 1), the optimiser of
+    the 2DGS training whose schedule Sec. 5.1 keeps.  For every element:
+    biased moments m and v, their bias-corrected values, then the parameter step.
+    Returns new (params, m, v) dicts; the inputs are not modified.  ``lr`` is a
+    number or a dict with one learning rate per array."""
+    keys = ("xyz", "quat", "scale", "opacity", "sh")
+    new_p, new_m, new_v = {}, {}, {}
+    for k in keys:
+        rate = float(lr[k]) if isinstance(lr, dict) else float(lr)
+        g = np.asarray(grads[k], np.float64)
+        mk = beta1 * np.asarray(m[k], np.float64) + (1.0 - beta1) * g
+        vk = beta2 * np.asarray(v[k], np.float64) + (1.0 - beta2) * g * g
+        m_hat = mk / (1.0 - beta1 ** step)
+        v_hat = vk / (1.0 - beta2 ** step)
+        new_p[k] = np.asarray(params[k], np.float64) - rate * m_hat / (np.sqrt(v_hat) + eps)
+        new_m[k] = mk
+        new_v[k] = vk
+    return new_p, new_m, new_v

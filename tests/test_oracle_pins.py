@@ -374,3 +374,71 @@ def test_lone_surfel_exact_score_at_centre_pixel():
     g = surfels([0, 0, 0], Q_FACE, [0.1, 0.1], 0.42, [0.5, 0.5, 0.5])
     score = oracle.contribution_score(g, [cam])
     assert score[0] == pytest.approx(0.42, abs=1e-14)
+
+
+# ----------------------------------------------------------------------------- Adam (Kingma & Ba, Algorithm 1)
+def _adam_arrays(rng, n=5, deg=1):
+    shapes = dict(xyz=(n, 3), quat=(n, 4), scale=(n, 2), opacity=(n,), sh=(n, (deg + 1) ** 2, 3))
+    return {k: rng.normal(size=s) for k, s in shapes.items()}, shapes
+
+
+def test_adam_first_step_is_lr_times_sign():
+    """From zero moments the bias corrections give m_hat = g and v_hat = g^2, so the
+    first step moves every element by lr g / (|g| + eps)."""
+    rng = np.random.default_rng(0)
+    p, shapes = _adam_arrays(rng)
+    g, _ = _adam_arrays(rng)
+    z = {k: np.zeros(s) for k, s in shapes.items()}
+    lr = dict(xyz=1e-3, quat=2e-3, scale=5e-3, opacity=5e-2, sh=2.5e-3)
+    eps = 1e-8
+    p1, m1, v1 = oracle.adam_step(p, g, z, z, lr, step=1, beta1=0.9, beta2=0.999, eps=eps)
+    for k in p:
+        np.testing.assert_allclose(p1[k], p[k] - lr[k] * g[k] / (np.abs(g[k]) + eps), rtol=0, atol=1e-15)
+        np.testing.assert_allclose(m1[k], 0.1 * g[k], rtol=1e-14)
+        np.testing.assert_allclose(v1[k], 0.001 * g[k] ** 2, rtol=1e-12)
+
+
+def test_adam_constant_gradient_moves_linearly():
+    """With a constant gradient m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2, so each
+    bias-corrected step is the same lr g / (|g| + eps): after t steps p = p0 - t lr g / (|g| + eps)."""
+    rng = np.random.default_rng(1)
+    p0, shapes = _adam_arrays(rng)
+    g, _ = _adam_arrays(rng)
+    m = {k: np.zeros(s) for k, s in shapes.items()}
+    v = {k: np.zeros(s) for k, s in shapes.items()}
+    p = p0
+    for t in range(1, 8):
+        p, m, v = oracle.adam_step(p, g, m, v, 1e-2, step=t, beta1=0.8, beta2=0.99, eps=1e-12)
+    for k in p:
+        np.testing.assert_allclose(p[k], p0[k] - 7 * 1e-2 * g[k] / (np.abs(g[k]) + 1e-12), rtol=0, atol=1e-12)
+        np.testing.assert_allclose(m[k], (1 - 0.8 ** 7) * g[k], rtol=1e-12)
+
+
+def test_adam_alternating_gradient_second_step():
+    """Gradients g then -g: m_2 = -(1 - b1)^2 g and v_2 = (1 - b2)(1 + b2) g^2, so
+    m_hat = -(1 - b1) g / (1 + b1), v_hat = g^2 and the second step is
+    +lr (1 - b1) / (1 + b1) g / (|g| + eps)  (a swapped b1 / 1 - b1 fails this)."""
+    rng = np.random.default_rng(2)
+    p0, shapes = _adam_arrays(rng)
+    g, _ = _adam_arrays(rng)
+    neg = {k: -x for k, x in g.items()}
+    z = {k: np.zeros(s) for k, s in shapes.items()}
+    b1, b2, lr, eps = 0.7, 0.95, 0.1, 1e-12
+    p1, m1, v1 = oracle.adam_step(p0, g, z, z, lr, 1, b1, b2, eps)
+    p2, m2, v2 = oracle.adam_step(p1, neg, m1, v1, lr, 2, b1, b2, eps)
+    for k in p0:
+        np.testing.assert_allclose(m2[k], -(1 - b1) ** 2 * g[k], rtol=1e-12)
+        np.testing.assert_allclose(v2[k], (1 - b2) * (1 + b2) * g[k] ** 2, rtol=1e-12)
+        step2 = lr * (1 - b1) / (1 + b1) * g[k] / (np.abs(g[k]) + eps)
+        np.testing.assert_allclose(p2[k] - p1[k], step2, rtol=1e-9, atol=1e-15)
+
+
+def test_adam_zero_gradient_keeps_everything():
+    rng = np.random.default_rng(3)
+    p, shapes = _adam_arrays(rng)
+    z = {k: np.zeros(s) for k, s in shapes.items()}
+    p1, m1, v1 = oracle.adam_step(p, z, z, z, 0.5, step=3)
+    for k in p:
+        np.testing.assert_array_equal(p1[k], p[k])
+        np.testing.assert_array_equal(m1[k], 0.0)
+        np.testing.assert_array_equal(v1[k], 0.0)
