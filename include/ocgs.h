@@ -127,7 +127,8 @@ typedef enum {
   OCGS_STAGE_RASTER_BWD = 6,      /* back-to-front adjoint of the compositing */
   OCGS_STAGE_PREPROCESS_BWD = 7,  /* chain rule to the parameters */
   OCGS_STAGE_PRUNE = 8,           /* keep-set and compaction */
-  OCGS_STAGE_COUNT = 9
+  OCGS_STAGE_ADAM = 9,            /* optimiser update of the parameters */
+  OCGS_STAGE_COUNT = 10
 } ocgs_stage;
 
 typedef struct {
@@ -275,6 +276,47 @@ ocgs_status ocgs_graph_destroy(ocgs_ctx* ctx, ocgs_graph* graph);
 ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold,
                        const ocgs_gaussians* in, const ocgs_gaussians_out* out, int64_t* n_kept,
                        int64_t* borderline, int64_t borderline_cap, int64_t* n_borderline);
+
+/*
+ * ocgs_adam_step — one Adam update of every parameter array, in one launch.
+ *
+ * The method trains its surfels with the optimiser of the 2DGS / 3DGS training
+ * it extends (Sec. 5.1 keeps their schedule and coefficients); that optimiser is
+ * Adam (Kingma & Ba, 2015, Algorithm 1), applied elementwise to each array with
+ * its own learning rate:
+ *     m <- beta1 m + (1 - beta1) g          v <- beta2 v + (1 - beta2) g^2
+ *     p <- p - lr * (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)
+ * The update acts on the arrays as given (the API's activated parameters: the
+ * caller owns any re-parameterisation).
+ *   grads   device gradients, read only; grads->n and grads->sh_degree give
+ *           the sizes (n may be 0): xyz [n,3], quat [n,4], scale [n,2],
+ *           opacity [n], sh [n,(deg+1)^2,3]
+ *   params  device, same layout, updated in place
+ *   m, v    device, same layout, first and second moments, updated in place
+ *           (zero before the first step)
+ *   cfg     host: lr[5] per array in the order xyz, quat, scale, opacity, sh;
+ *           beta1, beta2 in [0,1); eps > 0; step t >= 1 (the step being taken).
+ *           Double precision: 1 - beta and the bias corrections are formed in
+ *           double and rounded once to the single-precision factors the
+ *           kernel uses (a float beta2 = 0.999 alone would be 1.3e-5 off in
+ *           1 - beta2).
+ * Arrays of one parameter must not overlap each other.  Any 4-byte alignment is
+ * accepted (16-byte aligned arrays take the vector path).  Non-finite gradients
+ * propagate as in the formula and set the context's status word, which
+ * ocgs_sync reports as OCGS_ERR_NONFINITE (ocgs_render clears it when it
+ * starts).  Asynchronous on the context stream.
+ */
+typedef struct {
+  double lr[5];
+  double beta1;
+  double beta2;
+  double eps;
+  int64_t step;
+} ocgs_adam_config;
+
+ocgs_status ocgs_adam_step(ocgs_ctx* ctx, const ocgs_gaussians* grads, const ocgs_gaussians_out* params,
+                           const ocgs_gaussians_out* m, const ocgs_gaussians_out* v,
+                           const ocgs_adam_config* cfg);
 
 /*
  * ocgs_masked_l1 — the L1 part of the masked photometric loss of Eq. 2,

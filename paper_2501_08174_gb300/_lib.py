@@ -53,11 +53,16 @@ class StateInfo(C.Structure):
 
 
 STAGES = ["preprocess", "depth_sort", "binning", "tile_sort", "raster_fwd", "loss", "raster_bwd",
-          "preprocess_bwd", "prune"]
+          "preprocess_bwd", "prune", "adam"]
 
 
 class TuneResult(C.Structure):
     _fields_ = [("best", Options), ("best_ms", C.c_double), ("n_tried", C.c_int32), ("from_cache", C.c_int32)]
+
+
+class AdamConfig(C.Structure):
+    _fields_ = [("lr", C.c_double * 5), ("beta1", C.c_double), ("beta2", C.c_double), ("eps", C.c_double),
+                ("step", C.c_int64)]
 
 
 class Stats(C.Structure):
@@ -92,6 +97,8 @@ SIGNATURES = {
     "ocgs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(Gaussians),
                              C.POINTER(GaussiansOut), C.POINTER(C.c_int64), C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),
+    "ocgs_adam_step": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(GaussiansOut),
+                                 C.POINTER(GaussiansOut), C.POINTER(GaussiansOut), C.POINTER(AdamConfig)]),
     "ocgs_masked_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
                                  C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
     "ocgs_autotune": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32, C.c_char_p,

@@ -334,6 +334,25 @@ class Rasterizer:
         return kept, border[: min(n_border.value, borderline_cap)], n_border.value
 
 
+    def adam_step(self, params: dict, grads: dict, m: dict, v: dict, lr, step: int,
+                  beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-15):
+        """One fused Adam update (in place) of ``params`` and the moments ``m``, ``v``.
+
+        ``lr`` is one learning rate or a dict with one per parameter array."""
+        self._bind_stream()
+        gs = gaussians_struct(grads, self.device)
+        for name, d in (("params", params), ("m", m), ("v", v)):
+            for k in PARAM_KEYS:
+                if d[k].shape != grads[k].shape or d[k].dtype != torch.float32 or not d[k].is_contiguous() \
+                        or d[k].device != self.device:
+                    raise ValueError(f"{name}[{k}] must be a contiguous float32 {tuple(grads[k].shape)} on {self.device}")
+        outs = [_lib.GaussiansOut(*[_ptr(d[k]) for k in PARAM_KEYS]) for d in (params, m, v)]
+        rates = [float(lr[k]) for k in PARAM_KEYS] if isinstance(lr, dict) else [float(lr)] * 5
+        cfg = _lib.AdamConfig((C.c_double * 5)(*rates), float(beta1), float(beta2), float(eps), int(step))
+        self._call("ocgs_adam_step", self._ctx, C.byref(gs), C.byref(outs[0]), C.byref(outs[1]),
+                   C.byref(outs[2]), C.byref(cfg))
+
+
 class RenderFunction(torch.autograd.Function):
     """Differentiable render of a list of views through libocgs."""
 

@@ -600,7 +600,8 @@ ocgs_status ocgs_sync(ocgs_ctx* ctx) {
   CK(cudaGetLastError());
   if (status & kStatusCapacity)
     return set_err(ctx, OCGS_ERR_CAPACITY, "more (tile, Gaussian) pairs than a captured graph's capacity; re-create it");
-  if (status & kStatusNonFinite) return set_err(ctx, OCGS_ERR_NONFINITE, "non-finite Gaussian parameters");
+  if (status & kStatusNonFinite)
+    return set_err(ctx, OCGS_ERR_NONFINITE, "non-finite Gaussian parameters or optimiser gradients");
   if (status & kStatusTimeout) return set_err(ctx, OCGS_ERR_TIMEOUT, "a bounded device wait gave up");
   return OCGS_OK;
 }
@@ -851,6 +852,53 @@ ocgs_status ocgs_prune(ocgs_ctx* ctx, const float* score, float threshold, const
   const uint32_t* h = reinterpret_cast<const uint32_t*>(ctx->h_scalar);
   *n_kept = h[0];
   *n_borderline = h[1];
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_adam_step(ocgs_ctx* ctx, const ocgs_gaussians* grads, const ocgs_gaussians_out* params,
+                           const ocgs_gaussians_out* m, const ocgs_gaussians_out* v, const ocgs_adam_config* cfg) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!grads || !params || !m || !v || !cfg) return set_err(ctx, OCGS_ERR_ARG, "a required argument is NULL");
+  if (grads->n < 0) return set_err(ctx, OCGS_ERR_ARG, "grads.n < 0");
+  if (grads->sh_degree < 0 || grads->sh_degree > 3) return set_err(ctx, OCGS_ERR_ARG, "sh_degree must be 0..3");
+  if (!(cfg->beta1 >= 0.0 && cfg->beta1 < 1.0 && cfg->beta2 >= 0.0 && cfg->beta2 < 1.0))
+    return set_err(ctx, OCGS_ERR_ARG, "beta1 and beta2 must lie in [0, 1)");
+  if (!(std::isfinite(cfg->eps) && cfg->eps > 0.0 && (float)cfg->eps > 0.f))
+    return set_err(ctx, OCGS_ERR_ARG, "eps must be finite and > 0 in single precision");
+  for (int k = 0; k < 5; ++k)
+    if (!std::isfinite(cfg->lr[k]) || !std::isfinite((float)cfg->lr[k]))
+      return set_err(ctx, OCGS_ERR_ARG, "learning rates must be finite in single precision");
+  if (cfg->step < 1) return set_err(ctx, OCGS_ERR_ARG, "step must be >= 1");
+  if (grads->n == 0) return OCGS_OK;
+  const int64_t n = grads->n;
+  const int64_t K = (int64_t)(grads->sh_degree + 1) * (grads->sh_degree + 1);
+  const float* g[5] = {grads->xyz, grads->quat, grads->scale, grads->opacity, grads->sh};
+  float* p[5] = {params->xyz, params->quat, params->scale, params->opacity, params->sh};
+  float* mm[5] = {m->xyz, m->quat, m->scale, m->opacity, m->sh};
+  float* vv[5] = {v->xyz, v->quat, v->scale, v->opacity, v->sh};
+  const int64_t count[5] = {3 * n, 4 * n, 2 * n, n, 3 * K * n};
+  AdamArgs a;
+  for (int k = 0; k < 5; ++k) {
+    if (!g[k] || !p[k] || !mm[k] || !vv[k]) return set_err(ctx, OCGS_ERR_ARG, "a parameter, gradient or moment pointer is NULL");
+    const uintptr_t all = (uintptr_t)g[k] | (uintptr_t)p[k] | (uintptr_t)mm[k] | (uintptr_t)vv[k];
+    if (all % 4) return set_err(ctx, OCGS_ERR_ARG, "arrays must be 4-byte aligned");
+    a.seg[k] = AdamSeg{p[k], g[k], mm[k], vv[k], count[k], (float)cfg->lr[k], all % 16 == 0 ? 1 : 0};
+  }
+  // bias corrections 1 - beta^t in double, then single precision factors
+  const double bc1 = 1.0 - std::pow(cfg->beta1, (double)cfg->step);
+  const double bc2 = 1.0 - std::pow(cfg->beta2, (double)cfg->step);
+  if (!(bc1 > 0.0 && bc2 > 0.0)) return set_err(ctx, OCGS_ERR_ARG, "bias correction 1 - beta^t is zero");
+  a.beta1 = (float)cfg->beta1;
+  a.beta2 = (float)cfg->beta2;
+  a.one_m_beta1 = (float)(1.0 - cfg->beta1);
+  a.one_m_beta2 = (float)(1.0 - cfg->beta2);
+  a.inv_bc1 = (float)(1.0 / bc1);
+  a.inv_bc2 = (float)(1.0 / bc2);
+  a.eps = (float)cfg->eps;
+  a.status = ctx->d_status;
+  CK(cudaSetDevice(ctx->device));
+  StageTimer t(ctx, OCGS_STAGE_ADAM);
+  CK(launch_adam(a, ctx->sm_count, ctx->stream));
   return OCGS_OK;
 }
 

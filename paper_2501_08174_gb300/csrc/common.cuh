@@ -517,4 +517,21 @@ cudaError_t launch_prune_compact(const GaussPtrs& in, uint32_t n, int sh_degree,
                                  const uint32_t* border_pos, GaussOut out, int64_t* border_idx,
                                  int64_t border_cap, cudaStream_t s);
 
+// Adam (adam.cu): one segment per parameter array
+struct AdamSeg {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  int64_t count;  // floats
+  float lr;
+  int vector;     // all four pointers 16-byte aligned
+};
+struct AdamArgs {
+  AdamSeg seg[5];
+  float beta1, beta2, one_m_beta1, one_m_beta2, inv_bc1, inv_bc2, eps;
+  int* status;
+};
+cudaError_t launch_adam(const AdamArgs& a, int sm_count, cudaStream_t s);
+
 }  // namespace ocgs
