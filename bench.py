@@ -11,7 +11,12 @@ uneven resolution (640x480 / 800x800 / 1024x768 / 1600x1200), synthetic and
 seeded.  The metric is pixels per second of the step (Mpix/s), batched (all
 16 views in one pass) and per view (16 passes of one view).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload c4|c5]
+
+--workload c5 times the full training iteration instead: 1M surfels seen by
+64 views of 1600x1200, the same losses and backward, a fused Adam update of
+every parameter array and the pruning of the parameters and of both Adam
+moments with the same keep-set.
 
 prints one JSON line (rank 0).  With --impl reference the FP64 CPU oracle is
 timed instead, on a bounded pixel sample of the same workload.
@@ -35,7 +40,13 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "fwd+bwd Mpix/s at 500k surfels, batched vs per-view; % of HBM roofline"
+METRIC_C5 = "training-iteration Mpix/s at 1M surfels x 64 views (fwd+bwd, L_b, pruning, Adam)"
 UNIT = "Mpix/s"
+# Adam learning rates of the c5 iteration: the 3DGS defaults per array scaled by
+# 1e-3, so that the timed scene stays stationary over the timed steps (the
+# update does the same work at any rate; the parameters here are the activated
+# values, which the default rates would push out of range within a few steps)
+ADAM_LR = dict(xyz=1.6e-7, quat=1e-6, scale=5e-6, opacity=5e-5, sh=2.5e-6)
 GAMMA = 0.5      # background-loss weight (Sec. 5.1)
 TAU = 0.01       # pruning threshold of the sweep configuration
 # FP32 operations per evaluated (pixel, Gaussian) pair, counted from the kernels'
@@ -51,8 +62,11 @@ def parse_args():
     p.add_argument("--steps", type=int, default=10)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--n", type=int, default=500_000, help="surfels")
-    p.add_argument("--views", type=int, default=16)
+    p.add_argument("--workload", choices=("c4", "c5"), default="c4",
+                   help="c4: 500k surfels x 16 uneven views (the metric's workload); "
+                        "c5: training iteration, 1M surfels x 64 views 1600x1200 with Adam")
+    p.add_argument("--n", type=int, default=None, help="surfels (default 500k for c4, 1M for c5)")
+    p.add_argument("--views", type=int, default=None, help="views (default 16 for c4, 64 for c5)")
     p.add_argument("--tile", default="16x16")
     p.add_argument("--persistent", type=int, default=1)
     p.add_argument("--ppt", type=int, default=4, help="pixels per thread")
@@ -60,12 +74,25 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=384, help="pixels of the oracle's timed sample")
-    return p.parse_args()
+    a = p.parse_args()
+    if a.n is None:
+        a.n = 1_000_000 if a.workload == "c5" else 500_000
+    if a.views is None:
+        a.views = 64 if a.workload == "c5" else 16
+    return a
 
 
 def workload_name(a) -> str:
+    if a.workload == "c5":
+        return (f"object-centric 2DGS training iteration: {a.n} surfels SH3 (60% object ball r=0.8, 40% shell "
+                f"r=2-4), {a.views} hemisphere views 1600x1200 with object masks, masked L1 + 0.5 L_b, fwd+bwd, "
+                f"Adam on all parameters, prune of parameters and moments at tau={TAU}")
     return (f"object-centric 2DGS training step: {a.n} surfels SH3 (70% object ball r=0.8, 30% shell r=2-4), "
             f"{a.views} hemisphere views of uneven resolution, masked L1 + 0.5 L_b, fwd+bwd, prune tau={TAU}")
+
+
+def metric_name(a) -> str:
+    return METRIC if a.workload == "c4" else METRIC_C5
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -196,7 +223,8 @@ def measured_traffic(kernel: str, workload_args: str):
 
 
 # ----------------------------------------------------------------------------- roofline model
-def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile_passes: int, kept: int) -> dict:
+def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile_passes: int, kept: int,
+                prune_calls: int = 1) -> dict:
     """Minimum HBM bytes (and FP32 flops) of each stage for one step."""
     VN = V * N
     b = {
@@ -208,7 +236,8 @@ def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile
         "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24),
         "raster_bwd": VN * (72 + 80) + K * 4 + P * 40,
         "preprocess_bwd": N * 232 * 3 + VN * 84,
-        "prune": N * 24 + kept * 232 * 2,
+        "prune": prune_calls * (N * 24 + kept * 232 * 2),
+        "adam": N * 232 * 7,  # parameters, gradients, m, v read; parameters, m, v written
     }[stage]
     f = {"raster_fwd": E * FLOPS_FWD, "raster_bwd": E * FLOPS_BWD}.get(stage, 0)
     return {"bytes": b, "flops": f}
@@ -242,7 +271,7 @@ def run_reference(a, rank: int, world: int):
         return
     import synthetic
     import torch
-    sc = synthetic.config4(n=a.n, n_views=a.views)
+    sc = synthetic.config5(n=a.n, n_views=a.views) if a.workload == "c5" else synthetic.config4(n=a.n, n_views=a.views)
     n_pix = max(16, a.cpu_sample // 6)
     times = []
     for i in range(a.warmup + a.steps):
@@ -256,7 +285,7 @@ def run_reference(a, rank: int, world: int):
     ms = 1e3 * sum(times) / len(times)
     value = n_pix / (ms / 1e3) / 1e6
     cores = torch.get_num_threads()
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+    line = {"impl": "reference", "metric": metric_name(a), "value": value, "unit": UNIT, "n_gpus": a.gpus,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(a), "sample": f"{n_pix} pixels of one view per step"},
@@ -270,11 +299,16 @@ def run_reference(a, rank: int, world: int):
 class TrainingStep:
     """One training step through the library (all arithmetic in libocgs kernels)."""
 
-    def __init__(self, rast, g, cams, target, mask, per_view: bool):
+    def __init__(self, rast, g, cams, target, mask, per_view: bool, adam: bool = False):
         import torch
         from paper_2501_08174_gb300 import pixel_offsets
         self.rast, self.g, self.cams, self.target, self.mask = rast, g, cams, target, mask
         self.per_view = per_view
+        self.adam = adam
+        self.t = 0
+        if adam:
+            self.m = {k: torch.zeros_like(v) for k, v in g.items()}
+            self.v = {k: torch.zeros_like(v) for k, v in g.items()}
         self.off = pixel_offsets(cams)
         P = self.off[-1]
         dev = g["xyz"].device
@@ -312,7 +346,13 @@ class TrainingStep:
             l1, lb = self._views(self.cams, 0, self.off[-1])
             self.loss[0].copy_(l1)
             self.loss[1].copy_(lb)
+        if self.adam:
+            self.t += 1
+            self.rast.adam_step(self.g, self.grads, self.m, self.v, ADAM_LR, step=self.t)
         kept, _, _ = self.rast.prune(self.g, self.score, TAU)
+        if self.adam:  # the moments follow the parameters through the keep-set
+            self.rast.prune(self.m, self.score, TAU)
+            self.rast.prune(self.v, self.score, TAU)
         self.kept = kept["xyz"].shape[0]
 
 
@@ -355,7 +395,10 @@ def run_ours(a, rank: int, world: int, local: int):
     out_dir = os.path.join(ROOT, "gpurun_out")
     os.makedirs(out_dir, exist_ok=True)
 
-    sc = synthetic.config4(seed=4 + rank, n=a.n, n_views=a.views)
+    if a.workload == "c5":
+        sc = synthetic.config5(seed=5 + rank, n=a.n, n_views=a.views)
+    else:
+        sc = synthetic.config4(seed=4 + rank, n=a.n, n_views=a.views)
     cams = sc["cameras"]
     P = n_pixels(cams)
     P_job = int(sum_over_ranks(P, world, dev))  # pixels of one step over all replicas
@@ -379,7 +422,8 @@ def run_ours(a, rank: int, world: int, local: int):
     tile_passes = (tile_bits + 7) // 8
 
     # batched step, with the library's stage timers on
-    step = TrainingStep(rast, g, cams, target, mask, per_view=False)
+    adam = a.workload == "c5"
+    step = TrainingStep(rast, g, cams, target, mask, per_view=False, adam=adam)
     for _ in range(a.warmup):
         step()
     rast.profile(True)
@@ -392,7 +436,7 @@ def run_ours(a, rank: int, world: int, local: int):
 
     per_view = None
     if not a.no_per_view:
-        pstep = TrainingStep(rast, g, cams, target, mask, per_view=True)
+        pstep = TrainingStep(rast, g, cams, target, mask, per_view=True, adam=adam)
         pms, pwall, _ = timed(pstep, a.steps, a.warmup, world, dev)
         per_view = {"ms_per_step": pms, "value": P_job / (pms / 1e3) / 1e6,
                     "launch_sets": len(cams), "batched_speedup": pms / ms}
@@ -403,7 +447,7 @@ def run_ours(a, rank: int, world: int, local: int):
     stages = {}
     step_bytes = 0
     for name, (tot_ms, cnt) in prof.items():
-        alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept)
+        alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1)
         step_bytes += alg["bytes"]
         per_ms = tot_ms / a.steps
         stages[name] = {"ms": per_ms, "launch_sets": cnt / a.steps,
@@ -412,7 +456,7 @@ def run_ours(a, rank: int, world: int, local: int):
     dom = max(stages, key=lambda k: stages[k]["ms"])
     dstage = stages[dom]
     per_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
-    alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept)
+    alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1)
     stage_kernel = {"raster_fwd": "raster_fwd_kernel", "raster_bwd": "raster_bwd_kernel",
                     "preprocess": "preprocess_kernel", "preprocess_bwd": "preprocess_bwd_kernel"}
     traffic = None
@@ -461,7 +505,7 @@ def run_ours(a, rank: int, world: int, local: int):
         cpu = time_oracle(sc, a.cpu_sample)
 
     if rank == 0:
-        line = {"metric": METRIC, "value": P_job / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+        line = {"metric": metric_name(a), "value": P_job / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_name(a), "mode": "batched (one pass over all views)",
