@@ -293,8 +293,6 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   uint32_t *dkey, *order, *dkey_alt, *order_alt;
   uint64_t* counts;
   CK(tmp.alloc(&rect, VN));
-  uint64_t* roff;
-  CK(tmp.alloc(&roff, VN));
   CK(tmp.alloc(&dkey, VN));
   CK(tmp.alloc(&order, VN));
   CK(tmp.alloc(&dkey_alt, VN));
@@ -346,8 +344,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_duplicate(sorted, counts, roff, VN, st->ntiles, rect, st->rec, st->d_cams, N, tw, th, K, pkey, pval,
-                        s));
+    CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), VN, rect, st->rec,
+                        st->d_cams, N, tw, th, K, pkey, pval, s));
   }
   const int tbits = bits_for((uint64_t)pl.tiles);
   bool palt = false;
@@ -424,7 +422,7 @@ struct SweepWs {
   uint2* ranges = nullptr;
   int4* rect = nullptr;
   uint32_t *dkey = nullptr, *order = nullptr, *dkey_alt = nullptr, *order_alt = nullptr;
-  uint64_t *counts = nullptr, *roff = nullptr, *total = nullptr;
+  uint64_t *counts = nullptr, *total = nullptr;
   uint32_t* n32 = nullptr;
   char *scratch = nullptr, *pscratch = nullptr, *tscratch = nullptr;
   uint32_t *pkey = nullptr, *pval = nullptr, *pkey_alt = nullptr, *pval_alt = nullptr;
@@ -445,7 +443,7 @@ cudaError_t alloc_sweep_ws(Arena& a, SweepWs& w, uint32_t vn_max, int64_t tiles_
   OCGS_A(w.rec.a0, vn_max); OCGS_A(w.rec.a1, vn_max);
   OCGS_A(w.ntiles, vn_max); OCGS_A(w.ranges, tiles_max); OCGS_A(w.rect, vn_max);
   OCGS_A(w.dkey, vn_max); OCGS_A(w.order, vn_max); OCGS_A(w.dkey_alt, vn_max); OCGS_A(w.order_alt, vn_max);
-  OCGS_A(w.counts, vn_max); OCGS_A(w.roff, vn_max); OCGS_A(w.total, 1); OCGS_A(w.n32, 1);
+  OCGS_A(w.counts, vn_max); OCGS_A(w.total, 1); OCGS_A(w.n32, 1);
   OCGS_A(w.scratch, std::max(radix_scratch_bytes(vn_max), scan_scratch_bytes(vn_max)));
   OCGS_A(w.pkey, cap); OCGS_A(w.pval, cap); OCGS_A(w.pkey_alt, cap); OCGS_A(w.pval_alt, cap);
   OCGS_A(w.pscratch, radix_scratch_bytes(cap));
@@ -475,8 +473,7 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
   CK(launch_gather_counts(sorted, w.ntiles, w.counts, VN, s));
   CK(scan_exclusive_u64(w.counts, w.counts, VN, w.total, w.scratch, s));
   CK(launch_clamp_count(w.total, w.cap, w.n32, ctx->d_status, s));
-  CK(launch_duplicate(sorted, w.counts, w.roff, VN, w.ntiles, w.rect, w.rec, d_cams, N, tw, th, w.cap, w.pkey,
-                      w.pval, s));
+  CK(launch_duplicate(sorted, w.counts, w.total, VN, w.rect, w.rec, d_cams, N, tw, th, w.cap, w.pkey, w.pval, s));
   bool palt = false;
   CK(radix_sort_pairs(w.pkey, w.pval, w.pkey_alt, w.pval_alt, w.cap, bits_for((uint64_t)n_tiles), w.pscratch, &palt,
                       s, w.n32));

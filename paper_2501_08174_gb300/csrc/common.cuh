@@ -447,12 +447,12 @@ cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s);
 cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
                               uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* depth_key,
                               cudaStream_t s);
-// write the (tile, record) pairs: offsets are the scanned counts in depth order
-// (order), scattered to record order in roff [n_rec] first
-cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint64_t* roff, uint32_t n_rec,
-                             const int32_t* ntiles, const int4* rect, const RecPtrs rec, const DevCam* cams,
-                             int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs, uint32_t* keys,
-                             uint32_t* vals, cudaStream_t s);
+// write the (tile, record) pairs in depth order: offsets [n_rec] are the
+// exclusive scan of the tile counts taken in depth order (order), total their
+// sum (device); pairs at or past n_pairs are dropped
+cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, const uint64_t* total, uint32_t n_rec,
+                             const int4* rect, const RecPtrs rec, const DevCam* cams, int64_t n_gauss, int tile_w,
+                             int tile_h, uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s,
                                const uint32_t* d_n = nullptr);
 // n32 = min(*total, cap); raises kStatusCapacity when *total > cap

@@ -303,13 +303,6 @@ __global__ void __launch_bounds__(kThreads) tile_count_kernel(const RecPtrs rec,
   if (cnt == 0) depth_key[r] = 0xffffffffu;
 }
 
-// roff[order[i]] = offsets[i]: each record's first pair slot, in record order.
-__global__ void scatter_offsets_kernel(const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets,
-                                       uint32_t n, uint64_t* __restrict__ roff) {
-  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) roff[order[i]] = offsets[i];
-}
-
 __device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
                                                uint64_t stop, uint32_t* __restrict__ keys,
                                                uint32_t* __restrict__ vals) {
@@ -320,33 +313,41 @@ __device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowba
   return pos;
 }
 
-// The same rows again, in record order, writing each record's tiles from its
-// first pair slot (rows in order, tiles left to right).  Each lane computes
-// the row runs of its record when it is small; the warp then writes all the
-// small records' tiles as one flat list, 32 tiles per step, so the stores are
-// balanced over the lanes and contiguous within a record.  The rows of a
-// large record are shared out over the warp, with a warp scan of the row
-// counts for the positions.
+// The (tile, record) pairs, written in depth order: entry i of the depth
+// order (record order[i]) writes its tiles from offsets[i] on, rows in order
+// and tiles left to right, so the runs of consecutive entries are adjacent and
+// a warp's stores are contiguous.  A lane computes the row runs of its entry
+// when it spans few rows; the warp then writes all those entries' tiles as one
+// flat list, 32 consecutive slots per step.  The rows of an entry with many
+// rows are shared out over the warp, with a warp scan of the row counts.
 constexpr int kWarpsPerBlock = kThreads / 32;
 
 __global__ void __launch_bounds__(kThreads) duplicate_kernel(
-    const uint64_t* __restrict__ roff, const int32_t* __restrict__ ntiles, uint32_t n_rec,
-    const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams, int64_t n_gauss, int tw,
-    int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  __shared__ short4 s_runs[kWarpsPerBlock][32][kSmallRows];  // tile runs of each row (tile indices < 2^15)
+    const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
+    uint32_t n_rec, const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams,
+    int64_t n_gauss, int tw, int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  __shared__ short4 s_runs[kWarpsPerBlock][kSmallRows][32];  // [row][lane]: lanes in distinct banks
   __shared__ int s_incl[kWarpsPerBlock][32];
+  __shared__ uint32_t s_rowbase[kWarpsPerBlock][32];  // tile id of (first row, column 0)
+  __shared__ uint32_t s_tilesx[kWarpsPerBlock][32];
+  __shared__ uint32_t s_pos[kWarpsPerBlock][32];
+  __shared__ uint32_t s_rec[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
-  const uint32_t rbase = r - lane;
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  uint32_t r = 0;
   int cnt = 0;
   int4 rc = make_int4(0, 0, -1, -1);
   uint64_t o = 0;
-  if (r < n_rec) {
-    cnt = ntiles[r];
-    if (cnt > 0) {
-      rc = rect[r];
-      o = roff[r];
-    }
+  if (i < n_rec) {
+    o = offsets[i];
+    r = order[i];
+  }
+  // this entry's count: the next entry's offset (or the total) minus its own
+  uint64_t o_next = __shfl_down_sync(kFull, o, 1);
+  if (lane == 31 || i + 1 >= n_rec) o_next = (i + 1 < n_rec) ? offsets[i + 1] : *total;
+  if (i < n_rec && o < (uint64_t)n_pairs) {  // entries past a capacity write nothing
+    cnt = (int)(o_next - o);
+    if (cnt > 0) rc = rect[r];
   }
   const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
@@ -355,10 +356,14 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      s_runs[warp][lane][ty - rc.y] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
+      s_runs[warp][ty - rc.y][lane] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
     }
+    s_rowbase[warp][lane] = (uint32_t)(cam.tile_offset + rc.y * cam.tiles_x);
+    s_tilesx[warp][lane] = (uint32_t)cam.tiles_x;
+    s_pos[warp][lane] = (uint32_t)o;
+    s_rec[warp][lane] = r;
   }
-  // flat walk over the small records' tiles
+  // flat walk over the small entries' tiles
   const int scnt = small ? cnt : 0;
   int incl = scnt;
 #pragma unroll
@@ -367,35 +372,32 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     if (lane >= d) incl += t;
   }
   s_incl[warp][lane] = incl;
-  const int total = __shfl_sync(kFull, incl, 31);
+  const int all = __shfl_sync(kFull, incl, 31);
   __syncwarp();
-  for (int q0 = 0; q0 < total; q0 += 32) {
+  for (int q0 = 0; q0 < all; q0 += 32) {
     const int q = q0 + lane;
-    if (q < total) {
+    if (q < all) {
       int lo = 0, hi = 31;
       while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         if (s_incl[warp][mid] > q) hi = mid; else lo = mid + 1;
       }
       const int ri = lo;
-      const uint32_t rr = rbase + (uint32_t)ri;
-      const int excl = ri > 0 ? s_incl[warp][ri - 1] : 0;  // tiles of the warp's earlier small records
+      const int excl = ri > 0 ? s_incl[warp][ri - 1] : 0;  // tiles of the warp's earlier small entries
       int kth = q - excl;
-      const int4 bc = rect[rr];
-      const DevCam& cam = cams[rr / (uint64_t)n_gauss];
-      int tx = -1, ty = bc.y;
-      for (int row = 0; row <= bc.w - bc.y; ++row) {
-        const short4 ru = s_runs[warp][ri][row];
+      int tx = -1, row = 0;
+      for (; row < kSmallRows; ++row) {
+        const short4 ru = s_runs[warp][row][ri];
         const int la = max(0, (int)ru.y - (int)ru.x + 1), lb = max(0, (int)ru.w - (int)ru.z + 1);
-        if (kth < la) { tx = ru.x + kth; ty = bc.y + row; break; }
+        if (kth < la) { tx = ru.x + kth; break; }
         kth -= la;
-        if (kth < lb) { tx = ru.z + kth; ty = bc.y + row; break; }
+        if (kth < lb) { tx = ru.z + kth; break; }
         kth -= lb;
       }
-      const uint64_t pos = roff[rr] + (uint64_t)(q - excl);
+      const uint32_t pos = s_pos[warp][ri] + (uint32_t)(q - excl);
       if (tx >= 0 && pos < n_pairs) {
-        keys[pos] = (uint32_t)(cam.tile_offset + ty * cam.tiles_x + tx);
-        vals[pos] = rr;
+        keys[pos] = s_rowbase[warp][ri] + (uint32_t)row * s_tilesx[warp][ri] + (uint32_t)tx;
+        vals[pos] = s_rec[warp][ri];
       }
     }
   }
@@ -528,17 +530,13 @@ cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam*
   return launched();
 }
 
-cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, uint64_t* roff, uint32_t n_rec,
-                             const int32_t* ntiles, const int4* rect, const RecPtrs rec, const DevCam* cams,
-                             int64_t n_gauss, int tile_w, int tile_h, uint32_t n_pairs, uint32_t* keys,
-                             uint32_t* vals, cudaStream_t s) {
+cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, const uint64_t* total, uint32_t n_rec,
+                             const int4* rect, const RecPtrs rec, const DevCam* cams, int64_t n_gauss, int tile_w,
+                             int tile_h, uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
-  scatter_offsets_kernel<<<(n_rec + 255) / 256, 256, 0, s>>>(order, offsets, n_rec, roff);
-  cudaError_t e = launched();
-  if (e != cudaSuccess) return e;
-  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(roff, ntiles, n_rec, rect, rec, cams,
-                                                                          n_gauss, tile_w, tile_h, n_pairs, keys,
-                                                                          vals);
+  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, offsets, total, n_rec, rect, rec,
+                                                                          cams, n_gauss, tile_w, tile_h, n_pairs,
+                                                                          keys, vals);
   return launched();
 }
 
