@@ -436,14 +436,39 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
   }
 }
 
+// [start, end) of every tile in the sorted keys: each thread takes 4
+// consecutive keys with one 16-byte load and finds their neighbours across
+// lanes with shuffles (the warp's two outer neighbours come from memory).
 __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint32_t n, uint2* __restrict__ ranges,
                                    const uint32_t* __restrict__ d_n) {
   if (d_n) n = min(n, *d_n);
-  const uint32_t k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
-  const uint32_t t = keys[k];
-  if (k == 0 || keys[k - 1] != t) ranges[t].x = k;
-  if (k == n - 1 || keys[k + 1] != t) ranges[t].y = k + 1;
+  const int lane = threadIdx.x & 31;
+  const uint32_t groups = (n + 3) / 4;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < groups; base += gridDim.x * blockDim.x) {
+    const uint32_t i0 = (base + threadIdx.x) * 4;
+    uint32_t k[4];
+    if (i0 + 3 < n) {
+      const uint4 v = *reinterpret_cast<const uint4*>(keys + i0);
+      k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) k[j] = i0 + j < n ? keys[i0 + j] : 0xffffffffu;
+    }
+    uint32_t prev = __shfl_up_sync(kFull, k[3], 1);
+    uint32_t next = __shfl_down_sync(kFull, k[0], 1);
+    if (lane == 0 && i0 > 0 && i0 <= n) prev = keys[i0 - 1];
+    if (lane == 31 && i0 + 4 < n) next = keys[i0 + 4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const uint32_t idx = i0 + j;
+      if (idx < n) {
+        const uint32_t p = j ? k[j - 1] : prev;
+        const uint32_t q = j < 3 ? k[j + 1] : next;
+        if (idx == 0 || p != k[j]) ranges[k[j]].x = idx;
+        if (idx == n - 1 || q != k[j]) ranges[k[j]].y = idx + 1;
+      }
+    }
+  }
 }
 
 // work key for the persistent queue: heaviest tiles first (descending pair count)
@@ -543,7 +568,8 @@ cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, con
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s,
                                const uint32_t* d_n) {
   if (n_pairs == 0) return cudaSuccess;
-  tile_ranges_kernel<<<(n_pairs + 255) / 256, 256, 0, s>>>(keys, n_pairs, ranges, d_n);
+  const uint32_t blocks = (n_pairs / 4 + 256) / 256;
+  tile_ranges_kernel<<<blocks < 152u * 16u ? blocks : 152u * 16u, 256, 0, s>>>(keys, n_pairs, ranges, d_n);
   return launched();
 }
 
