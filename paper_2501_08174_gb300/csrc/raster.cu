@@ -148,27 +148,29 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             h.pass[1] = h.pass[1] && !done[k1];
             if (!(h.pass[0] || h.pass[1])) continue;
             const SplatEval2 e = splat_tail2<false>(g0, g2, h, rb);
-            const float2 Tn = __fmul2_rn(T[p], __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
-            const float2 w = __fmul2_rn(e.alpha, T[p]);
-            // an entry that would take T below kTEps ends the pixel unblended
-            const bool end0 = e.ok[0] && Tn.x < kTEps, end1 = e.ok[1] && Tn.y < kTEps;
-            const bool bl0 = e.ok[0] && !end0, bl1 = e.ok[1] && !end1;
-            done[k0] = done[k0] || end0;
-            done[k1] = done[k1] || end1;
-            const float2 wm = make_float2(bl0 ? w.x : 0.f, bl1 ? w.y : 0.f);
-            if (IMG) {
-              c0[p] = __ffma2_rn(wm, bc2(ap.x), c0[p]);
-              c1[p] = __ffma2_rn(wm, bc2(ap.y), c1[p]);
-              c2[p] = __ffma2_rn(wm, bc2(ap.z), c2[p]);
-              dep[p] = __ffma2_rn(wm, e.z, dep[p]);
-              n0[p] = __ffma2_rn(wm, bc2(ap.w), n0[p]);
-              n1[p] = __ffma2_rn(wm, bc2(an.x), n1[p]);
-              n2[p] = __ffma2_rn(wm, bc2(an.y), n2[p]);
+            // lanes that do not blend take alpha 0: T (1 - 0) = T and w = 0 exactly
+            const float2 a2 = make_float2(e.ok[0] ? e.alpha.x : 0.f, e.ok[1] ? e.alpha.y : 0.f);
+            float2 Tn = __fmul2_rn(T[p], __ffma2_rn(a2, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
+            float2 w = __fmul2_rn(a2, T[p]);
+            const uint32_t l0 = last[k0], l1 = last[k1];
+            if (e.ok[0]) last[k0] = pos;
+            if (e.ok[1]) last[k1] = pos;
+            if (Tn.x < kTEps || Tn.y < kTEps) {
+              // rare: an entry that would take T below kTEps ends the pixel unblended
+              if (Tn.x < kTEps) { done[k0] = true; w.x = 0.f; Tn.x = T[p].x; last[k0] = l0; }
+              if (Tn.y < kTEps) { done[k1] = true; w.y = 0.f; Tn.y = T[p].y; last[k1] = l1; }
             }
-            T[p] = make_float2(bl0 ? Tn.x : T[p].x, bl1 ? Tn.y : T[p].y);
-            if (bl0) last[k0] = pos;
-            if (bl1) last[k1] = pos;
-            wmax = fmaxf(wmax, fmaxf(wm.x, wm.y));
+            if (IMG) {
+              c0[p] = __ffma2_rn(w, bc2(ap.x), c0[p]);
+              c1[p] = __ffma2_rn(w, bc2(ap.y), c1[p]);
+              c2[p] = __ffma2_rn(w, bc2(ap.z), c2[p]);
+              dep[p] = __ffma2_rn(w, e.z, dep[p]);
+              n0[p] = __ffma2_rn(w, bc2(ap.w), n0[p]);
+              n1[p] = __ffma2_rn(w, bc2(an.x), n1[p]);
+              n2[p] = __ffma2_rn(w, bc2(an.y), n2[p]);
+            }
+            T[p] = Tn;
+            wmax = fmaxf(wmax, fmaxf(w.x, w.y));
           }
           alldone = true;
 #pragma unroll
