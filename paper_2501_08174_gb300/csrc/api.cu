@@ -289,10 +289,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(keep.alloc(&st->ranges, pl.tiles));
   CK(keep.alloc(&st->t_final, keep_state ? pl.P : 1));
   CK(keep.alloc(&st->last, keep_state ? pl.P : 1));
-  int4* rect;
+  float4* bin;
   uint32_t *dkey, *order, *dkey_alt, *order_alt;
   uint64_t* counts;
-  CK(tmp.alloc(&rect, VN));
+  CK(tmp.alloc(&bin, 3 * (size_t)VN));
   CK(tmp.alloc(&dkey, VN));
   CK(tmp.alloc(&order, VN));
   CK(tmp.alloc(&dkey_alt, VN));
@@ -306,12 +306,12 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
 
   {
     StageTimer t(ctx, OCGS_STAGE_PREPROCESS);
-    CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, rect, dkey,
+    CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, bin, dkey,
                          ctx->d_status, s));
   }
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_tile_count(st->rec, rect, st->d_cams, N, VN, tw, th, st->ntiles, dkey, s));
+    CK(launch_tile_count(bin, st->d_cams, N, VN, tw, th, st->ntiles, dkey, s));
   }
   bool alt = false;
   {
@@ -344,8 +344,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), VN, rect, st->rec,
-                        st->d_cams, N, tw, th, K, pkey, pval, s));
+    CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), VN, bin, st->d_cams,
+                        N, tw, th, K, pkey, pval, s));
   }
   const int tbits = bits_for((uint64_t)pl.tiles);
   bool palt = false;
@@ -420,7 +420,7 @@ struct SweepWs {
   RecPtrs rec{};
   int32_t* ntiles = nullptr;
   uint2* ranges = nullptr;
-  int4* rect = nullptr;
+  float4* bin = nullptr;
   uint32_t *dkey = nullptr, *order = nullptr, *dkey_alt = nullptr, *order_alt = nullptr;
   uint64_t *counts = nullptr, *total = nullptr;
   uint32_t* n32 = nullptr;
@@ -441,7 +441,7 @@ cudaError_t alloc_sweep_ws(Arena& a, SweepWs& w, uint32_t vn_max, int64_t tiles_
 #define OCGS_A(ptr, n) if (e == cudaSuccess) e = a.alloc(&(ptr), (size_t)(n))
   OCGS_A(w.rec.g0, vn_max); OCGS_A(w.rec.g1, vn_max); OCGS_A(w.rec.g2, vn_max);
   OCGS_A(w.rec.a0, vn_max); OCGS_A(w.rec.a1, vn_max);
-  OCGS_A(w.ntiles, vn_max); OCGS_A(w.ranges, tiles_max); OCGS_A(w.rect, vn_max);
+  OCGS_A(w.ntiles, vn_max); OCGS_A(w.ranges, tiles_max); OCGS_A(w.bin, 3 * (size_t)vn_max);
   OCGS_A(w.dkey, vn_max); OCGS_A(w.order, vn_max); OCGS_A(w.dkey_alt, vn_max); OCGS_A(w.order_alt, vn_max);
   OCGS_A(w.counts, vn_max); OCGS_A(w.total, 1); OCGS_A(w.n32, 1);
   OCGS_A(w.scratch, std::max(radix_scratch_bytes(vn_max), scan_scratch_bytes(vn_max)));
@@ -463,9 +463,9 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
   const int64_t N = g->n;
   const uint32_t VN = (uint32_t)(N * V);
   CK(cudaMemsetAsync(w.ranges, 0, sizeof(uint2) * n_tiles, s));
-  CK(launch_preprocess(gptrs(g), N, g->sh_degree, d_cams, V, tw, th, w.rec, w.ntiles, w.rect, w.dkey, ctx->d_status,
+  CK(launch_preprocess(gptrs(g), N, g->sh_degree, d_cams, V, tw, th, w.rec, w.ntiles, w.bin, w.dkey, ctx->d_status,
                        s));
-  CK(launch_tile_count(w.rec, w.rect, d_cams, N, VN, tw, th, w.ntiles, w.dkey, s));
+  CK(launch_tile_count(w.bin, d_cams, N, VN, tw, th, w.ntiles, w.dkey, s));
   CK(launch_iota(w.order, VN, s));
   bool alt = false;
   CK(radix_sort_pairs(w.dkey, w.order, w.dkey_alt, w.order_alt, VN, 32, w.scratch, &alt, s));
@@ -473,7 +473,7 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
   CK(launch_gather_counts(sorted, w.ntiles, w.counts, VN, s));
   CK(scan_exclusive_u64(w.counts, w.counts, VN, w.total, w.scratch, s));
   CK(launch_clamp_count(w.total, w.cap, w.n32, ctx->d_status, s));
-  CK(launch_duplicate(sorted, w.counts, w.total, VN, w.rect, w.rec, d_cams, N, tw, th, w.cap, w.pkey, w.pval, s));
+  CK(launch_duplicate(sorted, w.counts, w.total, VN, w.bin, d_cams, N, tw, th, w.cap, w.pkey, w.pval, s));
   bool palt = false;
   CK(radix_sort_pairs(w.pkey, w.pval, w.pkey_alt, w.pval_alt, w.cap, bits_for((uint64_t)n_tiles), w.pscratch, &palt,
                       s, w.n32));

@@ -391,6 +391,35 @@ __device__ __forceinline__ RowRuns row_runs(const SupportConic& k, int ty, int t
   return r;
 }
 
+// Binning record of one (view, surfel), 48 contiguous bytes (3 float4) so that
+// the depth-ordered gather of the binning fetches one span per record:
+//   b0 = (cx, cy, rb, A00), b1 = (A01, A10, A11, e0),
+//   b2 = (e1, e2, rect x | y << 16, rect z | w << 16)   (tile rect as int16)
+// with rb = support_rho(o), the bound the rasterizers derive from the opacity.
+struct BinView {
+  float4 g0, g1, g2;  // centre / matrix / denominator terms as the record keeps them
+  float rb;
+  int4 rc;
+};
+
+__device__ __forceinline__ uint32_t pack_i16x2(int lo, int hi) {
+  return (uint32_t)(uint16_t)(int16_t)lo | ((uint32_t)(uint16_t)(int16_t)hi << 16);
+}
+
+__device__ __forceinline__ BinView load_bin(const float4* __restrict__ bin, uint32_t r) {
+  const float4* p = bin + 3 * (size_t)r;
+  const float4 b0 = p[0], b1 = p[1], b2 = p[2];
+  BinView v;
+  v.g0 = make_float4(b0.x, b0.y, 0.f, 0.f);
+  v.g1 = make_float4(b0.w, b1.x, b1.y, b1.z);
+  v.g2 = make_float4(b1.w, b2.x, b2.y, 0.f);
+  v.rb = b0.z;
+  const uint32_t xy = __float_as_uint(b2.z), zw = __float_as_uint(b2.w);
+  v.rc = make_int4((int)(int16_t)(xy & 0xffffu), (int)(int16_t)(xy >> 16), (int)(int16_t)(zw & 0xffffu),
+                   (int)(int16_t)(zw >> 16));
+  return v;
+}
+
 // first global tile id -> view, by binary search over V+1 prefix offsets
 __device__ __forceinline__ int view_of_tile(const int* tile_prefix, int n_views, int tile) {
   int lo = 0, hi = n_views - 1;
@@ -415,7 +444,7 @@ inline cudaError_t launched() {
 
 cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams,
                               int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
-                              int4* rect, uint32_t* depth_key, int* status, cudaStream_t s);
+                              float4* bin, uint32_t* depth_key, int* status, cudaStream_t s);
 
 cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
                                        const DevCam* cams, int n_views, const float* grad_rec,
@@ -444,15 +473,14 @@ cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s);
 // exact tile counts: ntiles[r] = tiles of rect[r] the record's support reaches
 // (row_runs); a record with none gets depth key 0xffffffff so that it sorts to
 // the tail
-cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
-                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* depth_key,
-                              cudaStream_t s);
+cudaError_t launch_tile_count(const float4* bin, const DevCam* cams, int64_t n_gauss, uint32_t n_rec, int tile_w,
+                              int tile_h, int32_t* ntiles, uint32_t* depth_key, cudaStream_t s);
 // write the (tile, record) pairs in depth order: offsets [n_rec] are the
 // exclusive scan of the tile counts taken in depth order (order), total their
 // sum (device); pairs at or past n_pairs are dropped
 cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, const uint64_t* total, uint32_t n_rec,
-                             const int4* rect, const RecPtrs rec, const DevCam* cams, int64_t n_gauss, int tile_w,
-                             int tile_h, uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s);
+                             const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
+                             uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s);
 cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ranges, cudaStream_t s,
                                const uint32_t* d_n = nullptr);
 // n32 = min(*total, cap); raises kStatusCapacity when *total > cap

@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
                                                          const DevCam* __restrict__ cams, int n_views,
                                                          int tile_w, int tile_h, RecPtrs rec,
                                                          int32_t* __restrict__ ntiles,
-                                                         int4* __restrict__ rect,
+                                                         float4* __restrict__ bin,
                                                          uint32_t* __restrict__ depth_key,
                                                          int* __restrict__ status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
@@ -264,11 +264,10 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
     if (culled) {
       ntiles[idx] = 0;
       depth_key[idx] = 0xffffffffu;
-      rect[idx] = make_int4(0, 0, -1, -1);
+      bin[3 * idx + 2] = make_float4(0.f, 0.f, __uint_as_float(pack_i16x2(0, 0)), __uint_as_float(pack_i16x2(-1, -1)));
       continue;
     }
     ntiles[idx] = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-    rect[idx] = rc;
     depth_key[idx] = __float_as_uint(G.p[2]);  // positive: the bit pattern orders like the value
     const float pz = G.p[2];
     const float e0 = G.a * G.d - G.b * G.c;
@@ -276,9 +275,15 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
     const float e2 = G.U[2] * G.b - G.V[2] * G.a;
     float dirn[3], dlen, raw[3];
     view_colour<DEG>(cam, X, sh, dirn, &dlen, raw);
-    rec.g0[idx] = make_float4(cam.fx * G.pxn + cam.cx, cam.fy * G.pyn + cam.cy, o, pz);
-    rec.g1[idx] = make_float4(pz * G.d, -pz * G.b, -pz * G.c, pz * G.a);
+    const float4 g0 = make_float4(cam.fx * G.pxn + cam.cx, cam.fy * G.pyn + cam.cy, o, pz);
+    const float4 g1 = make_float4(pz * G.d, -pz * G.b, -pz * G.c, pz * G.a);
+    rec.g0[idx] = g0;
+    rec.g1[idx] = g1;
     rec.g2[idx] = make_float4(e0, e1, e2, pz * e0);
+    bin[3 * idx] = make_float4(g0.x, g0.y, rho_b, g1.x);
+    bin[3 * idx + 1] = make_float4(g1.y, g1.z, g1.w, e0);
+    bin[3 * idx + 2] = make_float4(e1, e2, __uint_as_float(pack_i16x2(rc.x, rc.y)),
+                                   __uint_as_float(pack_i16x2(rc.z, rc.w)));
     rec.a0[idx] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), G.n[0]);
     rec.a1[idx] = make_float2(G.n[1], G.n[2]);
   }
@@ -433,15 +438,15 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
 
 cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams,
                               int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
-                              int4* rect, uint32_t* depth_key, int* status, cudaStream_t s) {
+                              float4* bin, uint32_t* depth_key, int* status, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int bs = 128;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   switch (sh_degree) {
-    case 0: preprocess_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
-    case 1: preprocess_kernel<1><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
-    case 2: preprocess_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
-    default: preprocess_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, rect, depth_key, status); break;
+    case 0: preprocess_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    case 1: preprocess_kernel<1><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    case 2: preprocess_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    default: preprocess_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
   }
   return launched();
 }

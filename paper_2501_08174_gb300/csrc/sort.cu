@@ -284,20 +284,19 @@ __device__ __forceinline__ int row_count(const RowRuns& rr) {
 
 // Exact tile count of each record: one thread per record, one closed-form
 // coverage computation per candidate tile row.
-__global__ void __launch_bounds__(kThreads) tile_count_kernel(const RecPtrs rec, const int4* __restrict__ rect,
+__global__ void __launch_bounds__(kThreads) tile_count_kernel(const float4* __restrict__ bin,
                                                               const DevCam* __restrict__ cams, int64_t n_gauss,
                                                               uint32_t n_rec, int tw, int th,
                                                               int32_t* __restrict__ ntiles,
                                                               uint32_t* __restrict__ depth_key) {
   const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
   if (r >= n_rec) return;
-  const int4 rc = rect[r];
+  const BinView b = load_bin(bin, r);
   int cnt = 0;
-  if (rc.z >= rc.x) {
+  if (b.rc.z >= b.rc.x) {
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const float4 g0 = rec.g0[r];
-    const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
-    for (int ty = rc.y; ty <= rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, rc));
+    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, b.rc));
   }
   ntiles[r] = cnt;
   if (cnt == 0) depth_key[r] = 0xffffffffu;
@@ -324,8 +323,8 @@ constexpr int kWarpsPerBlock = kThreads / 32;
 
 __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
-    uint32_t n_rec, const int4* __restrict__ rect, const RecPtrs rec, const DevCam* __restrict__ cams,
-    int64_t n_gauss, int tw, int th, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+    uint32_t n_rec, const float4* __restrict__ bin, const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th,
+    uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   __shared__ short4 s_runs[kWarpsPerBlock][kSmallRows][32];  // [row][lane]: lanes in distinct banks
   __shared__ int s_incl[kWarpsPerBlock][32];
   __shared__ uint32_t s_rowbase[kWarpsPerBlock][32];  // tile id of (first row, column 0)
@@ -336,7 +335,8 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   uint32_t r = 0;
   int cnt = 0;
-  int4 rc = make_int4(0, 0, -1, -1);
+  BinView bv;
+  bv.rc = make_int4(0, 0, -1, -1);
   uint64_t o = 0;
   if (i < n_rec) {
     o = offsets[i];
@@ -347,13 +347,13 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
   if (lane == 31 || i + 1 >= n_rec) o_next = (i + 1 < n_rec) ? offsets[i + 1] : *total;
   if (i < n_rec && o < (uint64_t)n_pairs) {  // entries past a capacity write nothing
     cnt = (int)(o_next - o);
-    if (cnt > 0) rc = rect[r];
+    if (cnt > 0) bv = load_bin(bin, r);
   }
+  const int4 rc = bv.rc;
   const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const float4 g0 = rec.g0[r];
-    const SupportConic k = support_conic(g0, rec.g1[r], rec.g2[r], support_rho(g0.z));
+    const SupportConic k = support_conic(bv.g0, bv.g1, bv.g2, bv.rb);
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
       s_runs[warp][ty - rc.y][lane] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
@@ -408,10 +408,10 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
     const uint32_t rr = __shfl_sync(kFull, r, src);
     const uint64_t oo = __shfl_sync(kFull, o, src);
     const int bcnt = __shfl_sync(kFull, cnt, src);
-    const int4 bc = rect[rr];
+    const BinView bb = load_bin(bin, rr);
+    const int4 bc = bb.rc;
     const DevCam& cam = cams[rr / (uint64_t)n_gauss];
-    const float4 g0 = rec.g0[rr];
-    const SupportConic k = support_conic(g0, rec.g1[rr], rec.g2[rr], support_rho(g0.z));
+    const SupportConic k = support_conic(bb.g0, bb.g1, bb.g2, bb.rb);
     const uint64_t stop = min(oo + (uint64_t)bcnt, (uint64_t)n_pairs);
     uint64_t base = oo;
     for (int row0 = bc.y; row0 <= bc.w; row0 += 32) {
@@ -546,22 +546,21 @@ cudaError_t launch_iota(uint32_t* v, uint32_t n, cudaStream_t s) {
   return launched();
 }
 
-cudaError_t launch_tile_count(const RecPtrs rec, const int4* rect, const DevCam* cams, int64_t n_gauss,
-                              uint32_t n_rec, int tile_w, int tile_h, int32_t* ntiles, uint32_t* depth_key,
-                              cudaStream_t s) {
+cudaError_t launch_tile_count(const float4* bin, const DevCam* cams, int64_t n_gauss, uint32_t n_rec, int tile_w,
+                              int tile_h, int32_t* ntiles, uint32_t* depth_key, cudaStream_t s) {
   if (n_rec == 0) return cudaSuccess;
-  tile_count_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(rec, rect, cams, n_gauss, n_rec, tile_w,
-                                                                           tile_h, ntiles, depth_key);
+  tile_count_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(bin, cams, n_gauss, n_rec, tile_w, tile_h,
+                                                                           ntiles, depth_key);
   return launched();
 }
 
 cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, const uint64_t* total, uint32_t n_rec,
-                             const int4* rect, const RecPtrs rec, const DevCam* cams, int64_t n_gauss, int tile_w,
-                             int tile_h, uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s) {
+                             const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
+                             uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
-  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, offsets, total, n_rec, rect, rec,
-                                                                          cams, n_gauss, tile_w, tile_h, n_pairs,
-                                                                          keys, vals);
+  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, offsets, total, n_rec, bin, cams,
+                                                                          n_gauss, tile_w, tile_h, n_pairs, keys,
+                                                                          vals);
   return launched();
 }
 
