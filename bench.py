@@ -59,7 +59,7 @@ FLOPS_BWD = 90
 def parse_args():
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--workload", choices=("c4", "c5"), default="c4",
@@ -73,7 +73,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=384, help="pixels of the oracle's timed sample")
+    p.add_argument("--cpu-sample", type=int, default=1024, help="pixels of the oracle's timed sample")
     a = p.parse_args()
     if a.n is None:
         a.n = 1_000_000 if a.workload == "c5" else 500_000
@@ -97,7 +97,7 @@ def metric_name(a) -> str:
 
 # ----------------------------------------------------------------------------- clocks
 class ClockSampler:
-    """nvidia-smi samples during the timed region (every 200 ms)."""
+    """nvidia-smi samples during the timed region (every 50 ms)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -108,7 +108,7 @@ class ClockSampler:
         try:
             self.fh = open(path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(gpu_index)], stdout=self.fh,
+                                          "-lms", "50", "-i", str(gpu_index)], stdout=self.fh,
                                          stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -447,6 +447,8 @@ def run_ours(a, rank: int, world: int, local: int):
     stages = {}
     step_bytes = 0
     for name, (tot_ms, cnt) in prof.items():
+        if cnt == 0:
+            continue  # a stage this workload does not run
         alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1)
         step_bytes += alg["bytes"]
         per_ms = tot_ms / a.steps
