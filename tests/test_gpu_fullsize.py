@@ -226,3 +226,78 @@ def test_c4_batched_forward_and_gradient_at_sampled_pixels(rast, dev):
     assert max(errs.values()) <= GRAD_TOL, errs
     a = out["alpha"]
     assert float(a.min()) >= 0.0 and float(a.max()) < 1.0
+
+
+# ----------------------------------------------------------------------------- config 5: training iteration, 1M x 64 views
+def test_c5_training_iteration_at_sampled_pixels(rast, dev):
+    """One full iteration at the config-5 size (1M surfels, 64 views 1600x1200) in the launch
+    configuration bench.py times: the batched forward at sampled pixels of four views against
+    the oracle; the gradient of a colour + opacity loss restricted to those samples against the
+    oracle adjoint (the backward instantiation without depth and normal cotangents, as in the
+    training step); the Adam update against the oracle applied to the GPU's own gradient at
+    sampled elements; the pruning of parameters and of both moments with one keep-set."""
+    sc = synthetic.config5()
+    cams = sc["cameras"]
+    g_np = sc["gaussians"]
+    g = to_device(g_np, dev)
+    N = g["xyz"].shape[0]
+    from paper_2501_08174_gb300 import pixel_offsets
+    off = pixel_offsets(cams)
+    P = off[-1]
+    score = torch.zeros(N, device=dev)
+    out, state = rast.render(g, cams, score=score)
+    full_rgb = torch.zeros(P, 3, device=dev)
+    full_alpha = torch.zeros(P, device=dev)
+    grads_ref = {k: 0.0 for k in KEYS}
+    rng = np.random.default_rng(50)
+    worst = 0.0
+    for v in (0, 21, 42, 63):
+        cam = cams[v]
+        px = _sample(cam, 24, 500 + v)
+        d = dict(rgb=rng.normal(size=(len(px), 3)), alpha=rng.normal(size=len(px)), depth=np.zeros(len(px)),
+                 normal=np.zeros((len(px), 3)))
+        ref = oracle.render(g_np, cam, pixels=px, d_out=d)
+        if ref["fragile_grad"].any():  # no cotangent on either side at fragile pixels
+            keep = ~ref["fragile_grad"]
+            d = {k: np.where(keep.reshape((-1,) + (1,) * (x.ndim - 1)), x, 0.0) for k, x in d.items()}
+            ref = oracle.render(g_np, cam, pixels=px, d_out=d)
+        ok = ~ref["fragile"]
+        errs = forward_errors(_gather(out, px + off[v]), ref, ok)
+        worst = max(worst, max(errs.values()))
+        idx = torch.as_tensor(px + off[v], device=dev)
+        full_rgb[idx] = torch.tensor(d["rgb"], dtype=torch.float32, device=dev)
+        full_alpha[idx] = torch.tensor(d["alpha"], dtype=torch.float32, device=dev)
+        for k in KEYS:
+            grads_ref[k] = grads_ref[k] + ref["grads"][k]
+    assert worst <= FWD_TOL, worst
+    grads = rast.render_backward(state, g, {"rgb": full_rgb, "alpha": full_alpha})
+    state.release()
+    errs = grad_errors(grads, grads_ref)
+    assert max(errs.values()) <= GRAD_TOL, errs
+
+    lr = dict(xyz=1.6e-4, quat=1e-3, scale=5e-3, opacity=5e-2, sh=2.5e-3)
+    params = {k: v.clone() for k, v in g.items()}
+    m = {k: torch.zeros_like(v) for k, v in g.items()}
+    vv = {k: torch.zeros_like(v) for k, v in g.items()}
+    rast.adam_step(params, grads, m, vv, lr, step=1)
+    tau = 0.01
+    kept = [rast.prune(d, score, tau)[0] for d in (params, m, vv)]
+    torch.cuda.synchronize()
+    sel = {k: torch.as_tensor(rng.choice(grads[k].numel(), size=4096, replace=False), device=dev) for k in KEYS}
+
+    def at(d):
+        return {k: d[k].reshape(-1)[sel[k]].double().cpu().numpy() for k in KEYS}
+
+    z = {k: np.zeros(4096) for k in KEYS}
+    p_o, m_o, v_o = oracle.adam_step(at(g), at(grads), z, z, lr, step=1)
+    got_p, got_m = at(params), at(m)
+    for k in KEYS:
+        np.testing.assert_allclose(got_p[k], p_o[k], rtol=0, atol=2e-6, err_msg=k)
+        np.testing.assert_allclose(got_m[k], m_o[k], rtol=1e-6, atol=1e-30, err_msg=k)
+    keep = score > tau
+    n_keep = int(keep.sum())
+    assert 0 < n_keep < N
+    for d, kd in zip((params, m, vv), kept):
+        for k in KEYS:
+            assert kd[k].shape[0] == n_keep
+            assert torch.equal(kd[k], d[k][keep]), k
