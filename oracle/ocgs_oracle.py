@@ -29,7 +29,9 @@ normal flip) held fixed:
   all views; the surfel is "used" (visible, not occluded) iff the score is
   > 0 (Sec. 4.3), and the keep-set at threshold tau is {score > tau};
 * one Adam update of the parameters (the optimiser of the training Sec. 5.1
-  keeps; Kingma & Ba, 2015, Algorithm 1).
+  keeps; Kingma & Ba, 2015, Algorithm 1);
+* SSIM of masked images (the D-SSIM part of the photometric loss Eq. 2 masks,
+  and the masked SSIM of Sec. 5) and the masked PSNR of Sec. 5.
 
 Readings of points the paper leaves to prior work (documented with the
 project's design notes): culling of a surfel whose 3-sigma square reaches
@@ -406,3 +408,68 @@ def adam_step(params: dict, grads: dict, m: dict, v: dict, lr, step: int,
         new_m[k] = mk
         new_v[k] = vk
     return new_p, new_m, new_v
+
+
+# ----------------------------------------------------------------------------- photometric metrics and D-SSIM
+# SSIM as the 3DGS photometric loss (the L_c that Eq. 2 masks) and the evaluation of Sec. 5 use
+# it: windowed statistics under an 11x11 Gaussian window of sigma 1.5 (zero outside the
+# image), stabilising constants C1 = 0.01^2, C2 = 0.03^2 for intensities in [0, 1].
+SSIM_RADIUS = 5
+SSIM_SIGMA = 1.5
+SSIM_C1 = 0.01 ** 2
+SSIM_C2 = 0.03 ** 2
+
+
+def ssim_window() -> np.ndarray:
+    """The normalised 1-D Gaussian of the separable SSIM window (11 taps)."""
+    x = np.arange(-SSIM_RADIUS, SSIM_RADIUS + 1, dtype=np.float64)
+    w = np.exp(-x * x / (2.0 * SSIM_SIGMA ** 2))
+    return w / w.sum()
+
+
+def ssim_blur(x: torch.Tensor) -> torch.Tensor:
+    """Windowed mean of every channel of an [h, w, c] FP64 image, zero outside the image."""
+    g = torch.tensor(ssim_window(), dtype=torch.float64)
+    k = (g[:, None] * g[None, :])[None, None]                       # [1,1,11,11]
+    planes = x.permute(2, 0, 1).unsqueeze(1)                         # [c,1,h,w]
+    out = torch.nn.functional.conv2d(planes, k, padding=SSIM_RADIUS)
+    return out.squeeze(1).permute(1, 2, 0)
+
+
+def ssim_map(x1: torch.Tensor, x2: torch.Tensor) -> torch.Tensor:
+    """Per-pixel, per-channel SSIM of two [h, w, 3] images: luminance, contrast and structure
+    terms from the windowed means, variances and covariance."""
+    mu1, mu2 = ssim_blur(x1), ssim_blur(x2)
+    s11 = ssim_blur(x1 * x1) - mu1 * mu1
+    s22 = ssim_blur(x2 * x2) - mu2 * mu2
+    s12 = ssim_blur(x1 * x2) - mu1 * mu2
+    return ((2 * mu1 * mu2 + SSIM_C1) * (2 * s12 + SSIM_C2)) / \
+        ((mu1 * mu1 + mu2 * mu2 + SSIM_C1) * (s11 + s22 + SSIM_C2))
+
+
+def masked_ssim(rgb: np.ndarray, target: np.ndarray, mask: np.ndarray, weight: float = 0.0):
+    """SSIM of one view with both images masked first (Eq. 2 masks the inputs of L_c; Sec. 5
+    masks the inputs of the evaluation SSIM).  rgb, target [h, w, 3], mask [h, w] in {0, 1}.
+    Returns (mean over all 3 h w values, mean over the values of mask pixels, gradient of
+    weight (1 - mean over all) with respect to rgb)."""
+    m = torch.tensor(np.asarray(mask, np.float64))[..., None]
+    r = torch.tensor(np.asarray(rgb, np.float64), requires_grad=True)
+    t = torch.tensor(np.asarray(target, np.float64))
+    s = ssim_map(t * m, r * m)
+    s_all = s.mean()
+    n_m = float(m.sum()) * 3.0
+    s_masked = float((s * m).sum().detach()) / n_m if n_m > 0 else float("nan")
+    (weight * (1.0 - s_all)).backward()
+    return float(s_all.detach()), s_masked, r.grad.numpy()
+
+
+def masked_psnr(rgb: np.ndarray, target: np.ndarray, mask: np.ndarray, max_i: float = 1.0) -> float:
+    """PSNR = 20 log10(MAX_I / sqrt(MSE)) with the masked MSE of Sec. 5: the squared masked
+    differences summed over the image and divided by the number of mask values (3 per pixel)."""
+    m = np.asarray(mask, np.float64)[..., None]
+    d = (np.asarray(target, np.float64) - np.asarray(rgb, np.float64)) * m
+    n = 3.0 * float(np.asarray(mask, np.float64).sum())
+    if n == 0:
+        return float("nan")
+    mse = float((d * d).sum()) / n
+    return float("inf") if mse == 0 else 20.0 * np.log10(max_i / np.sqrt(mse))

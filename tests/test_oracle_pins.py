@@ -442,3 +442,88 @@ def test_adam_zero_gradient_keeps_everything():
         np.testing.assert_array_equal(p1[k], p[k])
         np.testing.assert_array_equal(m1[k], 0.0)
         np.testing.assert_array_equal(v1[k], 0.0)
+
+
+# ----------------------------------------------------------------------------- SSIM / PSNR (Eq. 2's L_c, Sec. 5)
+def test_ssim_window_blur_matches_scipy_gaussian_filter():
+    """The windowed mean is SciPy's Gaussian filter of sigma 1.5 truncated at radius 5, zero outside."""
+    from scipy import ndimage
+    rng = np.random.default_rng(0)
+    x = rng.uniform(size=(23, 17, 3))
+    got = oracle.ssim_blur(torch.tensor(x)).numpy()
+    for c in range(3):
+        ref = ndimage.gaussian_filter(x[..., c], sigma=1.5, mode="constant", cval=0.0, truncate=5.0 / 1.5)
+        np.testing.assert_allclose(got[..., c], ref, rtol=0, atol=1e-13)
+
+
+def test_ssim_of_identical_images_is_one_and_stationary():
+    rng = np.random.default_rng(1)
+    x = rng.uniform(size=(19, 14, 3))
+    m = (rng.uniform(size=(19, 14)) > 0.3).astype(np.uint8)
+    s_all, s_m, grad = oracle.masked_ssim(x, x, m, weight=0.2)
+    assert s_all == pytest.approx(1.0, abs=1e-14) and s_m == pytest.approx(1.0, abs=1e-14)
+    np.testing.assert_allclose(grad, 0.0, atol=1e-12)   # SSIM is maximal at x2 = x1
+
+
+def test_ssim_of_constant_images_in_the_interior():
+    """Constant images a and b: away from the border the variances vanish and
+    SSIM = (2ab + C1) / (a^2 + b^2 + C1)."""
+    a, b = 0.7, 0.4
+    s = oracle.ssim_map(torch.full((30, 30, 3), a, dtype=torch.float64),
+                        torch.full((30, 30, 3), b, dtype=torch.float64)).numpy()
+    expect = (2 * a * b + 1e-4) / (a * a + b * b + 1e-4)
+    np.testing.assert_allclose(s[5:25, 5:25], expect, rtol=1e-12)
+
+
+def test_ssim_map_matches_brute_force_windows():
+    rng = np.random.default_rng(2)
+    h, w = 9, 13
+    x1, x2 = rng.uniform(size=(h, w, 3)), rng.uniform(size=(h, w, 3))
+    g = [math.exp(-(k * k) / 4.5) for k in range(-5, 6)]
+    gs = sum(g)
+    g = [v / gs for v in g]
+    got = oracle.ssim_map(torch.tensor(x1), torch.tensor(x2)).numpy()
+    for y in range(h):
+        for x in range(w):
+            for c in range(3):
+                m1 = m2 = e11 = e22 = e12 = 0.0
+                for dy in range(-5, 6):
+                    for dx in range(-5, 6):
+                        yy, xx = y + dy, x + dx
+                        if 0 <= yy < h and 0 <= xx < w:
+                            wt = g[dy + 5] * g[dx + 5]
+                            p, q = x1[yy, xx, c], x2[yy, xx, c]
+                            m1 += wt * p; m2 += wt * q
+                            e11 += wt * p * p; e22 += wt * q * q; e12 += wt * p * q
+                v1, v2, cv = e11 - m1 * m1, e22 - m2 * m2, e12 - m1 * m2
+                ref = (2 * m1 * m2 + 1e-4) * (2 * cv + 9e-4) / ((m1 * m1 + m2 * m2 + 1e-4) * (v1 + v2 + 9e-4))
+                assert got[y, x, c] == pytest.approx(ref, abs=1e-12), (y, x, c)
+
+
+def test_dssim_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    h, w = 10, 8
+    r, t = rng.uniform(size=(h, w, 3)), rng.uniform(size=(h, w, 3))
+    m = (rng.uniform(size=(h, w)) > 0.25).astype(np.uint8)
+    _, _, grad = oracle.masked_ssim(r, t, m, weight=0.2)
+    for flat in rng.choice(h * w * 3, size=24, replace=False):
+        i = np.unravel_index(flat, r.shape)
+        rp, rm = r.copy(), r.copy()
+        rp[i] += 1e-6
+        rm[i] -= 1e-6
+        fd = (0.2 * (1 - oracle.masked_ssim(rp, t, m)[0]) - 0.2 * (1 - oracle.masked_ssim(rm, t, m)[0])) / 2e-6
+        assert grad[i] == pytest.approx(fd, abs=1e-8), i
+        if m[i[0], i[1]] == 0:
+            assert grad[i] == 0.0                          # masked-out pixels get no gradient
+
+
+def test_masked_psnr_hand_value():
+    """Target 0.5 everywhere; one masked value off by 0.1 and an unmasked pixel off by 0.3:
+    MSE = 0.01 / 9 over the 3 x 3 masked values, PSNR = 20 log10(30)."""
+    t = np.full((2, 2, 3), 0.5)
+    r = t.copy()
+    r[0, 0, 0] = 0.6
+    r[0, 1] = 0.8
+    m = np.array([[1, 0], [1, 1]], np.uint8)
+    assert oracle.masked_psnr(r, t, m) == pytest.approx(20 * math.log10(30.0), abs=1e-12)
+    assert oracle.masked_psnr(t, t, m) == float("inf")
