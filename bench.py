@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 import numpy as np  # noqa: E402
 
 METRIC = "fwd+bwd Mpix/s at 500k surfels, batched vs per-view; % of HBM roofline"
-METRIC_C5 = "training-iteration Mpix/s at 1M surfels x 64 views (fwd+bwd, L_b, pruning, Adam)"
+METRIC_C5 = "training-iteration Mpix/s at 1M surfels x 64 views (fwd+bwd, L1 + D-SSIM, L_b, pruning, Adam)"
 UNIT = "Mpix/s"
 # Adam learning rates of the c5 iteration: the 3DGS defaults per array scaled by
 # 1e-3, so that the timed scene stays stationary over the timed steps (the
@@ -48,6 +48,7 @@ UNIT = "Mpix/s"
 # values, which the default rates would push out of range within a few steps)
 ADAM_LR = dict(xyz=1.6e-7, quat=1e-6, scale=5e-6, opacity=5e-5, sh=2.5e-6)
 GAMMA = 0.5      # background-loss weight (Sec. 5.1)
+LAMBDA_DSSIM = 0.2  # D-SSIM share of the 3DGS photometric loss that Eq. 2 masks (training iteration)
 TAU = 0.01       # pruning threshold of the sweep configuration
 # FP32 operations per evaluated (pixel, Gaussian) pair, counted from the kernels'
 # arithmetic (an FMA counts 2): support test and alpha (31) plus blending (17)
@@ -85,7 +86,7 @@ def parse_args():
 def workload_name(a) -> str:
     if a.workload == "c5":
         return (f"object-centric 2DGS training iteration: {a.n} surfels SH3 (60% object ball r=0.8, 40% shell "
-                f"r=2-4), {a.views} hemisphere views 1600x1200 with object masks, masked L1 + 0.5 L_b, fwd+bwd, "
+                f"r=2-4), {a.views} hemisphere views 1600x1200 with object masks, masked 0.8 L1 + 0.2 D-SSIM + 0.5 L_b, fwd+bwd, "
                 f"Adam on all parameters, prune of parameters and moments at tau={TAU}")
     return (f"object-centric 2DGS training step: {a.n} surfels SH3 (70% object ball r=0.8, 30% shell r=2-4), "
             f"{a.views} hemisphere views of uneven resolution, masked L1 + 0.5 L_b, fwd+bwd, prune tau={TAU}")
@@ -227,13 +228,14 @@ def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile
                 prune_calls: int = 1) -> dict:
     """Minimum HBM bytes (and FP32 flops) of each stage for one step."""
     VN = V * N
+    ssim_px = 24 + 1 + 36 + 36 + 24 + 24  # images + mask, adjoint maps out and back, images again, d_rgb
     b = {
         "preprocess": N * 232 + VN * (72 + 4 + 16 + 4),
         "depth_sort": VN * 4 + 4 * VN * 20,
         "binning": VN * 68 + K * 12 + T * 8,
         "tile_sort": tile_passes * K * 20,
         "raster_fwd": VN * 72 + K * 4 + P * 40,
-        "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24),
+        "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24) + (ssim_px * P if prune_calls > 1 else 0),
         "raster_bwd": VN * (72 + 80) + K * 4 + P * 40,
         "preprocess_bwd": N * 232 * 3 + VN * 84,
         "prune": prune_calls * (N * 24 + kept * 232 * 2),
@@ -325,7 +327,11 @@ class TrainingStep:
         tgt = self.target[lo:hi]
         msk = self.mask[lo:hi]
         d_rgb, d_alpha = self.d_rgb[lo:hi], self.d_alpha[lo:hi]
-        l1 = r.masked_l1(out["rgb"], tgt, msk, cams, weight=1.0, d_rgb=d_rgb)
+        if self.adam:  # the full photometric loss of Eq. 2: (1 - lambda) L1 + lambda D-SSIM of masked images
+            l1 = r.masked_l1(out["rgb"], tgt, msk, cams, weight=1.0 - LAMBDA_DSSIM, d_rgb=d_rgb)
+            r.ssim(out["rgb"], tgt, msk, cams, weight=LAMBDA_DSSIM, d_rgb=d_rgb)
+        else:
+            l1 = r.masked_l1(out["rgb"], tgt, msk, cams, weight=1.0, d_rgb=d_rgb)
         lb = r.background_loss(out["alpha"], msk, cams, gamma=GAMMA, d_alpha=d_alpha)
         r.render_backward(st, self.g, {"rgb": d_rgb, "alpha": d_alpha}, grads=self.grads)
         st.release()

@@ -333,6 +333,36 @@ ocgs_status ocgs_masked_l1(ocgs_ctx* ctx, const float* rgb, const float* target,
                            const ocgs_camera* cams, int32_t n_views, float weight, double* loss,
                            float* d_rgb);
 
+/*
+ * ocgs_ssim — SSIM of masked images, per view: both images are multiplied by
+ * the mask first (Eq. 2 masks the inputs of the photometric loss; Sec. 5 masks
+ * the inputs of the evaluation SSIM), then SSIM is taken with windowed
+ * statistics under an 11x11 Gaussian window of sigma 1.5 (zero outside the
+ * image) and C1 = 0.01^2, C2 = 0.03^2, as the 3DGS photometric loss the method
+ * keeps defines it.
+ *   rgb, target  device [P,3] rendered R and reference I; mask device [P] uint8
+ *   ssim         device [n_views] float64, overwritten: mean of the SSIM map
+ *                over all 3*h*w values (the D-SSIM term of L_c is 1 - ssim)
+ *   ssim_masked  device [n_views] float64 or NULL: mean over the values of the
+ *                mask pixels (the masked SSIM of Sec. 5; NaN without any)
+ *   d_rgb        device [P,3] or NULL: d_rgb += weight * d(1 - ssim)/dR
+ * Deterministic (fixed-order FP64 sums).  Allocates 36 bytes per pixel of
+ * scratch when d_rgb is given.  Asynchronous on the context stream.
+ */
+ocgs_status ocgs_ssim(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                      const ocgs_camera* cams, int32_t n_views, float weight, double* ssim, double* ssim_masked,
+                      float* d_rgb);
+
+/*
+ * ocgs_masked_psnr — PSNR = 20 log10(max_i / sqrt(MSE)) per view, with the
+ * masked MSE of Sec. 5: squared differences of the mask pixels summed over
+ * pixels and channels, divided by the number of those values (3 per mask
+ * pixel).  psnr device [n_views] float64, overwritten (+inf when the masked
+ * images agree, NaN without mask pixels).  max_i > 0.
+ */
+ocgs_status ocgs_masked_psnr(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                             const ocgs_camera* cams, int32_t n_views, float max_i, double* psnr);
+
 /* Sizes of one forward state: K pairs, P pixels, and E = sum over pixels of
  * the length of the blended prefix of the pixel's tile list (the (pixel,
  * Gaussian) pairs that both the forward and the backward must evaluate).

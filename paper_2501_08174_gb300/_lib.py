@@ -99,6 +99,10 @@ SIGNATURES = {
                              C.POINTER(C.c_int64)]),
     "ocgs_adam_step": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(GaussiansOut),
                                  C.POINTER(GaussiansOut), C.POINTER(GaussiansOut), C.POINTER(AdamConfig)]),
+    "ocgs_ssim": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera), C.c_int32,
+                            C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ocgs_masked_psnr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera), C.c_int32,
+                                   C.c_float, C.c_void_p]),
     "ocgs_masked_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
                                  C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
     "ocgs_autotune": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32, C.c_char_p,

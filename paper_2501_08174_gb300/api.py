@@ -293,6 +293,36 @@ class Rasterizer:
                    len(cameras), float(weight), _ptr(loss), _ptr(d_rgb))
         return loss
 
+    def _check_images(self, rgb, target, mask, cameras, d_rgb=None):
+        P = n_pixels(cameras)
+        for name, t in (("rgb", rgb), ("target", target)) + ((("d_rgb", d_rgb),) if d_rgb is not None else ()):
+            if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != 3 * P:
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {P}x3 values")
+        if mask.dtype != torch.uint8 or not mask.is_cuda or not mask.is_contiguous() or mask.numel() != P:
+            raise ValueError(f"mask must be a contiguous uint8 CUDA tensor of {P} values")
+
+    def ssim(self, rgb: torch.Tensor, target: torch.Tensor, mask: torch.Tensor, cameras: Sequence[dict],
+             weight: float = 0.0, d_rgb: Optional[torch.Tensor] = None):
+        """Per-view SSIM of the masked images: (mean over all values, mean over mask values), both
+        float64 tensors; adds weight * d(1 - SSIM)/dR into ``d_rgb`` (the D-SSIM term of Eq. 2)."""
+        self._bind_stream()
+        self._check_images(rgb, target, mask, cameras, d_rgb)
+        s_all = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        s_m = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_ssim", self._ctx, _ptr(rgb), _ptr(target), _ptr(mask), camera_array(cameras), len(cameras),
+                   float(weight), _ptr(s_all), _ptr(s_m), _ptr(d_rgb))
+        return s_all, s_m
+
+    def masked_psnr(self, rgb: torch.Tensor, target: torch.Tensor, mask: torch.Tensor, cameras: Sequence[dict],
+                    max_i: float = 1.0) -> torch.Tensor:
+        """Per-view masked PSNR of Sec. 5 (float64 tensor)."""
+        self._bind_stream()
+        self._check_images(rgb, target, mask, cameras)
+        out = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_masked_psnr", self._ctx, _ptr(rgb), _ptr(target), _ptr(mask), camera_array(cameras),
+                   len(cameras), float(max_i), _ptr(out))
+        return out
+
     def accumulate_contribution(self, gaussians: dict, cameras: Sequence[dict],
                                 score: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Pruning sweep (Sec. 4.3): max blending weight of every Gaussian over all views."""

@@ -740,6 +740,65 @@ ocgs_status ocgs_masked_l1(ocgs_ctx* ctx, const float* rgb, const float* target,
   return OCGS_OK;
 }
 
+ocgs_status ocgs_ssim(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                      const ocgs_camera* cams, int32_t n_views, float weight, double* ssim, double* ssim_masked,
+                      float* d_rgb) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!rgb || !target || !mask || !ssim) return set_err(ctx, OCGS_ERR_ARG, "rgb, target, mask and ssim must be non-NULL");
+  if (!std::isfinite(weight)) return set_err(ctx, OCGS_ERR_ARG, "weight must be finite");
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
+  std::vector<int> prefix(n_views + 1, 0);
+  int64_t P = 0;
+  for (int v = 0; v < n_views; ++v) {
+    prefix[v + 1] = prefix[v] + ssim_tiles(lp.cams[v].W, lp.cams[v].H);
+    P += (int64_t)lp.cams[v].W * lp.cams[v].H;
+  }
+  const int tiles = prefix[n_views];
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  float* gmap = nullptr;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, 3 * (size_t)tiles));
+  if (d_rgb) CK(tmp.alloc(&gmap, 9 * (size_t)P));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_ssim(rgb, target, mask, d_cams, n_views, d_prefix, tiles, weight, partial, gmap, ssim, ssim_masked, d_rgb,
+                 s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_masked_psnr(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
+                             const ocgs_camera* cams, int32_t n_views, float max_i, double* psnr) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!rgb || !target || !mask || !psnr) return set_err(ctx, OCGS_ERR_ARG, "rgb, target, mask and psnr must be non-NULL");
+  if (!(std::isfinite(max_i) && max_i > 0.f)) return set_err(ctx, OCGS_ERR_ARG, "max_i must be finite and > 0");
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, 2 * (size_t)lp.blocks));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_masked_psnr(rgb, target, mask, d_cams, n_views, d_prefix, lp.blocks, (double)max_i, partial, psnr, s));
+  return OCGS_OK;
+}
+
 ocgs_status ocgs_state_query(ocgs_ctx* ctx, const ocgs_fwd_state* st, ocgs_state_info* info) {
   if (!ctx || !info) return OCGS_ERR_ARG;
   if (!st || st->ctx != ctx) return set_err(ctx, OCGS_ERR_STATE, "forward state missing or from another context");
