@@ -770,8 +770,8 @@ ocgs_status ocgs_ssim(ocgs_ctx* ctx, const float* rgb, const float* target, cons
   StageTimer t(ctx, OCGS_STAGE_LOSS);
   CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_prefix, prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
-  CK(launch_ssim(rgb, target, mask, d_cams, n_views, d_prefix, tiles, weight, partial, gmap, ssim, ssim_masked, d_rgb,
-                 s));
+  CK(launch_ssim(rgb, target, mask, d_cams, n_views, d_prefix, tiles, P, weight, partial, gmap, ssim, ssim_masked,
+                 d_rgb, s));
   return OCGS_OK;
 }
 

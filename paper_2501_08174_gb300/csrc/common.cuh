@@ -562,13 +562,13 @@ struct AdamArgs {
 };
 cudaError_t launch_adam(const AdamArgs& a, int sm_count, cudaStream_t s);
 
-// SSIM / PSNR (ssim.cu).  SSIM works on 16x16 output tiles per view:
+// SSIM / PSNR (ssim.cu).  SSIM works on 32x32 output tiles per view:
 // tile_prefix [n_views + 1] counts ssim_tiles(W, H) per view; partial holds 3
-// doubles per tile; gmap 9 floats per pixel (only when d_rgb is given).
+// doubles per tile; gmap 9 planes of p_total floats (only when d_rgb is given).
 int ssim_tiles(int width, int height);
 cudaError_t launch_ssim(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams, int n_views,
-                        const int* tile_prefix, int n_tiles, float weight, double* partial, float* gmap,
-                        double* ssim, double* ssim_masked, float* d_rgb, cudaStream_t s);
+                        const int* tile_prefix, int n_tiles, int64_t p_total, float weight, double* partial,
+                        float* gmap, double* ssim, double* ssim_masked, float* d_rgb, cudaStream_t s);
 // PSNR over the loss blocks (kLossBlockPixels per block); partial holds 2 doubles per block
 cudaError_t launch_masked_psnr(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams,
                                int n_views, const int* block_prefix, int n_blocks, double max_i, double* partial,

@@ -3,8 +3,10 @@
 //
 // SSIM statistics are windowed means under an 11x11 Gaussian window of sigma
 // 1.5, zero outside the image; the window is separable, so every block stages
-// a 26x26 patch (its 16x16 output tile plus a 5-pixel halo) of both masked
-// images in shared memory and applies the 11 taps along rows, then columns.
+// a 42x42 patch (its 32x32 output tile plus a 5-pixel halo) of one channel of
+// both masked images in shared memory and applies the 11 taps along rows, then
+// columns, each thread producing 4 neighbouring outputs from one 14-value
+// window so that a staged value is read once per 4 outputs.
 // The adjoint of the mean SSIM needs, at every pixel q,
 //     sum_p dS(p)/dE[x2](p) G(p-q) + 2 x2(q) sum_p dS(p)/dE[x2^2](p) G(p-q)
 //                                 +   x1(q) sum_p dS(p)/dE[x1 x2](p) G(p-q),
@@ -17,15 +19,18 @@
 namespace ocgs {
 namespace {
 
-constexpr int kT = 16;               // output tile side
+constexpr int kT = 32;               // output tile side
 constexpr int kR = 5;                // window radius
-constexpr int kP = kT + 2 * kR;      // staged patch side (26)
-constexpr int kThreadsSsim = kT * kT;
+constexpr int kP = kT + 2 * kR;      // staged patch side (42)
+constexpr int kSeg = 4;              // outputs per thread along a row (first pass) or column (second)
+constexpr int kThreadsSsim = 256;
+constexpr int kTaps = 2 * kR + 1;
+constexpr int kRowItems = kP * (kT / kSeg);  // row segments of one plane (336)
 constexpr float kC1 = 0.0001f;       // (0.01)^2
 constexpr float kC2 = 0.0009f;       // (0.03)^2
 
 struct Window {
-  float w[2 * kR + 1];
+  float w[kTaps];
 };
 
 __device__ __forceinline__ void tile_origin(const int* prefix, int n_views, const DevCam* cams, int* v, int* x0,
@@ -39,100 +44,109 @@ __device__ __forceinline__ void tile_origin(const int* prefix, int n_views, cons
   *y0 = (local / tx) * kT;
 }
 
+// kSeg consecutive outputs of an 11-tap window over 14 inputs
+__device__ __forceinline__ void taps4(const float (&in)[kSeg + 2 * kR], const Window& win, float (&out)[kSeg]) {
+#pragma unroll
+  for (int k = 0; k < kSeg; ++k) {
+    float acc = 0.f;
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) acc = __fmaf_rn(win.w[t], in[k + t], acc);
+    out[k] = acc;
+  }
+}
+
 // partial[3 b + k]: k = 0 sum of S over the tile's values, 1 sum over its mask
-// values, 2 number of mask values.  gmap [P,3,3] (or NULL): per pixel and
-// channel, dS/dE[x2], dS/dE[x2^2], dS/dE[x1 x2].
+// values, 2 number of mask values.  gmap (or NULL): planes [9][P_total], plane
+// 3 c + j holds, for channel c, j = 0 dS/dE[x2], 1 dS/dE[x2^2], 2 dS/dE[x1 x2].
 __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ prefix, const Window win,
-    double* __restrict__ partial, float* __restrict__ gmap) {
-  __shared__ float s1[3][kP][kP + 1], s2[3][kP][kP + 1];  // masked target x1, masked render x2
-  __shared__ float h[5][kP][kT + 1];
+    int64_t p_total, double* __restrict__ partial, float* __restrict__ gmap) {
+  __shared__ float2 sx[kP][kP + 1];               // (masked target x1, masked render x2) of one channel
+  __shared__ __align__(16) float h[5][kP][kT];    // row-windowed x1, x2, x1^2, x2^2, x1 x2
   __shared__ double red[3][kThreadsSsim / 32];
   int v, x0, y0;
   tile_origin(prefix, n_views, cams, &v, &x0, &y0);
   const DevCam& cam = cams[v];
   const int tid = threadIdx.x;
-  for (int i = tid; i < kP * kP; i += kThreadsSsim) {
-    const int py = i / kP, px = i % kP;
-    const int gy = y0 - kR + py, gx = x0 - kR + px;
-    float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
-    if (gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W) {
-      const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-      if (mask[p]) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-          a[c] = target[3 * p + c];
-          b[c] = rgb[3 * p + c];
-        }
-      }
-    }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      s1[c][py][px] = a[c];
-      s2[c][py][px] = b[c];
-    }
-  }
-  const int tx = tid % kT, ty = tid / kT;
-  const int gx = x0 + tx, gy = y0 + ty;
-  const bool inside = gx < cam.W && gy < cam.H;
-  const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-  const bool m = inside && mask[p];
-  double sum_all = 0.0, sum_m = 0.0;
+  const int col = tid % kT, r0 = (tid / kT) * kSeg;  // second pass: 4 rows of one column
+  double sum_all = 0.0, sum_m = 0.0, cnt = 0.0;
   for (int c = 0; c < 3; ++c) {
-    __syncthreads();
-    for (int i = tid; i < kP * kT; i += kThreadsSsim) {
-      const int r = i / kT, j = i % kT;
-      float m1 = 0.f, m2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
-#pragma unroll
-      for (int t = 0; t <= 2 * kR; ++t) {
-        const float a = s1[c][r][j + t], b = s2[c][r][j + t], w = win.w[t];
-        m1 = __fmaf_rn(w, a, m1);
-        m2 = __fmaf_rn(w, b, m2);
-        e11 = __fmaf_rn(w, a * a, e11);
-        e22 = __fmaf_rn(w, b * b, e22);
-        e12 = __fmaf_rn(w, a * b, e12);
+    if (c > 0) __syncthreads();  // the previous channel's second pass is done with sx and h
+    for (int i = tid; i < kP * kP; i += kThreadsSsim) {
+      const int py = i / kP, px = i % kP;
+      const int gy = y0 - kR + py, gx = x0 - kR + px;
+      float2 q = make_float2(0.f, 0.f);
+      if (gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W) {
+        const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
+        if (mask[p]) q = make_float2(target[3 * p + c], rgb[3 * p + c]);
       }
-      h[0][r][j] = m1;
-      h[1][r][j] = m2;
-      h[2][r][j] = e11;
-      h[3][r][j] = e22;
-      h[4][r][j] = e12;
+      sx[py][px] = q;
     }
     __syncthreads();
-    if (inside) {
-      float mu1 = 0.f, mu2 = 0.f, e11 = 0.f, e22 = 0.f, e12 = 0.f;
+    for (int i = tid; i < kRowItems; i += kThreadsSsim) {
+      const int r = i / (kT / kSeg), x = (i % (kT / kSeg)) * kSeg;
+      float a[kSeg + 2 * kR], b[kSeg + 2 * kR], aa[kSeg + 2 * kR], bb[kSeg + 2 * kR], ab[kSeg + 2 * kR];
 #pragma unroll
-      for (int t = 0; t <= 2 * kR; ++t) {
-        const float w = win.w[t];
-        mu1 = __fmaf_rn(w, h[0][ty + t][tx], mu1);
-        mu2 = __fmaf_rn(w, h[1][ty + t][tx], mu2);
-        e11 = __fmaf_rn(w, h[2][ty + t][tx], e11);
-        e22 = __fmaf_rn(w, h[3][ty + t][tx], e22);
-        e12 = __fmaf_rn(w, h[4][ty + t][tx], e12);
+      for (int t = 0; t < kSeg + 2 * kR; ++t) {
+        const float2 q = sx[r][x + t];
+        a[t] = q.x;
+        b[t] = q.y;
+        aa[t] = q.x * q.x;
+        bb[t] = q.y * q.y;
+        ab[t] = q.x * q.y;
       }
-      const float v11 = e11 - mu1 * mu1, v22 = e22 - mu2 * mu2, v12 = e12 - mu1 * mu2;
+      float o[kSeg];
+      taps4(a, win, o);
+      *reinterpret_cast<float4*>(&h[0][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+      taps4(b, win, o);
+      *reinterpret_cast<float4*>(&h[1][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+      taps4(aa, win, o);
+      *reinterpret_cast<float4*>(&h[2][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+      taps4(bb, win, o);
+      *reinterpret_cast<float4*>(&h[3][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+      taps4(ab, win, o);
+      *reinterpret_cast<float4*>(&h[4][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+    float st[5][kSeg];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      float in[kSeg + 2 * kR];
+#pragma unroll
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = h[q][r0 + t][col];
+      taps4(in, win, st[q]);
+    }
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+      const int gx = x0 + col, gy = y0 + r0 + k;
+      if (gx >= cam.W || gy >= cam.H) continue;
+      const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
+      const bool m = mask[p] != 0;
+      const float mu1 = st[0][k], mu2 = st[1][k];
+      const float v11 = st[2][k] - mu1 * mu1, v22 = st[3][k] - mu2 * mu2, v12 = st[4][k] - mu1 * mu2;
       const float n1 = 2.f * mu1 * mu2 + kC1, n2 = 2.f * v12 + kC2;
       const float d1 = mu1 * mu1 + mu2 * mu2 + kC1, d2 = v11 + v22 + kC2;
       const float inv = 1.f / (d1 * d2);
       const float S = n1 * n2 * inv;
       sum_all += (double)S;
-      if (m) sum_m += (double)S;
+      if (m) {
+        sum_m += (double)S;
+        cnt += 1.0;
+      }
       if (gmap) {
         // partial derivatives at fixed (mu, sigma), then through sigma22 = E[x2^2] - mu2^2
         // and sigma12 = E[x1 x2] - mu1 mu2 onto the three windowed means of x2
         const float dmu2 = 2.f * mu1 * n2 * inv - S * 2.f * mu2 / d1;
         const float dv22 = -S / d2;
         const float dv12 = 2.f * n1 * inv;
-        float* gm = gmap + 9 * p + 3 * c;
-        gm[0] = dmu2 - 2.f * mu2 * dv22 - mu1 * dv12;
-        gm[1] = dv22;
-        gm[2] = dv12;
+        gmap[(3 * c) * p_total + p] = dmu2 - 2.f * mu2 * dv22 - mu1 * dv12;
+        gmap[(3 * c + 1) * p_total + p] = dv22;
+        gmap[(3 * c + 2) * p_total + p] = dv12;
       }
     }
   }
   // block sums (fixed order: warp shuffles, then warps in order)
-  double cnt = m ? 3.0 : 0.0;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     sum_all += __shfl_down_sync(0xffffffffu, sum_all, o);
@@ -156,51 +170,54 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
 __global__ void __launch_bounds__(kThreadsSsim) ssim_grad_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ prefix, const Window win,
-    const float* __restrict__ gmap, float weight, float* __restrict__ d_rgb) {
-  __shared__ float sg[9][kP][kP + 1];
-  __shared__ float h[9][kP][kT + 1];
+    int64_t p_total, const float* __restrict__ gmap, float weight, float* __restrict__ d_rgb) {
+  __shared__ float sg[3][kP][kP + 1];
+  __shared__ __align__(16) float h[3][kP][kT];
   int v, x0, y0;
   tile_origin(prefix, n_views, cams, &v, &x0, &y0);
   const DevCam& cam = cams[v];
   const int tid = threadIdx.x;
-  for (int i = tid; i < kP * kP; i += kThreadsSsim) {
-    const int py = i / kP, px = i % kP;
-    const int gy = y0 - kR + py, gx = x0 - kR + px;
-    const bool in = gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W;
-    const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) sg[k][py][px] = in ? gmap[9 * p + k] : 0.f;
-  }
-  __syncthreads();
-  for (int i = tid; i < kP * kT; i += kThreadsSsim) {
-    const int r = i / kT, j = i % kT;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      float acc = 0.f;
-#pragma unroll
-      for (int t = 0; t <= 2 * kR; ++t) acc = __fmaf_rn(win.w[t], sg[k][r][j + t], acc);
-      h[k][r][j] = acc;
-    }
-  }
-  __syncthreads();
-  const int tx = tid % kT, ty = tid / kT;
-  const int gx = x0 + tx, gy = y0 + ty;
-  if (gx >= cam.W || gy >= cam.H) return;
-  const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-  if (!mask[p]) return;  // x2 = R M: no gradient where M = 0
+  const int col = tid % kT, r0 = (tid / kT) * kSeg;
   const float coef = -weight / (3.f * (float)cam.W * (float)cam.H);
-#pragma unroll
   for (int c = 0; c < 3; ++c) {
-    float ga = 0.f, gb = 0.f, gc = 0.f;
-#pragma unroll
-    for (int t = 0; t <= 2 * kR; ++t) {
-      const float w = win.w[t];
-      ga = __fmaf_rn(w, h[3 * c][ty + t][tx], ga);
-      gb = __fmaf_rn(w, h[3 * c + 1][ty + t][tx], gb);
-      gc = __fmaf_rn(w, h[3 * c + 2][ty + t][tx], gc);
+    if (c > 0) __syncthreads();
+    for (int i = tid; i < 3 * kP * kP; i += kThreadsSsim) {
+      const int j = i / (kP * kP), rem = i % (kP * kP);
+      const int py = rem / kP, px = rem % kP;
+      const int gy = y0 - kR + py, gx = x0 - kR + px;
+      float val = 0.f;
+      if (gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W)
+        val = gmap[(3 * c + j) * p_total + cam.pix_offset + (int64_t)gy * cam.W + gx];
+      sg[j][py][px] = val;
     }
-    const float x1 = target[3 * p + c], x2 = rgb[3 * p + c];
-    d_rgb[3 * p + c] += coef * (ga + 2.f * x2 * gb + x1 * gc);
+    __syncthreads();
+    for (int i = tid; i < 3 * kRowItems; i += kThreadsSsim) {
+      const int j = i / kRowItems, rem = i % kRowItems;
+      const int r = rem / (kT / kSeg), x = (rem % (kT / kSeg)) * kSeg;
+      float in[kSeg + 2 * kR], o[kSeg];
+#pragma unroll
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = sg[j][r][x + t];
+      taps4(in, win, o);
+      *reinterpret_cast<float4*>(&h[j][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+    }
+    __syncthreads();
+    float g[3][kSeg];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float in[kSeg + 2 * kR];
+#pragma unroll
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = h[j][r0 + t][col];
+      taps4(in, win, g[j]);
+    }
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+      const int gx = x0 + col, gy = y0 + r0 + k;
+      if (gx >= cam.W || gy >= cam.H) continue;
+      const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
+      if (!mask[p]) continue;  // x2 = R M: no gradient where M = 0
+      const float x1 = target[3 * p + c], x2 = rgb[3 * p + c];
+      d_rgb[3 * p + c] += coef * (g[0][k] + 2.f * x2 * g[1][k] + x1 * g[2][k]);
+    }
   }
 }
 
@@ -292,19 +309,19 @@ Window make_window() {
 int ssim_tiles(int width, int height) { return ((width + kT - 1) / kT) * ((height + kT - 1) / kT); }
 
 cudaError_t launch_ssim(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams, int n_views,
-                        const int* tile_prefix, int n_tiles, float weight, double* partial, float* gmap,
-                        double* ssim, double* ssim_masked, float* d_rgb, cudaStream_t s) {
+                        const int* tile_prefix, int n_tiles, int64_t p_total, float weight, double* partial,
+                        float* gmap, double* ssim, double* ssim_masked, float* d_rgb, cudaStream_t s) {
   if (n_tiles == 0) return cudaSuccess;
   const Window w = make_window();
-  ssim_stats_kernel<<<n_tiles, kThreadsSsim, 0, s>>>(rgb, target, mask, cams, n_views, tile_prefix, w, partial,
-                                                     d_rgb ? gmap : nullptr);
+  ssim_stats_kernel<<<n_tiles, kThreadsSsim, 0, s>>>(rgb, target, mask, cams, n_views, tile_prefix, w, p_total,
+                                                     partial, d_rgb ? gmap : nullptr);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   ssim_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, tile_prefix, cams, n_views, ssim, ssim_masked);
   e = launched();
   if (e != cudaSuccess || !d_rgb) return e;
-  ssim_grad_kernel<<<n_tiles, kThreadsSsim, 0, s>>>(rgb, target, mask, cams, n_views, tile_prefix, w, gmap, weight,
-                                                    d_rgb);
+  ssim_grad_kernel<<<n_tiles, kThreadsSsim, 0, s>>>(rgb, target, mask, cams, n_views, tile_prefix, w, p_total, gmap,
+                                                    weight, d_rgb);
   return launched();
 }
 
