@@ -31,7 +31,9 @@ normal flip) held fixed:
 * one Adam update of the parameters (the optimiser of the training Sec. 5.1
   keeps; Kingma & Ba, 2015, Algorithm 1);
 * SSIM of masked images (the D-SSIM part of the photometric loss Eq. 2 masks,
-  and the masked SSIM of Sec. 5) and the masked PSNR of Sec. 5.
+  and the masked SSIM of Sec. 5) and the masked PSNR of Sec. 5;
+* the 2DGS depth distortion and normal consistency of Eq. 3, from the composited
+  planes (their readings: squared depth distances, expected-depth normals).
 
 Readings of points the paper leaves to prior work (documented with the
 project's design notes): culling of a surfel whose 3-sigma square reaches
@@ -213,7 +215,7 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
     n = T.shape[0]
     if n == 0:
         z = torch.zeros(B, dtype=DT)
-        return dict(rgb=torch.zeros(B, 3, dtype=DT), alpha=z, depth=z.clone(),
+        return dict(rgb=torch.zeros(B, 3, dtype=DT), alpha=z, depth=z.clone(), depth2=z.clone(),
                     normal=torch.zeros(B, 3, dtype=DT), t_final=torch.ones(B, dtype=DT),
                     n_blended=torch.zeros(B, dtype=torch.int64),
                     fragile=torch.zeros(B, dtype=torch.bool),
@@ -246,7 +248,7 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
     t_excl = torch.cat([ones, t_incl[:, :-1]], dim=1)
     w = torch.where(blended, a * t_excl, torch.zeros_like(a))
     out = dict(
-        rgb=w @ rgb, alpha=w.sum(1), depth=(w * z).sum(1), normal=w @ normal,
+        rgb=w @ rgb, alpha=w.sum(1), depth=(w * z).sum(1), depth2=(w * z * z).sum(1), normal=w @ normal,
         t_final=torch.where(blended, one_minus, torch.ones_like(a)).prod(1),
         n_blended=blended.sum(1), w=w)
     # decisions that a float32 evaluation may take the other way
@@ -283,11 +285,12 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
            prefilter: bool = True, chunk: int = 256) -> dict:
     """Render one view at the given flat pixel indices (row-major, default all).
 
-    Returns numpy FP64 arrays: rgb [P,3], alpha [P], depth [P], normal [P,3],
-    t_final [P], n_blended [P], fragile [P], fragile_grad [P], and score [N]
-    (max blending weight of each surfel over these pixels).  If ``d_out`` holds
-    cotangents (rgb, alpha, depth, normal) for these pixels, also returns
-    ``grads``: d(sum <d_out, out>)/d(xyz, quat, scale, opacity, sh).
+    Returns numpy FP64 arrays: rgb [P,3], alpha [P], depth [P], depth2 [P]
+    (sum of w z^2, for the depth distortion), normal [P,3], t_final [P],
+    n_blended [P], fragile [P], fragile_grad [P], and score [N] (max blending
+    weight of each surfel over these pixels).  If ``d_out`` holds cotangents
+    (rgb, alpha, depth, normal, optionally depth2) for these pixels, also
+    returns ``grads``: d(sum <d_out, out>)/d(xyz, quat, scale, opacity, sh).
     """
     need_grad = d_out is not None
     params = param_tensors(g, requires_grad=need_grad)
@@ -300,12 +303,13 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
     keys = ("T", "z_c", "normal", "rgb", "opacity")
     base = {k: proj[k].detach() for k in keys}
     acc = {k: torch.zeros_like(base[k]) for k in keys} if need_grad else None
-    res = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), depth=np.zeros(P), normal=np.zeros((P, 3)),
+    res = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), depth=np.zeros(P), depth2=np.zeros(P), normal=np.zeros((P, 3)),
                t_final=np.ones(P), n_blended=np.zeros(P, np.int64), fragile=np.zeros(P, bool),
                fragile_grad=np.zeros(P, bool))
     score = torch.zeros(N, dtype=DT)
     if need_grad:
         dts = {k: _t(d_out[k]) for k in ("rgb", "alpha", "depth", "normal")}
+        dts["depth2"] = _t(d_out["depth2"]) if "depth2" in d_out else torch.zeros(P, dtype=DT)
     scale_d = params["scale"].detach()
     rgb_raw = proj["rgb_raw"].detach()
     for s in range(0, P, chunk):
@@ -321,13 +325,14 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
         sub = {k: base[k][cols].clone().requires_grad_(need_grad) for k in keys}
         out = composite(sub["T"], sub["z_c"], sub["normal"], sub["rgb"], sub["opacity"], xs, ys,
                         rgb_raw=rgb_raw[cols])
-        for k in ("rgb", "alpha", "depth", "normal", "t_final", "n_blended", "fragile", "fragile_grad"):
+        for k in ("rgb", "alpha", "depth", "depth2", "normal", "t_final", "n_blended", "fragile", "fragile_grad"):
             res[k][s:e] = out[k].detach().numpy()
         if len(cols):
             score[cols] = torch.maximum(score[cols], out["w"].detach().max(0).values)
         if need_grad and len(cols):
             loss = ((out["rgb"] * dts["rgb"][s:e]).sum() + (out["alpha"] * dts["alpha"][s:e]).sum()
-                    + (out["depth"] * dts["depth"][s:e]).sum() + (out["normal"] * dts["normal"][s:e]).sum())
+                    + (out["depth"] * dts["depth"][s:e]).sum() + (out["normal"] * dts["normal"][s:e]).sum()
+                    + (out["depth2"] * dts["depth2"][s:e]).sum())
             gs = torch.autograd.grad(loss, [sub[k] for k in keys], allow_unused=True)
             for k, gk in zip(keys, gs):
                 if gk is not None:
@@ -473,3 +478,52 @@ def masked_psnr(rgb: np.ndarray, target: np.ndarray, mask: np.ndarray, max_i: fl
         return float("nan")
     mse = float((d * d).sum()) / n
     return float("inf") if mse == 0 else 20.0 * np.log10(max_i / np.sqrt(mse))
+
+
+# ----------------------------------------------------------------------------- 2DGS regularisers of Eq. 3
+# Eq. 3 adds the depth distortion L_d and the normal consistency L_n of 2DGS.  Both are
+# functions of the composited planes of one view: A (alpha), D = sum w z (depth),
+# Q = sum w z^2 (depth2) and N_r = sum w n (normal).
+
+def depth_distortion(alpha, depth, depth2, weight: float = 1.0):
+    """Per pixel sum_{i,j} w_i w_j (z_i - z_j)^2 over the blended entries, which equals
+    2 (A Q - D^2); the loss is its mean over the view's pixels.  Returns (loss, gradients of
+    weight * loss with respect to alpha, depth, depth2), numpy FP64 [h w]."""
+    a = torch.tensor(np.asarray(alpha, np.float64), requires_grad=True)
+    d = torch.tensor(np.asarray(depth, np.float64), requires_grad=True)
+    q = torch.tensor(np.asarray(depth2, np.float64), requires_grad=True)
+    loss = (2.0 * (a * q - d * d)).mean()
+    (weight * loss).backward()
+    return float(loss.detach()), a.grad.numpy(), d.grad.numpy(), q.grad.numpy()
+
+
+def normal_consistency(alpha, depth, normal, cam: dict, weight: float = 1.0, a_min: float = 0.5):
+    """Per pixel sum_i w_i (1 - n_i . N) = A - N . N_r, with N the unit normal of the surface of
+    expected depth D / A: the camera-frame points P = (D / A) ((x - cx) / fx, (y - cy) / fy, 1)
+    at the pixel centres, N = normalize((P[x+1] - P[x-1]) x (P[y+1] - P[y-1])) turned towards the
+    camera.  A pixel counts when it and its four neighbours lie inside the image and have
+    A > a_min; the loss is the sum over those pixels divided by h w.  Returns (loss, gradients of
+    weight * loss with respect to alpha [h w], depth [h w], normal [h w, 3])."""
+    W, H = cam["width"], cam["height"]
+    a = torch.tensor(np.asarray(alpha, np.float64).reshape(H, W), requires_grad=True)
+    d = torch.tensor(np.asarray(depth, np.float64).reshape(H, W), requires_grad=True)
+    nr = torch.tensor(np.asarray(normal, np.float64).reshape(H, W, 3), requires_grad=True)
+    ok = (a.detach() > a_min)
+    xs = (torch.arange(W, dtype=DT) + 0.5 - cam["cx"]) / cam["fx"]
+    ys = (torch.arange(H, dtype=DT) + 0.5 - cam["cy"]) / cam["fy"]
+    ray = torch.stack([xs[None, :].expand(H, W), ys[:, None].expand(H, W), torch.ones(H, W, dtype=DT)], -1)
+    z = torch.where(ok, d / torch.where(ok, a, torch.ones_like(a)), torch.zeros_like(d))
+    P = z[..., None] * ray
+    dx = P[1:-1, 2:] - P[1:-1, :-2]
+    dy = P[2:, 1:-1] - P[:-2, 1:-1]
+    c = torch.linalg.cross(dx, dy)
+    valid = (ok[1:-1, 1:-1] & ok[1:-1, 2:] & ok[1:-1, :-2] & ok[2:, 1:-1] & ok[:-2, 1:-1])
+    norm = torch.where(valid, c.norm(dim=-1), torch.ones_like(c[..., 0]))
+    N = c / norm[..., None]
+    facing = ((N * P[1:-1, 1:-1]).sum(-1) > 0).detach()
+    N = torch.where(facing[..., None], -N, N)
+    term = a[1:-1, 1:-1] - (N * nr[1:-1, 1:-1]).sum(-1)
+    loss = torch.where(valid, term, torch.zeros_like(term)).sum() / (H * W)
+    (weight * loss).backward()
+    return (float(loss.detach()), a.grad.numpy().reshape(-1), d.grad.numpy().reshape(-1),
+            nr.grad.numpy().reshape(-1, 3))

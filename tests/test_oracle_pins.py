@@ -527,3 +527,79 @@ def test_masked_psnr_hand_value():
     m = np.array([[1, 0], [1, 1]], np.uint8)
     assert oracle.masked_psnr(r, t, m) == pytest.approx(20 * math.log10(30.0), abs=1e-12)
     assert oracle.masked_psnr(t, t, m) == float("inf")
+
+
+# ----------------------------------------------------------------------------- 2DGS regularisers (Eq. 3)
+def test_depth2_and_depth_distortion_of_two_stacked_surfels():
+    """Two fronto-parallel surfels hit at their centres at depths 3 and 3.5: w1 = o1,
+    w2 = (1 - o1) o2, Q = w1 z1^2 + w2 z2^2 and the pixel's distortion
+    sum_{i,j} w_i w_j (z_i - z_j)^2 = 2 w1 w2 (z1 - z2)^2."""
+    cam = cam65()
+    o1, o2 = 0.6, 0.7
+    g = surfels([[0, 0, 0], [0, 0.5, 0]], [Q_FACE] * 2, [[0.1, 0.1]] * 2, [o1, o2], [[0.5, 0.5, 0.5]] * 2)
+    r = oracle.render(g, cam, pix(cam, 32, 32))
+    w1, w2 = o1, (1 - o1) * o2
+    assert r["depth2"][0] == pytest.approx(w1 * 9.0 + w2 * 12.25, abs=1e-12)
+    ld, ga, gd, gq = oracle.depth_distortion(r["alpha"], r["depth"], r["depth2"])
+    assert ld == pytest.approx(2 * w1 * w2 * 0.25, abs=1e-12)
+    one = oracle.render(surfels([0, 0, 0], Q_FACE, [0.1, 0.1], o1, [0.5] * 3), cam, pix(cam, 32, 32))
+    assert oracle.depth_distortion(one["alpha"], one["depth"], one["depth2"])[0] == pytest.approx(0.0, abs=1e-12)
+
+
+def test_depth_distortion_equals_brute_force_pairs():
+    rng = np.random.default_rng(7)
+    A, D, Q, ref = [], [], [], []
+    for _ in range(6):
+        n = int(rng.integers(1, 9))
+        w, z = rng.uniform(0, 0.3, n), rng.uniform(1, 4, n)
+        A.append(w.sum()); D.append((w * z).sum()); Q.append((w * z * z).sum())
+        ref.append(sum(w[i] * w[j] * (z[i] - z[j]) ** 2 for i in range(n) for j in range(n)))
+    ld, ga, gd, gq = oracle.depth_distortion(np.array(A), np.array(D), np.array(Q), weight=1.0)
+    assert ld == pytest.approx(np.mean(ref), rel=1e-12)
+    np.testing.assert_allclose(gq, 2 * np.array(A) / 6, rtol=1e-12)   # d/dQ of the mean of 2 (A Q - D^2)
+
+
+def _plane_images(cam, n, p0, a=0.8):
+    """Planes of a surface with unit normal n through p0 (camera frame), seen with opacity a."""
+    W, H = cam["width"], cam["height"]
+    xs = (np.arange(W) + 0.5 - cam["cx"]) / cam["fx"]
+    ys = (np.arange(H) + 0.5 - cam["cy"]) / cam["fy"]
+    ray = np.stack([np.broadcast_to(xs[None, :], (H, W)), np.broadcast_to(ys[:, None], (H, W)), np.ones((H, W))], -1)
+    t = (np.dot(n, p0)) / (ray @ n)
+    alpha = np.full(H * W, a)
+    return alpha, (a * t).reshape(-1), np.broadcast_to(a * np.asarray(n), (H * W, 3)).copy()
+
+
+@pytest.mark.parametrize("n", [(0.0, 0.0, -1.0), (0.3, -0.2, -0.93)])
+def test_normal_consistency_vanishes_on_a_plane(n):
+    """Expected depth of a plane and its own normal as the rendered normal: N from the depth
+    map equals the plane normal at every interior pixel, so A - N . N_r = 0."""
+    cam = synthetic.make_camera((0.0, -3.0, 0.0), 24, 18)
+    n = np.asarray(n) / np.linalg.norm(n)
+    alpha, depth, normal = _plane_images(cam, n, np.array([0.0, 0.0, 3.0]))
+    ln, ga, gd, gn = oracle.normal_consistency(alpha, depth, normal, cam)
+    assert abs(ln) <= 1e-12
+    valid = np.zeros((18, 24), bool)
+    valid[1:-1, 1:-1] = True
+    assert np.all(gn.reshape(18, 24, 3)[~valid] == 0.0)        # border pixels carry no term
+
+
+def test_normal_consistency_gradient_matches_central_differences():
+    cam = synthetic.make_camera((0.0, -3.0, 0.0), 12, 10)
+    rng = np.random.default_rng(8)
+    alpha, depth, normal = _plane_images(cam, np.array([0.2, 0.1, -0.97]) / np.linalg.norm([0.2, 0.1, -0.97]),
+                                         np.array([0.0, 0.0, 3.0]))
+    alpha = alpha + rng.uniform(0, 0.15, alpha.shape)
+    depth = depth * (1 + rng.uniform(-0.02, 0.02, depth.shape))
+    normal = normal + rng.normal(scale=0.05, size=normal.shape)
+    ln, ga, gd, gn = oracle.normal_consistency(alpha, depth, normal, cam, weight=0.05)
+    for arr, g in ((alpha, ga), (depth, gd), (normal, gn)):
+        flat = arr.reshape(-1)
+        for i in rng.choice(flat.size, size=8, replace=False):
+            x0 = flat[i]
+            flat[i] = x0 + 1e-6
+            lp = oracle.normal_consistency(alpha, depth, normal, cam)[0]
+            flat[i] = x0 - 1e-6
+            lm = oracle.normal_consistency(alpha, depth, normal, cam)[0]
+            flat[i] = x0
+            assert g.reshape(-1)[i] == pytest.approx(0.05 * (lp - lm) / 2e-6, abs=1e-9)
