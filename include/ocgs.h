@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define OCGS_ABI_VERSION 1
+#define OCGS_ABI_VERSION 2
 
 typedef enum {
   OCGS_OK = 0,
@@ -86,13 +86,15 @@ typedef struct {
   int32_t reserved;
 } ocgs_camera;
 
-/* Per-pixel images (device, caller-owned). As render output every pointer
- * must be non-null.  As backward cotangents any pointer may be NULL (zero). */
+/* Per-pixel images (device, caller-owned). As render output rgb, alpha, depth
+ * and normal must be non-null; depth2 may be NULL (not computed).  As backward
+ * cotangents any pointer may be NULL (zero). */
 typedef struct {
   float* rgb;     /* [P,3] C = sum w rgb */
   float* alpha;   /* [P]   A = sum w, the accumulated opacity of Eq. 1 */
   float* depth;   /* [P]   D = sum w z  (not normalised by A) */
   float* normal;  /* [P,3] N = sum w n  (camera frame, not normalised) */
+  float* depth2;  /* [P]   Q = sum w z^2, for the depth distortion of Eq. 3 */
 } ocgs_image;
 
 /* Launch options.  None of them changes a result: the support test is exact
@@ -362,6 +364,40 @@ ocgs_status ocgs_ssim(ocgs_ctx* ctx, const float* rgb, const float* target, cons
  */
 ocgs_status ocgs_masked_psnr(ocgs_ctx* ctx, const float* rgb, const float* target, const uint8_t* mask,
                              const ocgs_camera* cams, int32_t n_views, float max_i, double* psnr);
+
+/*
+ * ocgs_depth_distortion — the 2DGS depth distortion that Eq. 3 adds (weight
+ * alpha there), per view: the mean over pixels of sum_{i,j} w_i w_j (z_i - z_j)^2
+ * over the pixel's blended entries, which equals 2 (A Q - D^2) with the planes
+ * A = alpha, D = depth and Q = depth2 of ocgs_render (squared distances: the
+ * form that the front-to-back accumulation gives exactly).
+ *   alpha, depth, depth2  device [P]
+ *   loss     device [n_views] float64, overwritten
+ *   d_alpha, d_depth, d_depth2  device [P] or all NULL: += weight * d loss / d plane
+ * Asynchronous on the context stream.
+ */
+ocgs_status ocgs_depth_distortion(ocgs_ctx* ctx, const float* alpha, const float* depth, const float* depth2,
+                                  const ocgs_camera* cams, int32_t n_views, float weight, double* loss, float* d_alpha,
+                                  float* d_depth, float* d_depth2);
+
+/*
+ * ocgs_normal_consistency — the 2DGS normal consistency that Eq. 3 adds (weight
+ * beta there), per view: sum over counted pixels of sum_i w_i (1 - n_i . N) =
+ * A - N . N_r, divided by h*w.  N_r is the normal plane of ocgs_render; N is the
+ * unit normal of the expected-depth surface: camera-frame points
+ * P = (D / A) ((x + 1/2 - cx) / fx, (y + 1/2 - cy) / fy, 1) at pixel centres,
+ * N = normalize((P[x+1] - P[x-1]) x (P[y+1] - P[y-1])) turned towards the camera.
+ * A pixel counts when it and its four neighbours lie inside the image and have
+ * A > a_min (the expected depth needs coverage).
+ *   alpha, depth  device [P];  normal device [P,3]
+ *   loss     device [n_views] float64, overwritten
+ *   d_alpha, d_depth, d_normal  device or all NULL: += weight * d loss / d plane
+ *            (through N as well; allocates 24 bytes per pixel of scratch)
+ * Asynchronous on the context stream.
+ */
+ocgs_status ocgs_normal_consistency(ocgs_ctx* ctx, const float* alpha, const float* depth, const float* normal,
+                                    const ocgs_camera* cams, int32_t n_views, float weight, float a_min, double* loss,
+                                    float* d_alpha, float* d_depth, float* d_normal);
 
 /* Sizes of one forward state: K pairs, P pixels, and E = sum over pixels of
  * the length of the blended prefix of the pixel's tile list (the (pixel,

@@ -35,7 +35,7 @@ class Camera(C.Structure):
 
 class Image(C.Structure):
     _fields_ = [("rgb", C.c_void_p), ("alpha", C.c_void_p), ("depth", C.c_void_p),
-                ("normal", C.c_void_p)]
+                ("normal", C.c_void_p), ("depth2", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -103,6 +103,11 @@ SIGNATURES = {
                             C.c_float, C.c_void_p, C.c_void_p, C.c_void_p]),
     "ocgs_masked_psnr": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera), C.c_int32,
                                    C.c_float, C.c_void_p]),
+    "ocgs_depth_distortion": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
+                                        C.c_int32, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "ocgs_normal_consistency": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
+                                          C.c_int32, C.c_float, C.c_float, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p]),
     "ocgs_masked_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(Camera),
                                  C.c_int32, C.c_float, C.c_void_p, C.c_void_p]),
     "ocgs_autotune": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera), C.c_int32, C.c_char_p,

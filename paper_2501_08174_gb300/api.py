@@ -218,21 +218,25 @@ class Rasterizer:
 
     # -- the method
     def render(self, gaussians: dict, cameras: Sequence[dict], score: Optional[torch.Tensor] = None,
-               keep_state: bool = True, out: Optional[dict] = None):
+               keep_state: bool = True, out: Optional[dict] = None, depth2: bool = False):
         """Forward rasterization of all ``cameras`` in one batched pass.
 
-        Returns ({rgb, alpha, depth, normal}, ForwardState or None).  When
+        Returns ({rgb, alpha, depth, normal[, depth2]}, ForwardState or None).
+        ``depth2`` adds the plane Q = sum w z^2 (for the depth distortion).  When
         ``score`` [N] is given it is max-accumulated with each Gaussian's
         largest blending weight."""
         self._bind_stream()
         gs = gaussians_struct(gaussians, self.device)
         cams = camera_array(cameras)
         P = n_pixels(cameras)
+        f32 = dict(dtype=torch.float32, device=self.device)
         if out is None:
-            f32 = dict(dtype=torch.float32, device=self.device)
             out = dict(rgb=torch.empty(P, 3, **f32), alpha=torch.empty(P, **f32),
                        depth=torch.empty(P, **f32), normal=torch.empty(P, 3, **f32))
-        img = _lib.Image(_ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["normal"]))
+        if depth2 and out.get("depth2") is None:
+            out["depth2"] = torch.empty(P, **f32)
+        img = _lib.Image(_ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["normal"]),
+                         _ptr(out.get("depth2")))
         if score is not None:
             _check_param("score", score, (), self.device)
         handle = C.c_void_p()
@@ -254,7 +258,7 @@ class Rasterizer:
         if grads is None:
             grads = {k: torch.zeros_like(gaussians[k]) for k in PARAM_KEYS}
         img = _lib.Image(_ptr(d_out.get("rgb")), _ptr(d_out.get("alpha")), _ptr(d_out.get("depth")),
-                         _ptr(d_out.get("normal")))
+                         _ptr(d_out.get("normal")), _ptr(d_out.get("depth2")))
         for k, v in d_out.items():
             if v is not None and (not v.is_cuda or v.dtype != torch.float32 or not v.is_contiguous()):
                 raise ValueError(f"d_out[{k}] must be a contiguous float32 CUDA tensor")
@@ -322,6 +326,42 @@ class Rasterizer:
         self._call("ocgs_masked_psnr", self._ctx, _ptr(rgb), _ptr(target), _ptr(mask), camera_array(cameras),
                    len(cameras), float(max_i), _ptr(out))
         return out
+
+    def _check_planes(self, cameras, **planes):
+        P = n_pixels(cameras)
+        for name, (t, ch) in planes.items():
+            if t is None:
+                continue
+            if not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or t.numel() != ch * P:
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of {P}x{ch} values")
+
+    def depth_distortion(self, alpha, depth, depth2, cameras: Sequence[dict], weight: float = 1.0,
+                         grads: Optional[dict] = None) -> torch.Tensor:
+        """Per-view 2DGS depth distortion (Eq. 3) from the alpha, depth and depth2 planes; with
+        ``grads`` = {alpha, depth, depth2} adds weight * d loss / d plane into them."""
+        self._bind_stream()
+        g = grads or {}
+        self._check_planes(cameras, alpha=(alpha, 1), depth=(depth, 1), depth2=(depth2, 1),
+                           d_alpha=(g.get("alpha"), 1), d_depth=(g.get("depth"), 1), d_depth2=(g.get("depth2"), 1))
+        loss = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_depth_distortion", self._ctx, _ptr(alpha), _ptr(depth), _ptr(depth2), camera_array(cameras),
+                   len(cameras), float(weight), _ptr(loss), _ptr(g.get("alpha")), _ptr(g.get("depth")),
+                   _ptr(g.get("depth2")))
+        return loss
+
+    def normal_consistency(self, alpha, depth, normal, cameras: Sequence[dict], weight: float = 1.0,
+                           a_min: float = 0.5, grads: Optional[dict] = None) -> torch.Tensor:
+        """Per-view 2DGS normal consistency (Eq. 3) from the alpha, depth and normal planes; with
+        ``grads`` = {alpha, depth, normal} adds weight * d loss / d plane into them."""
+        self._bind_stream()
+        g = grads or {}
+        self._check_planes(cameras, alpha=(alpha, 1), depth=(depth, 1), normal=(normal, 3),
+                           d_alpha=(g.get("alpha"), 1), d_depth=(g.get("depth"), 1), d_normal=(g.get("normal"), 3))
+        loss = torch.empty(len(cameras), dtype=torch.float64, device=self.device)
+        self._call("ocgs_normal_consistency", self._ctx, _ptr(alpha), _ptr(depth), _ptr(normal),
+                   camera_array(cameras), len(cameras), float(weight), float(a_min), _ptr(loss),
+                   _ptr(g.get("alpha")), _ptr(g.get("depth")), _ptr(g.get("normal")))
+        return loss
 
     def accumulate_contribution(self, gaussians: dict, cameras: Sequence[dict],
                                 score: Optional[torch.Tensor] = None) -> torch.Tensor:

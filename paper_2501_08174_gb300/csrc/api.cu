@@ -229,6 +229,10 @@ ocgs_status plan_loss(ocgs_ctx* ctx, const ocgs_camera* cams, int n_views, LossP
     std::memset(&d, 0, sizeof(DevCam));
     d.W = cams[v].width;
     d.H = cams[v].height;
+    d.fx = cams[v].fx;
+    d.fy = cams[v].fy;
+    d.cx = cams[v].cx;
+    d.cy = cams[v].cy;
     d.pix_offset = pix;
     const int64_t np = (int64_t)cams[v].width * cams[v].height;
     lp->prefix[v] = blocks;
@@ -387,7 +391,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   ra.ranges = st->ranges;
   ra.vals = st->vals;
   ra.rec = st->rec;
-  if (out) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal};
+  if (out) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
   ra.t_final = st->t_final;
   ra.last = st->last;
   ra.score = score;
@@ -662,7 +666,7 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   ba.rec = st->rec;
   ba.t_final = st->t_final;
   ba.last = st->last;
-  ba.d_out = ImgPtrs{d_out->rgb, d_out->alpha, d_out->depth, d_out->normal};
+  ba.d_out = ImgPtrs{d_out->rgb, d_out->alpha, d_out->depth, d_out->normal, d_out->depth2};
   ba.grad_rec = grad_rec;
   ba.tile_order = st->tile_order;
   uint32_t* queue = nullptr;
@@ -796,6 +800,71 @@ ocgs_status ocgs_masked_psnr(ocgs_ctx* ctx, const float* rgb, const float* targe
   CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
   CK(launch_masked_psnr(rgb, target, mask, d_cams, n_views, d_prefix, lp.blocks, (double)max_i, partial, psnr, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_depth_distortion(ocgs_ctx* ctx, const float* alpha, const float* depth, const float* depth2,
+                                  const ocgs_camera* cams, int32_t n_views, float weight, double* loss, float* d_alpha,
+                                  float* d_depth, float* d_depth2) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!alpha || !depth || !depth2 || !loss) return set_err(ctx, OCGS_ERR_ARG, "alpha, depth, depth2 and loss must be non-NULL");
+  if ((d_alpha != nullptr) != (d_depth != nullptr) || (d_alpha != nullptr) != (d_depth2 != nullptr))
+    return set_err(ctx, OCGS_ERR_ARG, "d_alpha, d_depth and d_depth2 must all be given or all be NULL");
+  if (!std::isfinite(weight)) return set_err(ctx, OCGS_ERR_ARG, "weight must be finite");
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, lp.blocks));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_depth_distortion(alpha, depth, depth2, d_cams, n_views, d_prefix, lp.blocks, weight, partial, loss,
+                             d_alpha, d_depth, d_depth2, s));
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_normal_consistency(ocgs_ctx* ctx, const float* alpha, const float* depth, const float* normal,
+                                    const ocgs_camera* cams, int32_t n_views, float weight, float a_min, double* loss,
+                                    float* d_alpha, float* d_depth, float* d_normal) {
+  if (!ctx) return OCGS_ERR_ARG;
+  if (!alpha || !depth || !normal || !loss) return set_err(ctx, OCGS_ERR_ARG, "alpha, depth, normal and loss must be non-NULL");
+  if ((d_alpha != nullptr) != (d_depth != nullptr) || (d_alpha != nullptr) != (d_normal != nullptr))
+    return set_err(ctx, OCGS_ERR_ARG, "d_alpha, d_depth and d_normal must all be given or all be NULL");
+  if (!std::isfinite(weight) || !std::isfinite(a_min) || a_min < 0.f)
+    return set_err(ctx, OCGS_ERR_ARG, "weight must be finite and a_min finite and >= 0");
+  LossPlan lp;
+  ocgs_status r = plan_loss(ctx, cams, n_views, &lp);
+  if (r != OCGS_OK) return r;
+  int64_t P = 0;
+  for (int v = 0; v < n_views; ++v) {
+    if (!(cams[v].fx > 0.f && cams[v].fy > 0.f) || !std::isfinite(cams[v].cx) || !std::isfinite(cams[v].cy))
+      return set_err(ctx, OCGS_ERR_ARG, "camera intrinsics must be finite with fx, fy > 0");
+    P += (int64_t)cams[v].width * cams[v].height;
+  }
+  CK(cudaSetDevice(ctx->device));
+  cudaStream_t s = ctx->stream;
+  Arena tmp(ctx);
+  DevCam* d_cams;
+  int* d_prefix;
+  double* partial;
+  float* gmap = nullptr;
+  CK(tmp.alloc(&d_cams, n_views));
+  CK(tmp.alloc(&d_prefix, n_views + 1));
+  CK(tmp.alloc(&partial, lp.blocks));
+  if (d_alpha) CK(tmp.alloc(&gmap, 6 * (size_t)P));
+  StageTimer t(ctx, OCGS_STAGE_LOSS);
+  CK(cudaMemcpyAsync(d_cams, lp.cams.data(), sizeof(DevCam) * n_views, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(d_prefix, lp.prefix.data(), sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s));
+  CK(launch_normal_consistency(alpha, depth, normal, d_cams, n_views, d_prefix, lp.blocks, weight, a_min, partial,
+                               gmap, loss, d_alpha, d_depth, d_normal, s));
   return OCGS_OK;
 }
 

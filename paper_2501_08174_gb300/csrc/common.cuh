@@ -60,6 +60,7 @@ struct ImgPtrs {
   float* alpha;
   float* depth;
   float* normal;
+  float* depth2;  // sum w z^2, optional
 };
 
 struct GaussPtrs {
@@ -569,6 +570,16 @@ int ssim_tiles(int width, int height);
 cudaError_t launch_ssim(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams, int n_views,
                         const int* tile_prefix, int n_tiles, int64_t p_total, float weight, double* partial,
                         float* gmap, double* ssim, double* ssim_masked, float* d_rgb, cudaStream_t s);
+// 2DGS regularisers (regularisers.cu), over the loss blocks; partial holds one
+// double per block; gmap 6 floats per pixel (normal consistency, with adjoints)
+cudaError_t launch_depth_distortion(const float* alpha, const float* depth, const float* depth2, const DevCam* cams,
+                                    int n_views, const int* block_prefix, int n_blocks, float weight,
+                                    double* partial, double* loss, float* d_alpha, float* d_depth, float* d_depth2,
+                                    cudaStream_t s);
+cudaError_t launch_normal_consistency(const float* alpha, const float* depth, const float* normal, const DevCam* cams,
+                                      int n_views, const int* block_prefix, int n_blocks, float weight, float a_min,
+                                      double* partial, float* gmap, double* loss, float* d_alpha, float* d_depth,
+                                      float* d_normal, cudaStream_t s);
 // PSNR over the loss blocks (kLossBlockPixels per block); partial holds 2 doubles per block
 cudaError_t launch_masked_psnr(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams,
                                int n_views, const int* block_prefix, int n_blocks, double max_i, double* partial,

@@ -45,7 +45,8 @@ __device__ unsigned long long g_diag[8];
 #define OCGS_BWD_WARPS 16
 #endif
 
-template <int TW, int TH, int PPT, bool IMG, bool SCORE>
+// Q2: also accumulate Q = sum w z^2 (the depth distortion's third plane)
+template <int TW, int TH, int PPT, bool IMG, bool SCORE, bool Q2>
 __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW * TH)) raster_fwd_kernel(const RasterArgs a) {
   constexpr int NT = TW * TH / PPT;  // threads, and records per shared-memory batch
   __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
@@ -83,14 +84,14 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
     // pixel k of this thread is lane (k & 1) of pair k / 2; an odd PPT leaves a
     // dummy lane that starts done
     constexpr int NP = (PPT + 1) / 2;
-    float2 T[NP], c0[NP], c1[NP], c2[NP], dep[NP], n0[NP], n1[NP], n2[NP];
+    float2 T[NP], c0[NP], c1[NP], c2[NP], dep[NP], n0[NP], n1[NP], n2[NP], qz[NP];
     uint32_t last[2 * NP];
     bool done[2 * NP];
     bool alldone = true;
 #pragma unroll
     for (int p = 0; p < NP; ++p) {
       T[p] = bc2(1.f);
-      c0[p] = c1[p] = c2[p] = dep[p] = n0[p] = n1[p] = n2[p] = bc2(0.f);
+      c0[p] = c1[p] = c2[p] = dep[p] = n0[p] = n1[p] = n2[p] = qz[p] = bc2(0.f);
     }
 #pragma unroll
     for (int k = 0; k < 2 * NP; ++k) {
@@ -165,6 +166,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
               c1[p] = __ffma2_rn(w, bc2(ap.y), c1[p]);
               c2[p] = __ffma2_rn(w, bc2(ap.z), c2[p]);
               dep[p] = __ffma2_rn(w, e.z, dep[p]);
+              if (Q2) qz[p] = __ffma2_rn(__fmul2_rn(w, e.z), e.z, qz[p]);
               n0[p] = __ffma2_rn(w, bc2(ap.w), n0[p]);
               n1[p] = __ffma2_rn(w, bc2(an.x), n1[p]);
               n2[p] = __ffma2_rn(w, bc2(an.y), n2[p]);
@@ -203,6 +205,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
           a.out.rgb[3 * pix + 2] = lane2(c2[p], i);
           a.out.alpha[pix] = 1.f - Tk;
           a.out.depth[pix] = lane2(dep[p], i);
+          if (Q2) a.out.depth2[pix] = lane2(qz[p], i);
           a.out.normal[3 * pix + 0] = lane2(n0[p], i);
           a.out.normal[3 * pix + 1] = lane2(n1[p], i);
           a.out.normal[3 * pix + 2] = lane2(n2[p], i);
@@ -260,8 +263,9 @@ __device__ __forceinline__ int warp_reduce(float* v, int lane) {
   return real >= 1 ? base : -1;
 }
 
-// GEO: a depth or normal cotangent is given; without one the depth and normal
-// terms of the adjoint are zero and are not evaluated (13 slots instead of 18).
+// GEO: a depth, depth2 or normal cotangent is given; without one the depth and
+// normal terms of the adjoint are zero and are not evaluated (13 slots instead
+// of 18).
 template <int TW, int TH, int PPT, bool GEO>
 __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW * TH)) raster_bwd_kernel(const RasterBwdArgs a) {
   constexpr int NT = TW * TH / PPT;
@@ -300,7 +304,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
     // pixel k of this thread is lane (k & 1) of pair k / 2 (an odd PPT leaves an idle lane)
     constexpr int NP = (PPT + 1) / 2;
     float2 T[NP], gAT[NP], S[NP];
-    float2 gC0[NP], gC1[NP], gC2[NP], gD[NP], gN0[NP], gN1[NP], gN2[NP];
+    float2 gC0[NP], gC1[NP], gC2[NP], gD[NP], gN0[NP], gN1[NP], gN2[NP], gQ[NP];
     uint32_t last[2 * NP];
     uint32_t thread_last = 0;
 #pragma unroll
@@ -308,7 +312,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
       T[p] = bc2(1.f);
       gAT[p] = bc2(0.f);
       S[p] = bc2(0.f);  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
-      gC0[p] = gC1[p] = gC2[p] = gD[p] = gN0[p] = gN1[p] = gN2[p] = bc2(0.f);
+      gC0[p] = gC1[p] = gC2[p] = gD[p] = gN0[p] = gN1[p] = gN2[p] = gQ[p] = bc2(0.f);
     }
 #pragma unroll
     for (int k = 0; k < 2 * NP; ++k) {
@@ -327,6 +331,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
         }
         if (a.d_out.alpha) set_lane2(gAT[p], i, a.d_out.alpha[pix] * Tf);
         if (GEO && a.d_out.depth) set_lane2(gD[p], i, a.d_out.depth[pix]);
+        if (GEO && a.d_out.depth2) set_lane2(gQ[p], i, a.d_out.depth2[pix]);
         if (GEO && a.d_out.normal) {
           set_lane2(gN0[p], i, a.d_out.normal[3 * pix]);
           set_lane2(gN1[p], i, a.d_out.normal[3 * pix + 1]);
@@ -408,6 +413,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               F = __ffma2_rn(gC2[p], bc2(ap.z), F);
               if (GEO) {
                 F = __ffma2_rn(gD[p], e.z, F);
+                F = __ffma2_rn(__fmul2_rn(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
                 F = __ffma2_rn(gN0[p], bc2(ap.w), F);
                 F = __ffma2_rn(gN1[p], bc2(an.x), F);
                 F = __ffma2_rn(gN2[p], bc2(an.y), F);
@@ -439,7 +445,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
               const float2 grf = __ffma2_rn(grs, bc2(-1.f), grho);  // grho where the filter won, else 0
               float2 gzs = bc2(0.f);
               if (GEO) {
-                const float2 gz = __fmul2_rn(gD[p], wm);
+                // d/dz of w (gD z + gQ z^2)
+                const float2 gz = __fmul2_rn(__ffma2_rn(__fmul2_rn(bc2(2.f), gQ[p]), e.z, gD[p]), wm);
                 gzs = make_float2(s0 ? gz.x : 0.f, s1 ? gz.y : 0.f);
                 acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
                 acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
@@ -509,9 +516,12 @@ cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
   if (grid == 0) return cudaSuccess;
   constexpr int NT = TW * TH / PPT;
   const bool score = a.score != nullptr;
-  if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true><<<grid, NT, 0, s>>>(a);
-  else if (img) raster_fwd_kernel<TW, TH, PPT, true, false><<<grid, NT, 0, s>>>(a);
-  else if (score) raster_fwd_kernel<TW, TH, PPT, false, true><<<grid, NT, 0, s>>>(a);
+  const bool q2 = img && a.out.depth2 != nullptr;
+  if (img && score && q2) raster_fwd_kernel<TW, TH, PPT, true, true, true><<<grid, NT, 0, s>>>(a);
+  else if (img && q2) raster_fwd_kernel<TW, TH, PPT, true, false, true><<<grid, NT, 0, s>>>(a);
+  else if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true, false><<<grid, NT, 0, s>>>(a);
+  else if (img) raster_fwd_kernel<TW, TH, PPT, true, false, false><<<grid, NT, 0, s>>>(a);
+  else if (score) raster_fwd_kernel<TW, TH, PPT, false, true, false><<<grid, NT, 0, s>>>(a);
   else return cudaSuccess;
   return launched();
 }
@@ -520,7 +530,8 @@ template <int TW, int TH, int PPT>
 cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
   const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
   if (grid == 0) return cudaSuccess;
-  if (a.d_out.depth || a.d_out.normal) raster_bwd_kernel<TW, TH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
+  if (a.d_out.depth || a.d_out.normal || a.d_out.depth2)
+    raster_bwd_kernel<TW, TH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
   else raster_bwd_kernel<TW, TH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
   return launched();
 }

@@ -1,0 +1,220 @@
+// The 2DGS regularisers that Eq. 3 adds to the loss, on the composited planes of
+// every view:
+//  * depth distortion: per pixel sum_{i,j} w_i w_j (z_i - z_j)^2 = 2 (A Q - D^2),
+//    from A = sum w, D = sum w z and Q = sum w z^2; mean over the view's pixels;
+//  * normal consistency: per pixel sum_i w_i (1 - n_i . N) = A - N . N_r, with N_r
+//    = sum w n and N the unit normal of the expected-depth surface, from central
+//    differences of the camera-frame points P = (D / A) ray at the four
+//    neighbours, turned towards the camera; counted where the pixel and its four
+//    neighbours lie inside the image and have A > a_min; summed and divided by h w.
+// Both adjoints are written as cotangents of the planes, which the backward
+// rasterizer takes.  Every pixel writes only its own entries: the normal
+// consistency's stencil adjoint goes through a per-pixel map that a second pass
+// gathers.
+#include "common.cuh"
+
+namespace ocgs {
+namespace {
+
+constexpr int kRegThreads = 256;
+
+struct Block {
+  int v;
+  int64_t lo, hi;  // pixels [lo, hi) of view v
+};
+
+__device__ __forceinline__ Block loss_block(const int* block_prefix, int n_views, const DevCam* cams) {
+  Block b;
+  b.v = view_of_tile(block_prefix, n_views, blockIdx.x);
+  const DevCam& cam = cams[b.v];
+  const int64_t npix = (int64_t)cam.W * cam.H;
+  b.lo = (int64_t)(blockIdx.x - block_prefix[b.v]) * kLossBlockPixels;
+  b.hi = (b.lo + kLossBlockPixels < npix) ? b.lo + kLossBlockPixels : npix;
+  return b;
+}
+
+__device__ __forceinline__ void block_sum(double acc, double* out) {
+  __shared__ double part[kRegThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kRegThreads / 32; ++w) t += part[w];
+    *out = t;
+  }
+}
+
+__global__ void __launch_bounds__(kRegThreads) depth_distortion_kernel(
+    const float* __restrict__ alpha, const float* __restrict__ depth, const float* __restrict__ depth2,
+    const DevCam* __restrict__ cams, int n_views, const int* __restrict__ block_prefix, float weight,
+    double* __restrict__ partial, float* __restrict__ d_alpha, float* __restrict__ d_depth,
+    float* __restrict__ d_depth2) {
+  const Block b = loss_block(block_prefix, n_views, cams);
+  const DevCam& cam = cams[b.v];
+  const float k = weight / ((float)cam.W * (float)cam.H);
+  double acc = 0.0;
+  for (int64_t i = b.lo + threadIdx.x; i < b.hi; i += kRegThreads) {
+    const int64_t p = cam.pix_offset + i;
+    const float A = alpha[p], D = depth[p], Q = depth2[p];
+    acc += 2.0 * ((double)A * (double)Q - (double)D * (double)D);
+    if (d_alpha) {
+      d_alpha[p] += k * 2.f * Q;
+      d_depth[p] += k * -4.f * D;
+      d_depth2[p] += k * 2.f * A;
+    }
+  }
+  block_sum(acc, partial + blockIdx.x);
+}
+
+struct Pt {
+  float3 P;
+  bool ok;
+};
+
+__device__ __forceinline__ Pt surface_point(const float* __restrict__ alpha, const float* __restrict__ depth,
+                                            const DevCam& cam, int x, int y, float a_min) {
+  Pt r;
+  r.ok = false;
+  r.P = make_float3(0.f, 0.f, 0.f);
+  if (x < 0 || x >= cam.W || y < 0 || y >= cam.H) return r;
+  const int64_t p = cam.pix_offset + (int64_t)y * cam.W + x;
+  const float A = alpha[p];
+  if (!(A > a_min)) return r;
+  const float d = depth[p] / A;
+  r.P = make_float3(d * (((float)x + 0.5f - cam.cx) / cam.fx), d * (((float)y + 0.5f - cam.cy) / cam.fy), d);
+  r.ok = true;
+  return r;
+}
+
+__device__ __forceinline__ float3 sub3(float3 a, float3 b) { return make_float3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float dot3(float3 a, float3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ float3 cross3(float3 a, float3 b) {
+  return make_float3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+
+// gmap [P][6] (or NULL): d(weight term)/d(dx) and d/d(dy) of the pixel's central differences
+__global__ void __launch_bounds__(kRegThreads) normal_consistency_kernel(
+    const float* __restrict__ alpha, const float* __restrict__ depth, const float* __restrict__ normal,
+    const DevCam* __restrict__ cams, int n_views, const int* __restrict__ block_prefix, float weight, float a_min,
+    double* __restrict__ partial, float* __restrict__ gmap, float* __restrict__ d_alpha,
+    float* __restrict__ d_normal) {
+  const Block b = loss_block(block_prefix, n_views, cams);
+  const DevCam& cam = cams[b.v];
+  const float k = weight / ((float)cam.W * (float)cam.H);
+  double acc = 0.0;
+  for (int64_t i = b.lo + threadIdx.x; i < b.hi; i += kRegThreads) {
+    const int64_t p = cam.pix_offset + i;
+    const int x = (int)(i % cam.W), y = (int)(i / cam.W);
+    float g6[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    const Pt c = surface_point(alpha, depth, cam, x, y, a_min);
+    const Pt xp = surface_point(alpha, depth, cam, x + 1, y, a_min), xm = surface_point(alpha, depth, cam, x - 1, y, a_min);
+    const Pt yp = surface_point(alpha, depth, cam, x, y + 1, a_min), ym = surface_point(alpha, depth, cam, x, y - 1, a_min);
+    if (c.ok && xp.ok && xm.ok && yp.ok && ym.ok) {
+      const float3 dx = sub3(xp.P, xm.P), dy = sub3(yp.P, ym.P);
+      const float3 cr = cross3(dx, dy);
+      const float len = sqrtf(dot3(cr, cr));
+      if (len > 0.f) {
+        const float3 ch = make_float3(cr.x / len, cr.y / len, cr.z / len);
+        const float s = dot3(ch, c.P) > 0.f ? -1.f : 1.f;  // turned towards the camera
+        const float3 N = make_float3(s * ch.x, s * ch.y, s * ch.z);
+        const float3 Nr = make_float3(normal[3 * p], normal[3 * p + 1], normal[3 * p + 2]);
+        const float A = alpha[p];
+        acc += (double)A - (double)dot3(N, Nr);
+        if (gmap) {
+          d_alpha[p] += k;
+          d_normal[3 * p] -= k * N.x;
+          d_normal[3 * p + 1] -= k * N.y;
+          d_normal[3 * p + 2] -= k * N.z;
+          // term depends on cr through N = s cr / |cr|: g_cr = s (I - ch ch^T) g_N / |cr|, g_N = -k Nr
+          const float3 gN = make_float3(-k * Nr.x, -k * Nr.y, -k * Nr.z);
+          const float pr = dot3(ch, gN);
+          const float3 gc = make_float3(s * (gN.x - ch.x * pr) / len, s * (gN.y - ch.y * pr) / len,
+                                        s * (gN.z - ch.z * pr) / len);
+          const float3 gdx = cross3(dy, gc), gdy = cross3(gc, dx);  // d(gc . (dx x dy))
+          g6[0] = gdx.x; g6[1] = gdx.y; g6[2] = gdx.z;
+          g6[3] = gdy.x; g6[4] = gdy.y; g6[5] = gdy.z;
+        }
+      }
+    }
+    if (gmap) {
+#pragma unroll
+      for (int j = 0; j < 6; ++j) gmap[6 * p + j] = g6[j];
+    }
+  }
+  block_sum(acc, partial + blockIdx.x);
+}
+
+// point gradient of pixel q: it is the x+1 point of q - x, the x-1 point of
+// q + x, the y+1 point of q - W and the y-1 point of q + W; then P = (D / A) ray
+__global__ void __launch_bounds__(kRegThreads) normal_consistency_gather_kernel(
+    const float* __restrict__ alpha, const float* __restrict__ depth, const DevCam* __restrict__ cams, int n_views,
+    const int* __restrict__ block_prefix, float a_min, const float* __restrict__ gmap, float* __restrict__ d_alpha,
+    float* __restrict__ d_depth) {
+  const Block b = loss_block(block_prefix, n_views, cams);
+  const DevCam& cam = cams[b.v];
+  for (int64_t i = b.lo + threadIdx.x; i < b.hi; i += kRegThreads) {
+    const int64_t q = cam.pix_offset + i;
+    const int x = (int)(i % cam.W), y = (int)(i / cam.W);
+    const float A = alpha[q];
+    if (!(A > a_min)) continue;  // not a point of any counted stencil
+    float3 g = make_float3(0.f, 0.f, 0.f);
+    if (x > 0) { const float* m = gmap + 6 * (q - 1); g.x += m[0]; g.y += m[1]; g.z += m[2]; }
+    if (x + 1 < cam.W) { const float* m = gmap + 6 * (q + 1); g.x -= m[0]; g.y -= m[1]; g.z -= m[2]; }
+    if (y > 0) { const float* m = gmap + 6 * (q - cam.W); g.x += m[3]; g.y += m[4]; g.z += m[5]; }
+    if (y + 1 < cam.H) { const float* m = gmap + 6 * (q + cam.W); g.x -= m[3]; g.y -= m[4]; g.z -= m[5]; }
+    const float3 ray = make_float3(((float)x + 0.5f - cam.cx) / cam.fx, ((float)y + 0.5f - cam.cy) / cam.fy, 1.f);
+    const float gr = dot3(g, ray);
+    d_depth[q] += gr / A;
+    d_alpha[q] -= gr * depth[q] / (A * A);
+  }
+}
+
+__global__ void reg_final_kernel(const double* __restrict__ partial, const int* __restrict__ block_prefix,
+                                 const DevCam* __restrict__ cams, int n_views, double* __restrict__ loss) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_views) return;
+  double t = 0.0;
+  for (int b = block_prefix[v]; b < block_prefix[v + 1]; ++b) t += partial[b];
+  loss[v] = t / ((double)cams[v].W * (double)cams[v].H);
+}
+
+}  // namespace
+
+cudaError_t launch_depth_distortion(const float* alpha, const float* depth, const float* depth2, const DevCam* cams,
+                                    int n_views, const int* block_prefix, int n_blocks, float weight,
+                                    double* partial, double* loss, float* d_alpha, float* d_depth, float* d_depth2,
+                                    cudaStream_t s) {
+  if (n_blocks > 0) {
+    depth_distortion_kernel<<<n_blocks, kRegThreads, 0, s>>>(alpha, depth, depth2, cams, n_views, block_prefix,
+                                                             weight, partial, d_alpha, d_depth, d_depth2);
+    cudaError_t e = launched();
+    if (e != cudaSuccess) return e;
+  }
+  reg_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  return launched();
+}
+
+cudaError_t launch_normal_consistency(const float* alpha, const float* depth, const float* normal, const DevCam* cams,
+                                      int n_views, const int* block_prefix, int n_blocks, float weight, float a_min,
+                                      double* partial, float* gmap, double* loss, float* d_alpha, float* d_depth,
+                                      float* d_normal, cudaStream_t s) {
+  if (n_blocks > 0) {
+    normal_consistency_kernel<<<n_blocks, kRegThreads, 0, s>>>(alpha, depth, normal, cams, n_views, block_prefix,
+                                                               weight, a_min, partial, d_alpha ? gmap : nullptr,
+                                                               d_alpha, d_normal);
+    cudaError_t e = launched();
+    if (e != cudaSuccess) return e;
+    if (d_alpha) {
+      normal_consistency_gather_kernel<<<n_blocks, kRegThreads, 0, s>>>(alpha, depth, cams, n_views, block_prefix,
+                                                                        a_min, gmap, d_alpha, d_depth);
+      e = launched();
+      if (e != cudaSuccess) return e;
+    }
+  }
+  reg_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  return launched();
+}
+
+}  // namespace ocgs
