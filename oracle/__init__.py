@@ -8,4 +8,5 @@ from .ocgs_oracle import (ALPHA_MAX, ALPHA_MIN, RHO_CUT, SIGMA_F2, T_EPS, backgr
                           background_loss_grad, composite, contribution_score, keep_set, project,
                           prune, quat_to_rotmat, render, render_views, sh_basis, adam_step,
                           masked_psnr, masked_ssim, ssim_blur, ssim_map, ssim_window,
-                          depth_distortion, normal_consistency)
+                          depth_distortion, normal_consistency, project_ewa, render_3d,
+                          contribution_score_3d)

@@ -527,3 +527,94 @@ def normal_consistency(alpha, depth, normal, cam: dict, weight: float = 1.0, a_m
     (weight * loss).backward()
     return (float(loss.detach()), a.grad.numpy().reshape(-1), d.grad.numpy().reshape(-1),
             nr.grad.numpy().reshape(-1, 3))
+
+
+# ----------------------------------------------------------------------------- 3DGS variant (Appendix B)
+# Appendix B runs the same pruning record in 3DGS: 3D Gaussians splatted with the EWA
+# projection of their covariance.  Same skip (rho > 9, alpha < 1/255), clamp, stop rule,
+# depth order and contribution score as the 2DGS path; rho is the Mahalanobis distance
+# under the projected covariance dilated by the 3DGS screen-space low-pass (0.3 px^2).
+EWA_DILATION = 0.3
+
+
+def project_ewa(g: dict, cam: dict) -> dict:
+    """Per-Gaussian EWA projection: camera-frame mean t, 3D covariance R diag(s^2) R^T,
+    image covariance J W Sigma W^T J^T + 0.3 I (J the Jacobian of the pinhole projection
+    at t, W the world-to-camera rotation), its inverse (the conic), centre pixel, colour
+    and centre depth.  Scales are [N,3]."""
+    r_cw, t_cw, K = camera_tensors(cam)
+    xyz, quat, scale = _t(g["xyz"]), _t(g["quat"]), _t(g["scale"])
+    rot = quat_to_rotmat(quat / quat.norm(dim=-1, keepdim=True))
+    sig3 = rot @ torch.diag_embed(scale * scale) @ rot.transpose(1, 2)
+    t = xyz @ r_cw.T + t_cw
+    tx, ty, tz = t[:, 0], t[:, 1], t[:, 2]
+    fx, fy = cam["fx"], cam["fy"]
+    zero = torch.zeros_like(tz)
+    J = torch.stack([torch.stack([fx / tz, zero, -fx * tx / (tz * tz)], -1),
+                     torch.stack([zero, fy / tz, -fy * ty / (tz * tz)], -1)], 1)     # [N,2,3]
+    Tm = J @ r_cw
+    cov2 = Tm @ sig3 @ Tm.transpose(1, 2) + EWA_DILATION * torch.eye(2, dtype=DT)
+    conic = torch.linalg.inv(cov2)
+    centre = torch.stack([fx * tx / tz + cam["cx"], fy * ty / tz + cam["cy"]], -1)
+    campos = -(r_cw.T @ t_cw)
+    d = xyz - campos
+    d = d / d.norm(dim=-1, keepdim=True)
+    rgb = ((sh_basis(d, g["sh_degree"])[:, :, None] * _t(g["sh"])).sum(1) + 0.5).clamp(min=0.0)
+    return dict(conic=conic, cov2=cov2, centre=centre, z=tz, rgb=rgb, opacity=_t(g["opacity"]),
+                culled=tz <= cam["near"])
+
+
+def render_3d(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, chunk: int = 256) -> dict:
+    """Forward of the 3DGS variant at the given flat pixel indices (default all): per pixel,
+    the non-culled Gaussians in ascending centre depth (ties by index), rho = d^T conic d
+    with d = x - centre, alpha = min(0.99, o exp(-rho/2)), skipped if rho > 9 or
+    alpha < 1/255, stopped at the first candidate with T (1 - alpha) < 1e-4 (not blended).
+    Returns numpy rgb [P,3], alpha [P], depth [P] (sum w z), t_final [P], n_blended [P],
+    fragile [P] and score [N] (max blending weight over these pixels)."""
+    pr = project_ewa(g, cam)
+    N = pr["z"].shape[0]
+    alive = torch.nonzero(~pr["culled"]).flatten()
+    order = alive[depth_order(pr["z"][alive])]
+    pixels, xs_all, ys_all = pixel_centres(cam, pixels)
+    P = len(pixels)
+    res = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), depth=np.zeros(P), t_final=np.ones(P),
+               n_blended=np.zeros(P, np.int64), fragile=np.zeros(P, bool))
+    score = torch.zeros(N, dtype=DT)
+    C, ctr = pr["conic"][order], pr["centre"][order]
+    o, z, rgb = pr["opacity"][order], pr["z"][order], pr["rgb"][order]
+    for s in range(0, P, chunk):
+        e = min(P, s + chunk)
+        dx = xs_all[s:e, None] - ctr[None, :, 0]
+        dy = ys_all[s:e, None] - ctr[None, :, 1]
+        rho = C[None, :, 0, 0] * dx * dx + 2.0 * C[None, :, 0, 1] * dx * dy + C[None, :, 1, 1] * dy * dy
+        a_raw = o[None] * torch.exp(-0.5 * rho)
+        alpha = a_raw.clamp(max=ALPHA_MAX)
+        valid = (rho <= RHO_CUT) & (alpha >= ALPHA_MIN)
+        a = torch.where(valid, alpha, torch.zeros_like(alpha))
+        t_incl = torch.cumprod(1.0 - a, dim=1)
+        blended = valid & (t_incl >= T_EPS)
+        t_excl = torch.cat([torch.ones(e - s, 1, dtype=DT), t_incl[:, :-1]], dim=1)
+        w = torch.where(blended, a * t_excl, torch.zeros_like(a))
+        res["rgb"][s:e] = (w @ rgb).numpy()
+        res["alpha"][s:e] = w.sum(1).numpy()
+        res["depth"][s:e] = (w @ z).numpy()
+        res["t_final"][s:e] = torch.where(blended, 1.0 - a, torch.ones_like(a)).prod(1).numpy()
+        res["n_blended"][s:e] = blended.sum(1).numpy()
+        if len(order):
+            score[order] = torch.maximum(score[order], w.max(0).values)
+        f = FRAGILE_REL
+        a_cut = (o * math.exp(-0.5 * RHO_CUT)).clamp(max=ALPHA_MAX)
+        fragile = (((rho - RHO_CUT).abs() <= f * RHO_CUT) & (a_cut[None] >= ALPHA_MIN * (1 - f))) | \
+                  (((a_raw - ALPHA_MIN).abs() <= f * ALPHA_MIN) & (rho <= RHO_CUT * (1 + f))) | \
+                  (valid & ((t_incl - T_EPS).abs() <= f * T_EPS))
+        res["fragile"][s:e] = fragile.any(1).numpy()
+    res["score"] = score.numpy()
+    return res
+
+
+def contribution_score_3d(g: dict, cams: list) -> np.ndarray:
+    """Max blending weight of every 3D Gaussian over all pixels of all views (Appendix B)."""
+    s = np.zeros(len(np.asarray(g["opacity"])))
+    for cam in cams:
+        s = np.maximum(s, render_3d(g, cam)["score"])
+    return s

@@ -603,3 +603,64 @@ def test_normal_consistency_gradient_matches_central_differences():
             lm = oracle.normal_consistency(alpha, depth, normal, cam)[0]
             flat[i] = x0
             assert g.reshape(-1)[i] == pytest.approx(0.05 * (lp - lm) / 2e-6, abs=1e-9)
+
+
+# ----------------------------------------------------------------------------- 3DGS variant (Appendix B)
+def _g3(xyz, scale, opacity, rgb, quat=None):
+    xyz = np.asarray(xyz, np.float64).reshape(-1, 3)
+    n = len(xyz)
+    q = np.tile([1.0, 0.0, 0.0, 0.0], (n, 1)) if quat is None else np.asarray(quat, np.float64).reshape(n, 4)
+    return dict(xyz=xyz, quat=q, scale=np.asarray(scale, np.float64).reshape(n, 3),
+                opacity=np.asarray(opacity, np.float64).reshape(n),
+                sh=((np.asarray(rgb, np.float64).reshape(n, 1, 3) - 0.5) * SQ2PI), sh_degree=0)
+
+
+def test_ewa_isotropic_gaussian_on_the_axis():
+    """An isotropic Gaussian of scale s at distance d on the optical axis projects to the
+    image covariance ((f s / d)^2 + 0.3) I, so alpha at k pixels from the centre is
+    o exp(-k^2 / (2 ((f s / d)^2 + 0.3)))."""
+    cam = cam65()
+    s, o = 0.04, 0.8
+    g = _g3([0, 0, 0], [s, s, s], o, [0.3, 0.6, 0.9])
+    var = (cam["fx"] * s / 3.0) ** 2 + 0.3
+    for k in (0, 1, 2, 4):
+        r = oracle.render_3d(g, cam, pix(cam, 32 + k, 32))
+        a = o * math.exp(-0.5 * k * k / var)
+        expect = a if (k * k / var <= 9.0 and a >= 1.0 / 255.0) else 0.0   # k = 4 lies past the cut
+        assert r["alpha"][0] == pytest.approx(expect, abs=1e-13)
+        assert r["depth"][0] == pytest.approx(3.0 * r["alpha"][0], abs=1e-12)
+        np.testing.assert_allclose(r["rgb"][0], r["alpha"][0] * np.array([0.3, 0.6, 0.9]), atol=1e-13)
+
+
+def test_ewa_covariance_is_the_linearised_projection():
+    """J W Sigma W^T J^T equals the covariance pushed through the Jacobian of the pinhole
+    projection of the world point, taken here by central differences."""
+    cam = synthetic.make_camera((1.0, -3.0, 0.5), 80, 60)
+    rng = np.random.default_rng(9)
+    g = _g3(rng.uniform(-0.5, 0.5, (5, 3)), rng.uniform(0.02, 0.2, (5, 3)), [0.5] * 5, [[0.5] * 3] * 5,
+            quat=rng.normal(size=(5, 4)))
+    pr = oracle.project_ewa(g, cam)
+    R, t = np.asarray(cam["viewmat"])[:3, :3], np.asarray(cam["viewmat"])[:3, 3]
+
+    def proj(X):
+        c = R @ X + t
+        return np.array([cam["fx"] * c[0] / c[2] + cam["cx"], cam["fy"] * c[1] / c[2] + cam["cy"]])
+
+    for i in range(5):
+        X = g["xyz"][i]
+        J = np.stack([(proj(X + h) - proj(X - h)) / 2e-6 for h in np.eye(3) * 1e-6], 1)   # [2,3]
+        q = g["quat"][i] / np.linalg.norm(g["quat"][i])
+        Rq = Rotation.from_quat([q[1], q[2], q[3], q[0]]).as_matrix()
+        S = Rq @ np.diag(g["scale"][i] ** 2) @ Rq.T
+        ref = J @ S @ J.T + 0.3 * np.eye(2)
+        np.testing.assert_allclose(pr["cov2"][i].numpy(), ref, rtol=1e-6, atol=1e-9)
+        np.testing.assert_allclose(pr["centre"][i].numpy(), proj(X), rtol=1e-12)
+
+
+def test_ewa_hidden_gaussian_scores_zero():
+    cam = cam65()
+    g = _g3([[0, -1.0, 0], [0, -0.98, 0], [0, -0.96, 0], [0, 0.5, 0]], [[1.0, 0.01, 1.0]] * 3 + [[0.05] * 3],
+            [0.97, 0.97, 0.97, 0.9], [[0.5] * 3] * 4)
+    score = oracle.contribution_score_3d(g, [cam])
+    assert score[3] == 0.0                                # behind three nearly opaque sheets
+    assert score[0] == pytest.approx(0.97, abs=1e-12)     # the front sheet, hit at its centre
