@@ -67,6 +67,20 @@ typedef struct {
   int32_t reserved;
 } ocgs_gaussians;
 
+/* Read-only 3D Gaussians for the 3DGS variant of the pruning record (Appendix
+ * B): the layout of ocgs_gaussians with three scales per Gaussian, scale [n,3]
+ * (any 4-byte alignment); quat [n,4] 16-byte aligned. */
+typedef struct {
+  const float* xyz;
+  const float* quat;
+  const float* scale;
+  const float* opacity;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree; /* 0..3 */
+  int32_t reserved;
+} ocgs_gaussians3d;
+
 /* Writable arrays in the parameter layout (device, caller-owned): gradients
  * (accumulated with +=) or the destination of a pruning compaction. */
 typedef struct {
@@ -262,6 +276,22 @@ ocgs_status ocgs_contribution_graph_create(ocgs_ctx* ctx, const ocgs_gaussians* 
 /* Launch the captured sweep on the context stream (asynchronous). */
 ocgs_status ocgs_graph_launch(ocgs_ctx* ctx, ocgs_graph* graph);
 ocgs_status ocgs_graph_destroy(ocgs_ctx* ctx, ocgs_graph* graph);
+
+/*
+ * ocgs_render_3d / ocgs_accumulate_contribution_3d — the pruning record of Sec.
+ * 4.3 in 3DGS, as Appendix B runs it: 3D Gaussians splatted by the EWA
+ * projection of their covariance, image covariance J W Sigma W^T J^T + 0.3 I
+ * (Sigma = R diag(s^2) R^T, J the Jacobian of the pinhole projection at the
+ * camera-frame mean), rho the Mahalanobis distance under it, and the same
+ * skip (rho > 9, alpha < 1/255), 0.99 clamp, stop rule, depth order (centre
+ * depth) and score (max blending weight) as the surfel path.  render_3d writes
+ * rgb, alpha and depth (sum w z_c); normal is written as 0 and depth2 must be
+ * NULL; score as for ocgs_render (may be NULL).  Forward only (no state).
+ */
+ocgs_status ocgs_render_3d(ocgs_ctx* ctx, const ocgs_gaussians3d* gaussians, const ocgs_camera* cams,
+                           int32_t n_views, const ocgs_image* out, float* score);
+ocgs_status ocgs_accumulate_contribution_3d(ocgs_ctx* ctx, const ocgs_gaussians3d* gaussians,
+                                            const ocgs_camera* cams, int32_t n_views, float* score);
 
 /*
  * ocgs_prune — keep-set {i : score[i] > threshold} (threshold 0 reproduces

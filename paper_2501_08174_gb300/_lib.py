@@ -22,6 +22,12 @@ class Gaussians(C.Structure):
                 ("sh_degree", C.c_int32), ("reserved", C.c_int32)]
 
 
+class Gaussians3d(C.Structure):
+    _fields_ = [("xyz", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p),
+                ("opacity", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64),
+                ("sh_degree", C.c_int32), ("reserved", C.c_int32)]
+
+
 class GaussiansOut(C.Structure):
     _fields_ = [("xyz", C.c_void_p), ("quat", C.c_void_p), ("scale", C.c_void_p),
                 ("opacity", C.c_void_p), ("sh", C.c_void_p)]
@@ -94,6 +100,10 @@ SIGNATURES = {
                                                C.c_void_p, C.c_void_p, C.c_void_p]),
     "ocgs_accumulate_contribution": (C.c_int, [C.c_void_p, C.POINTER(Gaussians), C.POINTER(Camera),
                                                C.c_int32, C.c_void_p]),
+    "ocgs_render_3d": (C.c_int, [C.c_void_p, C.POINTER(Gaussians3d), C.POINTER(Camera), C.c_int32,
+                                 C.POINTER(Image), C.c_void_p]),
+    "ocgs_accumulate_contribution_3d": (C.c_int, [C.c_void_p, C.POINTER(Gaussians3d), C.POINTER(Camera),
+                                                  C.c_int32, C.c_void_p]),
     "ocgs_prune": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(Gaussians),
                              C.POINTER(GaussiansOut), C.POINTER(C.c_int64), C.c_void_p, C.c_int64,
                              C.POINTER(C.c_int64)]),

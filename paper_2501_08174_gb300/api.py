@@ -59,6 +59,19 @@ def gaussians_struct(g: dict, device) -> _lib.Gaussians:
                           _ptr(g["sh"]), n, deg, 0)
 
 
+def gaussians3d_struct(g: dict, device) -> _lib.Gaussians3d:
+    """3D Gaussians (the 3DGS variant): scale [N,3]."""
+    n = g["xyz"].shape[0]
+    deg = sh_degree_of(g["sh"])
+    for key, tail in (("xyz", (3,)), ("quat", (4,)), ("scale", (3,)), ("opacity", ()),
+                      ("sh", ((deg + 1) ** 2, 3))):
+        _check_param(key, g[key], tail, device)
+        if g[key].shape[0] != n:
+            raise ValueError(f"{key} has {g[key].shape[0]} rows, expected {n}")
+    return _lib.Gaussians3d(_ptr(g["xyz"]), _ptr(g["quat"]), _ptr(g["scale"]), _ptr(g["opacity"]),
+                            _ptr(g["sh"]), n, deg, 0)
+
+
 def camera_array(cameras: Sequence[dict]):
     arr = (_lib.Camera * len(cameras))()
     for i, cam in enumerate(cameras):
@@ -362,6 +375,35 @@ class Rasterizer:
                    camera_array(cameras), len(cameras), float(weight), float(a_min), _ptr(loss),
                    _ptr(g.get("alpha")), _ptr(g.get("depth")), _ptr(g.get("normal")))
         return loss
+
+    def render_3d(self, gaussians: dict, cameras: Sequence[dict], score: Optional[torch.Tensor] = None) -> dict:
+        """Forward of the 3DGS variant (Appendix B): {rgb, alpha, depth} of all ``cameras``;
+        ``score`` [N] is max-accumulated as in ``render``."""
+        self._bind_stream()
+        gs = gaussians3d_struct(gaussians, self.device)
+        P = n_pixels(cameras)
+        f32 = dict(dtype=torch.float32, device=self.device)
+        out = dict(rgb=torch.empty(P, 3, **f32), alpha=torch.empty(P, **f32), depth=torch.empty(P, **f32),
+                   normal=torch.empty(P, 3, **f32))
+        if score is not None:
+            _check_param("score", score, (), self.device)
+        img = _lib.Image(_ptr(out["rgb"]), _ptr(out["alpha"]), _ptr(out["depth"]), _ptr(out["normal"]), None)
+        self._call("ocgs_render_3d", self._ctx, C.byref(gs), camera_array(cameras), len(cameras), C.byref(img),
+                   _ptr(score))
+        del out["normal"]
+        return out
+
+    def accumulate_contribution_3d(self, gaussians: dict, cameras: Sequence[dict],
+                                   score: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Pruning record of the 3DGS variant: max blending weight of every 3D Gaussian over all views."""
+        self._bind_stream()
+        gs = gaussians3d_struct(gaussians, self.device)
+        if score is None:
+            score = torch.zeros(gs.n, dtype=torch.float32, device=self.device)
+        _check_param("score", score, (), self.device)
+        self._call("ocgs_accumulate_contribution_3d", self._ctx, C.byref(gs), camera_array(cameras), len(cameras),
+                   _ptr(score))
+        return score
 
     def accumulate_contribution(self, gaussians: dict, cameras: Sequence[dict],
                                 score: Optional[torch.Tensor] = None) -> torch.Tensor:

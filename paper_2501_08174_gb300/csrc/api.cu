@@ -266,7 +266,8 @@ void free_state(ocgs_fwd_state* st) {
 // The forward pipeline shared by ocgs_render and ocgs_accumulate_contribution:
 // preprocess, depth sort, duplication, tile sort, ranges, rasterization.
 ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* cams, int V,
-                         const ocgs_image* out, float* score, ocgs_fwd_state* st, bool keep_state) {
+                         const ocgs_image* out, float* score, ocgs_fwd_state* st, bool keep_state,
+                         bool ewa = false) {
   const int tw = ctx->opts.tile_w, th = ctx->opts.tile_h;
   const int64_t N = g->n;
   CamPlan pl = plan_cameras(cams, V, tw, th);
@@ -310,8 +311,12 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
 
   {
     StageTimer t(ctx, OCGS_STAGE_PREPROCESS);
-    CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, bin, dkey,
-                         ctx->d_status, s));
+    if (ewa)
+      CK(launch_preprocess_ewa(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, bin, dkey,
+                               ctx->d_status, s));
+    else
+      CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, bin, dkey,
+                           ctx->d_status, s));
   }
   {
     StageTimer t(ctx, OCGS_STAGE_BINNING);
@@ -383,6 +388,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   }
 
   RasterArgs ra{};
+  ra.ewa = ewa ? 1 : 0;
   ra.cams = st->d_cams;
   ra.tile_prefix = st->d_tile_prefix;
   ra.n_views = V;
@@ -933,6 +939,61 @@ ocgs_status ocgs_accumulate_contribution(ocgs_ctx* ctx, const ocgs_gaussians* g,
   }
   ctx->stats.n_views = n_views;
   ctx->stats.n_pairs = pairs;
+  return worst;
+}
+
+// The 3DGS variant of the pruning record (Appendix B): 3D Gaussians whose scale has
+// three entries; the record format is the surfel one, so the pipeline is shared.
+static ocgs_status check_gaussians3d(ocgs_ctx* ctx, const ocgs_gaussians3d* g, ocgs_gaussians* as2d) {
+  if (!g) return set_err(ctx, OCGS_ERR_ARG, "gaussians is NULL");
+  if (g->n < 0) return set_err(ctx, OCGS_ERR_ARG, "gaussians.n < 0");
+  if (g->sh_degree < 0 || g->sh_degree > 3) return set_err(ctx, OCGS_ERR_ARG, "sh_degree must be 0..3");
+  if (g->n > 0 && (!g->xyz || !g->quat || !g->scale || !g->opacity || !g->sh))
+    return set_err(ctx, OCGS_ERR_ARG, "a Gaussian parameter pointer is NULL");
+  if (g->n > 0 && (uintptr_t)g->quat % 16) return set_err(ctx, OCGS_ERR_ARG, "quat must be 16-byte aligned");
+  *as2d = ocgs_gaussians{g->xyz, g->quat, g->scale, g->opacity, g->sh, g->n, g->sh_degree, 0};
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_render_3d(ocgs_ctx* ctx, const ocgs_gaussians3d* g, const ocgs_camera* cams, int32_t n_views,
+                           const ocgs_image* out, float* score) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ocgs_gaussians g2;
+  ocgs_status r = check_gaussians3d(ctx, g, &g2);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  if (!out || !out->rgb || !out->alpha || !out->depth || !out->normal)
+    return set_err(ctx, OCGS_ERR_ARG, "rgb, alpha, depth and normal must be non-NULL");
+  if (out->depth2) return set_err(ctx, OCGS_ERR_ARG, "the 3DGS variant has no depth2 plane");
+  CK(cudaSetDevice(ctx->device));
+  ocgs_fwd_state st;
+  r = forward_pass(ctx, &g2, cams, n_views, out, score, &st, false, true);
+  free_state(&st);
+  return r;
+}
+
+ocgs_status ocgs_accumulate_contribution_3d(ocgs_ctx* ctx, const ocgs_gaussians3d* g, const ocgs_camera* cams,
+                                            int32_t n_views, float* score) {
+  if (!ctx) return OCGS_ERR_ARG;
+  ocgs_gaussians g2;
+  ocgs_status r = check_gaussians3d(ctx, g, &g2);
+  if (r != OCGS_OK) return r;
+  r = check_cameras(ctx, cams, n_views);
+  if (r != OCGS_OK) return r;
+  if (!score && g->n > 0) return set_err(ctx, OCGS_ERR_ARG, "score is NULL");
+  if (g->n == 0) return OCGS_OK;
+  CK(cudaSetDevice(ctx->device));
+  const int chunk = 16;
+  ocgs_status worst = OCGS_OK;
+  for (int v0 = 0; v0 < n_views; v0 += chunk) {
+    const int nv = std::min(chunk, n_views - v0);
+    ocgs_fwd_state st;
+    r = forward_pass(ctx, &g2, cams + v0, nv, nullptr, score, &st, false, true);
+    free_state(&st);
+    if (r == OCGS_ERR_NONFINITE) worst = r;
+    else if (r != OCGS_OK) return r;
+  }
   return worst;
 }
 

@@ -202,6 +202,9 @@ struct SplatHead2 {
   bool pass[2];
 };
 
+// EWA: a projected 3D Gaussian (constant denominator, the screen filter already
+// folded into its covariance): the support test is the Mahalanobis term alone.
+template <bool EWA = false>
 __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
                                                   const SplatColumn& c, float2 py, float rb) {
   SplatHead2 h;
@@ -214,8 +217,8 @@ __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 
   const float2 lim = __fmul2_rn(bc2(rb), __fmul2_rn(h.den, h.den));
   h.in3[0] = (h.den.x != 0.0f) && (h.q.x <= lim.x);
   h.in3[1] = (h.den.y != 0.0f) && (h.q.y <= lim.y);
-  h.pass[0] = h.in3[0] || (h.rho2.x <= rb);
-  h.pass[1] = h.in3[1] || (h.rho2.y <= rb);
+  h.pass[0] = h.in3[0] || (!EWA && h.rho2.x <= rb);
+  h.pass[1] = h.in3[1] || (!EWA && h.rho2.y <= rb);
   return h;
 }
 
@@ -228,13 +231,15 @@ struct SplatEval2 {
 
 // FINITE: r and rho3 are zeroed where the filter term won, so that products
 // the backward masks with zero stay finite (the forward only reads z there).
-template <bool FINITE>
+template <bool FINITE, bool EWA = false>
 __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
   SplatEval2 e;
-  const float2 r = make_float2(h.in3[0] ? __fdividef(1.0f, h.den.x) : 0.0f, h.in3[1] ? __fdividef(1.0f, h.den.y) : 0.0f);
-  const float2 r3 = __fmul2_rn(h.q, __fmul2_rn(r, r));
-  e.surf[0] = h.in3[0] && (r3.x <= h.rho2.x);
-  e.surf[1] = h.in3[1] && (r3.y <= h.rho2.y);
+  const float2 r = EWA ? make_float2(h.in3[0] ? 1.0f : 0.0f, h.in3[1] ? 1.0f : 0.0f)
+                       : make_float2(h.in3[0] ? __fdividef(1.0f, h.den.x) : 0.0f,
+                                     h.in3[1] ? __fdividef(1.0f, h.den.y) : 0.0f);
+  const float2 r3 = EWA ? h.q : __fmul2_rn(h.q, __fmul2_rn(r, r));
+  e.surf[0] = h.in3[0] && (EWA || r3.x <= h.rho2.x);
+  e.surf[1] = h.in3[1] && (EWA || r3.y <= h.rho2.y);
   if (FINITE) {
     e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
     e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
@@ -447,6 +452,10 @@ cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, cons
                               int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
                               float4* bin, uint32_t* depth_key, int* status, cudaStream_t s);
 
+// EWA projection of 3D Gaussians (scale [n,3]) into the same record format
+cudaError_t launch_preprocess_ewa(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams, int n_views,
+                                  int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles, float4* bin,
+                                  uint32_t* depth_key, int* status, cudaStream_t s);
 cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
                                        const DevCam* cams, int n_views, const float* grad_rec,
                                        const int32_t* ntiles, GaussOut out, cudaStream_t s);
@@ -490,6 +499,7 @@ cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* w
                               uint32_t* tile_ids, cudaStream_t s);
 
 struct RasterArgs {
+  int ewa;  // records are projected 3D Gaussians (preprocess_ewa)
   const DevCam* cams;
   const int* tile_prefix;   // [V+1]
   int n_views;

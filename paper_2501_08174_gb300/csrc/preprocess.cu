@@ -434,6 +434,127 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
   for (int k = 0; k < 3 * K; ++k) out.sh[(int64_t)3 * K * i + k] += gsh[k];
 }
 
+// EWA projection of 3D Gaussians, for the 3DGS variant of the pruning record
+// (Appendix B).  The image covariance is J W Sigma W^T J^T + 0.3 I, Sigma =
+// R diag(s^2) R^T, J the Jacobian of the pinhole projection at the camera-frame
+// mean and 0.3 px^2 the 3DGS screen-space low-pass.  The record is written in the
+// surfel record's form: centre, u = M00 dx + M01 dy, v = M11 dy with M^T M the
+// inverse covariance (so u^2 + v^2 is the Mahalanobis distance), a constant
+// denominator (e = (1, 0, 0)) and the centre depth; binning, sorting and the
+// contribution record then run unchanged, and the rasterizer's EWA flag leaves
+// out the screen filter, which the dilation already contains.  Scales are [n,3].
+template <int DEG>
+__global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_t n,
+                                                             const DevCam* __restrict__ cams, int n_views,
+                                                             int tile_w, int tile_h, RecPtrs rec,
+                                                             int32_t* __restrict__ ntiles,
+                                                             float4* __restrict__ bin,
+                                                             uint32_t* __restrict__ depth_key,
+                                                             int* __restrict__ status) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
+  const float4 q = reinterpret_cast<const float4*>(g.quat)[i];
+  const float s3[3] = {g.scale[3 * i], g.scale[3 * i + 1], g.scale[3 * i + 2]};
+  const float o = g.opacity[i];
+  float sh[3 * K];
+  bool finite = finitef(X[0]) && finitef(X[1]) && finitef(X[2]) && finitef(q.x) && finitef(q.y) &&
+                finitef(q.z) && finitef(q.w) && finitef(s3[0]) && finitef(s3[1]) && finitef(s3[2]) && finitef(o);
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) {
+    sh[k] = g.sh[(int64_t)3 * K * i + k];
+    finite = finite && finitef(sh[k]);
+  }
+  const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
+  if (!finite) atomicOr(status, kStatusNonFinite);
+  const bool bad = !finite || !(qn2 > 0.f) || !(s3[0] > 0.f) || !(s3[1] > 0.f) || !(s3[2] > 0.f) ||
+                   !(o >= kAlphaMin);
+  const Frame f = make_frame(q);
+  // world-frame 3D covariance (symmetric: xx xy xz yy yz zz)
+  const float v0 = s3[0] * s3[0], v1 = s3[1] * s3[1], v2 = s3[2] * s3[2];
+  float S[3][3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S[r][c] = v0 * f.tu[r] * f.tu[c] + v1 * f.tv[r] * f.tv[c] + v2 * f.tw[r] * f.tw[c];
+  const float rho_b = bad ? 0.f : support_rho(o);
+
+  for (int v = 0; v < n_views; ++v) {
+    const DevCam& cam = cams[v];
+    const int64_t idx = (int64_t)v * n + i;
+    float t[3];
+    rot3(cam.R, X, t);
+    t[0] += cam.t[0]; t[1] += cam.t[1]; t[2] += cam.t[2];
+    bool culled = bad || !(t[2] > cam.near_plane);
+    int4 rc = make_int4(0, 0, -1, -1);
+    float m00 = 0.f, m01 = 0.f, m11 = 0.f, ccx = 0.f, ccy = 0.f;
+    if (!culled) {
+      const float iz = 1.0f / t[2];
+      // T = J W (2 x 3): rows of the Jacobian times the camera rotation
+      const float j0[3] = {cam.fx * iz, 0.f, -cam.fx * t[0] * iz * iz};
+      const float j1[3] = {0.f, cam.fy * iz, -cam.fy * t[1] * iz * iz};
+      float T0[3], T1[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        T0[c] = j0[0] * cam.R[c] + j0[1] * cam.R[3 + c] + j0[2] * cam.R[6 + c];
+        T1[c] = j1[0] * cam.R[c] + j1[1] * cam.R[3 + c] + j1[2] * cam.R[6 + c];
+      }
+      float ST0[3], ST1[3];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        ST0[r] = S[r][0] * T0[0] + S[r][1] * T0[1] + S[r][2] * T0[2];
+        ST1[r] = S[r][0] * T1[0] + S[r][1] * T1[1] + S[r][2] * T1[2];
+      }
+      const float a = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + 0.3f;
+      const float b = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
+      const float c = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + 0.3f;
+      const float det = a * c - b * b;
+      if (!(det > 0.f) || !isfinite(det)) {
+        culled = true;
+      } else {
+        const float A = c / det, B = -b / det;  // conic [[A, B], [B, C]], C = a / det
+        m00 = sqrtf(A);
+        m01 = B / m00;
+        m11 = 1.0f / sqrtf(c);  // m11^2 = C - m01^2 = C - B^2 / A = 1 / c
+        ccx = cam.fx * t[0] * iz + cam.cx;
+        ccy = cam.fy * t[1] * iz + cam.cy;
+        // {d^T conic d <= rb} lies in the disc of radius sqrt(rb * lambda_max(cov))
+        const float mid = 0.5f * (a + c);
+        const float lmax = mid + sqrtf(fmaxf(0.25f * (a - c) * (a - c) + b * b, 0.f));
+        const float rad = sqrtf(rho_b * lmax) * 1.001f + 0.05f;
+        const float lo_x = fmaxf(ceilf(ccx - rad - 0.5f), 0.f), hi_x = fminf(floorf(ccx + rad - 0.5f), (float)(cam.W - 1));
+        const float lo_y = fmaxf(ceilf(ccy - rad - 0.5f), 0.f), hi_y = fminf(floorf(ccy + rad - 0.5f), (float)(cam.H - 1));
+        if (lo_x <= hi_x && lo_y <= hi_y)
+          rc = make_int4((int)lo_x / tile_w, (int)lo_y / tile_h, (int)hi_x / tile_w, (int)hi_y / tile_h);
+        else
+          culled = true;
+      }
+    }
+    if (culled) {
+      ntiles[idx] = 0;
+      depth_key[idx] = 0xffffffffu;
+      bin[3 * idx + 2] = make_float4(0.f, 0.f, __uint_as_float(pack_i16x2(0, 0)), __uint_as_float(pack_i16x2(-1, -1)));
+      continue;
+    }
+    ntiles[idx] = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
+    depth_key[idx] = __float_as_uint(t[2]);
+    float dirn[3], dlen, raw[3];
+    view_colour<DEG>(cam, X, sh, dirn, &dlen, raw);
+    const float4 g0 = make_float4(ccx, ccy, o, t[2]);
+    const float4 g1 = make_float4(m00, m01, 0.f, m11);
+    rec.g0[idx] = g0;
+    rec.g1[idx] = g1;
+    rec.g2[idx] = make_float4(1.f, 0.f, 0.f, t[2]);
+    rec.a0[idx] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
+    rec.a1[idx] = make_float2(0.f, 0.f);
+    bin[3 * idx] = make_float4(g0.x, g0.y, rho_b, g1.x);
+    bin[3 * idx + 1] = make_float4(g1.y, g1.z, g1.w, 1.f);
+    bin[3 * idx + 2] = make_float4(0.f, 0.f, __uint_as_float(pack_i16x2(rc.x, rc.y)),
+                                   __uint_as_float(pack_i16x2(rc.z, rc.w)));
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams,
@@ -466,4 +587,21 @@ cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_deg
   return launched();
 }
 
+}  // namespace ocgs
+
+namespace ocgs {
+cudaError_t launch_preprocess_ewa(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams, int n_views,
+                                  int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles, float4* bin,
+                                  uint32_t* depth_key, int* status, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const int bs = 128;
+  const unsigned grid = (unsigned)((n + bs - 1) / bs);
+  switch (sh_degree) {
+    case 0: preprocess_ewa_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    case 1: preprocess_ewa_kernel<1><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    case 2: preprocess_ewa_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+    default: preprocess_ewa_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
+  }
+  return launched();
+}
 }  // namespace ocgs

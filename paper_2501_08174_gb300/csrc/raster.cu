@@ -46,7 +46,8 @@ __device__ unsigned long long g_diag[8];
 #endif
 
 // Q2: also accumulate Q = sum w z^2 (the depth distortion's third plane)
-template <int TW, int TH, int PPT, bool IMG, bool SCORE, bool Q2>
+// EWA: the records are projected 3D Gaussians (the 3DGS variant of Appendix B)
+template <int TW, int TH, int PPT, bool IMG, bool SCORE, bool Q2, bool EWA>
 __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW * TH)) raster_fwd_kernel(const RasterArgs a) {
   constexpr int NT = TW * TH / PPT;  // threads, and records per shared-memory batch
   __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
@@ -144,11 +145,11 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             const int k0 = 2 * p, k1 = 2 * p + 1;
             if (done[k0] && done[k1]) continue;
             const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
-            SplatHead2 h = splat_head2(g0, g1, g2, col, py, rb);
+            SplatHead2 h = splat_head2<EWA>(g0, g1, g2, col, py, rb);
             h.pass[0] = h.pass[0] && !done[k0];
             h.pass[1] = h.pass[1] && !done[k1];
             if (!(h.pass[0] || h.pass[1])) continue;
-            const SplatEval2 e = splat_tail2<false>(g0, g2, h, rb);
+            const SplatEval2 e = splat_tail2<false, EWA>(g0, g2, h, rb);
             // lanes that do not blend take alpha 0: T (1 - 0) = T and w = 0 exactly
             const float2 a2 = make_float2(e.ok[0] ? e.alpha.x : 0.f, e.ok[1] ? e.alpha.y : 0.f);
             float2 Tn = __fmul2_rn(T[p], __ffma2_rn(a2, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
@@ -517,11 +518,16 @@ cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
   constexpr int NT = TW * TH / PPT;
   const bool score = a.score != nullptr;
   const bool q2 = img && a.out.depth2 != nullptr;
-  if (img && score && q2) raster_fwd_kernel<TW, TH, PPT, true, true, true><<<grid, NT, 0, s>>>(a);
-  else if (img && q2) raster_fwd_kernel<TW, TH, PPT, true, false, true><<<grid, NT, 0, s>>>(a);
-  else if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true, false><<<grid, NT, 0, s>>>(a);
-  else if (img) raster_fwd_kernel<TW, TH, PPT, true, false, false><<<grid, NT, 0, s>>>(a);
-  else if (score) raster_fwd_kernel<TW, TH, PPT, false, true, false><<<grid, NT, 0, s>>>(a);
+  if (a.ewa) {
+    if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true, false, true><<<grid, NT, 0, s>>>(a);
+    else if (img) raster_fwd_kernel<TW, TH, PPT, true, false, false, true><<<grid, NT, 0, s>>>(a);
+    else if (score) raster_fwd_kernel<TW, TH, PPT, false, true, false, true><<<grid, NT, 0, s>>>(a);
+    else return cudaSuccess;
+  } else if (img && score && q2) raster_fwd_kernel<TW, TH, PPT, true, true, true, false><<<grid, NT, 0, s>>>(a);
+  else if (img && q2) raster_fwd_kernel<TW, TH, PPT, true, false, true, false><<<grid, NT, 0, s>>>(a);
+  else if (img && score) raster_fwd_kernel<TW, TH, PPT, true, true, false, false><<<grid, NT, 0, s>>>(a);
+  else if (img) raster_fwd_kernel<TW, TH, PPT, true, false, false, false><<<grid, NT, 0, s>>>(a);
+  else if (score) raster_fwd_kernel<TW, TH, PPT, false, true, false, false><<<grid, NT, 0, s>>>(a);
   else return cudaSuccess;
   return launched();
 }

@@ -50,7 +50,8 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     structs = {"ocgs_gaussians": _lib.Gaussians, "ocgs_gaussians_out": _lib.GaussiansOut,
                "ocgs_camera": _lib.Camera, "ocgs_image": _lib.Image, "ocgs_options": _lib.Options,
                "ocgs_stats": _lib.Stats, "ocgs_profile": _lib.Profile, "ocgs_state_info": _lib.StateInfo,
-               "ocgs_tune_result": _lib.TuneResult, "ocgs_adam_config": _lib.AdamConfig}
+               "ocgs_tune_result": _lib.TuneResult, "ocgs_adam_config": _lib.AdamConfig,
+               "ocgs_gaussians3d": _lib.Gaussians3d}
     lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "ocgs.h"', 'int main(void){']
     for cname, py in structs.items():
         lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
