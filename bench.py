@@ -65,9 +65,10 @@ def parse_args():
     p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--workload", choices=("c4", "c5"), default="c4",
+    p.add_argument("--workload", choices=("c4", "c5", "ewa"), default="c4",
                    help="c4: 500k surfels x 16 uneven views (the metric's workload); "
-                        "c5: training iteration, 1M surfels x 64 views 1600x1200 with Adam")
+                        "c5: training iteration, 1M surfels x 64 views 1600x1200 with Adam; "
+                        "ewa: the 3DGS pruning sweep (Appendix B) over the c4 views")
     p.add_argument("--n", type=int, default=None, help="surfels (default 500k for c4, 1M for c5)")
     p.add_argument("--views", type=int, default=None, help="views (default 16 for c4, 64 for c5)")
     p.add_argument("--tile", default="16x16")
@@ -548,11 +549,75 @@ def run_ours(a, rank: int, world: int, local: int):
         dist.destroy_process_group()
 
 
+METRIC_EWA = "3DGS pruning-sweep Mpix/s at 500k Gaussians x 16 views (EWA forward + contribution record)"
+
+
+def run_ewa(a, rank: int, world: int, local: int):
+    """The 3DGS variant of the pruning record (Appendix B): the contribution sweep of
+    500k 3D Gaussians (config 4's scene with a third scale axis) over config 4's views."""
+    import torch
+    import torch.distributed as dist
+
+    import synthetic
+    from paper_2501_08174_gb300 import Rasterizer, n_pixels
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    sc = synthetic.config4(seed=4 + rank, n=a.n, n_views=a.views)
+    cams = sc["cameras"]
+    P = n_pixels(cams)
+    P_job = int(sum_over_ranks(P, world, dev))
+    rng = np.random.default_rng(44 + rank)
+    g_np = dict(sc["gaussians"])
+    third = np.exp(rng.uniform(np.log(0.01), np.log(0.1), size=(a.n, 1)))
+    g_np["scale"] = np.concatenate([np.asarray(g_np["scale"], np.float64), third], 1)
+    g = {k: torch.tensor(np.asarray(g_np[k], np.float32), device=dev) for k in ("xyz", "quat", "scale", "opacity", "sh")}
+    tw, th = (int(x) for x in a.tile.split("x"))
+    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt)
+    score = torch.zeros(a.n, device=dev)
+
+    def step():
+        score.zero_()
+        rast.accumulate_contribution_3d(g, cams, score)
+
+    for _ in range(a.warmup):
+        step()
+    rast.profile(True)
+    launches0 = rast.kernel_launches()
+    out_dir = os.path.join(ROOT, "gpurun_out")
+    os.makedirs(out_dir, exist_ok=True)
+    ms, wall_ms, clocks = timed(step, a.steps, 0, world, dev, os.path.join(out_dir, f"clocks_rank{rank}.csv"), local)
+    launches = rast.kernel_launches() - launches0
+    prof = rast.profile_read()
+    rast.profile(False)
+    kept = int((score > TAU).sum())
+    if rank == 0:
+        stages = {k: {"ms": v[0] / a.steps, "launch_sets": v[1] / a.steps} for k, v in prof.items() if v[1] > 0}
+        line = {"metric": METRIC_EWA, "value": P_job / (ms / 1e3) / 1e6, "unit": UNIT, "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"3DGS pruning sweep: {a.n} Gaussians SH3, {a.views} hemisphere views of "
+                                       f"uneven resolution, EWA forward with the contribution record",
+                           "pixels_per_gpu": P, "tile": a.tile, "pixels_per_thread": a.ppt,
+                           "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+                "stages": stages, "clocks": clocks, "gpu_launches": int(launches), "wall_ms_per_step": wall_ms,
+                "kept_at_tau": kept}
+        print(json.dumps(line), flush=True)
+    rast.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
 def main():
     a = parse_args()
     rank, world, local = dist_info()
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.workload == "ewa":
+        run_ewa(a, rank, world, local)
         return
     run_ours(a, rank, world, local)
 
