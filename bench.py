@@ -77,7 +77,7 @@ def parse_args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
-    p.add_argument("--cpu-sample", type=int, default=1024, help="pixels of the oracle's timed sample")
+    p.add_argument("--cpu-sample", type=int, default=1536, help="pixels of the oracle's timed sample")
     a = p.parse_args()
     if a.n is None:
         a.n = 1_000_000 if a.workload == "c5" else 500_000
@@ -233,9 +233,11 @@ def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile
     VN = V * N
     ssim_px = 24 + 1 + 36 + 36 + 24 + 24  # images + mask, adjoint maps out and back, images again, d_rgb
     b = {
-        "preprocess": N * 232 + VN * (72 + 4 + 16 + 4),
+        "preprocess": N * 232 + VN * (72 + 4 + 48 + 4),   # record, ntiles, binning record, depth key
         "depth_sort": VN * 4 + 4 * VN * 20,
-        "binning": VN * 68 + K * 12 + T * 8,
+        # counts (48 B record in, 8 B out), count gather + scan (28 B), duplication (60 B in per
+        # record, 8 B out per pair), tile ranges (4 B per pair, 8 B per tile)
+        "binning": VN * (56 + 28 + 60) + K * 12 + T * 8,
         "tile_sort": tile_passes * K * 20,
         "raster_fwd": VN * 72 + K * 4 + P * 40,
         "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24) + (ssim_px * P if prune_calls > 1 else 0),
