@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define OCGS_ABI_VERSION 2
+#define OCGS_ABI_VERSION 3
 
 typedef enum {
   OCGS_OK = 0,
@@ -112,12 +112,24 @@ typedef struct {
 } ocgs_image;
 
 /* Launch options.  None of them changes a result: the support test is exact
- * and the screen bounds are conservative, so tiles only reshape the work. */
+ * and the screen bounds are conservative, so tiles only reshape the work, and
+ * the two-pass binning below renders every tile from the same list as one pass.
+ *
+ * front_fraction (persistent renders with images only; 0 = one pass): the
+ * front-to-back walk of Sec. 4.3 stops a pixel once T falls below its bound,
+ * so most (tile, Gaussian) pairs behind an opaque surface are never read.  In
+ * two passes the renderer first bins and renders only the first
+ * ceil(front_fraction * n * n_views) records of the depth order; each tile
+ * with a pixel still running at the end of that prefix is then binned with
+ * the records behind it and continues from where its pixels stopped.  The
+ * tile's list is the one-pass list in two segments, and the backward walks
+ * both. */
 typedef struct {
   int32_t tile_w;             /* 8, 16 or 32 */
   int32_t tile_h;             /* 8 or 16: 16x16, 16x8, 8x8 or 32x8 */
   int32_t persistent;         /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
   int32_t pixels_per_thread;  /* vertically adjacent pixels per thread: 1, 2 (0 = 2), or 4 for 16x16 and 16x8 */
+  float front_fraction;       /* in [0, 1]: share of the depth order binned in the first pass (0 = one pass) */
 } ocgs_options;
 
 /* Counters of the last ocgs_render / ocgs_accumulate_contribution. */

@@ -150,10 +150,15 @@ class ContributionGraph:
             pass
 
 
+# share of the depth order binned in the first pass of a persistent render
+FRONT_FRACTION = 0.1
+
+
 class Rasterizer:
     """One libocgs context on one CUDA device."""
 
-    def __init__(self, device=None, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2):
+    def __init__(self, device=None, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2,
+                 front_fraction: float = FRONT_FRACTION):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device) \
             if not isinstance(device, torch.device) else device
@@ -162,7 +167,8 @@ class Rasterizer:
         if st != _lib.OK:
             raise _lib.OcgsError(st, "ocgs_create failed (is a CUDA device present?)")
         self._ctx = ctx
-        self.set_options(tile=tile, persistent=persistent, pixels_per_thread=pixels_per_thread)
+        self.set_options(tile=tile, persistent=persistent, pixels_per_thread=pixels_per_thread,
+                         front_fraction=front_fraction)
 
     # -- plumbing
     def _call(self, name: str, *args) -> int:
@@ -186,12 +192,17 @@ class Rasterizer:
         except Exception:
             pass
 
-    def set_options(self, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2) -> None:
-        o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), int(pixels_per_thread))
+    def set_options(self, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2,
+                    front_fraction: float = FRONT_FRACTION) -> None:
+        """Launch options (see ocgs_options); none changes a result.  ``front_fraction``: share
+        of the depth order binned in the first of two passes (persistent renders; 0 = one pass)."""
+        o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), int(pixels_per_thread),
+                         float(front_fraction))
         self._call("ocgs_set_options", self._ctx, C.byref(o))
         self.tile = (int(tile[0]), int(tile[1]))
         self.persistent = bool(persistent)
         self.pixels_per_thread = int(pixels_per_thread)
+        self.front_fraction = float(front_fraction)
 
     def autotune(self, gaussians: dict, cameras: Sequence[dict], cache_path: Optional[str] = None) -> dict:
         """Time the launch-option candidates on this workload and keep the fastest (see ocgs_autotune)."""

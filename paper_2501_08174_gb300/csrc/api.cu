@@ -57,6 +57,8 @@ struct ocgs_fwd_state {
   int32_t* ntiles = nullptr;
   uint32_t* vals = nullptr;
   uint2* ranges = nullptr;
+  uint2* ranges2 = nullptr;   // two-pass renders: second segment of each tile's list
+  uint32_t* vals2 = nullptr;
   float* t_final = nullptr;
   uint32_t* last = nullptr;
   uint32_t* tile_order = nullptr;
@@ -318,95 +320,277 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(launch_preprocess(gptrs(g), N, g->sh_degree, st->d_cams, V, tw, th, st->rec, st->ntiles, bin, dkey,
                            ctx->d_status, s));
   }
-  {
-    StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_tile_count(bin, st->d_cams, N, VN, tw, th, st->ntiles, dkey, s));
-  }
-  bool alt = false;
-  {
-    StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
-    CK(launch_iota(order, VN, s));
-    CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
-  }
-  uint32_t* sorted = alt ? order_alt : order;
-  {
-    StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_gather_counts(sorted, st->ntiles, counts, VN, s));
-    CK(scan_exclusive_u64(counts, counts, VN, ctx->d_scalar, scratch, s));
-  }
-  CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
   int status = 0;
-  ocgs_status rs = read_status(ctx, &status);
-  if (rs != OCGS_OK) return rs;
-  const uint64_t K64 = VN ? ctx->h_scalar[0] : 0;
-  if (K64 > (uint64_t)INT32_MAX)
-    return set_err(ctx, OCGS_ERR_CAPACITY, "more than 2^31-1 (tile, Gaussian) pairs; split the views");
-  const uint32_t K = (uint32_t)K64;
-  st->K = K;
+  uint32_t K = 0;
+  const bool two_pass = out != nullptr && st->persistent && ctx->opts.front_fraction > 0.f && VN > 0;
+  if (!two_pass) {
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_tile_count(bin, st->d_cams, N, VN, tw, th, st->ntiles, dkey, s));
+    }
+    bool alt = false;
+    {
+      StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
+      CK(launch_iota(order, VN, s));
+      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+    }
+    uint32_t* sorted = alt ? order_alt : order;
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_gather_counts(sorted, st->ntiles, counts, VN, s));
+      CK(scan_exclusive_u64(counts, counts, VN, ctx->d_scalar, scratch, s));
+    }
+    CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    ocgs_status rs = read_status(ctx, &status);
+    if (rs != OCGS_OK) return rs;
+    const uint64_t K64 = VN ? ctx->h_scalar[0] : 0;
+    if (K64 > (uint64_t)INT32_MAX)
+      return set_err(ctx, OCGS_ERR_CAPACITY, "more than 2^31-1 (tile, Gaussian) pairs; split the views");
+    K = (uint32_t)K64;
+    st->K = K;
 
-  uint32_t *pkey, *pval, *pkey_alt, *pval_alt;
-  CK(tmp.alloc(&pkey, K));
-  CK(keep.alloc(&pval, K));
-  CK(tmp.alloc(&pkey_alt, K));
-  CK(keep.alloc(&pval_alt, K));
-  char* pscratch;
-  CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
-  {
-    StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), VN, bin, st->d_cams,
-                        N, tw, th, K, pkey, pval, s));
-  }
-  const int tbits = bits_for((uint64_t)pl.tiles);
-  bool palt = false;
-  {
-    StageTimer t(ctx, OCGS_STAGE_TILE_SORT);
-    CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K, tbits, pscratch, &palt, s));
-  }
-  uint32_t* skey = palt ? pkey_alt : pkey;
-  st->vals = palt ? pval_alt : pval;
-  {
-    StageTimer t(ctx, OCGS_STAGE_BINNING);
-    CK(launch_tile_ranges(skey, K, st->ranges, s));
-  }
+    uint32_t *pkey, *pval, *pkey_alt, *pval_alt;
+    CK(tmp.alloc(&pkey, K));
+    CK(keep.alloc(&pval, K));
+    CK(tmp.alloc(&pkey_alt, K));
+    CK(keep.alloc(&pval_alt, K));
+    char* pscratch;
+    CK(tmp.alloc(&pscratch, radix_scratch_bytes(K)));
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), VN, bin, st->d_cams,
+                          N, tw, th, K, pkey, pval, s));
+    }
+    const int tbits = bits_for((uint64_t)pl.tiles);
+    bool palt = false;
+    {
+      StageTimer t(ctx, OCGS_STAGE_TILE_SORT);
+      CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K, tbits, pscratch, &palt, s));
+    }
+    uint32_t* skey = palt ? pkey_alt : pkey;
+    st->vals = palt ? pval_alt : pval;
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_tile_ranges(skey, K, st->ranges, s));
+    }
 
-  uint32_t* queue = nullptr;
-  st->tile_order = nullptr;
-  if (st->persistent) {
+    uint32_t* queue = nullptr;
+    st->tile_order = nullptr;
+    if (st->persistent) {
+      CK(tmp.alloc(&queue, 1));
+      CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+      uint32_t *wk, *ids, *wk_alt, *ids_alt;
+      CK(tmp.alloc(&wk, pl.tiles));
+      CK(keep.alloc(&ids, pl.tiles));
+      CK(tmp.alloc(&wk_alt, pl.tiles));
+      CK(keep.alloc(&ids_alt, pl.tiles));
+      char* tscratch;
+      CK(tmp.alloc(&tscratch, radix_scratch_bytes((uint32_t)pl.tiles)));
+      CK(launch_tile_order(st->ranges, (uint32_t)pl.tiles, wk, ids, s));
+      bool talt = false;
+      CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, (uint32_t)pl.tiles, 32, tscratch, &talt, s));
+      st->tile_order = talt ? ids_alt : ids;
+    }
+
+    RasterArgs ra{};
+    ra.ewa = ewa ? 1 : 0;
+    ra.cams = st->d_cams;
+    ra.tile_prefix = st->d_tile_prefix;
+    ra.n_views = V;
+    ra.n_gauss = N;
+    ra.n_tiles = (uint32_t)pl.tiles;
+    ra.ranges = st->ranges;
+    ra.vals = st->vals;
+    ra.rec = st->rec;
+    if (out) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
+    ra.t_final = keep_state ? st->t_final : nullptr;  // no state kept: nothing to write
+    ra.last = keep_state ? st->last : nullptr;
+    ra.score = score;
+    ra.tile_order = st->tile_order;
+    ra.queue = queue;
+    ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 * st->ppt / (tw * th)) : 0;
+    {
+      StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
+      CK(launch_raster_forward(ra, tw, th, st->ppt, out != nullptr, s));
+    }
+
+  } else {
+    // Two passes.  The front of the depth order is binned and rendered first.
+    // Each tile with a pixel still running at the end of that prefix is then
+    // binned with the records behind the front and continues from the state
+    // the first pass left (T, the sums, the last blended position, the stop
+    // flags): every pixel walks the same list, in the same order, as in one pass.
+    bool alt = false;
+    {
+      StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
+      CK(launch_iota(order, VN, s));
+      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+    }
+    uint32_t* sorted = alt ? order_alt : order;
+    const uint32_t* skeys = alt ? dkey_alt : dkey;
+    const double front = std::ceil((double)ctx->opts.front_fraction * (double)VN);
+    const uint32_t M = (uint32_t)std::min<double>((double)VN, std::max(1.0, front));
+    uint32_t* d_valid = reinterpret_cast<uint32_t*>(ctx->d_scalar + 4);
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_tile_count_sorted(sorted, M, bin, st->d_cams, N, tw, th, st->ntiles, counts, s));
+      CK(scan_exclusive_u64(counts, counts, M, ctx->d_scalar, scratch, s));
+      CK(launch_count_below(skeys, VN, 0xffffffffu, d_valid, s));  // records with a non-empty screen box
+    }
+    CK(cudaMemcpyAsync(ctx->h_scalar, ctx->d_scalar, 5 * sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+    ocgs_status rs = read_status(ctx, &status);
+    if (rs != OCGS_OK) return rs;
+    const uint64_t K1_64 = ctx->h_scalar[0];
+    const uint32_t n_valid = *reinterpret_cast<const uint32_t*>(ctx->h_scalar + 4);
+    if (K1_64 > (uint64_t)INT32_MAX)
+      return set_err(ctx, OCGS_ERR_CAPACITY, "more than 2^31-1 (tile, Gaussian) pairs; split the views");
+    const uint32_t K1 = (uint32_t)K1_64;
+    const bool second = M < n_valid;  // records behind the front remain
+    const int tbits = bits_for((uint64_t)pl.tiles);
+    const uint32_t n_t = (uint32_t)pl.tiles;
+
+    uint32_t *pkey, *pval, *pkey_alt, *pval_alt;
+    CK(tmp.alloc(&pkey, K1));
+    CK(keep.alloc(&pval, K1));
+    CK(tmp.alloc(&pkey_alt, K1));
+    CK(keep.alloc(&pval_alt, K1));
+    char* pscratch;
+    CK(tmp.alloc(&pscratch, radix_scratch_bytes(K1)));
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_duplicate(sorted, counts, reinterpret_cast<const uint64_t*>(ctx->d_scalar), M, bin, st->d_cams, N,
+                          tw, th, K1, pkey, pval, s));
+    }
+    bool palt = false;
+    {
+      StageTimer t(ctx, OCGS_STAGE_TILE_SORT);
+      CK(radix_sort_pairs(pkey, pval, pkey_alt, pval_alt, K1, tbits, pscratch, &palt, s));
+    }
+    st->vals = palt ? pval_alt : pval;
+    {
+      StageTimer t(ctx, OCGS_STAGE_BINNING);
+      CK(launch_tile_ranges(palt ? pkey_alt : pkey, K1, st->ranges, s));
+    }
+    uint32_t *queue, *wk, *ids, *wk_alt, *ids_alt;
     CK(tmp.alloc(&queue, 1));
-    CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
-    uint32_t *wk, *ids, *wk_alt, *ids_alt;
-    CK(tmp.alloc(&wk, pl.tiles));
-    CK(keep.alloc(&ids, pl.tiles));
-    CK(tmp.alloc(&wk_alt, pl.tiles));
-    CK(keep.alloc(&ids_alt, pl.tiles));
+    CK(tmp.alloc(&wk, n_t));
+    CK(tmp.alloc(&ids, n_t));
+    CK(tmp.alloc(&wk_alt, n_t));
+    CK(tmp.alloc(&ids_alt, n_t));
     char* tscratch;
-    CK(tmp.alloc(&tscratch, radix_scratch_bytes((uint32_t)pl.tiles)));
-    CK(launch_tile_order(st->ranges, (uint32_t)pl.tiles, wk, ids, s));
+    CK(tmp.alloc(&tscratch, std::max(radix_scratch_bytes(n_t), scan_scratch_bytes(n_t + 1))));
+    CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+    CK(launch_tile_order(st->ranges, n_t, wk, ids, s));
     bool talt = false;
-    CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, (uint32_t)pl.tiles, 32, tscratch, &talt, s));
-    st->tile_order = talt ? ids_alt : ids;
-  }
-
-  RasterArgs ra{};
-  ra.ewa = ewa ? 1 : 0;
-  ra.cams = st->d_cams;
-  ra.tile_prefix = st->d_tile_prefix;
-  ra.n_views = V;
-  ra.n_gauss = N;
-  ra.n_tiles = (uint32_t)pl.tiles;
-  ra.ranges = st->ranges;
-  ra.vals = st->vals;
-  ra.rec = st->rec;
-  if (out) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
-  ra.t_final = st->t_final;
-  ra.last = st->last;
-  ra.score = score;
-  ra.tile_order = st->tile_order;
-  ra.queue = queue;
-  ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 * st->ppt / (tw * th)) : 0;
-  {
-    StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-    CK(launch_raster_forward(ra, tw, th, st->ppt, out != nullptr, s));
+    CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 32, tscratch, &talt, s));
+    // the first pass leaves each pixel's state for the second: T and the last
+    // blended position (the kept state, or scratch), the stop flags, the open tiles
+    float* t_fin = keep_state ? st->t_final : nullptr;
+    uint32_t* lst = keep_state ? st->last : nullptr;
+    uint32_t* open = nullptr;
+    uint8_t* done = nullptr;
+    if (second) {
+      if (!keep_state) {
+        CK(tmp.alloc(&t_fin, pl.P));
+        CK(tmp.alloc(&lst, pl.P));
+      }
+      CK(tmp.alloc(&open, n_t));
+      CK(tmp.alloc(&done, pl.P));
+      CK(cudaMemsetAsync(open, 0, sizeof(uint32_t) * n_t, s));
+    }
+    RasterArgs ra{};
+    ra.ewa = ewa ? 1 : 0;
+    ra.cams = st->d_cams;
+    ra.tile_prefix = st->d_tile_prefix;
+    ra.n_views = V;
+    ra.n_gauss = N;
+    ra.n_tiles = n_t;
+    ra.ranges = st->ranges;
+    ra.vals = st->vals;
+    ra.rec = st->rec;
+    ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
+    ra.t_final = t_fin;
+    ra.last = lst;
+    ra.score = score;
+    ra.tile_order = talt ? ids_alt : ids;
+    ra.queue = queue;
+    ra.persistent_ctas = ctx->sm_count * (2048 * st->ppt / (tw * th));
+    ra.open = open;
+    ra.done = done;
+    {
+      StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
+      CK(launch_raster_forward(ra, tw, th, st->ppt, true, s));
+    }
+    uint32_t K2 = 0;
+    uint32_t* P = nullptr;
+    const uint32_t n_back = second ? n_valid - M : 0u;  // records behind the front
+    if (second) {
+      CK(tmp.alloc(&P, (size_t)n_t + 1));
+      {
+        StageTimer t(ctx, OCGS_STAGE_BINNING);
+        CK(scan_exclusive_u32(open, P, n_t, P + n_t, tscratch, s));
+        CK(launch_open_count(sorted + M, n_back, bin, st->d_cams, N, tw, th, P, counts, s));
+        CK(scan_exclusive_u64(counts, counts, n_back, ctx->d_scalar + 5, scratch, s));
+      }
+      CK(cudaMemcpyAsync(ctx->h_scalar + 5, ctx->d_scalar + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      const uint64_t K2_64 = ctx->h_scalar[5];
+      if ((uint64_t)K1 + K2_64 > (uint64_t)INT32_MAX)
+        return set_err(ctx, OCGS_ERR_CAPACITY, "more than 2^31-1 (tile, Gaussian) pairs; split the views");
+      K2 = (uint32_t)K2_64;
+    }
+    if (K2) {
+      uint32_t *qkey, *qval, *qkey_alt, *qval_alt;
+      CK(tmp.alloc(&qkey, K2));
+      CK(keep.alloc(&qval, K2));
+      CK(tmp.alloc(&qkey_alt, K2));
+      CK(keep.alloc(&qval_alt, K2));
+      char* qscratch;
+      CK(tmp.alloc(&qscratch, radix_scratch_bytes(K2)));
+      CK(keep.alloc(&st->ranges2, n_t));
+      CK(cudaMemsetAsync(st->ranges2, 0, sizeof(uint2) * n_t, s));
+      {
+        StageTimer t(ctx, OCGS_STAGE_BINNING);
+        CK(launch_duplicate_open(sorted + M, counts, ctx->d_scalar + 5, n_back, bin, st->d_cams, N, tw, th, open, P,
+                                 K2, qkey, qval, s));
+      }
+      bool qalt = false;
+      {
+        StageTimer t(ctx, OCGS_STAGE_TILE_SORT);
+        CK(radix_sort_pairs(qkey, qval, qkey_alt, qval_alt, K2, tbits, qscratch, &qalt, s));
+      }
+      st->vals2 = qalt ? qval_alt : qval;
+      uint32_t* n_again = reinterpret_cast<uint32_t*>(ctx->d_scalar + 6);
+      {
+        StageTimer t(ctx, OCGS_STAGE_BINNING);
+        CK(launch_tile_ranges(qalt ? qkey_alt : qkey, K2, st->ranges2, s));
+        CK(cudaMemsetAsync(n_again, 0, sizeof(uint32_t), s));
+        CK(launch_second_queue(st->ranges2, n_t, wk, ids, n_again, s));
+        CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 32, tscratch, &talt, s));
+      }
+      RasterArgs rb = ra;
+      rb.ranges = st->ranges2;
+      rb.vals = st->vals2;
+      rb.prior = st->ranges;
+      rb.tile_order = talt ? ids_alt : ids;
+      rb.n_queue = n_again;
+      rb.open = nullptr;
+      CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
+      {
+        StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
+        CK(launch_raster_forward(rb, tw, th, st->ppt, true, s));
+      }
+    }
+    K = K1 + K2;
+    st->K = K;
+    // the backward's work order: longest complete lists first
+    uint32_t *bids, *bids_alt;
+    CK(keep.alloc(&bids, n_t));
+    CK(keep.alloc(&bids_alt, n_t));
+    CK(launch_tile_order(st->ranges, n_t, wk, bids, s, st->ranges2));
+    bool balt = false;
+    CK(radix_sort_pairs(wk, bids, wk_alt, bids_alt, n_t, 32, tscratch, &balt, s));
+    st->tile_order = balt ? bids_alt : bids;
   }
 
   ctx->stats.n_gaussians = N;
@@ -581,6 +765,8 @@ ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
   const int ppt = o->pixels_per_thread == 0 ? 2 : o->pixels_per_thread;
   if (!valid_tile(o->tile_w, o->tile_h, ppt))
     return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8 with 1 or 2 pixels per thread (4 for 16x16 and 16x8)");
+  if (!(o->front_fraction >= 0.f && o->front_fraction <= 1.f))
+    return set_err(ctx, OCGS_ERR_ARG, "front_fraction must lie in [0, 1]");
   ctx->opts = *o;
   ctx->opts.pixels_per_thread = ppt;
   return OCGS_OK;
@@ -669,6 +855,8 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   ba.n_tiles = st->n_tiles;
   ba.ranges = st->ranges;
   ba.vals = st->vals;
+  ba.ranges2 = st->ranges2;
+  ba.vals2 = st->vals2;
   ba.rec = st->rec;
   ba.t_final = st->t_final;
   ba.last = st->last;
@@ -1131,6 +1319,7 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
       std::istringstream ls(line);
       std::string k;
       ocgs_options o{};
+      o.front_fraction = ctx->opts.front_fraction;
       double ms = 0.0;
       if ((ls >> k >> o.tile_w >> o.tile_h >> o.pixels_per_thread >> o.persistent >> ms) && k == key &&
           ocgs_set_options(ctx, &o) == OCGS_OK) {
@@ -1172,7 +1361,7 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
   ocgs_status status = OCGS_OK;
   for (const auto& sh : shapes) {
     for (int pers = 0; pers <= 1; ++pers) {
-      ocgs_options o{sh[0], sh[1], pers, sh[2]};
+      ocgs_options o{sh[0], sh[1], pers, sh[2], saved.front_fraction};
       if (ocgs_set_options(ctx, &o) != OCGS_OK) continue;
       double ms_sum = 0.0;
       for (int rep = 0; rep < 3 && status == OCGS_OK; ++rep) {

@@ -495,8 +495,34 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ra
                                const uint32_t* d_n = nullptr);
 // n32 = min(*total, cap); raises kStatusCapacity when *total > cap
 cudaError_t launch_clamp_count(const uint64_t* total, uint32_t cap, uint32_t* n32, int* status, cudaStream_t s);
+// work keys of the persistent queue, heaviest tiles first (ranges2: an optional second
+// segment of each tile's list, counted with the first)
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
-                              uint32_t* tile_ids, cudaStream_t s);
+                              uint32_t* tile_ids, cudaStream_t s, const uint2* ranges2 = nullptr);
+
+// Two-pass binning (front records first, then the records behind them into the tiles left open):
+// exact tile counts of the first n entries of the depth order (counts[i], and ntiles[order[i]])
+cudaError_t launch_tile_count_sorted(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                                     int64_t n_gauss, int tile_w, int tile_h, int32_t* ntiles, uint64_t* counts,
+                                     cudaStream_t s);
+// *out = number of entries of the ascending sorted_keys[n] below key
+cudaError_t launch_count_below(const uint32_t* sorted_keys, uint32_t n, uint32_t key, uint32_t* out,
+                               cudaStream_t s);
+// counts[i] = open tiles reached by entry i of the depth order; open_prefix [n_tiles + 1]
+// is the exclusive prefix sum of the 0/1 open flags
+cudaError_t launch_open_count(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                              int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open_prefix, uint64_t* counts,
+                              cudaStream_t s);
+// the (open tile, record) pairs in depth order from the scan of those counts (order, offsets
+// and n_rec cover the entries counted)
+cudaError_t launch_duplicate_open(const uint32_t* order, const uint64_t* offsets, const uint64_t* total,
+                                  uint32_t n_rec, const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w,
+                                  int tile_h, const uint32_t* open, const uint32_t* open_prefix, uint32_t n_pairs,
+                                  uint32_t* keys, uint32_t* vals, cudaStream_t s);
+// the second pass's queue: tiles with a non-empty ranges2 first (longest first);
+// n_again (zeroed by the caller) counts them
+cudaError_t launch_second_queue(const uint2* ranges2, uint32_t n_tiles, uint32_t* work_key, uint32_t* ids,
+                                uint32_t* n_again, cudaStream_t s);
 
 struct RasterArgs {
   int ewa;  // records are projected 3D Gaussians (preprocess_ewa)
@@ -509,12 +535,21 @@ struct RasterArgs {
   const uint32_t* vals;     // sorted record indices
   RecPtrs rec;
   ImgPtrs out;
-  float* t_final;
+  float* t_final;           // NULL: the pass keeps no backward state
   uint32_t* last;
   float* score;
   const uint32_t* tile_order;  // persistent: tiles in work order (NULL = natural)
   uint32_t* queue;             // persistent: global tile counter (zeroed)
   int persistent_ctas;         // 0 = one CTA per tile
+  const uint32_t* n_queue;     // persistent: device-side queue length (NULL = n_tiles)
+  // Two-pass rendering.  First pass: open[t] is set to 1 for each tile with a
+  // pixel still running at the end of its list, and done[pixel] records which
+  // pixels have stopped.  Second pass: prior[t] is the tile's first-pass range;
+  // the tile continues where that list ended (position prior.y - prior.x) from
+  // the first pass's images, t_final, last and done.
+  uint32_t* open;
+  uint8_t* done;
+  const uint2* prior;
 };
 // ppt: pixels per thread (vertically adjacent): 1 or 2, and 4 for 16x16 tiles
 cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, int ppt, bool write_image,
@@ -528,6 +563,8 @@ struct RasterBwdArgs {
   uint32_t n_tiles;
   const uint2* ranges;
   const uint32_t* vals;
+  const uint2* ranges2;     // two-pass renders: the second segment of each tile's list (NULL: none)
+  const uint32_t* vals2;
   RecPtrs rec;
   const float* t_final;
   const uint32_t* last;

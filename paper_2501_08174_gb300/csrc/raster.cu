@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
   const int lane = tid & 31;
   const int lx = tid % TW, ly0 = (tid / TW) * PPT;  // this thread's column and first of PPT rows
   if (SCORE) s_best[tid] = 0u;
+  const uint32_t n_queue = a.n_queue ? *a.n_queue : a.n_tiles;
   for (uint32_t it = 0;; ++it) {
     uint32_t tile;
     if (a.persistent_ctas) {
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
       if (tid == 0) s_tile = atomicAdd(a.queue, 1u);
       __syncthreads();
       tile = s_tile;
-      if (tile >= a.n_tiles) break;
+      if (tile >= n_queue) break;
       if (a.tile_order) tile = a.tile_order[tile];
     } else {
       if (it > 0) break;
@@ -98,8 +99,35 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
     for (int k = 0; k < 2 * NP; ++k) {
       last[k] = 0u;
       done[k] = !(k < PPT && px < cam.W && py0 + k < cam.H);
-      alldone = alldone && done[k];
     }
+    uint32_t pos0 = 0u;  // list position before this pass's first entry
+    if (a.prior) {
+      // second pass: continue each pixel from the end of the tile's first-pass list
+      const uint2 pr = a.prior[tile];
+      pos0 = pr.y - pr.x;
+#pragma unroll
+      for (int k = 0; k < PPT; ++k) {
+        if (!done[k]) {
+          const int64_t pix = cam.pix_offset + (int64_t)(py0 + k) * cam.W + px;
+          const int p = k >> 1, i = k & 1;
+          set_lane2(T[p], i, a.t_final[pix]);
+          if (IMG) {
+            set_lane2(c0[p], i, a.out.rgb[3 * pix]);
+            set_lane2(c1[p], i, a.out.rgb[3 * pix + 1]);
+            set_lane2(c2[p], i, a.out.rgb[3 * pix + 2]);
+            set_lane2(dep[p], i, a.out.depth[pix]);
+            if (Q2) set_lane2(qz[p], i, a.out.depth2[pix]);
+            set_lane2(n0[p], i, a.out.normal[3 * pix]);
+            set_lane2(n1[p], i, a.out.normal[3 * pix + 1]);
+            set_lane2(n2[p], i, a.out.normal[3 * pix + 2]);
+          }
+          last[k] = a.last[pix];
+          done[k] = a.done[pix] != 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) alldone = alldone && done[k];
     for (uint32_t b0 = start; b0 < end; b0 += NT) {
       if (__syncthreads_count(!alldone) == 0) break;
       const uint32_t kk = b0 + tid;
@@ -139,7 +167,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             ap = s_a0[j];
             an = s_a1[j];
           }
-          const uint32_t pos = b0 + (uint32_t)j - start + 1u;
+          const uint32_t pos = pos0 + b0 + (uint32_t)j - start + 1u;
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             const int k0 = 2 * p, k1 = 2 * p + 1;
@@ -193,6 +221,10 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
         }
       }
     }
+    if (a.open) {
+      // the tile stays open if a pixel has not stopped within its list
+      if (__syncthreads_count(!alldone) > 0 && tid == 0) a.open[tile] = 1u;
+    }
     if (IMG) {
 #pragma unroll
       for (int k = 0; k < PPT; ++k) {
@@ -210,8 +242,11 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
           a.out.normal[3 * pix + 0] = lane2(n0[p], i);
           a.out.normal[3 * pix + 1] = lane2(n1[p], i);
           a.out.normal[3 * pix + 2] = lane2(n2[p], i);
-          a.t_final[pix] = Tk;
-          a.last[pix] = last[k];
+          if (a.t_final) {  // the backward's state, when the pass keeps it
+            a.t_final[pix] = Tk;
+            a.last[pix] = last[k];
+          }
+          if (a.open) a.done[pix] = done[k] ? 1 : 0;
         }
       }
     }
@@ -301,7 +336,11 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
     const int px = (local % cam.tiles_x) * TW + lx;
     const int py0 = (local / cam.tiles_x) * TH + ly0;
     const float pxf = (float)px + 0.5f;
-    const uint32_t start = a.ranges[tile].x;
+    const uint2 rg1 = a.ranges[tile];
+    const uint32_t start = rg1.x;
+    // a two-pass list continues in the second segment after its first rg1.y - rg1.x entries
+    const uint32_t len1 = a.ranges2 ? rg1.y - rg1.x : 0xffffffffu;
+    const uint32_t start2 = a.ranges2 ? a.ranges2[tile].x : 0u;
     // pixel k of this thread is lane (k & 1) of pair k / 2 (an odd PPT leaves an idle lane)
     constexpr int NP = (PPT + 1) / 2;
     float2 T[NP], gAT[NP], S[NP];
@@ -352,7 +391,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
       const int bstart = max(0, bend - NT);
       __syncthreads();
       if (bstart + tid < bend) {
-        const uint32_t idx = a.vals[start + (uint32_t)(bstart + tid)];
+        const uint32_t q = (uint32_t)(bstart + tid);
+        const uint32_t idx = q < len1 ? a.vals[start + q] : a.vals2[start2 + (q - len1)];
         const float4 g0 = a.rec.g0[idx], g1 = a.rec.g1[idx], g2 = a.rec.g2[idx];
         const float rb = support_rho(g0.z);
         s_g0[tid] = g0;

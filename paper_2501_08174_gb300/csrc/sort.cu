@@ -472,12 +472,14 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint32_t n
 }
 
 // work key for the persistent queue: heaviest tiles first (descending pair count)
-__global__ void tile_work_kernel(const uint2* __restrict__ ranges, uint32_t n, uint32_t* __restrict__ work_key,
-                                 uint32_t* __restrict__ ids) {
+__global__ void tile_work_kernel(const uint2* __restrict__ ranges, const uint2* __restrict__ ranges2, uint32_t n,
+                                 uint32_t* __restrict__ work_key, uint32_t* __restrict__ ids) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   const uint2 r = ranges[t];
-  work_key[t] = 0xffffffffu - (r.y - r.x);
+  uint32_t len = r.y - r.x;
+  if (ranges2) len += ranges2[t].y - ranges2[t].x;
+  work_key[t] = 0xffffffffu - len;
   ids[t] = t;
 }
 
@@ -573,9 +575,9 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ra
 }
 
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
-                              uint32_t* tile_ids, cudaStream_t s) {
+                              uint32_t* tile_ids, cudaStream_t s, const uint2* ranges2) {
   if (n_tiles == 0) return cudaSuccess;
-  tile_work_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, n_tiles, work_key, tile_ids);
+  tile_work_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, ranges2, n_tiles, work_key, tile_ids);
   return launched();
 }
 
@@ -593,6 +595,238 @@ __global__ void clamp_count_kernel(const uint64_t* __restrict__ total, uint32_t 
 
 cudaError_t launch_clamp_count(const uint64_t* total, uint32_t cap, uint32_t* n32, int* status, cudaStream_t s) {
   clamp_count_kernel<<<1, 1, 0, s>>>(total, cap, n32, status);
+  return launched();
+}
+
+}  // namespace ocgs
+
+// ------------------------------------------------------------------ two-pass binning
+// The first pass bins only the records at the front of the depth order; the
+// tiles whose pixels all stop inside that prefix (the front-to-back walk of
+// Sec. 4.3 ends when T falls below its bound) are final.  The second pass bins
+// the records behind the front, but only into the tiles still open, and those
+// tiles continue from where the first pass stopped.  Each tile's list is the
+// one a single pass builds (records in depth order), split in two segments.
+namespace ocgs {
+namespace {
+
+__device__ __forceinline__ int4 bin_rect(const float4 b2) {
+  const uint32_t xy = __float_as_uint(b2.z), zw = __float_as_uint(b2.w);
+  return make_int4((int)(int16_t)(xy & 0xffffu), (int)(int16_t)(xy >> 16), (int)(int16_t)(zw & 0xffffu),
+                   (int)(int16_t)(zw >> 16));
+}
+
+// open tiles among [rowbase + x0, rowbase + x1] from the exclusive prefix P of the open flags
+__device__ __forceinline__ int open_in(const uint32_t* __restrict__ P, uint32_t rowbase, int x0, int x1) {
+  return x1 < x0 ? 0 : (int)(P[rowbase + (uint32_t)x1 + 1u] - P[rowbase + (uint32_t)x0]);
+}
+
+__global__ void __launch_bounds__(kThreads) tile_count_sorted_kernel(const uint32_t* __restrict__ order, uint32_t n,
+                                                                     const float4* __restrict__ bin,
+                                                                     const DevCam* __restrict__ cams, int64_t n_gauss,
+                                                                     int tw, int th, int32_t* __restrict__ ntiles,
+                                                                     uint64_t* __restrict__ counts) {
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t r = order[i];
+  const BinView b = load_bin(bin, r);
+  int cnt = 0;
+  if (b.rc.z >= b.rc.x) {
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, b.rc));
+  }
+  ntiles[r] = cnt;
+  counts[i] = (uint64_t)cnt;
+}
+
+// number of entries of an ascending array below key (one thread)
+__global__ void count_below_kernel(const uint32_t* __restrict__ sorted_keys, uint32_t n, uint32_t key,
+                                   uint32_t* __restrict__ out) {
+  uint32_t lo = 0, hi = n;
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo) / 2u;
+    if (sorted_keys[mid] < key) lo = mid + 1u; else hi = mid;
+  }
+  *out = lo;
+}
+
+// Second-pass count of entry i of the depth order: its tiles that are open.
+// The candidate rectangle is tested first, from the prefix of the open flags,
+// so that a record over closed tiles only skips the coverage arithmetic.
+__global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __restrict__ order, uint32_t n,
+                                                              const float4* __restrict__ bin,
+                                                              const DevCam* __restrict__ cams, int64_t n_gauss,
+                                                              int tw, int th, const uint32_t* __restrict__ P,
+                                                              uint64_t* __restrict__ counts) {
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t r = order[i];
+  const int4 rc = bin_rect(bin[3 * (size_t)r + 2]);
+  int cnt = 0;
+  if (rc.z >= rc.x) {
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    int cand = 0;
+    for (int ty = rc.y; ty <= rc.w && cand == 0; ++ty)
+      cand += open_in(P, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), rc.x, rc.z);
+    if (cand > 0) {
+      const BinView b = load_bin(bin, r);
+      const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+      for (int ty = rc.y; ty <= rc.w; ++ty) {
+        const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
+        const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+        cnt += open_in(P, rowbase, rr.a0, rr.a1) + open_in(P, rowbase, rr.b0, rr.b1);
+      }
+    }
+  }
+  counts[i] = (uint64_t)cnt;
+}
+
+__device__ __forceinline__ uint64_t write_open_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
+                                                    uint64_t stop, const uint32_t* __restrict__ open,
+                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
+  for (int tx = rr.a0; tx <= rr.a1; ++tx) {
+    const uint32_t t = rowbase + (uint32_t)tx;
+    if (open[t]) {
+      if (pos < stop) { keys[pos] = t; vals[pos] = r; }
+      ++pos;
+    }
+  }
+  for (int tx = rr.b0; tx <= rr.b1; ++tx) {
+    const uint32_t t = rowbase + (uint32_t)tx;
+    if (open[t]) {
+      if (pos < stop) { keys[pos] = t; vals[pos] = r; }
+      ++pos;
+    }
+  }
+  return pos;
+}
+
+// Second-pass pairs, in depth order: entry i writes its open tiles from
+// offsets[i] on (rows in order, tiles left to right).  An entry with few rows
+// is written by its own lane; the rows of a taller one are shared out over
+// the warp with a scan of their open counts.
+__global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
+    const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
+    uint32_t n_rec, const float4* __restrict__ bin, const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th,
+    const uint32_t* __restrict__ open, const uint32_t* __restrict__ P, uint32_t n_pairs, uint32_t* __restrict__ keys,
+    uint32_t* __restrict__ vals) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  uint32_t r = 0;
+  uint64_t o = 0;
+  if (i < n_rec) {
+    o = offsets[i];
+    r = order[i];
+  }
+  uint64_t o_next = __shfl_down_sync(kFull, o, 1);
+  if (lane == 31 || i + 1 >= n_rec) o_next = (i + 1 < n_rec) ? offsets[i + 1] : *total;
+  int cnt = 0;
+  int4 rc = make_int4(0, 0, -1, -1);
+  if (i < n_rec && o < (uint64_t)n_pairs) {
+    cnt = (int)(o_next - o);
+    if (cnt > 0) rc = bin_rect(bin[3 * (size_t)r + 2]);
+  }
+  const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
+  if (small) {
+    const BinView b = load_bin(bin, r);
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+    const uint64_t stop = min(o + (uint64_t)cnt, (uint64_t)n_pairs);
+    uint64_t pos = o;
+    for (int ty = rc.y; ty <= rc.w; ++ty) {
+      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
+      pos = write_open_runs(rr, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), r, pos, stop, open, keys, vals);
+    }
+  }
+  unsigned big = __ballot_sync(kFull, cnt > 0 && !small);
+  while (big) {
+    const int src = __ffs(big) - 1;
+    big &= big - 1u;
+    const uint32_t rr = __shfl_sync(kFull, r, src);
+    const uint64_t oo = __shfl_sync(kFull, o, src);
+    const int bcnt = __shfl_sync(kFull, cnt, src);
+    const BinView bb = load_bin(bin, rr);
+    const int4 bc = bb.rc;
+    const DevCam& cam = cams[rr / (uint64_t)n_gauss];
+    const SupportConic k = support_conic(bb.g0, bb.g1, bb.g2, bb.rb);
+    const uint64_t stop = min(oo + (uint64_t)bcnt, (uint64_t)n_pairs);
+    uint64_t base = oo;
+    for (int row0 = bc.y; row0 <= bc.w; row0 += 32) {
+      const int ty = row0 + lane;
+      RowRuns runs{1, 0, 1, 0};
+      int c = 0;
+      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+      if (ty <= bc.w) {
+        runs = row_runs(k, ty, tw, th, cam.W, cam.H, bc);
+        c = open_in(P, rowbase, runs.a0, runs.a1) + open_in(P, rowbase, runs.b0, runs.b1);
+      }
+      int inc = c;
+#pragma unroll
+      for (int s2 = 1; s2 < 32; s2 <<= 1) {
+        const int t = __shfl_up_sync(kFull, inc, s2);
+        if (lane >= s2) inc += t;
+      }
+      if (c > 0) write_open_runs(runs, rowbase, rr, base + (uint64_t)(inc - c), stop, open, keys, vals);
+      base += (uint64_t)__shfl_sync(kFull, inc, 31);
+    }
+  }
+}
+
+// The second pass's queue: tiles with a second-pass segment, longest first,
+// every other tile last; n_again counts the former.
+__global__ void second_queue_kernel(const uint2* __restrict__ ranges2, uint32_t n_tiles,
+                                    uint32_t* __restrict__ work_key, uint32_t* __restrict__ ids,
+                                    uint32_t* __restrict__ n_again) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  const uint2 r2 = ranges2[t];
+  const uint32_t len = r2.y - r2.x;
+  if (len) atomicAdd(n_again, 1u);
+  work_key[t] = 0xffffffffu - len;
+  ids[t] = t;
+}
+
+}  // namespace
+
+cudaError_t launch_tile_count_sorted(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                                     int64_t n_gauss, int tile_w, int tile_h, int32_t* ntiles, uint64_t* counts,
+                                     cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  tile_count_sorted_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, n, bin, cams, n_gauss, tile_w,
+                                                                              tile_h, ntiles, counts);
+  return launched();
+}
+
+cudaError_t launch_count_below(const uint32_t* sorted_keys, uint32_t n, uint32_t key, uint32_t* out,
+                               cudaStream_t s) {
+  count_below_kernel<<<1, 1, 0, s>>>(sorted_keys, n, key, out);
+  return launched();
+}
+
+cudaError_t launch_open_count(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                              int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open_prefix, uint64_t* counts,
+                              cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  open_count_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, n, bin, cams, n_gauss, tile_w, tile_h,
+                                                                       open_prefix, counts);
+  return launched();
+}
+
+cudaError_t launch_duplicate_open(const uint32_t* order, const uint64_t* offsets, const uint64_t* total,
+                                  uint32_t n_rec, const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w,
+                                  int tile_h, const uint32_t* open, const uint32_t* open_prefix, uint32_t n_pairs,
+                                  uint32_t* keys, uint32_t* vals, cudaStream_t s) {
+  if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
+  duplicate_open_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(
+      order, offsets, total, n_rec, bin, cams, n_gauss, tile_w, tile_h, open, open_prefix, n_pairs, keys, vals);
+  return launched();
+}
+
+cudaError_t launch_second_queue(const uint2* ranges2, uint32_t n_tiles, uint32_t* work_key, uint32_t* ids,
+                                uint32_t* n_again, cudaStream_t s) {
+  if (n_tiles == 0) return cudaSuccess;
+  second_queue_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges2, n_tiles, work_key, ids, n_again);
   return launched();
 }
 
