@@ -74,6 +74,9 @@ def parse_args():
     p.add_argument("--tile", default="16x16")
     p.add_argument("--persistent", type=int, default=1)
     p.add_argument("--ppt", type=int, default=4, help="pixels per thread")
+    p.add_argument("--front", type=float, default=None,
+                   help="share of the depth order binned in the first of two passes (0 = one pass; "
+                        "default: the library's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
@@ -176,7 +179,9 @@ def sum_over_ranks(x: float, world: int, device=None) -> float:
 
 
 def workload_args(a) -> str:
-    return f"--n {a.n} --views {a.views} --tile {a.tile} --persistent {a.persistent} --ppt {a.ppt}"
+    from paper_2501_08174_gb300 import FRONT_FRACTION
+    front = FRONT_FRACTION if a.front is None else a.front
+    return f"--n {a.n} --views {a.views} --tile {a.tile} --persistent {a.persistent} --ppt {a.ppt} --front {front:g}"
 
 
 def load_peaks() -> dict:
@@ -471,7 +476,7 @@ def run_ours(a, rank: int, world: int, local: int):
     import torch.distributed as dist
 
     import synthetic
-    from paper_2501_08174_gb300 import Rasterizer, n_pixels
+    from paper_2501_08174_gb300 import FRONT_FRACTION, Rasterizer, n_pixels
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -496,7 +501,8 @@ def run_ours(a, rank: int, world: int, local: int):
     target = torch.tensor(target_np, device=dev)
     mask = torch.tensor(mask_np, device=dev)
     tw, th = (int(x) for x in a.tile.split("x"))
-    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt)
+    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt,
+                      front_fraction=FRONT_FRACTION if a.front is None else a.front)
 
     # sizes of the workload (outside the timed region)
     _, st = rast.render(g, cams)
@@ -612,7 +618,7 @@ def run_ewa(a, rank: int, world: int, local: int):
     import torch.distributed as dist
 
     import synthetic
-    from paper_2501_08174_gb300 import Rasterizer, n_pixels
+    from paper_2501_08174_gb300 import FRONT_FRACTION, Rasterizer, n_pixels
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -628,7 +634,8 @@ def run_ewa(a, rank: int, world: int, local: int):
     g_np["scale"] = np.concatenate([np.asarray(g_np["scale"], np.float64), third], 1)
     g = {k: torch.tensor(np.asarray(g_np[k], np.float32), device=dev) for k in ("xyz", "quat", "scale", "opacity", "sh")}
     tw, th = (int(x) for x in a.tile.split("x"))
-    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt)
+    rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt,
+                      front_fraction=FRONT_FRACTION if a.front is None else a.front)
     score = torch.zeros(a.n, device=dev)
 
     def step():

@@ -524,12 +524,19 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     uint32_t K2 = 0;
     uint32_t* P = nullptr;
     const uint32_t n_back = second ? n_valid - M : 0u;  // records behind the front
+    // candidates of the second pass: the sorted order's first M entries are no longer
+    // needed, nor are the depth keys (flag and position scratch)
+    uint32_t* cand = order == sorted ? order_alt : order;
+    uint32_t* n_cand = reinterpret_cast<uint32_t*>(ctx->d_scalar + 7);
     if (second) {
       CK(tmp.alloc(&P, (size_t)n_t + 1));
       {
         StageTimer t(ctx, OCGS_STAGE_BINNING);
         CK(scan_exclusive_u32(open, P, n_t, P + n_t, tscratch, s));
-        CK(launch_open_count(sorted + M, n_back, bin, st->d_cams, N, tw, th, P, counts, s));
+        // the records behind the front whose screen box meets an open tile, then their exact counts
+        CK(launch_open_candidates(sorted + M, n_back, bin, st->d_cams, N, P, dkey, dkey_alt, cand, n_cand, scratch,
+                                  s));
+        CK(launch_open_count(cand, n_back, n_cand, bin, st->d_cams, N, tw, th, P, counts, s));
         CK(scan_exclusive_u64(counts, counts, n_back, ctx->d_scalar + 5, scratch, s));
       }
       CK(cudaMemcpyAsync(ctx->h_scalar + 5, ctx->d_scalar + 5, sizeof(uint64_t), cudaMemcpyDeviceToHost, s));
@@ -551,8 +558,8 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(cudaMemsetAsync(st->ranges2, 0, sizeof(uint2) * n_t, s));
       {
         StageTimer t(ctx, OCGS_STAGE_BINNING);
-        CK(launch_duplicate_open(sorted + M, counts, ctx->d_scalar + 5, n_back, bin, st->d_cams, N, tw, th, open, P,
-                                 K2, qkey, qval, s));
+        CK(launch_duplicate_open(cand, counts, ctx->d_scalar + 5, n_back, n_cand, bin, st->d_cams, N, tw, th, open,
+                                 P, K2, qkey, qval, s));
       }
       bool qalt = false;
       {

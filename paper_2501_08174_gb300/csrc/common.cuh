@@ -508,17 +508,23 @@ cudaError_t launch_tile_count_sorted(const uint32_t* order, uint32_t n, const fl
 // *out = number of entries of the ascending sorted_keys[n] below key
 cudaError_t launch_count_below(const uint32_t* sorted_keys, uint32_t n, uint32_t key, uint32_t* out,
                                cudaStream_t s);
-// counts[i] = open tiles reached by entry i of the depth order; open_prefix [n_tiles + 1]
-// is the exclusive prefix sum of the 0/1 open flags
-cudaError_t launch_open_count(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
-                              int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open_prefix, uint64_t* counts,
-                              cudaStream_t s);
-// the (open tile, record) pairs in depth order from the scan of those counts (order, offsets
-// and n_rec cover the entries counted)
-cudaError_t launch_duplicate_open(const uint32_t* order, const uint64_t* offsets, const uint64_t* total,
-                                  uint32_t n_rec, const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w,
-                                  int tile_h, const uint32_t* open, const uint32_t* open_prefix, uint32_t n_pairs,
-                                  uint32_t* keys, uint32_t* vals, cudaStream_t s);
+// Second pass over the n entries behind the front (order: their records in depth order).
+// open_prefix [n_tiles + 1] is the exclusive prefix sum of the 0/1 open flags.
+// Candidates (a screen box holding an open tile), compacted in depth order into
+// cand[*n_cand]; flag and pos are [n] scratch, scratch holds scan_scratch_bytes(n).
+cudaError_t launch_open_candidates(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                                   int64_t n_gauss, const uint32_t* open_prefix, uint32_t* flag, uint32_t* pos,
+                                   uint32_t* cand, uint32_t* n_cand, void* scratch, cudaStream_t s);
+// counts[c] = open tiles reached by candidate c (0 for c >= *n_cand; counts is [n])
+cudaError_t launch_open_count(const uint32_t* cand, uint32_t n, const uint32_t* n_cand, const float4* bin,
+                              const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
+                              const uint32_t* open_prefix, uint64_t* counts, cudaStream_t s);
+// the (open tile, record) pairs of the candidates, in depth order, from the scan of those counts
+cudaError_t launch_duplicate_open(const uint32_t* cand, const uint64_t* offsets, const uint64_t* total,
+                                  uint32_t n_rec, const uint32_t* n_cand, const float4* bin, const DevCam* cams,
+                                  int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open,
+                                  const uint32_t* open_prefix, uint32_t n_pairs, uint32_t* keys, uint32_t* vals,
+                                  cudaStream_t s);
 // the second pass's queue: tiles with a non-empty ranges2 first (longest first);
 // n_again (zeroed by the caller) counts them
 cudaError_t launch_second_queue(const uint2* ranges2, uint32_t n_tiles, uint32_t* work_key, uint32_t* ids,

@@ -651,35 +651,58 @@ __global__ void count_below_kernel(const uint32_t* __restrict__ sorted_keys, uin
   *out = lo;
 }
 
-// Second-pass count of entry i of the depth order: its tiles that are open.
-// The candidate rectangle is tested first, from the prefix of the open flags,
-// so that a record over closed tiles only skips the coverage arithmetic.
-__global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __restrict__ order, uint32_t n,
-                                                              const float4* __restrict__ bin,
-                                                              const DevCam* __restrict__ cams, int64_t n_gauss,
-                                                              int tw, int th, const uint32_t* __restrict__ P,
-                                                              uint64_t* __restrict__ counts) {
+// Second pass, step 1: flag the entries (records behind the front, in depth
+// order) whose candidate rectangle holds an open tile (row sums of the open
+// flags from their prefix P, all rows loaded independently).
+__global__ void __launch_bounds__(kThreads) open_candidate_kernel(const uint32_t* __restrict__ order, uint32_t n,
+                                                                  const float4* __restrict__ bin,
+                                                                  const DevCam* __restrict__ cams, int64_t n_gauss,
+                                                                  const uint32_t* __restrict__ P,
+                                                                  uint32_t* __restrict__ flag) {
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
   if (i >= n) return;
   const uint32_t r = order[i];
   const int4 rc = bin_rect(bin[3 * (size_t)r + 2]);
-  int cnt = 0;
+  int cand = 0;
   if (rc.z >= rc.x) {
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    int cand = 0;
-    for (int ty = rc.y; ty <= rc.w && cand == 0; ++ty)
-      cand += open_in(P, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), rc.x, rc.z);
-    if (cand > 0) {
-      const BinView b = load_bin(bin, r);
-      const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-      for (int ty = rc.y; ty <= rc.w; ++ty) {
-        const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-        const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
-        cnt += open_in(P, rowbase, rr.a0, rr.a1) + open_in(P, rowbase, rr.b0, rr.b1);
-      }
+    const uint32_t base = (uint32_t)(cam.tile_offset + rc.y * cam.tiles_x);
+    for (int ty = rc.y; ty <= rc.w; ++ty)
+      cand += open_in(P, base + (uint32_t)((ty - rc.y) * cam.tiles_x), rc.x, rc.z);
+  }
+  flag[i] = cand > 0 ? 1u : 0u;
+}
+
+// step 2: the flagged entries' records, in depth order (pos: exclusive scan of the flags)
+__global__ void compact_candidates_kernel(const uint32_t* __restrict__ order, uint32_t n,
+                                          const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos,
+                                          uint32_t* __restrict__ cand) {
+  const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && flag[i]) cand[pos[i]] = order[i];
+}
+
+// step 3: open tiles reached by each candidate (counts[c] = 0 for c >= *n_cand)
+__global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __restrict__ cand, uint32_t n,
+                                                              const uint32_t* __restrict__ n_cand,
+                                                              const float4* __restrict__ bin,
+                                                              const DevCam* __restrict__ cams, int64_t n_gauss,
+                                                              int tw, int th, const uint32_t* __restrict__ P,
+                                                              uint64_t* __restrict__ counts) {
+  const uint32_t c = blockIdx.x * kThreads + threadIdx.x;
+  if (c >= n) return;
+  int cnt = 0;
+  if (c < *n_cand) {
+    const uint32_t r = cand[c];
+    const BinView b = load_bin(bin, r);
+    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) {
+      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, b.rc);
+      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+      cnt += open_in(P, rowbase, rr.a0, rr.a1) + open_in(P, rowbase, rr.b0, rr.b1);
     }
   }
-  counts[i] = (uint64_t)cnt;
+  counts[c] = (uint64_t)cnt;
 }
 
 __device__ __forceinline__ uint64_t write_open_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
@@ -702,17 +725,18 @@ __device__ __forceinline__ uint64_t write_open_runs(const RowRuns& rr, uint32_t 
   return pos;
 }
 
-// Second-pass pairs, in depth order: entry i writes its open tiles from
-// offsets[i] on (rows in order, tiles left to right).  An entry with few rows
+// step 4, the second-pass pairs in depth order: candidate i writes its open
+// tiles from offsets[i] on (rows in order, tiles left to right).  An entry with few rows
 // is written by its own lane; the rows of a taller one are shared out over
 // the warp with a scan of their open counts.
 __global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
-    uint32_t n_rec, const float4* __restrict__ bin, const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th,
-    const uint32_t* __restrict__ open, const uint32_t* __restrict__ P, uint32_t n_pairs, uint32_t* __restrict__ keys,
-    uint32_t* __restrict__ vals) {
+    uint32_t n_rec, const uint32_t* __restrict__ n_cand, const float4* __restrict__ bin,
+    const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th, const uint32_t* __restrict__ open,
+    const uint32_t* __restrict__ P, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
   const int lane = threadIdx.x & 31;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  n_rec = min(n_rec, *n_cand);
   uint32_t r = 0;
   uint64_t o = 0;
   if (i < n_rec) {
@@ -804,22 +828,38 @@ cudaError_t launch_count_below(const uint32_t* sorted_keys, uint32_t n, uint32_t
   return launched();
 }
 
-cudaError_t launch_open_count(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
-                              int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open_prefix, uint64_t* counts,
-                              cudaStream_t s) {
-  if (n == 0) return cudaSuccess;
-  open_count_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, n, bin, cams, n_gauss, tile_w, tile_h,
-                                                                       open_prefix, counts);
+cudaError_t launch_open_candidates(const uint32_t* order, uint32_t n, const float4* bin, const DevCam* cams,
+                                   int64_t n_gauss, const uint32_t* open_prefix, uint32_t* flag, uint32_t* pos,
+                                   uint32_t* cand, uint32_t* n_cand, void* scratch, cudaStream_t s) {
+  if (n == 0) return cudaMemsetAsync(n_cand, 0, sizeof(uint32_t), s);
+  open_candidate_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, n, bin, cams, n_gauss,
+                                                                           open_prefix, flag);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  e = scan_exclusive<uint32_t>(flag, pos, n, n_cand, static_cast<char*>(scratch), s);
+  if (e != cudaSuccess) return e;
+  compact_candidates_kernel<<<(n + 255) / 256, 256, 0, s>>>(order, n, flag, pos, cand);
   return launched();
 }
 
-cudaError_t launch_duplicate_open(const uint32_t* order, const uint64_t* offsets, const uint64_t* total,
-                                  uint32_t n_rec, const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w,
-                                  int tile_h, const uint32_t* open, const uint32_t* open_prefix, uint32_t n_pairs,
-                                  uint32_t* keys, uint32_t* vals, cudaStream_t s) {
+cudaError_t launch_open_count(const uint32_t* cand, uint32_t n, const uint32_t* n_cand, const float4* bin,
+                              const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
+                              const uint32_t* open_prefix, uint64_t* counts, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  open_count_kernel<<<(n + kThreads - 1) / kThreads, kThreads, 0, s>>>(cand, n, n_cand, bin, cams, n_gauss, tile_w,
+                                                                       tile_h, open_prefix, counts);
+  return launched();
+}
+
+cudaError_t launch_duplicate_open(const uint32_t* cand, const uint64_t* offsets, const uint64_t* total,
+                                  uint32_t n_rec, const uint32_t* n_cand, const float4* bin, const DevCam* cams,
+                                  int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open,
+                                  const uint32_t* open_prefix, uint32_t n_pairs, uint32_t* keys, uint32_t* vals,
+                                  cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
   duplicate_open_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(
-      order, offsets, total, n_rec, bin, cams, n_gauss, tile_w, tile_h, open, open_prefix, n_pairs, keys, vals);
+      cand, offsets, total, n_rec, n_cand, bin, cams, n_gauss, tile_w, tile_h, open, open_prefix, n_pairs, keys,
+      vals);
   return launched();
 }
 
