@@ -233,16 +233,25 @@ def measured_traffic(kernel: str, workload_args: str):
 
 # ----------------------------------------------------------------------------- roofline model
 def algorithmic(stage: str, N: int, V: int, P: int, K: int, T: int, E: int, tile_passes: int, kept: int,
-                prune_calls: int = 1) -> dict:
-    """Minimum HBM bytes (and FP32 flops) of each stage for one step."""
+                prune_calls: int = 1, M: int = 0) -> dict:
+    """Minimum HBM bytes (and FP32 flops) of each stage for one step (M: records binned in the
+    first of two passes, 0 for one pass)."""
     VN = V * N
+    if M:
+        # front: counts (order, 48 B record, count, ntiles), scan, duplication; behind the front:
+        # the open-tile test (order, 16 B box, flag), its scan and compaction, the counts and their
+        # scan (the candidates' coverage reads are left out: a lower bound); pairs and tile
+        # ranges of both passes, the open flags and their prefix
+        binning = (M * (64 + 16 + 60) + (VN - M) * (24 + 12 + 24) + K * 12 + T * 32)
+    else:
+        # counts (48 B record in, 8 B out), count gather + scan (28 B), duplication (60 B in per
+        # record, 8 B out per pair), tile ranges (4 B per pair, 8 B per tile)
+        binning = VN * (56 + 28 + 60) + K * 12 + T * 8
     ssim_px = 24 + 1 + 36 + 36 + 24 + 24  # images + mask, adjoint maps out and back, images again, d_rgb
     b = {
         "preprocess": N * 232 + VN * (72 + 4 + 48 + 4),   # record, ntiles, binning record, depth key
         "depth_sort": VN * 4 + 4 * VN * 20,
-        # counts (48 B record in, 8 B out), count gather + scan (28 B), duplication (60 B in per
-        # record, 8 B out per pair), tile ranges (4 B per pair, 8 B per tile)
-        "binning": VN * (56 + 28 + 60) + K * 12 + T * 8,
+        "binning": binning,
         "tile_sort": tile_passes * K * 20,
         "raster_fwd": VN * 72 + K * 4 + P * 40,
         "loss": P * (4 + 1 + 8) + P * (12 + 12 + 1 + 24) + (ssim_px * P if prune_calls > 1 else 0),
@@ -511,6 +520,8 @@ def run_ours(a, rank: int, world: int, local: int):
     K, E, T = info["n_pairs"], info["n_evals"], info["n_tiles"]
     tile_bits = max(1, math.ceil(math.log2(max(T, 2))))
     tile_passes = (tile_bits + 7) // 8
+    front = rast.front_fraction if rast.persistent else 0.0
+    M = min(N * len(cams), max(1, math.ceil(front * N * len(cams)))) if front > 0 else 0
 
     # batched step, with the library's stage timers on
     adam = a.workload == "c5"
@@ -540,7 +551,7 @@ def run_ours(a, rank: int, world: int, local: int):
     for name, (tot_ms, cnt) in prof.items():
         if cnt == 0:
             continue  # a stage this workload does not run
-        alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1)
+        alg = algorithmic(name, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1, M)
         step_bytes += alg["bytes"]
         per_ms = tot_ms / a.steps
         stages[name] = {"ms": per_ms, "launch_sets": cnt / a.steps,
@@ -549,7 +560,7 @@ def run_ours(a, rank: int, world: int, local: int):
     dom = max(stages, key=lambda k: stages[k]["ms"])
     dstage = stages[dom]
     per_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
-    alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1)
+    alg = algorithmic(dom, N, len(cams), P, K, T, E, tile_passes, kept, 3 if adam else 1, M)
     stage_kernel = {"raster_fwd": "raster_fwd_kernel", "raster_bwd": "raster_bwd_kernel",
                     "preprocess": "preprocess_kernel", "preprocess_bwd": "preprocess_bwd_kernel"}
     traffic = None
@@ -596,7 +607,7 @@ def run_ours(a, rank: int, world: int, local: int):
                            "n_gaussians": N, "n_views": len(cams), "pixels_per_gpu": P,
                            "resolutions": [f"{c['width']}x{c['height']}" for c in cams],
                            "tile": a.tile, "pixels_per_thread": a.ppt, "persistent": bool(a.persistent),
-                           "pairs": K, "evals": E,
+                           "front_fraction": front, "pairs": K, "evals": E,
                            "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB algorithmic traffic per step",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "per_view": per_view, "stages": stages, "roofline": roofline, "hbm_roofline_step": hbm_step,
