@@ -115,7 +115,8 @@ typedef struct {
  * and the screen bounds are conservative, so tiles only reshape the work, and
  * the two-pass binning below renders every tile from the same list as one pass.
  *
- * front_fraction (persistent renders with images only; 0 = one pass): the
+ * front_fraction (persistent renders and sweeps; 0 = one pass; the captured
+ * sweep graph always bins in one pass): the
  * front-to-back walk of Sec. 4.3 stops a pixel once T falls below its bound,
  * so most (tile, Gaussian) pairs behind an opaque surface are never read.  In
  * two passes the renderer first bins and renders only the first

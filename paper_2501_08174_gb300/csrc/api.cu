@@ -322,7 +322,9 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
   }
   int status = 0;
   uint32_t K = 0;
-  const bool two_pass = out != nullptr && st->persistent && ctx->opts.front_fraction > 0.f && VN > 0;
+  // two passes need something to continue: images, or the contribution score
+  const bool two_pass = (out != nullptr || score != nullptr) && st->persistent && ctx->opts.front_fraction > 0.f &&
+                        VN > 0;
   if (!two_pass) {
     {
       StageTimer t(ctx, OCGS_STAGE_BINNING);
@@ -485,15 +487,14 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 32, tscratch, &talt, s));
     // the first pass leaves each pixel's state for the second: T and the last
     // blended position (the kept state, or scratch), the stop flags, the open tiles
-    float* t_fin = keep_state ? st->t_final : nullptr;
-    uint32_t* lst = keep_state ? st->last : nullptr;
+    const bool img = out != nullptr;
+    float* t_fin = keep_state && img ? st->t_final : nullptr;
+    uint32_t* lst = keep_state && img ? st->last : nullptr;
     uint32_t* open = nullptr;
     uint8_t* done = nullptr;
     if (second) {
-      if (!keep_state) {
-        CK(tmp.alloc(&t_fin, pl.P));
-        CK(tmp.alloc(&lst, pl.P));
-      }
+      if (!t_fin) CK(tmp.alloc(&t_fin, pl.P));
+      if (!lst && img) CK(tmp.alloc(&lst, pl.P));
       CK(tmp.alloc(&open, n_t));
       CK(tmp.alloc(&done, pl.P));
       CK(cudaMemsetAsync(open, 0, sizeof(uint32_t) * n_t, s));
@@ -508,7 +509,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     ra.ranges = st->ranges;
     ra.vals = st->vals;
     ra.rec = st->rec;
-    ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
+    if (img) ra.out = ImgPtrs{out->rgb, out->alpha, out->depth, out->normal, out->depth2};
     ra.t_final = t_fin;
     ra.last = lst;
     ra.score = score;
@@ -519,7 +520,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     ra.done = done;
     {
       StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-      CK(launch_raster_forward(ra, tw, th, st->ppt, true, s));
+      CK(launch_raster_forward(ra, tw, th, st->ppt, img, s));
     }
     uint32_t K2 = 0;
     uint32_t* P = nullptr;
@@ -585,19 +586,21 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
       {
         StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-        CK(launch_raster_forward(rb, tw, th, st->ppt, true, s));
+        CK(launch_raster_forward(rb, tw, th, st->ppt, img, s));
       }
     }
     K = K1 + K2;
     st->K = K;
-    // the backward's work order: longest complete lists first
-    uint32_t *bids, *bids_alt;
-    CK(keep.alloc(&bids, n_t));
-    CK(keep.alloc(&bids_alt, n_t));
-    CK(launch_tile_order(st->ranges, n_t, wk, bids, s, st->ranges2));
-    bool balt = false;
-    CK(radix_sort_pairs(wk, bids, wk_alt, bids_alt, n_t, 32, tscratch, &balt, s));
-    st->tile_order = balt ? bids_alt : bids;
+    if (keep_state) {
+      // the backward's work order: longest complete lists first
+      uint32_t *bids, *bids_alt;
+      CK(keep.alloc(&bids, n_t));
+      CK(keep.alloc(&bids_alt, n_t));
+      CK(launch_tile_order(st->ranges, n_t, wk, bids, s, st->ranges2));
+      bool balt = false;
+      CK(radix_sort_pairs(wk, bids, wk_alt, bids_alt, n_t, 32, tscratch, &balt, s));
+      st->tile_order = balt ? bids_alt : bids;
+    }
   }
 
   ctx->stats.n_gaussians = N;

@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
             set_lane2(n1[p], i, a.out.normal[3 * pix + 1]);
             set_lane2(n2[p], i, a.out.normal[3 * pix + 2]);
           }
-          last[k] = a.last[pix];
+          if (a.last) last[k] = a.last[pix];
           done[k] = a.done[pix] != 0;
         }
       }
@@ -224,6 +224,17 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
     if (a.open) {
       // the tile stays open if a pixel has not stopped within its list
       if (__syncthreads_count(!alldone) > 0 && tid == 0) a.open[tile] = 1u;
+      if (!IMG) {
+        // a pass without images keeps only what the continuation needs: T and the stop flags
+#pragma unroll
+        for (int k = 0; k < PPT; ++k) {
+          if (px < cam.W && py0 + k < cam.H) {
+            const int64_t pix = cam.pix_offset + (int64_t)(py0 + k) * cam.W + px;
+            a.t_final[pix] = lane2(T[k >> 1], k & 1);
+            a.done[pix] = done[k] ? 1 : 0;
+          }
+        }
+      }
     }
     if (IMG) {
 #pragma unroll

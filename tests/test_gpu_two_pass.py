@@ -104,6 +104,28 @@ def test_two_pass_other_tile_shapes(dev, tile, ppt):
         assert torch.equal(base[k], cur[k]), k
 
 
+def test_two_pass_pruning_sweeps_equal_one_pass(dev):
+    """The image-free sweeps (2DGS and the 3DGS variant) continue from T and the stop flags alone."""
+    from paper_2501_08174_gb300 import Rasterizer
+    gn, cams = opaque_scene(seed=905, n=30_000)
+    g = to_device(gn, dev)
+    rng = np.random.default_rng(906)
+    g3 = dict(g)
+    g3["scale"] = torch.cat([g["scale"], torch.tensor(np.exp(rng.uniform(np.log(0.01), np.log(0.1),
+                                                                         size=(len(gn["opacity"]), 1))),
+                                                      dtype=torch.float32, device=dev)], 1).contiguous()
+    res = {}
+    for f in (0.0, 0.05, 0.3):
+        r = Rasterizer(dev, tile=(16, 16), persistent=True, pixels_per_thread=4, front_fraction=f)
+        res[f] = (r.accumulate_contribution(g, cams), r.accumulate_contribution_3d(g3, cams))
+        torch.cuda.synchronize()
+        r.close()
+    for f in (0.05, 0.3):
+        assert torch.equal(res[0.0][0], res[f][0]), f
+        assert torch.equal(res[0.0][1], res[f][1]), f
+    assert float(res[0.0][0].max()) > 0.5 and float(res[0.0][1].max()) > 0.5
+
+
 def test_two_pass_with_nothing_visible(dev):
     """Every Gaussian behind the camera: no record has a screen box, the first pass is the
     whole render and the image is background."""
