@@ -1,33 +1,38 @@
 // Tile rasterizer: front-to-back compositing (forward) and its reverse-order
 // adjoint (backward).
 //
-// One CTA owns one screen tile; each thread owns PPT vertically adjacent
-// pixels of it.  The tile's sorted (depth, Gaussian) list is streamed through
-// shared memory in batches of one record per thread; every thread then
-// evaluates the batch against its pixel centres, so one shared-memory read of
-// a record (and, in the backward, one warp reduction of its gradient) serves
-// PPT pixels.  Compositing of a pixel stops at the first blended candidate that
+// A warp owns one band of a screen tile (32 threads x PPT vertically adjacent
+// pixels each: full tile rows) and walks the tile's sorted (depth, Gaussian)
+// list on its own, with no CTA barrier: its own slot of the persistent queue,
+// its own shared-memory batches of one record per lane.  Every lane evaluates
+// the batch against its pixel centres, so one shared-memory read of a record
+// (and, in the backward, one warp reduction of its gradient) serves PPT
+// pixels; the forward first drops, in order, the entries whose support misses
+// the band.  Compositing of a pixel stops at the first blended candidate that
 // would bring its transmittance below 1e-4 (Sec. 4.3: rendering ends once the
-// pixel reaches an opacity close to 1), warps stop once all their pixels have
-// stopped, and the CTA stops once every pixel has.  The forward optionally
-// records, for each Gaussian, the max blending weight over the pixels where it
-// was blended (the per-Gaussian visibility record that Sec. 4.3 and Sec. 5.1
-// keep while colours accumulate), with one warp max-reduction and at most one
-// atomic per warp.
+// pixel reaches an opacity close to 1), and a warp stops once all its pixels
+// have stopped.  The forward optionally records, for each Gaussian, the max
+// blending weight over the pixels where it was blended (the per-Gaussian
+// visibility record that Sec. 4.3 and Sec. 5.1 keep while colours accumulate),
+// with one warp max-reduction and at most one atomic per warp.
 //
 // The backward walks the same list back to front from each pixel's last
 // blended entry, recovering the transmittance T_i = T_{i+1} / (1 - alpha_i)
 // from the stored final transmittance, so nothing per (pixel, Gaussian) is
 // stored between the passes.  Per-Gaussian gradients are summed over the
 // thread's pixels, reduced over the warp with a halving transpose (about 20
-// shuffles for 18 values), accumulated per tile in shared memory and added to
-// global memory with one vector atomic per 4 values, entry and tile.
+// shuffles for 18 values), gathered per batch in the warp's shared memory and
+// added to global memory with one vector atomic per 4 values, entry and warp.
 #include "common.cuh"
 
 namespace ocgs {
 namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
+// Warps per CTA.  Each warp owns one band of full tile rows (32 threads x PPT
+// pixels) and walks its tile's list on its own: its own queue slot, its own
+// shared-memory batches, no CTA barrier.
+constexpr int kBlockWarps = 4;
 
 #ifdef OCGS_COUNT
 // diagnostic build only: warp iterations and evaluated (lane, pixel) pairs
@@ -45,35 +50,57 @@ __device__ unsigned long long g_diag[8];
 #define OCGS_BWD_WARPS 16
 #endif
 
+// Whether a record's support (the binning's conservative closed form: the
+// ellipse and the filter disc, grown by their margins) reaches pixel centres
+// x in [xb0, xb1], y in [yb0, yb1].  An entry it rejects passes the support
+// test at none of those pixels, so dropping it changes nothing.
+__device__ __forceinline__ bool band_reached(const float4 g0, const float4 g1, const float4 g2, float rb, float xb0,
+                                             float xb1, float yb0, float yb1) {
+  const SupportConic k = support_conic(g0, g1, g2, rb);
+  const RowSpan sp = support_row_span(k, yb0, yb1, xb0, xb1);
+  return (sp.lo0 <= sp.hi0 && sp.lo0 <= xb1 && sp.hi0 >= xb0) || (sp.lo1 <= sp.hi1 && sp.lo1 <= xb1 && sp.hi1 >= xb0);
+}
+
+// The band of a warp: its pixel rows of the tile (32 threads x PPT rows) and
+// the tile's columns, as pixel-centre bounds clipped to the image.
+template <int TW, int TH, int PPT>
+__device__ __forceinline__ float4 warp_band(const DevCam& cam, int local, int wt) {
+  constexpr int kRows = (32 / TW) * PPT;
+  const int x0 = (local % cam.tiles_x) * TW, y0 = (local / cam.tiles_x) * TH + ((wt * 32) / TW) * PPT;
+  return make_float4((float)x0 + 0.5f, (float)(min(x0 + TW, cam.W) - 1) + 0.5f, (float)y0 + 0.5f,
+                     (float)(min(y0 + kRows, cam.H) - 1) + 0.5f);
+}
+
 // Q2: also accumulate Q = sum w z^2 (the depth distortion's third plane)
 // EWA: the records are projected 3D Gaussians (the 3DGS variant of Appendix B)
 template <int TW, int TH, int PPT, bool IMG, bool SCORE, bool Q2, bool EWA>
-__global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW * TH)) raster_fwd_kernel(const RasterArgs a) {
-  constexpr int NT = TW * TH / PPT;  // threads, and records per shared-memory batch
-  __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
-  __shared__ float2 s_a1[NT];
-  __shared__ uint32_t s_gid[NT];
-  __shared__ uint32_t s_best[NT];  // per-batch max blending weight bits of each entry (SCORE)
-  __shared__ float s_rb[NT];
-  __shared__ uint32_t s_tile;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int lx = tid % TW, ly0 = (tid / TW) * PPT;  // this thread's column and first of PPT rows
-  if (SCORE) s_best[tid] = 0u;
-  const uint32_t n_queue = a.n_queue ? *a.n_queue : a.n_tiles;
+__global__ void __launch_bounds__(kBlockWarps * 32, OCGS_FWD_WARPS / kBlockWarps) raster_fwd_kernel(const RasterArgs a) {
+  constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
+  __shared__ float4 s_g0[kBlockWarps][32], s_g1[kBlockWarps][32], s_g2[kBlockWarps][32], s_a0[kBlockWarps][32];
+  __shared__ float2 s_a1[kBlockWarps][32];
+  __shared__ uint32_t s_gid[kBlockWarps][32];
+  __shared__ uint32_t s_pos[kBlockWarps][32];  // list index of each kept entry
+  __shared__ float s_rb[kBlockWarps][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  const uint32_t n_units = (a.n_queue ? *a.n_queue : a.n_tiles) * (uint32_t)WPT;
   for (uint32_t it = 0;; ++it) {
-    uint32_t tile;
+    // work unit: one warp's band of one tile; the warps run independently
+    uint32_t unit;
     if (a.persistent_ctas) {
-      __syncthreads();
-      if (tid == 0) s_tile = atomicAdd(a.queue, 1u);
-      __syncthreads();
-      tile = s_tile;
-      if (tile >= n_queue) break;
-      if (a.tile_order) tile = a.tile_order[tile];
+      uint32_t u = 0;
+      if (lane == 0) u = atomicAdd(a.queue, 1u);
+      unit = __shfl_sync(kFull, u, 0);
+      if (unit >= n_units) break;
     } else {
       if (it > 0) break;
-      tile = blockIdx.x;
+      unit = blockIdx.x * kBlockWarps + wib;
+      if (unit >= n_units) break;
     }
+    uint32_t tile = unit / WPT;
+    if (a.persistent_ctas && a.tile_order) tile = a.tile_order[tile];
+    const int tid = (int)(unit % WPT) * 32 + lane;  // thread of the tile
+    const int lx = tid % TW, ly0 = (tid / TW) * PPT;  // this thread's column and first of PPT rows
     const int v = view_of_tile(a.tile_prefix, a.n_views, (int)tile);
     const DevCam& cam = a.cams[v];
     const int local = (int)tile - cam.tile_offset;
@@ -128,23 +155,40 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
     }
 #pragma unroll
     for (int k = 0; k < 2 * NP; ++k) alldone = alldone && done[k];
-    for (uint32_t b0 = start; b0 < end; b0 += NT) {
-      if (__syncthreads_count(!alldone) == 0) break;
-      const uint32_t kk = b0 + tid;
+    const float4 band = warp_band<TW, TH, PPT>(cam, local, (int)(unit % WPT));
+    for (uint32_t b0 = start; b0 < end; b0 += 32) {
+      if (__all_sync(kFull, alldone)) break;
+      const uint32_t kk = b0 + lane;
+      // load a batch of the list, keep (in order) the entries whose support reaches this warp's band
+      bool keep = false;
+      uint32_t idx = 0;
+      float4 g0, g1, g2;
+      float rb = 0.f;
       if (kk < end) {
-        const uint32_t idx = a.vals[kk];
-        const float4 g0 = a.rec.g0[idx], g1 = a.rec.g1[idx], g2 = a.rec.g2[idx];
-        const float rb = support_rho(g0.z);
-        s_g0[tid] = g0;
-        s_g1[tid] = g1;
-        s_g2[tid] = g2;
-        s_a0[tid] = a.rec.a0[idx];
-        s_a1[tid] = a.rec.a1[idx];
-        s_rb[tid] = rb;
-        if (SCORE) s_gid[tid] = (uint32_t)((int64_t)idx - gbase);
+        idx = a.vals[kk];
+        g0 = a.rec.g0[idx];
+        g1 = a.rec.g1[idx];
+        g2 = a.rec.g2[idx];
+        rb = support_rho(g0.z);
+        keep = band_reached(g0, g1, g2, rb, band.x, band.y, band.z, band.w);
       }
-      __syncthreads();
-      const int cnt = (end - b0 < (uint32_t)NT) ? (int)(end - b0) : NT;
+      const unsigned km = __ballot_sync(kFull, keep);
+      const int slot = __popc(km & lt);
+      __syncwarp();  // the previous batch is consumed
+      if (keep) {
+        s_g0[wib][slot] = g0;
+        s_g1[wib][slot] = g1;
+        s_g2[wib][slot] = g2;
+        if (IMG) {
+          s_a0[wib][slot] = a.rec.a0[idx];
+          s_a1[wib][slot] = a.rec.a1[idx];
+        }
+        s_rb[wib][slot] = rb;
+        s_pos[wib][slot] = kk;
+        if (SCORE) s_gid[wib][slot] = (uint32_t)((int64_t)idx - gbase);
+      }
+      __syncwarp();
+      const int cnt = __popc(km);
       for (int j = 0; j < cnt; ++j) {
         if ((j & 7) == 0 && __all_sync(kFull, alldone)) break;
         float wmax = 0.f;
@@ -158,16 +202,16 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
         }
 #endif
         if (!alldone) {
-          const float4 g0 = s_g0[j], g1 = s_g1[j], g2 = s_g2[j];
-          const float rb = s_rb[j];
+          const float4 g0 = s_g0[wib][j], g1 = s_g1[wib][j], g2 = s_g2[wib][j];
+          const float rb = s_rb[wib][j];
           const SplatColumn col = splat_column(g0, g1, g2, pxf);
           float4 ap = make_float4(0.f, 0.f, 0.f, 0.f);
           float2 an = make_float2(0.f, 0.f);
           if (IMG) {
-            ap = s_a0[j];
-            an = s_a1[j];
+            ap = s_a0[wib][j];
+            an = s_a1[wib][j];
           }
-          const uint32_t pos = pos0 + b0 + (uint32_t)j - start + 1u;
+          const uint32_t pos = pos0 + s_pos[wib][j] - start + 1u;
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             const int k0 = 2 * p, k1 = 2 * p + 1;
@@ -208,22 +252,15 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_FWD_WARPS * 32 * PPT / (TW
           for (int k = 0; k < 2 * NP; ++k) alldone = alldone && done[k];
         }
         if (SCORE) {
+          // one global max per entry and warp (non-negative floats order like their bits)
           const unsigned m = __reduce_max_sync(kFull, __float_as_uint(wmax));
-          if (lane == 0 && m != 0u) atomicMax(&s_best[j], m);
-        }
-      }
-      if (SCORE) {
-        // one global max per entry and tile (non-negative floats order like their bits)
-        __syncthreads();
-        if (tid < cnt && s_best[tid] != 0u) {
-          atomicMax(reinterpret_cast<unsigned*>(a.score) + s_gid[tid], s_best[tid]);
-          s_best[tid] = 0u;
+          if (lane == 0 && m != 0u) atomicMax(reinterpret_cast<unsigned*>(a.score) + s_gid[wib][j], m);
         }
       }
     }
     if (a.open) {
-      // the tile stays open if a pixel has not stopped within its list
-      if (__syncthreads_count(!alldone) > 0 && tid == 0) a.open[tile] = 1u;
+      // the tile stays open if a pixel of any of its warps has not stopped within its list
+      if (__any_sync(kFull, !alldone) && lane == 0) a.open[tile] = 1u;
       if (!IMG) {
         // a pass without images keeps only what the continuation needs: T and the stop flags
 #pragma unroll
@@ -314,33 +351,36 @@ __device__ __forceinline__ int warp_reduce(float* v, int lane) {
 // normal terms of the adjoint are zero and are not evaluated (13 slots instead
 // of 18).
 template <int TW, int TH, int PPT, bool GEO>
-__global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW * TH)) raster_bwd_kernel(const RasterBwdArgs a) {
-  constexpr int NT = TW * TH / PPT;
+__global__ void __launch_bounds__(kBlockWarps * 32, OCGS_BWD_WARPS / kBlockWarps) raster_bwd_kernel(const RasterBwdArgs a) {
+  constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
   constexpr int NG = GEO ? kGradSlots : kGradSlotsRGB;
-  __shared__ float4 s_g0[NT], s_g1[NT], s_g2[NT], s_a0[NT];
-  __shared__ float2 s_a1[NT];
-  __shared__ uint32_t s_idx[NT];
-  __shared__ __align__(16) float s_grad[NT * kGradStride];  // per-batch gradient sums of each entry
-  __shared__ float s_rb[NT];
-  __shared__ uint32_t s_tile, s_max;
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int lx = tid % TW, ly0 = (tid / TW) * PPT;
+  __shared__ float4 s_g0[kBlockWarps][32], s_g1[kBlockWarps][32], s_g2[kBlockWarps][32], s_a0[kBlockWarps][32];
+  __shared__ float2 s_a1[kBlockWarps][32];
+  __shared__ uint32_t s_idx[kBlockWarps][32];
+  __shared__ __align__(16) float s_grad[kBlockWarps][32 * kGradStride];  // per-batch gradient sums of each entry
+  __shared__ float s_rb[kBlockWarps][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* const grow = &s_grad[wib][lane * kGradStride];  // this lane's entry row of a batch
 #pragma unroll
-  for (int q = 0; q < kGradStride; ++q) s_grad[tid * kGradStride + q] = 0.f;
+  for (int q = 0; q < kGradStride; ++q) grow[q] = 0.f;
+  const uint32_t n_units = a.n_tiles * (uint32_t)WPT;
   for (uint32_t it = 0;; ++it) {
-    uint32_t tile;
+    // work unit: one warp's band of one tile; the warps run independently
+    uint32_t unit;
     if (a.persistent_ctas) {
-      __syncthreads();
-      if (tid == 0) s_tile = atomicAdd(a.queue, 1u);
-      __syncthreads();
-      tile = s_tile;
-      if (tile >= a.n_tiles) break;
-      if (a.tile_order) tile = a.tile_order[tile];
+      uint32_t u = 0;
+      if (lane == 0) u = atomicAdd(a.queue, 1u);
+      unit = __shfl_sync(kFull, u, 0);
+      if (unit >= n_units) break;
     } else {
       if (it > 0) break;
-      tile = blockIdx.x;
+      unit = blockIdx.x * kBlockWarps + wib;
+      if (unit >= n_units) break;
     }
+    uint32_t tile = unit / WPT;
+    if (a.persistent_ctas && a.tile_order) tile = a.tile_order[tile];
+    const int tid = (int)(unit % WPT) * 32 + lane;  // thread of the tile
+    const int lx = tid % TW, ly0 = (tid / TW) * PPT;
     const int v = view_of_tile(a.tile_prefix, a.n_views, (int)tile);
     const DevCam& cam = a.cams[v];
     const int local = (int)tile - cam.tile_offset;
@@ -391,32 +431,25 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
         thread_last = max(thread_last, last[k]);
       }
     }
-    __syncthreads();
-    if (tid == 0) s_max = 0u;
-    __syncthreads();
-    if (thread_last) atomicMax(&s_max, thread_last);
-    __syncthreads();
-    const int max_last = (int)s_max;
     const int warp_last = (int)__reduce_max_sync(kFull, thread_last);  // entries beyond it are idle for this warp
-    for (int bend = max_last; bend > 0; bend -= NT) {
-      const int bstart = max(0, bend - NT);
-      __syncthreads();
-      if (bstart + tid < bend) {
-        const uint32_t q = (uint32_t)(bstart + tid);
+    for (int bend = warp_last; bend > 0; bend -= 32) {
+      const int bstart = max(0, bend - 32);
+      __syncwarp();  // the previous batch is consumed and flushed
+      if (bstart + lane < bend) {
+        const uint32_t q = (uint32_t)(bstart + lane);
         const uint32_t idx = q < len1 ? a.vals[start + q] : a.vals2[start2 + (q - len1)];
-        const float4 g0 = a.rec.g0[idx], g1 = a.rec.g1[idx], g2 = a.rec.g2[idx];
-        const float rb = support_rho(g0.z);
-        s_g0[tid] = g0;
-        s_g1[tid] = g1;
-        s_g2[tid] = g2;
-        s_a0[tid] = a.rec.a0[idx];
-        s_a1[tid] = a.rec.a1[idx];
-        s_rb[tid] = rb;
-        s_idx[tid] = idx;
+        const float4 g0 = a.rec.g0[idx];
+        s_g0[wib][lane] = g0;
+        s_g1[wib][lane] = a.rec.g1[idx];
+        s_g2[wib][lane] = a.rec.g2[idx];
+        s_a0[wib][lane] = a.rec.a0[idx];
+        s_a1[wib][lane] = a.rec.a1[idx];
+        s_rb[wib][lane] = support_rho(g0.z);
+        s_idx[wib][lane] = idx;
       }
-      __syncthreads();
-      const int jtop = min(bend, warp_last) - 1 - bstart;
-      for (int j = jtop; j >= 0; --j) {
+      __syncwarp();
+      const int cnt = bend - bstart;
+      for (int j = cnt - 1; j >= 0; --j) {
         const int jj = bstart + j;
         float gr[kGradSlots];
 #pragma unroll
@@ -426,8 +459,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
         if (lane == 0) OCGS_DIAG(2, 1);
 #endif
         if (jj < (int)thread_last) {
-          const float4 g0 = s_g0[j], g1 = s_g1[j], g2 = s_g2[j];
-          const float rb = s_rb[j];
+          const float4 g0 = s_g0[wib][j], g1 = s_g1[wib][j], g2 = s_g2[wib][j];
+          const float rb = s_rb[wib][j];
           const SplatColumn col = splat_column(g0, g1, g2, pxf);
           SplatHead2 hd[NP];
           bool any = false;
@@ -440,8 +473,8 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
             any = any || hd[p].pass[0] || hd[p].pass[1];
           }
           if (any) {
-            const float4 ap = s_a0[j];
-            const float2 an = s_a1[j];
+            const float4 ap = s_a0[wib][j];
+            const float2 an = s_a1[wib][j];
             const float2 dx = bc2(col.dx);
             const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
             float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
@@ -541,14 +574,14 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
           }
 #endif
           const int slot = warp_reduce<NG>(gr, lane);
-          if (slot >= 0 && gr[0] != 0.f) atomicAdd(&s_grad[j * kGradStride + slot], gr[0]);
+          if (slot >= 0) s_grad[wib][j * kGradStride + slot] = gr[0];  // one lane per slot
         }
       }
-      // flush the batch: one vector atomic per 4 slots and entry for the whole tile
-      __syncthreads();
-      if (bstart + tid < bend) {
-        float4* row = reinterpret_cast<float4*>(&s_grad[tid * kGradStride]);
-        float4* dst = reinterpret_cast<float4*>(a.grad_rec + (size_t)s_idx[tid] * kGradStride);
+      // flush the batch: one vector atomic per 4 slots and entry for the warp
+      __syncwarp();
+      if (lane < cnt) {
+        float4* row = reinterpret_cast<float4*>(grow);
+        float4* dst = reinterpret_cast<float4*>(a.grad_rec + (size_t)s_idx[wib][lane] * kGradStride);
 #pragma unroll
         for (int q = 0; q < kGradStride / 4; ++q) {
           const float4 g4 = row[q];
@@ -562,11 +595,20 @@ __global__ void __launch_bounds__(TW * TH / PPT, OCGS_BWD_WARPS * 32 * PPT / (TW
   }
 }
 
+// CTAs of kBlockWarps independent warps: persistent_ctas counts tile-sized CTAs
+// (TW*TH/PPT threads), converted to the same number of warps
+template <int TW, int TH, int PPT>
+unsigned warp_grid(int persistent_ctas, uint32_t n_tiles) {
+  constexpr uint64_t WPT = TW * TH / PPT / 32;
+  const uint64_t warps = (persistent_ctas ? (uint64_t)persistent_ctas : (uint64_t)n_tiles) * WPT;
+  return (unsigned)((warps + kBlockWarps - 1) / kBlockWarps);
+}
+
 template <int TW, int TH, int PPT>
 cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
-  const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
+  const unsigned grid = warp_grid<TW, TH, PPT>(a.persistent_ctas, a.n_tiles);
   if (grid == 0) return cudaSuccess;
-  constexpr int NT = TW * TH / PPT;
+  constexpr int NT = kBlockWarps * 32;
   const bool score = a.score != nullptr;
   const bool q2 = img && a.out.depth2 != nullptr;
   if (a.ewa) {
@@ -585,11 +627,11 @@ cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
 
 template <int TW, int TH, int PPT>
 cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
-  const unsigned grid = a.persistent_ctas ? (unsigned)a.persistent_ctas : a.n_tiles;
+  const unsigned grid = warp_grid<TW, TH, PPT>(a.persistent_ctas, a.n_tiles);
   if (grid == 0) return cudaSuccess;
   if (a.d_out.depth || a.d_out.normal || a.d_out.depth2)
-    raster_bwd_kernel<TW, TH, PPT, true><<<grid, TW * TH / PPT, 0, s>>>(a);
-  else raster_bwd_kernel<TW, TH, PPT, false><<<grid, TW * TH / PPT, 0, s>>>(a);
+    raster_bwd_kernel<TW, TH, PPT, true><<<grid, kBlockWarps * 32, 0, s>>>(a);
+  else raster_bwd_kernel<TW, TH, PPT, false><<<grid, kBlockWarps * 32, 0, s>>>(a);
   return launched();
 }
 
