@@ -52,7 +52,7 @@ struct RecPtrs {
   float4* g1;
   float4* g2;
   float4* a0;
-  float2* a1;
+  float4* a1;  // (n_y, n_z, lowest, highest pixel-centre row the support reaches)
 };
 
 struct ImgPtrs {
@@ -355,6 +355,27 @@ __device__ __forceinline__ RowSpan support_row_span(const SupportConic& k, float
     s.hi1 = xh + (0.02f + 2e-6f * fabsf(xh));
   }
   return s;
+}
+
+// Pixel-centre rows [lo, hi] the support can reach (a superset of every band
+// support_row_span finds non-empty): the filter disc and, when the support is a
+// proper ellipse in FP32, the ellipse, padded by 0.1 px (0.02 px more than the
+// row spans' own margin, for the rounding of the rearranged bounds) plus 1e-5 of
+// their magnitude; the whole column otherwise.
+__device__ __forceinline__ float2 support_rows(const float4 g0, const float4 g1, const float4 g2, float rb) {
+  const SupportConic k = support_conic(g0, g1, g2, rb);
+  const float rf = fast_sqrt(k.r2f);
+  float lo = __fsub_rn(k.cy, rf), hi = __fadd_rn(k.cy, rf);
+  if (k.ellipse) {
+    const float c = __fadd_rn(k.cy, k.my);
+    lo = fminf(lo, __fsub_rn(c, k.vmax));
+    hi = fmaxf(hi, __fadd_rn(c, k.vmax));
+  } else {
+    lo = -INFINITY;
+    hi = INFINITY;
+  }
+  const float pad = 0.1f + 1e-5f * fmaxf(fabsf(lo), fabsf(hi));
+  return make_float2(lo - pad, hi + pad);
 }
 
 // Tiles [t0, t1] of a row whose pixel-centre columns i (centre i + 0.5) meet

@@ -50,17 +50,6 @@ __device__ unsigned long long g_diag[8];
 #define OCGS_BWD_WARPS 16
 #endif
 
-// Whether a record's support (the binning's conservative closed form: the
-// ellipse and the filter disc, grown by their margins) reaches pixel centres
-// x in [xb0, xb1], y in [yb0, yb1].  An entry it rejects passes the support
-// test at none of those pixels, so dropping it changes nothing.
-__device__ __forceinline__ bool band_reached(const float4 g0, const float4 g1, const float4 g2, float rb, float xb0,
-                                             float xb1, float yb0, float yb1) {
-  const SupportConic k = support_conic(g0, g1, g2, rb);
-  const RowSpan sp = support_row_span(k, yb0, yb1, xb0, xb1);
-  return (sp.lo0 <= sp.hi0 && sp.lo0 <= xb1 && sp.hi0 >= xb0) || (sp.lo1 <= sp.hi1 && sp.lo1 <= xb1 && sp.hi1 >= xb0);
-}
-
 // The band of a warp: its pixel rows of the tile (32 threads x PPT rows) and
 // the tile's columns, as pixel-centre bounds clipped to the image.
 template <int TW, int TH, int PPT>
@@ -159,31 +148,28 @@ __global__ void __launch_bounds__(kBlockWarps * 32, OCGS_FWD_WARPS / kBlockWarps
     for (uint32_t b0 = start; b0 < end; b0 += 32) {
       if (__all_sync(kFull, alldone)) break;
       const uint32_t kk = b0 + lane;
-      // load a batch of the list, keep (in order) the entries whose support reaches this warp's band
+      // a batch of the list; keep (in order) the entries whose rows meet this warp's band
       bool keep = false;
       uint32_t idx = 0;
-      float4 g0, g1, g2;
-      float rb = 0.f;
       if (kk < end) {
         idx = a.vals[kk];
-        g0 = a.rec.g0[idx];
-        g1 = a.rec.g1[idx];
-        g2 = a.rec.g2[idx];
-        rb = support_rho(g0.z);
-        keep = band_reached(g0, g1, g2, rb, band.x, band.y, band.z, band.w);
+        const float4 a1 = a.rec.a1[idx];
+        keep = a1.w >= band.z && a1.z <= band.w;
       }
       const unsigned km = __ballot_sync(kFull, keep);
       const int slot = __popc(km & lt);
       __syncwarp();  // the previous batch is consumed
       if (keep) {
+        const float4 g0 = a.rec.g0[idx];
         s_g0[wib][slot] = g0;
-        s_g1[wib][slot] = g1;
-        s_g2[wib][slot] = g2;
+        s_g1[wib][slot] = a.rec.g1[idx];
+        s_g2[wib][slot] = a.rec.g2[idx];
         if (IMG) {
+          const float4 a1 = a.rec.a1[idx];
           s_a0[wib][slot] = a.rec.a0[idx];
-          s_a1[wib][slot] = a.rec.a1[idx];
+          s_a1[wib][slot] = make_float2(a1.x, a1.y);
         }
-        s_rb[wib][slot] = rb;
+        s_rb[wib][slot] = support_rho(g0.z);
         s_pos[wib][slot] = kk;
         if (SCORE) s_gid[wib][slot] = (uint32_t)((int64_t)idx - gbase);
       }
@@ -357,9 +343,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, OCGS_BWD_WARPS / kBlockWarps
   __shared__ float4 s_g0[kBlockWarps][32], s_g1[kBlockWarps][32], s_g2[kBlockWarps][32], s_a0[kBlockWarps][32];
   __shared__ float2 s_a1[kBlockWarps][32];
   __shared__ uint32_t s_idx[kBlockWarps][32];
+  __shared__ int s_q[kBlockWarps][32];  // list position of each kept entry
   __shared__ __align__(16) float s_grad[kBlockWarps][32 * kGradStride];  // per-batch gradient sums of each entry
   __shared__ float s_rb[kBlockWarps][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
   float* const grow = &s_grad[wib][lane * kGradStride];  // this lane's entry row of a batch
 #pragma unroll
   for (int q = 0; q < kGradStride; ++q) grow[q] = 0.f;
@@ -432,25 +420,37 @@ __global__ void __launch_bounds__(kBlockWarps * 32, OCGS_BWD_WARPS / kBlockWarps
       }
     }
     const int warp_last = (int)__reduce_max_sync(kFull, thread_last);  // entries beyond it are idle for this warp
+    const float4 band = warp_band<TW, TH, PPT>(cam, local, (int)(unit % WPT));
     for (int bend = warp_last; bend > 0; bend -= 32) {
       const int bstart = max(0, bend - 32);
-      __syncwarp();  // the previous batch is consumed and flushed
+      // a batch of the list, ending at bend; keep (in order) the entries whose rows meet the band
+      bool keep = false;
+      uint32_t idx = 0;
+      float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
       if (bstart + lane < bend) {
         const uint32_t q = (uint32_t)(bstart + lane);
-        const uint32_t idx = q < len1 ? a.vals[start + q] : a.vals2[start2 + (q - len1)];
+        idx = q < len1 ? a.vals[start + q] : a.vals2[start2 + (q - len1)];
+        a1 = a.rec.a1[idx];
+        keep = a1.w >= band.z && a1.z <= band.w;
+      }
+      const unsigned km = __ballot_sync(kFull, keep);
+      const int slot = __popc(km & lt);
+      __syncwarp();  // the previous batch is consumed and flushed
+      if (keep) {
         const float4 g0 = a.rec.g0[idx];
-        s_g0[wib][lane] = g0;
-        s_g1[wib][lane] = a.rec.g1[idx];
-        s_g2[wib][lane] = a.rec.g2[idx];
-        s_a0[wib][lane] = a.rec.a0[idx];
-        s_a1[wib][lane] = a.rec.a1[idx];
-        s_rb[wib][lane] = support_rho(g0.z);
-        s_idx[wib][lane] = idx;
+        s_g0[wib][slot] = g0;
+        s_g1[wib][slot] = a.rec.g1[idx];
+        s_g2[wib][slot] = a.rec.g2[idx];
+        s_a0[wib][slot] = a.rec.a0[idx];
+        s_a1[wib][slot] = make_float2(a1.x, a1.y);
+        s_rb[wib][slot] = support_rho(g0.z);
+        s_idx[wib][slot] = idx;
+        s_q[wib][slot] = bstart + lane;
       }
       __syncwarp();
-      const int cnt = bend - bstart;
+      const int cnt = __popc(km);
       for (int j = cnt - 1; j >= 0; --j) {
-        const int jj = bstart + j;
+        const int jj = s_q[wib][j];
         float gr[kGradSlots];
 #pragma unroll
         for (int q = 0; q < NG; ++q) gr[q] = 0.f;
