@@ -390,7 +390,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(tmp.alloc(&tscratch, radix_scratch_bytes((uint32_t)pl.tiles)));
       CK(launch_tile_order(st->ranges, (uint32_t)pl.tiles, wk, ids, s));
       bool talt = false;
-      CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, (uint32_t)pl.tiles, 32, tscratch, &talt, s));
+      CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, (uint32_t)pl.tiles, 8, tscratch, &talt, s));
       st->tile_order = talt ? ids_alt : ids;
     }
 
@@ -484,7 +484,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
     CK(launch_tile_order(st->ranges, n_t, wk, ids, s));
     bool talt = false;
-    CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 32, tscratch, &talt, s));
+    CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 8, tscratch, &talt, s));
     // the first pass leaves each pixel's state for the second: T and the last
     // blended position (the kept state, or scratch), the stop flags, the open tiles
     const bool img = out != nullptr;
@@ -574,7 +574,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
         CK(launch_tile_ranges(qalt ? qkey_alt : qkey, K2, st->ranges2, s));
         CK(cudaMemsetAsync(n_again, 0, sizeof(uint32_t), s));
         CK(launch_second_queue(st->ranges2, n_t, wk, ids, n_again, s));
-        CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 32, tscratch, &talt, s));
+        CK(radix_sort_pairs(wk, ids, wk_alt, ids_alt, n_t, 8, tscratch, &talt, s));
       }
       RasterArgs rb = ra;
       rb.ranges = st->ranges2;
@@ -598,7 +598,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(keep.alloc(&bids_alt, n_t));
       CK(launch_tile_order(st->ranges, n_t, wk, bids, s, st->ranges2));
       bool balt = false;
-      CK(radix_sort_pairs(wk, bids, wk_alt, bids_alt, n_t, 32, tscratch, &balt, s));
+      CK(radix_sort_pairs(wk, bids, wk_alt, bids_alt, n_t, 8, tscratch, &balt, s));
       st->tile_order = balt ? bids_alt : bids;
     }
   }
@@ -700,7 +700,7 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
     CK(cudaMemsetAsync(w.queue, 0, sizeof(uint32_t), s));
     CK(launch_tile_order(w.ranges, (uint32_t)n_tiles, w.wk, w.ids, s));
     bool talt = false;
-    CK(radix_sort_pairs(w.wk, w.ids, w.wk_alt, w.ids_alt, (uint32_t)n_tiles, 32, w.tscratch, &talt, s));
+    CK(radix_sort_pairs(w.wk, w.ids, w.wk_alt, w.ids_alt, (uint32_t)n_tiles, 8, w.tscratch, &talt, s));
     ra.tile_order = talt ? w.ids_alt : w.ids;
     ra.queue = w.queue;
     ra.persistent_ctas = ctx->sm_count * (2048 * ppt / (tw * th));

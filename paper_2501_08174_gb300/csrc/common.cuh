@@ -390,6 +390,16 @@ __device__ __forceinline__ void span_tiles(float lo, float hi, int tw, int W, in
   *t1 = min((int)ihi / tw, c1);
 }
 
+// 8-bit log-scale code of a tile's pair count, 16 steps per octave: the
+// persistent queues only need the heaviest tiles roughly first, and one 8-bit
+// radix pass orders them (0 for an empty tile, increasing with the count).
+__device__ __forceinline__ uint32_t work_code(uint32_t len) {
+  const uint32_t x = min(len, 32767u) + 1u;
+  const uint32_t e = 31u - (uint32_t)__clz(x);
+  const uint32_t m = e >= 4u ? (x >> (e - 4u)) & 15u : (x << (4u - e)) & 15u;
+  return e * 16u + m;
+}
+
 // Tile runs of one row of a record's candidate rectangle: the union of the
 // runs of the two intervals, as at most two disjoint runs in increasing order.
 struct RowRuns {

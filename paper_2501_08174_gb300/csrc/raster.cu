@@ -42,9 +42,13 @@ __device__ unsigned long long g_diag[8];
 #define OCGS_DIAG(slot, v)
 #endif
 
-// Resident warps per SM the compiler is asked to fit (caps registers per thread).
+// Resident warps per SM the compiler is asked to fit (caps registers per thread);
+// the forward with the Q plane keeps more registers.
 #ifndef OCGS_FWD_WARPS
-#define OCGS_FWD_WARPS 20
+#define OCGS_FWD_WARPS 24
+#endif
+#ifndef OCGS_FWD_WARPS_Q2
+#define OCGS_FWD_WARPS_Q2 20
 #endif
 #ifndef OCGS_BWD_WARPS
 #define OCGS_BWD_WARPS 16
@@ -63,7 +67,8 @@ __device__ __forceinline__ float4 warp_band(const DevCam& cam, int local, int wt
 // Q2: also accumulate Q = sum w z^2 (the depth distortion's third plane)
 // EWA: the records are projected 3D Gaussians (the 3DGS variant of Appendix B)
 template <int TW, int TH, int PPT, bool IMG, bool SCORE, bool Q2, bool EWA>
-__global__ void __launch_bounds__(kBlockWarps * 32, OCGS_FWD_WARPS / kBlockWarps) raster_fwd_kernel(const RasterArgs a) {
+__global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OCGS_FWD_WARPS) / kBlockWarps)
+    raster_fwd_kernel(const RasterArgs a) {
   constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
   __shared__ float4 s_g0[kBlockWarps][32], s_g1[kBlockWarps][32], s_g2[kBlockWarps][32], s_a0[kBlockWarps][32];
   __shared__ float2 s_a1[kBlockWarps][32];
@@ -198,15 +203,16 @@ __global__ void __launch_bounds__(kBlockWarps * 32, OCGS_FWD_WARPS / kBlockWarps
             an = s_a1[wib][j];
           }
           const uint32_t pos = pos0 + s_pos[wib][j] - start + 1u;
+          // every pair is evaluated without a per-pair branch: lanes that do not
+          // blend are masked to exact zeros below, and straight-line code lets the
+          // pairs' dependency chains interleave
 #pragma unroll
           for (int p = 0; p < NP; ++p) {
             const int k0 = 2 * p, k1 = 2 * p + 1;
-            if (done[k0] && done[k1]) continue;
             const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
             SplatHead2 h = splat_head2<EWA>(g0, g1, g2, col, py, rb);
             h.pass[0] = h.pass[0] && !done[k0];
             h.pass[1] = h.pass[1] && !done[k1];
-            if (!(h.pass[0] || h.pass[1])) continue;
             const SplatEval2 e = splat_tail2<false, EWA>(g0, g2, h, rb);
             // lanes that do not blend take alpha 0: T (1 - 0) = T and w = 0 exactly
             const float2 a2 = make_float2(e.ok[0] ? e.alpha.x : 0.f, e.ok[1] ? e.alpha.y : 0.f);
@@ -480,13 +486,13 @@ __global__ void __launch_bounds__(kBlockWarps * 32, OCGS_BWD_WARPS / kBlockWarps
             float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
 #pragma unroll
             for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
+            // no per-pair branch (see the forward): a pair without a blended pixel
+            // adds exact zeros
 #pragma unroll
             for (int p = 0; p < NP; ++p) {
-              if (!(hd[p].pass[0] || hd[p].pass[1])) continue;
               const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb);
               const bool ok0 = e.ok[0], ok1 = e.ok[1];
-              if (!(ok0 || ok1)) continue;
-              contrib = true;
+              contrib = contrib || ok0 || ok1;
               // undo the entry: T before it, its weight, and dL/dalpha (lanes that did
               // not blend get zero weight and zero dL/dalpha, which zeroes every term)
               const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha

@@ -471,7 +471,8 @@ __global__ void tile_ranges_kernel(const uint32_t* __restrict__ keys, uint32_t n
   }
 }
 
-// work key for the persistent queue: heaviest tiles first (descending pair count)
+// work key for the persistent queue: heaviest tiles first (descending log-scale
+// pair count, one 8-bit radix pass)
 __global__ void tile_work_kernel(const uint2* __restrict__ ranges, const uint2* __restrict__ ranges2, uint32_t n,
                                  uint32_t* __restrict__ work_key, uint32_t* __restrict__ ids) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -479,7 +480,7 @@ __global__ void tile_work_kernel(const uint2* __restrict__ ranges, const uint2* 
   const uint2 r = ranges[t];
   uint32_t len = r.y - r.x;
   if (ranges2) len += ranges2[t].y - ranges2[t].x;
-  work_key[t] = 0xffffffffu - len;
+  work_key[t] = 255u - work_code(len);
   ids[t] = t;
 }
 
@@ -797,7 +798,7 @@ __global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
   }
 }
 
-// The second pass's queue: tiles with a second-pass segment, longest first,
+// The second pass's queue: tiles with a second-pass segment, longest first (log scale),
 // every other tile last; n_again counts the former.
 __global__ void second_queue_kernel(const uint2* __restrict__ ranges2, uint32_t n_tiles,
                                     uint32_t* __restrict__ work_key, uint32_t* __restrict__ ids,
@@ -807,7 +808,7 @@ __global__ void second_queue_kernel(const uint2* __restrict__ ranges2, uint32_t 
   const uint2 r2 = ranges2[t];
   const uint32_t len = r2.y - r2.x;
   if (len) atomicAdd(n_again, 1u);
-  work_key[t] = 0xffffffffu - len;
+  work_key[t] = 255u - work_code(len);
   ids[t] = t;
 }
 
