@@ -316,20 +316,36 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
 
+  // the next view's tile count and record gradient are requested before the
+  // current view is processed, so their memory latency overlaps its arithmetic
+  constexpr int NQ = kGradStride / 4;
+  int nt_next = 0;
+  float4 g_next[NQ];
+  if (n_views > 0) {
+    nt_next = ntiles[i];
+    const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + i * kGradStride);
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) g_next[q] = gr4[q];
+  }
   for (int v = 0; v < n_views; ++v) {
-    const int64_t idx = (int64_t)v * n + i;
-    if (ntiles[idx] == 0) continue;
-    const DevCam& cam = cams[v];
-    const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + idx * kGradStride);
+    const int nt = nt_next;
     float gq[kGradStride];
 #pragma unroll
-    for (int q = 0; q < kGradStride / 4; ++q) {
-      const float4 t = gr4[q];
-      gq[4 * q] = t.x;
-      gq[4 * q + 1] = t.y;
-      gq[4 * q + 2] = t.z;
-      gq[4 * q + 3] = t.w;
+    for (int q = 0; q < NQ; ++q) {
+      gq[4 * q] = g_next[q].x;
+      gq[4 * q + 1] = g_next[q].y;
+      gq[4 * q + 2] = g_next[q].z;
+      gq[4 * q + 3] = g_next[q].w;
     }
+    if (v + 1 < n_views) {
+      const int64_t idx1 = (int64_t)(v + 1) * n + i;
+      nt_next = ntiles[idx1];
+      const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + idx1 * kGradStride);
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) g_next[q] = gr4[q];
+    }
+    if (nt == 0) continue;
+    const DevCam& cam = cams[v];
     const float g_cx = gq[kGcx], g_cy = gq[kGcy], g_o = gq[kGo], g_zc = gq[kGzc];
     const float gA00 = gq[kGA00], gA01 = gq[kGA01], gA10 = gq[kGA10], gA11 = gq[kGA11];
     float ge0 = gq[kGe0];

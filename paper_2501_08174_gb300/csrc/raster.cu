@@ -211,8 +211,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             const int k0 = 2 * p, k1 = 2 * p + 1;
             const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
             SplatHead2 h = splat_head2<EWA>(g0, g1, g2, col, py, rb);
-            h.pass[0] = h.pass[0] && !done[k0];
-            h.pass[1] = h.pass[1] && !done[k1];
+            // a surfel pixel outside the support bound fails the tail's rho <= rb test
+            // on its own (rho is then the filter term rho2 > rb), so the head's pass
+            // flag only needs the stop state here; the EWA support is in3 alone
+            h.pass[0] = (EWA ? h.pass[0] : true) && !done[k0];
+            h.pass[1] = (EWA ? h.pass[1] : true) && !done[k1];
             const SplatEval2 e = splat_tail2<false, EWA>(g0, g2, h, rb);
             // lanes that do not blend take alpha 0: T (1 - 0) = T and w = 0 exactly
             const float2 a2 = make_float2(e.ok[0] ? e.alpha.x : 0.f, e.ok[1] ? e.alpha.y : 0.f);
