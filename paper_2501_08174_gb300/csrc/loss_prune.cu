@@ -213,7 +213,8 @@ extern "C" ocgs_status ocgs_background_loss_noalloc(const float* alpha, const ui
                                                     const ocgs_camera* cams, int32_t n_views, float gamma,
                                                     double* loss, float* d_alpha, void* stream) {
   if (!alpha || !mask || !loss || !cams) return OCGS_ERR_ARG;
-  if (n_views < 1 || n_views > kNoAllocMaxViews) return OCGS_ERR_ARG;
+  if (n_views < 1) return OCGS_ERR_ARG;
+  if (n_views > kNoAllocMaxViews) return OCGS_ERR_CAPACITY;  // beyond the static view table
   if (!std::isfinite(gamma)) return OCGS_ERR_ARG;
   int64_t blocks = 0;
   for (int v = 0; v < n_views; ++v) {

@@ -43,7 +43,8 @@ __device__ unsigned long long g_diag[8];
 #endif
 
 // Resident warps per SM the compiler is asked to fit (caps registers per thread);
-// the forward with the Q plane keeps more registers.
+// the forward with the Q plane and the backward with depth and normal
+// cotangents keep more registers.
 #ifndef OCGS_FWD_WARPS
 #define OCGS_FWD_WARPS 24
 #endif
@@ -52,6 +53,9 @@ __device__ unsigned long long g_diag[8];
 #endif
 #ifndef OCGS_BWD_WARPS
 #define OCGS_BWD_WARPS 16
+#endif
+#ifndef OCGS_BWD_WARPS_GEO
+#define OCGS_BWD_WARPS_GEO 12
 #endif
 
 // The band of a warp: its pixel rows of the tile (32 threads x PPT rows) and
@@ -346,7 +350,7 @@ __device__ __forceinline__ int warp_reduce(float* v, int lane) {
 // normal terms of the adjoint are zero and are not evaluated (13 slots instead
 // of 18).
 template <int TW, int TH, int PPT, bool GEO>
-__global__ void __launch_bounds__(kBlockWarps * 32, OCGS_BWD_WARPS / kBlockWarps) raster_bwd_kernel(const RasterBwdArgs a) {
+__global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD_WARPS) / kBlockWarps) raster_bwd_kernel(const RasterBwdArgs a) {
   constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
   constexpr int NG = GEO ? kGradSlots : kGradSlotsRGB;
   __shared__ float4 s_g0[kBlockWarps][32], s_g1[kBlockWarps][32], s_g2[kBlockWarps][32], s_a0[kBlockWarps][32];

@@ -94,5 +94,5 @@ def test_noalloc_rejects_requests_beyond_its_limits(setup):
                                                 C.c_void_p(loss.data_ptr()), None, stream)
     # the checks come before any device work, so these pointers are never read
     assert call(_cams(((16384, 16384),) * 2)) == _lib.ERR_CAPACITY   # 2 x 65536 blocks > 65536
-    assert call(_cams(((4, 4),) * 1025)) == _lib.ERR_ARG              # more than 1024 views
+    assert call(_cams(((4, 4),) * 1025)) == _lib.ERR_CAPACITY         # more than 1024 views
     assert call(_cams(((0, 4),))) == _lib.ERR_ARG
