@@ -178,6 +178,15 @@ def sum_over_ranks(x: float, world: int, device=None) -> float:
     return _all_reduce(x, world, "sum", device)
 
 
+def samples_dir() -> str:
+    """Where the raw nvidia-smi clock samples of the timed region go (the JSON line
+    carries their summary): $OCGS_BENCH_OUT, else the system temporary directory."""
+    import tempfile
+    d = os.environ.get("OCGS_BENCH_OUT") or tempfile.gettempdir()
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
 def workload_args(a) -> str:
     from paper_2501_08174_gb300 import FRONT_FRACTION
     front = FRONT_FRACTION if a.front is None else a.front
@@ -491,8 +500,7 @@ def run_ours(a, rank: int, world: int, local: int):
     torch.cuda.set_device(dev)
     if world > 1:
         dist.init_process_group("nccl", device_id=dev)
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    os.makedirs(out_dir, exist_ok=True)
+    out_dir = samples_dir()
 
     if a.workload == "c5":
         sc = synthetic.config5(seed=5 + rank, n=a.n, n_views=a.views)
@@ -657,8 +665,7 @@ def run_ewa(a, rank: int, world: int, local: int):
         step()
     rast.profile(True)
     launches0 = rast.kernel_launches()
-    out_dir = os.path.join(ROOT, "gpurun_out")
-    os.makedirs(out_dir, exist_ok=True)
+    out_dir = samples_dir()
     ms, wall_ms, clocks = timed(step, a.steps, 0, world, dev, os.path.join(out_dir, f"clocks_rank{rank}.csv"), local)
     launches = rast.kernel_launches() - launches0
     prof = rast.profile_read()
