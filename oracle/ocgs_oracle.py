@@ -30,6 +30,7 @@ normal flip) held fixed:
   > 0 (Sec. 4.3), and the keep-set at threshold tau is {score > tau};
 * one Adam update of the parameters (the optimiser of the training Sec. 5.1
   keeps; Kingma & Ba, 2015, Algorithm 1);
+* the L1 part of the masked photometric loss of Eq. 2 with its adjoint;
 * SSIM of masked images (the D-SSIM part of the photometric loss Eq. 2 masks,
   and the masked SSIM of Sec. 5) and the masked PSNR of Sec. 5;
 * the 2DGS depth distortion and normal consistency of Eq. 3, from the composited
@@ -368,6 +369,23 @@ def background_loss_grad(mask: np.ndarray, gamma: float) -> np.ndarray:
     """d(gamma L_b)/dA = gamma (1 - M) / (h w) (Eq. 1 weighted as in Eq. 3)."""
     m = np.asarray(mask, np.float64)
     return gamma * (1.0 - m) / m.size
+
+
+def masked_l1(rgb: np.ndarray, target: np.ndarray, mask: np.ndarray, weight: float = 1.0):
+    """L1 part of the photometric loss of Eq. 2 on the masked images of one view.
+
+    rgb (the rendering R) and target (the image I) are [h*w, 3], mask M is [h*w]
+    and multiplies every colour channel.  Returns the mean over the 3 h w values
+    of |I M - R M| and d(weight L1)/dR = weight sign(R M - I M) M / (3 h w), which
+    is 0 where the two masked values are equal (the subgradient taken at the kink).
+    """
+    r = np.asarray(rgb, np.float64).reshape(-1, 3)
+    t = np.asarray(target, np.float64).reshape(-1, 3)
+    m = np.asarray(mask, np.float64).reshape(-1, 1)
+    diff = r * m - t * m
+    loss = float(np.abs(diff).sum() / diff.size)
+    grad = weight * np.sign(diff) * m / diff.size
+    return loss, grad
 
 
 def contribution_score(g: dict, cams: list, prefilter: bool = True) -> np.ndarray:

@@ -350,6 +350,40 @@ def test_background_loss_hand_sum():
     np.testing.assert_allclose(oracle.background_loss_grad(m, 0.5), 0.5 * (1 - m) / 16, atol=0)
 
 
+def test_masked_l1_hand_sum():
+    with open(os.path.join(GOLDEN, "masked_l1_2x2.json")) as f:
+        case = json.load(f)
+    loss, grad = oracle.masked_l1(case["rgb"], case["target"], case["mask"], weight=1.0)
+    assert loss == pytest.approx(case["loss"], abs=1e-15)
+    np.testing.assert_allclose(grad * 12.0, np.array(case["grad_times_12"], np.float64), atol=1e-15)
+    _, g2 = oracle.masked_l1(case["rgb"], case["target"], case["mask"], weight=0.8)
+    np.testing.assert_allclose(g2, 0.8 * grad, atol=1e-17)
+
+
+def test_masked_l1_special_masks_and_central_differences():
+    rng = np.random.default_rng(31)
+    r = rng.uniform(0, 1, size=(60, 3))
+    t = rng.uniform(0, 1, size=(60, 3))
+    # an all-ones mask gives the plain mean absolute error, an all-zeros mask nothing
+    loss, grad = oracle.masked_l1(r, t, np.ones(60))
+    assert loss == pytest.approx(np.mean(np.abs(r - t)), abs=1e-15)
+    np.testing.assert_allclose(grad, np.sign(r - t) / r.size, atol=0)
+    loss0, grad0 = oracle.masked_l1(r, t, np.zeros(60))
+    assert loss0 == 0.0 and not grad0.any()
+    # the adjoint against central differences of the loss, away from the kinks
+    m = (rng.uniform(size=60) < 0.6).astype(np.float64)
+    _, grad = oracle.masked_l1(r, t, m)
+    h = 1e-6
+    for i, c in zip(rng.integers(0, 60, 40), rng.integers(0, 3, 40)):
+        if abs(r[i, c] - t[i, c]) < 1e-3:
+            continue
+        rp, rm = r.copy(), r.copy()
+        rp[i, c] += h
+        rm[i, c] -= h
+        fd = (oracle.masked_l1(rp, t, m)[0] - oracle.masked_l1(rm, t, m)[0]) / (2 * h)
+        assert fd == pytest.approx(grad[i, c], abs=1e-9)
+
+
 def test_hidden_surfel_scores_zero_and_lone_surfel_scores_opacity():
     cam = cam65()
     m = 6
