@@ -91,3 +91,25 @@ def test_create_without_gpu_fails_loudly(lib):
     from paper_2501_08174_gb300 import OcgsError, Rasterizer
     with pytest.raises(OcgsError):
         Rasterizer(0)
+
+
+def test_noalloc_limits_are_checked_before_any_device_work(lib):
+    # the allocation-free background loss validates its sizes on the host first, so these
+    # placeholder pointers are never read and no device is needed
+    import synthetic
+    from paper_2501_08174_gb300 import _lib, camera_array
+
+    def call(sizes, gamma=0.5, alpha=C.c_void_p(16), loss=C.c_void_p(16)):
+        cams = [synthetic.make_camera((0.0, -3.0, 0.0), w, h) for w, h in sizes]
+        return lib.ocgs_background_loss_noalloc(alpha, C.c_void_p(16), camera_array(cams), len(cams), gamma,
+                                                loss, None, None)
+
+    assert call([(16384, 16384)] * 2) == _lib.ERR_CAPACITY     # 2 x 65,536 blocks of 4,096 pixels
+    assert call([(4, 4)] * 1025) == _lib.ERR_CAPACITY          # more than 1,024 views
+    assert call([(0, 4)]) == _lib.ERR_ARG
+    assert call([(4, 16385)]) == _lib.ERR_ARG
+    assert call([(4, 4)], gamma=float("nan")) == _lib.ERR_ARG
+    assert call([(4, 4)], alpha=None) == _lib.ERR_ARG
+    assert call([(4, 4)], loss=None) == _lib.ERR_ARG
+    assert lib.ocgs_background_loss_noalloc(C.c_void_p(16), C.c_void_p(16), None, 0, 0.5, C.c_void_p(16),
+                                            None, None) == _lib.ERR_ARG
