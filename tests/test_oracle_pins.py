@@ -350,6 +350,21 @@ def test_background_loss_hand_sum():
     np.testing.assert_allclose(oracle.background_loss_grad(m, 0.5), 0.5 * (1 - m) / 16, atol=0)
 
 
+def test_parameter_layout_matches_the_storage_per_gaussian_of_table3():
+    """58 float32 values per surfel at SH degree 3 (xyz 3, quaternion 4, two scales, opacity 1,
+    48 SH coefficients), the layout the oracle, the generators and the library share, against the
+    bytes per Gaussian the paper's storage figures imply; a third scale (59 values, 236 bytes)
+    would miss them by 1.5 %."""
+    with open(os.path.join(GOLDEN, "storage_per_gaussian_table3.json")) as f:
+        case = json.load(f)
+    g = synthetic.small_scene(3, 5, 8, 8, degree=3)["gaussians"]
+    floats = sum(int(np.prod(np.asarray(g[k]).shape[1:])) for k in ("xyz", "quat", "scale", "opacity", "sh"))
+    assert floats == 58
+    for row in case["rows"]:
+        per_gaussian = row["storage_mb"] * 1e6 / row["gaussians"]
+        assert abs(per_gaussian - 4 * floats) < 0.5, row
+
+
 def test_masked_l1_hand_sum():
     with open(os.path.join(GOLDEN, "masked_l1_2x2.json")) as f:
         case = json.load(f)
