@@ -195,7 +195,9 @@ ocgs_status ocgs_sync(ocgs_ctx* ctx);
  *              and Sec. 5.1). The caller zeroes it before the first view.
  *   state      NULL, or receives an opaque forward state for
  *              ocgs_render_backward; release it with ocgs_state_release.
- * Synchronises once to size the pair buffers.
+ * Synchronises with the host to size the pair buffers: once in one-pass
+ * binning, twice in two-pass binning (the persistent default with images or a
+ * score: the second pass's pair count is known only after the first pass).
  */
 ocgs_status ocgs_render(ocgs_ctx* ctx, const ocgs_gaussians* gaussians, const ocgs_camera* cams,
                         int32_t n_views, const ocgs_image* out, float* score,
