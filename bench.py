@@ -52,11 +52,12 @@ LAMBDA_DSSIM = 0.2  # D-SSIM share of the 3DGS photometric loss that Eq. 2 masks
 ALPHA_DIST = 1000.0  # 2DGS depth-distortion weight of Eq. 3 (bounded scenes)
 BETA_NORMAL = 0.05   # 2DGS normal-consistency weight of Eq. 3
 TAU = 0.01       # pruning threshold of the sweep configuration
-# FP32 operations per evaluated (pixel, Gaussian) pair, counted from the kernels'
-# arithmetic (an FMA counts 2): support test and alpha (31) plus blending (17)
-# in the forward; the same test plus the adjoint and the warp reduction in the backward.
-FLOPS_FWD = 48
-FLOPS_BWD = 90
+# Algorithmic FP32 operations per evaluated (pixel, Gaussian) pair of the method (an FMA
+# counts 2): about 35 in the forward (intersection, rho, alpha, blending) and about 100 in
+# the backward (the same evaluation plus the adjoint), the per-unit figures of the roofline
+# model; they are fixed, so a kernel that needs fewer instructions shows as a higher rate.
+FLOPS_FWD = 35
+FLOPS_BWD = 100
 
 
 def parse_args():
@@ -77,6 +78,10 @@ def parse_args():
     p.add_argument("--front", type=float, default=None,
                    help="share of the depth order binned in the first of two passes (0 = one pass; "
                         "default: the library's)")
+    p.add_argument("--no-tune", action="store_true",
+                   help="time the options given by --tile/--persistent/--ppt/--front/--batch instead of the "
+                        "autotuner's choice")
+    p.add_argument("--batch", type=int, default=32, help="Gaussians per batch (16, 32 or 64)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
@@ -187,10 +192,11 @@ def samples_dir() -> str:
     return d
 
 
-def workload_args(a) -> str:
-    from paper_2501_08174_gb300 import FRONT_FRACTION
-    front = FRONT_FRACTION if a.front is None else a.front
-    return f"--n {a.n} --views {a.views} --tile {a.tile} --persistent {a.persistent} --ppt {a.ppt} --front {front:g}"
+def workload_args(a, opts: dict) -> str:
+    """The bench arguments that reproduce this workload with launch options ``opts``."""
+    tw, th = opts["tile"]
+    return (f"--n {a.n} --views {a.views} --tile {tw}x{th} --persistent {int(opts['persistent'])} "
+            f"--ppt {opts['pixels_per_thread']} --front {opts['front_fraction']:g} --batch {opts['batch']} --no-tune")
 
 
 def load_peaks() -> dict:
@@ -519,7 +525,12 @@ def run_ours(a, rank: int, world: int, local: int):
     mask = torch.tensor(mask_np, device=dev)
     tw, th = (int(x) for x in a.tile.split("x"))
     rast = Rasterizer(dev, tile=(tw, th), persistent=bool(a.persistent), pixels_per_thread=a.ppt,
-                      front_fraction=FRONT_FRACTION if a.front is None else a.front)
+                      front_fraction=FRONT_FRACTION if a.front is None else a.front, batch=a.batch)
+    tuned = None
+    if not a.no_tune:
+        # the autotuner picks the launch options of the timed step (they never change a result)
+        tuned = rast.autotune(g, cams, cache_path=os.path.join(out_dir, "autotune_cache.txt"))
+    opts = rast.options()
 
     # sizes of the workload (outside the timed region)
     _, st = rast.render(g, cams)
@@ -549,11 +560,21 @@ def run_ours(a, rank: int, world: int, local: int):
         pstep = TrainingStep(rast, g, cams, target, mask, per_view=True, adam=adam)
         pms, pwall, _ = timed(pstep, a.steps, a.warmup, world, dev)
         per_view = {"ms_per_step": pms, "value": P_job / (pms / 1e3) / 1e6,
-                    "launch_sets": len(cams), "batched_speedup": pms / ms}
+                    "launch_sets": len(cams), "batched_speedup": pms / ms,
+                    "front_fraction": rast.front_fraction if rast.persistent else 0.0}
+        if rast.persistent and rast.front_fraction > 0:
+            # the same per-view step with one-pass binning: no host read of the second pass's
+            # pair count in the middle of each one-view render
+            rast.set_options(**dict(opts, front_fraction=0.0))
+            oms, _, _ = timed(pstep, a.steps, a.warmup, world, dev)
+            rast.set_options(**opts)
+            per_view["one_pass"] = {"ms_per_step": oms, "value": P_job / (oms / 1e3) / 1e6,
+                                    "batched_speedup": oms / ms, "front_fraction": 0.0}
 
     # roofline of the dominant stage and of the whole step
     peaks = load_peaks()
-    fp32_peak = 152 * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12  # TFLOP/s: SMs x FP32 lanes x FMA x clock
     stages = {}
     step_bytes = 0
     for name, (tot_ms, cnt) in prof.items():
@@ -573,12 +594,13 @@ def run_ours(a, rank: int, world: int, local: int):
                     "preprocess": "preprocess_kernel", "preprocess_bwd": "preprocess_bwd_kernel"}
     traffic = None
     if dom in stage_kernel:
-        traffic = measured_traffic(stage_kernel[dom], workload_args(a))
+        traffic = measured_traffic(stage_kernel[dom], workload_args(a, opts))
     if alg["flops"]:
         ach = alg["flops"] / (per_launch_ms * 1e-3) / 1e12
         roofline = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
                     "frac": ach / fp32_peak, "traffic": traffic,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz"}
+                    "peak_source": f"{n_sm} SMs (queried) x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz "
+                                   f"(maximum SM clock, {peaks['source']})"}
     else:
         ach = alg["bytes"] / (per_launch_ms * 1e-3) / 1e9
         roofline = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -614,8 +636,11 @@ def run_ours(a, rank: int, world: int, local: int):
                 "config": {"workload": workload_name(a), "mode": "batched (one pass over all views)",
                            "n_gaussians": N, "n_views": len(cams), "pixels_per_gpu": P,
                            "resolutions": [f"{c['width']}x{c['height']}" for c in cams],
-                           "tile": a.tile, "pixels_per_thread": a.ppt, "persistent": bool(a.persistent),
-                           "front_fraction": front, "pairs": K, "evals": E,
+                           "tile": f"{opts['tile'][0]}x{opts['tile'][1]}",
+                           "pixels_per_thread": opts["pixels_per_thread"], "persistent": opts["persistent"],
+                           "front_fraction": front, "gaussians_per_batch": opts["batch"],
+                           "options_from": "autotuner" if tuned else "command line",
+                           "autotune": tuned, "pairs": K, "evals": E,
                            "l2": f"inputs larger than L2: {step_bytes / 1e9:.1f} GB algorithmic traffic per step",
                            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
                 "per_view": per_view, "stages": stages, "roofline": roofline, "hbm_roofline_step": hbm_step,

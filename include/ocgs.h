@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define OCGS_ABI_VERSION 3
+#define OCGS_ABI_VERSION 4
 
 typedef enum {
   OCGS_OK = 0,
@@ -131,6 +131,9 @@ typedef struct {
   int32_t persistent;         /* 1: persistent CTAs draining a global tile queue, heaviest tiles first */
   int32_t pixels_per_thread;  /* vertically adjacent pixels per thread: 1, 2 (0 = 2), or 4 for 16x16 and 16x8 */
   float front_fraction;       /* in [0, 1]: share of the depth order binned in the first pass (0 = one pass) */
+  int32_t batch;              /* Gaussians per batch: records a warp stages in shared memory at a time:
+                                 32 (0 = 32), or 16 or 64 with 16x16 tiles and 2 or 4 pixels per
+                                 thread or 16x8 tiles and 4 */
 } ocgs_options;
 
 /* Counters of the last ocgs_render / ocgs_accumulate_contribution. */
@@ -249,11 +252,14 @@ ocgs_status ocgs_background_loss(ocgs_ctx* ctx, const float* alpha, const uint8_
  * (268,435,456 pixels) per call; larger requests return OCGS_ERR_CAPACITY,
  * other bad arguments OCGS_ERR_ARG, before any device work.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress),
- * so make that first call before any stream capture.  Every call shares the
- * one array and leaves its contents behind; each call overwrites all it
- * reads, so nothing needs clearing, but calls whose work overlaps on the GPU
- * (different streams) race on it.  Errors are returned only (there is no
- * context for ocgs_last_error).
+ * so make that first call before any stream capture.  The address is kept
+ * for the life of the process: do not call this entry point on a device
+ * after cudaDeviceReset on it.  The view sizes reach the device as a kernel
+ * argument, and the host memory of cams is not read after the call returns.
+ * Every call shares the one array and leaves its contents behind; each call
+ * overwrites all it reads, so nothing needs clearing, but calls whose work
+ * overlaps on the GPU (different streams) race on it.  Errors are returned
+ * only (there is no context for ocgs_last_error).
  */
 ocgs_status ocgs_background_loss_noalloc(const float* alpha, const uint8_t* mask, const ocgs_camera* cams,
                                          int32_t n_views, float gamma, double* loss, float* d_alpha,
@@ -469,16 +475,20 @@ typedef struct {
 } ocgs_tune_result;
 
 /*
- * ocgs_autotune — pick the launch options (tile shape, pixels per thread,
- * persistent queue) that make one forward + backward of this workload
- * fastest on this GPU, and set them on the context.  Options never change a
- * result (see ocgs_options), only the time.  Each candidate runs once
- * untimed and twice timed (CUDA events on the context stream); the
- * cotangent is dL/dA = 1.  cache_path (host string or NULL) names a text
- * file of earlier choices keyed by GPU, SM count, SH degree, views and
- * power-of-two buckets of Gaussians and pixels; a hit skips the timing, a
- * miss appends a line.  Synchronises; allocates its buffers from the context
- * pool for the duration of the call.
+ * ocgs_autotune — pick the launch options that make this workload's training
+ * render and backward fastest on this GPU, and set them on the context.
+ * Options never change a result (see ocgs_options), only the time.  The timed
+ * pass is what a training step runs: a render with images and a contribution
+ * score, then the backward of a colour and opacity loss (dL/dC = dL/dA = 1).
+ * The search is staged: (1) tile shape, pixels per thread and persistence at
+ * the context's front_fraction and 32 Gaussians per batch; (2) for a
+ * persistent choice, front_fraction in {0, 0.05, 0.1, 0.2}; (3) 16 or 64
+ * Gaussians per batch where the chosen shape offers them.  Each candidate runs
+ * once untimed and twice timed (CUDA events on the context stream).
+ * cache_path (host string or NULL) names a text file of earlier choices keyed
+ * by GPU, SM count, SH degree, views and power-of-two buckets of Gaussians and
+ * pixels; a hit skips the timing, a miss appends a line.  Synchronises;
+ * allocates its buffers from the context pool for the duration of the call.
  */
 ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* gaussians, const ocgs_camera* cams,
                           int32_t n_views, const char* cache_path, ocgs_tune_result* result);

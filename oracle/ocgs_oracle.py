@@ -48,6 +48,7 @@ Inputs are numpy arrays (see ``synthetic.py`` for the layout).
 """
 from __future__ import annotations
 
+import contextlib
 import math
 from typing import Optional
 
@@ -63,6 +64,20 @@ ALPHA_MAX = 0.99        # opacity clamp
 T_EPS = 1e-4            # stop once the transmittance would fall below this
 
 FRAGILE_REL = 1e-5      # relative margin for flagging decisions FP32 may take differently
+
+
+@contextlib.contextmanager
+def evaluated_in(dtype):
+    """Evaluate the same definitions in another floating-point type inside the block (not
+    thread-safe).  Tests use float32 to measure how far any float32 evaluation of the
+    definition lands from FP64 for each output, the conditioning their tolerances allow for;
+    results outside the block are FP64."""
+    global DT
+    old, DT = DT, dtype
+    try:
+        yield
+    finally:
+        DT = old
 
 
 # ----------------------------------------------------------------------------- helpers
@@ -174,8 +189,11 @@ def project(p: dict, cam: dict, sh_degree: int) -> dict:
 
 
 def depth_order(z_c: torch.Tensor) -> torch.Tensor:
-    """Front-to-back order: ascending centre depth, ties by ascending index."""
-    return torch.sort(z_c.detach(), stable=True).indices
+    """Front-to-back order: ascending centre depth, ties by ascending index.  The depth that
+    decides the order is rounded to float32, the precision of the device's sort keys: an
+    order is a discrete decision, so both sides take it in the same precision (two surfels
+    whose depths round to the same float32 value are ordered by index on both sides)."""
+    return torch.sort(z_c.detach().to(torch.float32), stable=True).indices
 
 
 # ----------------------------------------------------------------------------- candidates
@@ -220,7 +238,8 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
                     normal=torch.zeros(B, 3, dtype=DT), t_final=torch.ones(B, dtype=DT),
                     n_blended=torch.zeros(B, dtype=torch.int64),
                     fragile=torch.zeros(B, dtype=torch.bool),
-                    fragile_grad=torch.zeros(B, dtype=torch.bool), w=torch.zeros(B, 0, dtype=DT))
+                    fragile_grad=torch.zeros(B, dtype=torch.bool), w=torch.zeros(B, 0, dtype=DT),
+                    z=torch.zeros(B, 0, dtype=DT))
     # homogeneous pixel planes h_x = (-1, 0, x), h_y = (0, -1, y) pulled back to (u, v, 1)
     row0, row1, row2 = T[:, 0, :], T[:, 1, :], T[:, 2, :]
     h_u = -row0[None] + xs[:, None, None] * row2[None]   # [B,n,3]
@@ -251,7 +270,7 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
     out = dict(
         rgb=w @ rgb, alpha=w.sum(1), depth=(w * z).sum(1), depth2=(w * z * z).sum(1), normal=w @ normal,
         t_final=torch.where(blended, one_minus, torch.ones_like(a)).prod(1),
-        n_blended=blended.sum(1), w=w)
+        n_blended=blended.sum(1), w=w, z=z)
     # decisions that a float32 evaluation may take the other way
     with torch.no_grad():
         e = FRAGILE_REL
@@ -260,7 +279,8 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
         f_amin = ((alpha_raw - ALPHA_MIN).abs() <= e * ALPHA_MIN) & (rho <= RHO_CUT * (1 + e))
         f_stop = valid & ((t_incl - T_EPS).abs() <= e * T_EPS)
         f_branch = blended & ((rho3 - rho2).abs() <= e * torch.maximum(rho3.clamp(max=1e30), rho2))
-        fragile = (f_cut | f_amin | f_stop | f_branch).any(1)
+        at_edge = f_cut | f_amin | f_stop | f_branch
+        fragile = at_edge.any(1)
         f_clamp = blended & ((alpha_raw - ALPHA_MAX).abs() <= e)
         f_grad = f_clamp
         if rgb_raw is not None:
@@ -268,6 +288,7 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
             f_grad = f_grad | (blended & g_col[None])
         out["fragile"] = fragile
         out["fragile_grad"] = fragile | f_grad.any(1)
+        out["at_edge"] = at_edge  # [B, n]: the candidate itself is at a fragile threshold
     return out
 
 
@@ -283,15 +304,23 @@ def pixel_centres(cam: dict, pixels: Optional[np.ndarray]):
 
 
 def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optional[dict] = None,
-           prefilter: bool = True, chunk: int = 256) -> dict:
+           prefilter: bool = True, chunk: int = 256, pair_powers=()) -> dict:
     """Render one view at the given flat pixel indices (row-major, default all).
 
     Returns numpy FP64 arrays: rgb [P,3], alpha [P], depth [P], depth2 [P]
     (sum of w z^2, for the depth distortion), normal [P,3], t_final [P],
     n_blended [P], fragile [P], fragile_grad [P], and score [N] (max blending
-    weight of each surfel over these pixels).  If ``d_out`` holds cotangents
+    weight of each surfel over these pixels), with score_firm [N] (the same max
+    over the pixels that are not fragile) and at_edge [N] (the surfel is itself
+    at a fragile threshold at some pixel).  A score is certain in float32 where
+    the surfel is not at_edge and its max is reached at a firm pixel (score ==
+    score_firm); elsewhere a float32 evaluation may differ.  If ``d_out`` holds cotangents
     (rgb, alpha, depth, normal, optionally depth2) for these pixels, also
     returns ``grads``: d(sum <d_out, out>)/d(xyz, quat, scale, opacity, sh).
+    For every p in ``pair_powers`` it also returns ``distortion_pairs_<p>`` [P]:
+    the depth distortion of Eq. 3 by brute force over each pixel's blended
+    pairs, sum_{i,j} w_i w_j |z_i - z_j|^p (p = 1 is the form 2DGS prints,
+    p = 2 the squared reading; a diagnostic, not differentiated).
     """
     need_grad = d_out is not None
     params = param_tensors(g, requires_grad=need_grad)
@@ -307,7 +336,11 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
     res = dict(rgb=np.zeros((P, 3)), alpha=np.zeros(P), depth=np.zeros(P), depth2=np.zeros(P), normal=np.zeros((P, 3)),
                t_final=np.ones(P), n_blended=np.zeros(P, np.int64), fragile=np.zeros(P, bool),
                fragile_grad=np.zeros(P, bool))
+    for pw in pair_powers:
+        res[f"distortion_pairs_{pw}"] = np.zeros(P)
     score = torch.zeros(N, dtype=DT)
+    score_firm = torch.zeros(N, dtype=DT)        # max weight over the pixels that are not fragile
+    at_edge = torch.zeros(N, dtype=torch.bool)   # the surfel is itself at a fragile threshold somewhere
     if need_grad:
         dts = {k: _t(d_out[k]) for k in ("rgb", "alpha", "depth", "normal")}
         dts["depth2"] = _t(d_out["depth2"]) if "depth2" in d_out else torch.zeros(P, dtype=DT)
@@ -329,7 +362,19 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
         for k in ("rgb", "alpha", "depth", "depth2", "normal", "t_final", "n_blended", "fragile", "fragile_grad"):
             res[k][s:e] = out[k].detach().numpy()
         if len(cols):
-            score[cols] = torch.maximum(score[cols], out["w"].detach().max(0).values)
+            w_d = out["w"].detach()
+            score[cols] = torch.maximum(score[cols], w_d.max(0).values)
+            firm = ~out["fragile"]
+            if firm.any():
+                score_firm[cols] = torch.maximum(score_firm[cols], w_d[firm].max(0).values)
+            at_edge[cols] |= out["at_edge"].any(0)
+        for pw in pair_powers:
+            w_d, z_d = out["w"].detach(), out["z"].detach()
+            for b in range(e - s):
+                nz = torch.nonzero(w_d[b]).flatten()
+                wb, zb = w_d[b, nz], z_d[b, nz]
+                res[f"distortion_pairs_{pw}"][s + b] = float(
+                    (wb[:, None] * wb[None, :] * (zb[:, None] - zb[None, :]).abs() ** pw).sum())
         if need_grad and len(cols):
             loss = ((out["rgb"] * dts["rgb"][s:e]).sum() + (out["alpha"] * dts["alpha"][s:e]).sum()
                     + (out["depth"] * dts["depth"][s:e]).sum() + (out["normal"] * dts["normal"][s:e]).sum()
@@ -339,6 +384,8 @@ def render(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, d_out: Optio
                 if gk is not None:
                     acc[k].index_add_(0, cols, gk)
     res["score"] = score.numpy()
+    res["score_firm"] = score_firm.numpy()
+    res["at_edge"] = at_edge.numpy()
     res["cull_margin"] = proj["cull_margin"].numpy()
     if need_grad:
         torch.autograd.backward([proj[k] for k in keys], [acc[k] for k in keys])

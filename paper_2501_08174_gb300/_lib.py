@@ -46,7 +46,7 @@ class Image(C.Structure):
 
 class Options(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("persistent", C.c_int32),
-                ("pixels_per_thread", C.c_int32), ("front_fraction", C.c_float)]
+                ("pixels_per_thread", C.c_int32), ("front_fraction", C.c_float), ("batch", C.c_int32)]
 
 
 class Profile(C.Structure):

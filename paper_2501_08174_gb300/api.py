@@ -158,7 +158,7 @@ class Rasterizer:
     """One libocgs context on one CUDA device."""
 
     def __init__(self, device=None, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2,
-                 front_fraction: float = FRONT_FRACTION):
+                 front_fraction: float = FRONT_FRACTION, batch: int = 32):
         self.lib = _lib.load()
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device) \
             if not isinstance(device, torch.device) else device
@@ -168,7 +168,7 @@ class Rasterizer:
             raise _lib.OcgsError(st, "ocgs_create failed (is a CUDA device present?)")
         self._ctx = ctx
         self.set_options(tile=tile, persistent=persistent, pixels_per_thread=pixels_per_thread,
-                         front_fraction=front_fraction)
+                         front_fraction=front_fraction, batch=batch)
 
     # -- plumbing
     def _call(self, name: str, *args) -> int:
@@ -193,19 +193,27 @@ class Rasterizer:
             pass
 
     def set_options(self, tile=(16, 16), persistent: bool = False, pixels_per_thread: int = 2,
-                    front_fraction: float = FRONT_FRACTION) -> None:
+                    front_fraction: float = FRONT_FRACTION, batch: int = 32) -> None:
         """Launch options (see ocgs_options); none changes a result.  ``front_fraction``: share
-        of the depth order binned in the first of two passes (persistent renders; 0 = one pass)."""
+        of the depth order binned in the first of two passes (persistent renders; 0 = one pass);
+        ``batch``: Gaussians a warp stages in shared memory at a time (16, 32 or 64)."""
         o = _lib.Options(int(tile[0]), int(tile[1]), int(bool(persistent)), int(pixels_per_thread),
-                         float(front_fraction))
+                         float(front_fraction), int(batch))
         self._call("ocgs_set_options", self._ctx, C.byref(o))
         self.tile = (int(tile[0]), int(tile[1]))
         self.persistent = bool(persistent)
         self.pixels_per_thread = int(pixels_per_thread)
         self.front_fraction = float(front_fraction)
+        self.batch = int(batch)
+
+    def options(self) -> dict:
+        """The context's launch options, as ``set_options`` takes them."""
+        return dict(tile=self.tile, persistent=self.persistent, pixels_per_thread=self.pixels_per_thread,
+                    front_fraction=self.front_fraction, batch=self.batch)
 
     def autotune(self, gaussians: dict, cameras: Sequence[dict], cache_path: Optional[str] = None) -> dict:
-        """Time the launch-option candidates on this workload and keep the fastest (see ocgs_autotune)."""
+        """Time the launch-option candidates on this workload's training render and backward and keep
+        the fastest (see ocgs_autotune); returns the chosen options and their time."""
         self._bind_stream()
         gs = gaussians_struct(gaussians, self.device)
         res = _lib.TuneResult()
@@ -215,7 +223,10 @@ class Rasterizer:
         self.tile = (b.tile_w, b.tile_h)
         self.persistent = bool(b.persistent)
         self.pixels_per_thread = b.pixels_per_thread
+        self.front_fraction = float(b.front_fraction)
+        self.batch = int(b.batch)
         return {"tile": self.tile, "pixels_per_thread": b.pixels_per_thread, "persistent": bool(b.persistent),
+                "front_fraction": self.front_fraction, "batch": self.batch,
                 "ms": res.best_ms, "n_tried": res.n_tried, "from_cache": bool(res.from_cache)}
 
     def stats(self) -> dict:
@@ -477,7 +488,17 @@ class Rasterizer:
 
 
 class RenderFunction(torch.autograd.Function):
-    """Differentiable render of a list of views through libocgs."""
+    """Differentiable render of a list of views through libocgs: outputs (rgb, alpha, depth,
+    normal) of ``Rasterizer.render``, gradients from ``Rasterizer.render_backward``.
+
+    * Cotangents of unused outputs reach the backward as None (they are not materialised as
+      zeros), so a loss on colour and opacity alone runs the backward without the depth and
+      normal terms.
+    * The parameters are kept with ``save_for_backward``: changing one in place between the
+      forward and the backward raises torch's version-counter error instead of differentiating
+      at another point than the one rendered.
+    * The first backward releases the forward state; a second backward through the same render
+      (``retain_graph=True``) raises RuntimeError."""
 
     @staticmethod
     def forward(ctx, rast: Rasterizer, cameras, xyz, quat, scale, opacity, sh):
@@ -486,15 +507,26 @@ class RenderFunction(torch.autograd.Function):
         out, state = rast.render(g, cameras)
         ctx.rast = rast
         ctx.state = state
-        ctx.g = g
+        ctx.save_for_backward(xyz, quat, scale, opacity, sh)
+        ctx.set_materialize_grads(False)
         return out["rgb"], out["alpha"], out["depth"], out["normal"]
 
     @staticmethod
     def backward(ctx, g_rgb, g_alpha, g_depth, g_normal):
-        d_out = {k: (None if v is None else v.contiguous()) for k, v in
-                 (("rgb", g_rgb), ("alpha", g_alpha), ("depth", g_depth), ("normal", g_normal))}
-        grads = ctx.rast.render_backward(ctx.state, ctx.g, d_out)
-        ctx.state.release()
+        if ctx.state is None or not ctx.state.handle:
+            raise RuntimeError("RenderFunction: the forward state of this render was released by an earlier "
+                               "backward; render again to differentiate again")
+        params = ctx.saved_tensors  # raises if a parameter was modified in place after the forward
+        g = {k: p.detach() for k, p in zip(PARAM_KEYS, params)}
+        d_out = {k: v.contiguous() for k, v in
+                 (("rgb", g_rgb), ("alpha", g_alpha), ("depth", g_depth), ("normal", g_normal)) if v is not None}
+        state, ctx.state = ctx.state, None
+        try:
+            if not d_out:
+                return (None,) * (2 + len(PARAM_KEYS))
+            grads = ctx.rast.render_backward(state, g, d_out)
+        finally:
+            state.release()
         return (None, None) + tuple(grads[k] for k in PARAM_KEYS)
 
 

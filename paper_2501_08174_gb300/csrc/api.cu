@@ -25,7 +25,7 @@ struct ocgs_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
-  ocgs_options opts{16, 16, 0, 2};
+  ocgs_options opts{16, 16, 0, 2, 0.f, 32};
   ocgs_stats stats{};
   std::string err;
   int* d_status = nullptr;
@@ -49,7 +49,7 @@ struct ocgs_fwd_state {
   int64_t P = 0;
   uint32_t K = 0;
   uint32_t n_tiles = 0;
-  int tile_w = 16, tile_h = 16, ppt = 1;
+  int tile_w = 16, tile_h = 16, ppt = 1, batch = 32;
   int persistent = 0;
   DevCam* d_cams = nullptr;
   int* d_tile_prefix = nullptr;
@@ -253,9 +253,12 @@ ocgs_status read_status(ocgs_ctx* ctx, int* status) {
   return OCGS_OK;
 }
 
-bool valid_tile(int tw, int th, int ppt) {
+bool valid_tile(int tw, int th, int ppt, int batch) {
   const bool shape = (tw == 16 && th == 16) || (tw == 16 && th == 8) || (tw == 8 && th == 8) || (tw == 32 && th == 8);
-  return shape && (ppt == 1 || ppt == 2 || (ppt == 4 && tw == 16 && (th == 16 || th == 8)));
+  if (!(shape && (ppt == 1 || ppt == 2 || (ppt == 4 && tw == 16 && (th == 16 || th == 8))))) return false;
+  // the shapes built with other batch sizes (OCGS_RASTER_SHAPES)
+  const bool small_big = tw == 16 && ((th == 16 && (ppt == 2 || ppt == 4)) || (th == 8 && ppt == 4));
+  return batch == 32 || ((batch == 16 || batch == 64) && small_big);
 }
 
 GaussPtrs gptrs(const ocgs_gaussians* g) { return GaussPtrs{g->xyz, g->quat, g->scale, g->opacity, g->sh}; }
@@ -282,6 +285,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
 
   st->ctx = ctx; st->V = V; st->N = N; st->deg = g->sh_degree; st->P = pl.P;
   st->n_tiles = (uint32_t)pl.tiles; st->tile_w = tw; st->tile_h = th; st->ppt = ctx->opts.pixels_per_thread;
+  st->batch = ctx->opts.batch;
   st->persistent = ctx->opts.persistent;
   CK(keep.alloc(&st->d_cams, V));
   CK(keep.alloc(&st->d_tile_prefix, V + 1));
@@ -413,7 +417,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     ra.persistent_ctas = st->persistent ? ctx->sm_count * (2048 * st->ppt / (tw * th)) : 0;
     {
       StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-      CK(launch_raster_forward(ra, tw, th, st->ppt, out != nullptr, s));
+      CK(launch_raster_forward(ra, tw, th, st->ppt, st->batch, out != nullptr, s));
     }
 
   } else {
@@ -520,7 +524,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     ra.done = done;
     {
       StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-      CK(launch_raster_forward(ra, tw, th, st->ppt, img, s));
+      CK(launch_raster_forward(ra, tw, th, st->ppt, st->batch, img, s));
     }
     uint32_t K2 = 0;
     uint32_t* P = nullptr;
@@ -586,7 +590,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(cudaMemsetAsync(queue, 0, sizeof(uint32_t), s));
       {
         StageTimer t(ctx, OCGS_STAGE_RASTER_FWD);
-        CK(launch_raster_forward(rb, tw, th, st->ppt, img, s));
+        CK(launch_raster_forward(rb, tw, th, st->ppt, st->batch, img, s));
       }
     }
     K = K1 + K2;
@@ -705,7 +709,7 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
     ra.queue = w.queue;
     ra.persistent_ctas = ctx->sm_count * (2048 * ppt / (tw * th));
   }
-  CK(launch_raster_forward(ra, tw, th, ppt, false, s));
+  CK(launch_raster_forward(ra, tw, th, ppt, ctx->opts.batch, false, s));
   return OCGS_OK;
 }
 
@@ -773,12 +777,17 @@ ocgs_status ocgs_set_stream(ocgs_ctx* ctx, void* stream) {
 ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
   if (!ctx || !o) return OCGS_ERR_ARG;
   const int ppt = o->pixels_per_thread == 0 ? 2 : o->pixels_per_thread;
-  if (!valid_tile(o->tile_w, o->tile_h, ppt))
+  const int batch = o->batch == 0 ? 32 : o->batch;
+  if (!valid_tile(o->tile_w, o->tile_h, ppt, 32))
     return set_err(ctx, OCGS_ERR_ARG, "tile must be 16x16, 16x8, 8x8 or 32x8 with 1 or 2 pixels per thread (4 for 16x16 and 16x8)");
+  if (!valid_tile(o->tile_w, o->tile_h, ppt, batch))
+    return set_err(ctx, OCGS_ERR_ARG, "batch must be 32, or 16 or 64 with 16x16 tiles and 2 or 4 pixels per thread "
+                                      "or 16x8 tiles and 4");
   if (!(o->front_fraction >= 0.f && o->front_fraction <= 1.f))
     return set_err(ctx, OCGS_ERR_ARG, "front_fraction must lie in [0, 1]");
   ctx->opts = *o;
   ctx->opts.pixels_per_thread = ppt;
+  ctx->opts.batch = batch;
   return OCGS_OK;
 }
 
@@ -880,7 +889,7 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
     ba.persistent_ctas = ctx->sm_count * (2048 * st->ppt / (st->tile_w * st->tile_h));
   }
   ba.queue = queue;
-  CK(launch_raster_backward(ba, st->tile_w, st->tile_h, st->ppt, s));
+  CK(launch_raster_backward(ba, st->tile_w, st->tile_h, st->ppt, st->batch, s));
   t_bwd.stop();
   GaussOut go{d_params->xyz, d_params->quat, d_params->scale, d_params->opacity, d_params->sh};
   {
@@ -1305,7 +1314,7 @@ std::string tune_key(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_camera* 
   std::ostringstream os;
   std::string name(prop.name);
   for (char& c : name) if (c == ' ') c = '_';
-  os << name << "/sm" << prop.multiProcessorCount << "/deg" << g->sh_degree << "/v" << V << "/n2^"
+  os << "v2/" << name << "/sm" << prop.multiProcessorCount << "/deg" << g->sh_degree << "/v" << V << "/n2^"
      << log2_bucket(g->n) << "/p2^" << log2_bucket(pix);
   return os.str();
 }
@@ -1329,10 +1338,10 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
       std::istringstream ls(line);
       std::string k;
       ocgs_options o{};
-      o.front_fraction = ctx->opts.front_fraction;
       double ms = 0.0;
-      if ((ls >> k >> o.tile_w >> o.tile_h >> o.pixels_per_thread >> o.persistent >> ms) && k == key &&
-          ocgs_set_options(ctx, &o) == OCGS_OK) {
+      if ((ls >> k >> o.tile_w >> o.tile_h >> o.pixels_per_thread >> o.persistent >> o.front_fraction >> o.batch >>
+           ms) &&
+          k == key && ocgs_set_options(ctx, &o) == OCGS_OK) {
         result->best = ctx->opts;
         result->best_ms = ms;
         result->from_cache = 1;
@@ -1340,61 +1349,78 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
     }
     if (result->from_cache) return OCGS_OK;
   }
-  // buffers for the timed passes
+  // buffers for the timed passes: the images, a contribution score and the
+  // colour and opacity cotangents of a training step (dL/dC = dL/dA = 1)
   int64_t P = 0;
   for (int v = 0; v < n_views; ++v) P += (int64_t)cams[v].width * cams[v].height;
   const int64_t N = g->n;
   const int64_t K3 = 3 * (int64_t)(g->sh_degree + 1) * (g->sh_degree + 1);
   cudaStream_t s = ctx->stream;
   Arena tmp(ctx);
-  float *img, *ones, *grad;
+  float *img, *ones, *grad, *score;
   CK(tmp.alloc(&img, (size_t)P * 8));
-  CK(tmp.alloc(&ones, (size_t)P));
+  CK(tmp.alloc(&ones, (size_t)P * 4));
   CK(tmp.alloc(&grad, (size_t)N * (10 + K3)));
+  CK(tmp.alloc(&score, (size_t)std::max<int64_t>(N, 1)));
   std::vector<float> h_ones(1 << 16, 1.0f);
-  for (int64_t off = 0; off < P; off += (int64_t)h_ones.size()) {
-    const int64_t n = std::min<int64_t>((int64_t)h_ones.size(), P - off);
+  for (int64_t off = 0; off < 4 * P; off += (int64_t)h_ones.size()) {
+    const int64_t n = std::min<int64_t>((int64_t)h_ones.size(), 4 * P - off);
     CK(cudaMemcpyAsync(ones + off, h_ones.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
   }
-  const ocgs_image out{img, img + 3 * P, img + 4 * P, img + 5 * P};
-  const ocgs_image d_out{nullptr, ones, nullptr, nullptr};
+  const ocgs_image out{img, img + 3 * P, img + 4 * P, img + 5 * P, nullptr};
+  const ocgs_image d_out{ones, ones + 3 * P, nullptr, nullptr, nullptr};
   const ocgs_gaussians_out dp{grad, grad + 3 * N, grad + 7 * N, grad + 9 * N, grad + 10 * N};
-  const int shapes[][3] = {{16, 16, 4}, {16, 16, 2}, {16, 8, 4}, {16, 8, 2}, {8, 8, 2}, {32, 8, 2}, {16, 16, 1}};
   const ocgs_options saved = ctx->opts;
   const bool prof = ctx->prof;
   ctx->prof = false;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
+  ocgs_status status = OCGS_OK;
+  // ms of one render + backward with options o (once untimed, twice timed), or < 0
+  auto time_options = [&](const ocgs_options& o) -> double {
+    if (status != OCGS_OK || ocgs_set_options(ctx, &o) != OCGS_OK) return -1.0;
+    for (int rep = 0; rep < 3 && status == OCGS_OK; ++rep) {
+      if (rep == 1) cudaEventRecord(e0, s);
+      ocgs_fwd_state* st = nullptr;
+      status = ocgs_render(ctx, g, cams, n_views, &out, score, &st);
+      if (status == OCGS_ERR_NONFINITE) status = OCGS_OK;
+      if (status == OCGS_OK) status = ocgs_render_backward(ctx, st, g, &d_out, &dp);
+      if (st) ocgs_state_release(ctx, st);
+    }
+    if (status != OCGS_OK) return -1.0;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    result->n_tried++;
+    return ms / 2.0;
+  };
   double best = 1e30;
   ocgs_options best_opts = saved;
-  ocgs_status status = OCGS_OK;
-  for (const auto& sh : shapes) {
-    for (int pers = 0; pers <= 1; ++pers) {
-      ocgs_options o{sh[0], sh[1], pers, sh[2], saved.front_fraction};
-      if (ocgs_set_options(ctx, &o) != OCGS_OK) continue;
-      double ms_sum = 0.0;
-      for (int rep = 0; rep < 3 && status == OCGS_OK; ++rep) {
-        if (rep == 1) cudaEventRecord(e0, s);
-        ocgs_fwd_state* st = nullptr;
-        status = ocgs_render(ctx, g, cams, n_views, &out, nullptr, &st);
-        if (status == OCGS_ERR_NONFINITE) status = OCGS_OK;
-        if (status == OCGS_OK) status = ocgs_render_backward(ctx, st, g, &d_out, &dp);
-        if (st) ocgs_state_release(ctx, st);
-      }
-      if (status != OCGS_OK) break;
-      cudaEventRecord(e1, s);
-      cudaEventSynchronize(e1);
-      float ms = 0.f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      ms_sum = ms / 2.0;
-      result->n_tried++;
-      if (ms_sum < best) {
-        best = ms_sum;
-        best_opts = ctx->opts;
-      }
+  auto consider = [&](const ocgs_options& o) {
+    const double ms = time_options(o);
+    if (ms >= 0.0 && ms < best) {
+      best = ms;
+      best_opts = ctx->opts;
     }
-    if (status != OCGS_OK) break;
+  };
+  // 1. tile shape, pixels per thread and persistence at the context's split and 32 per batch
+  const int shapes[][3] = {{16, 16, 4}, {16, 16, 2}, {16, 8, 4}, {16, 8, 2}, {8, 8, 2}, {32, 8, 2}, {16, 16, 1}};
+  for (const auto& sh : shapes)
+    for (int pers = 0; pers <= 1; ++pers) consider(ocgs_options{sh[0], sh[1], pers, sh[2], saved.front_fraction, 32});
+  // 2. the two-pass split, for a persistent choice (the only renders that use it)
+  if (status == OCGS_OK && best_opts.persistent) {
+    const ocgs_options base = best_opts;
+    for (float f : {0.0f, 0.05f, 0.1f, 0.2f})
+      if (f != base.front_fraction) consider(ocgs_options{base.tile_w, base.tile_h, 1, base.pixels_per_thread, f, 32});
+  }
+  // 3. Gaussians per batch, where the chosen shape offers more than 32
+  if (status == OCGS_OK) {
+    const ocgs_options base = best_opts;
+    for (int b : {16, 64})
+      if (valid_tile(base.tile_w, base.tile_h, base.pixels_per_thread, b))
+        consider(ocgs_options{base.tile_w, base.tile_h, base.persistent, base.pixels_per_thread, base.front_fraction, b});
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
@@ -1409,7 +1435,7 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
   if (cache_path) {
     std::ofstream outf(cache_path, std::ios::app);
     outf << key << " " << best_opts.tile_w << " " << best_opts.tile_h << " " << best_opts.pixels_per_thread << " "
-         << best_opts.persistent << " " << best << "\n";
+         << best_opts.persistent << " " << best_opts.front_fraction << " " << best_opts.batch << " " << best << "\n";
   }
   return OCGS_OK;
 }

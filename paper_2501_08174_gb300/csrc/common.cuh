@@ -90,175 +90,6 @@ enum GradSlot {
 constexpr int kGradSlotsRGB = 13;
 constexpr int kGradSlots = 18;
 
-// Result of evaluating one surfel at one pixel centre.  All arithmetic uses
-// explicitly rounded intrinsics so that the forward and the backward kernels
-// take bit-identical decisions (skip, clamp, branch) for the same inputs, and
-// the value at a pixel does not depend on the tile shape or on how many
-// pixels a thread owns.
-struct SplatEval {
-  float dx, dy, un, vn, den, r, rho3, rho, G, oG, alpha, z;
-  bool surf;  // the surfel term rho3 <= rho2 is used (else the screen filter)
-  bool ok;    // rho <= 9 and alpha >= 1/255: the candidate is blended unless the pixel stops
-};
-
-// Terms of the ray-splat map that depend only on the pixel column.
-struct SplatColumn {
-  float dx, ux, vx, ex, dx2;
-};
-
-__device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float4 g1, const float4 g2, float px) {
-  SplatColumn c;
-  c.dx = __fsub_rn(px, g0.x);
-  c.ux = __fmul_rn(g1.x, c.dx);
-  c.vx = __fmul_rn(g1.z, c.dx);
-  c.ex = __fmaf_rn(g2.y, c.dx, g2.x);
-  c.dx2 = __fmul_rn(c.dx, c.dx);
-  return c;
-}
-
-// rb: the record's support bound support_rho(o) <= 9.  Candidates with
-// rho > rb have o exp(-rho/2) < 1/255, so testing rb instead of 9 first only
-// skips work; every decision is the one the 9 cut and the 1/255 floor give.
-//
-// The evaluation is split in two so that a thread can run the cheap support
-// test of all its pixels as straight-line code and finish only the pixels
-// that pass: splat_head (support test) and splat_tail (rho, alpha, depth).
-struct SplatHead {
-  float dy, un, vn, den, rho2, q, dd;
-  bool in3;   // rho3 <= rb
-  bool pass;  // rho3 <= rb or rho2 <= rb
-};
-
-__device__ __forceinline__ SplatHead splat_head(const float4 g0, const float4 g1, const float4 g2,
-                                                const SplatColumn& c, float py, float rb) {
-  SplatHead h;
-  h.dy = __fsub_rn(py, g0.y);
-  h.un = __fmaf_rn(g1.y, h.dy, c.ux);
-  h.vn = __fmaf_rn(g1.w, h.dy, c.vx);
-  h.den = __fmaf_rn(g2.z, h.dy, c.ex);
-  h.rho2 = __fmul_rn(kInvSigmaF2, __fmaf_rn(h.dy, h.dy, c.dx2));
-  h.q = __fmaf_rn(h.un, h.un, __fmul_rn(h.vn, h.vn));
-  h.dd = __fmul_rn(h.den, h.den);
-  h.in3 = (h.den != 0.0f) && (h.q <= __fmul_rn(rb, h.dd));
-  h.pass = h.in3 || (h.rho2 <= rb);
-  return h;
-}
-
-__device__ __forceinline__ SplatEval splat_tail(const float4 g0, const float4 g2, const SplatColumn& c,
-                                                const SplatHead& h, float rb) {
-  SplatEval e;
-  e.dx = c.dx;
-  e.dy = h.dy;
-  e.un = h.un;
-  e.vn = h.vn;
-  e.den = h.den;
-  e.r = 0.0f;
-  e.rho3 = __int_as_float(0x7f800000);  // +inf
-  e.G = 0.0f;
-  e.oG = 0.0f;
-  e.alpha = 0.0f;
-  e.z = 0.0f;
-  e.ok = false;
-  e.surf = false;
-  e.rho = h.rho2;
-  if (!h.pass) return e;  // outside the support
-  if (h.in3) {
-    e.r = __fdividef(1.0f, h.den);
-    e.rho3 = __fmul_rn(h.q, __fmul_rn(e.r, e.r));
-  }
-  e.surf = h.in3 && (e.rho3 <= h.rho2);
-  e.rho = e.surf ? e.rho3 : h.rho2;
-  if (e.rho <= rb) {
-    e.G = __expf(__fmul_rn(-0.5f, e.rho));
-    e.oG = __fmul_rn(g0.z, e.G);
-    e.alpha = fminf(kAlphaMax, e.oG);
-    e.ok = e.alpha >= kAlphaMin;
-    e.z = e.surf ? __fmul_rn(g2.w, e.r) : g0.w;
-  }
-  return e;
-}
-
-__device__ __forceinline__ SplatEval eval_splat(const float4 g0, const float4 g1, const float4 g2,
-                                                const SplatColumn& c, float py, float rb) {
-  return splat_tail(g0, g2, c, splat_head(g0, g1, g2, c, py, rb), rb);
-}
-
-// ----------------------------------------------------------------------------- two pixels at once
-// The same evaluation for two pixels of one column (rows py.x and py.y) on the
-// packed FP32x2 pipes of sm_100+: every lane of __ffma2_rn / __fmul2_rn /
-// __fadd2_rn rounds as the scalar operation does, so a pair gives the two scalar
-// results bit for bit with half the issued instructions.  All lanes are
-// evaluated; the flags say which results count.
-__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
-__device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
-__device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
-  if (i) v.y = x;
-  else v.x = x;
-}
-
-struct SplatHead2 {
-  float2 dy, un, vn, den, rho2, q;
-  bool in3[2];
-  bool pass[2];
-};
-
-// EWA: a projected 3D Gaussian (constant denominator, the screen filter already
-// folded into its covariance): the support test is the Mahalanobis term alone.
-template <bool EWA = false>
-__device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
-                                                  const SplatColumn& c, float2 py, float rb) {
-  SplatHead2 h;
-  h.dy = __fadd2_rn(py, bc2(-g0.y));
-  h.un = __ffma2_rn(bc2(g1.y), h.dy, bc2(c.ux));
-  h.vn = __ffma2_rn(bc2(g1.w), h.dy, bc2(c.vx));
-  h.den = __ffma2_rn(bc2(g2.z), h.dy, bc2(c.ex));
-  h.rho2 = __fmul2_rn(bc2(kInvSigmaF2), __ffma2_rn(h.dy, h.dy, bc2(c.dx2)));
-  h.q = __ffma2_rn(h.un, h.un, __fmul2_rn(h.vn, h.vn));
-  const float2 lim = __fmul2_rn(bc2(rb), __fmul2_rn(h.den, h.den));
-  h.in3[0] = (h.den.x != 0.0f) && (h.q.x <= lim.x);
-  h.in3[1] = (h.den.y != 0.0f) && (h.q.y <= lim.y);
-  h.pass[0] = h.in3[0] || (!EWA && h.rho2.x <= rb);
-  h.pass[1] = h.in3[1] || (!EWA && h.rho2.y <= rb);
-  return h;
-}
-
-struct SplatEval2 {
-  float2 r, rho3;  // 1 / den and the surfel rho where the surfel term won, else 0
-  float2 G, oG, alpha, z;
-  bool surf[2];
-  bool ok[2];  // pass, rho <= rb and alpha >= 1/255
-};
-
-// FINITE: r and rho3 are zeroed where the filter term won, so that products
-// the backward masks with zero stay finite (the forward only reads z there).
-template <bool FINITE, bool EWA = false>
-__device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
-  SplatEval2 e;
-  const float2 r = EWA ? make_float2(h.in3[0] ? 1.0f : 0.0f, h.in3[1] ? 1.0f : 0.0f)
-                       : make_float2(h.in3[0] ? __fdividef(1.0f, h.den.x) : 0.0f,
-                                     h.in3[1] ? __fdividef(1.0f, h.den.y) : 0.0f);
-  const float2 r3 = EWA ? h.q : __fmul2_rn(h.q, __fmul2_rn(r, r));
-  e.surf[0] = h.in3[0] && (EWA || r3.x <= h.rho2.x);
-  e.surf[1] = h.in3[1] && (EWA || r3.y <= h.rho2.y);
-  if (FINITE) {
-    e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
-    e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
-  } else {
-    e.r = r;
-    e.rho3 = r3;
-  }
-  const float2 rho = make_float2(e.surf[0] ? r3.x : h.rho2.x, e.surf[1] ? r3.y : h.rho2.y);
-  const float2 ex = __fmul2_rn(bc2(-0.5f), rho);
-  e.G = make_float2(__expf(ex.x), __expf(ex.y));
-  e.oG = __fmul2_rn(bc2(g0.z), e.G);
-  e.alpha = make_float2(fminf(kAlphaMax, e.oG.x), fminf(kAlphaMax, e.oG.y));
-  e.ok[0] = h.pass[0] && (rho.x <= rb) && (e.alpha.x >= kAlphaMin);
-  e.ok[1] = h.pass[1] && (rho.y <= rb) && (e.alpha.y >= kAlphaMin);
-  const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
-  e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);
-  return e;
-}
-
 __device__ __forceinline__ bool finitef(float x) { return isfinite(x); }
 
 // Support bound in rho of a surfel of opacity o: the 3-sigma cut, tightened to
@@ -588,8 +419,10 @@ struct RasterArgs {
   uint8_t* done;
   const uint2* prior;
 };
-// ppt: pixels per thread (vertically adjacent): 1 or 2, and 4 for 16x16 tiles
-cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, int ppt, bool write_image,
+// ppt: pixels per thread (vertically adjacent): 1 or 2, and 4 for 16-wide tiles;
+// batch: records a warp stages per batch (32; also 16 and 64 for the 16-wide
+// shapes with 2 or 4 pixels per thread, see OCGS_RASTER_SHAPES)
+cudaError_t launch_raster_forward(const RasterArgs& a, int tile_w, int tile_h, int ppt, int batch, bool write_image,
                                   cudaStream_t s);
 
 struct RasterBwdArgs {
@@ -611,7 +444,8 @@ struct RasterBwdArgs {
   uint32_t* queue;
   int persistent_ctas;
 };
-cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, cudaStream_t s);
+cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, int batch,
+                                   cudaStream_t s);
 // sum of the per-pixel blended-prefix lengths (the pairs both passes must evaluate)
 cudaError_t launch_sum_u32(const uint32_t* v, int64_t n, unsigned long long* out, cudaStream_t s);
 

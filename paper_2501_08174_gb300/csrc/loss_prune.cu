@@ -46,7 +46,11 @@ __global__ void __launch_bounds__(kLossThreads) bg_loss_partial_kernel(
 }
 
 // Masked L1 (Eq. 2, L1 part): |I M - R M| summed in FP64 per block, with the
-// adjoint weight * sign(R - I) * M / (3 h w) added into d_rgb.
+// adjoint weight * sign(R - I) * M / (3 h w) added into d_rgb.  The difference
+// of the two FP32 values is taken in FP64, where it is exact unless their
+// exponents differ by more than 28 (then within 2^-53 relative), so the loss
+// differs from the exact one by the FP64 summation order alone; its sign is
+// the sign of the exact difference.
 __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ block_prefix, float weight,
@@ -65,9 +69,9 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
     if (!mask[p]) continue;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const float d = rgb[3 * p + c] - target[3 * p + c];
-      acc += fabs((double)d);
-      if (d_rgb) d_rgb[3 * p + c] += d > 0.f ? g : (d < 0.f ? -g : 0.f);
+      const double d = (double)rgb[3 * p + c] - (double)target[3 * p + c];
+      acc += fabs(d);
+      if (d_rgb) d_rgb[3 * p + c] += d > 0.0 ? g : (d < 0.0 ? -g : 0.f);
     }
   }
 #pragma unroll
@@ -188,6 +192,9 @@ cudaError_t launch_prune_compact(const GaussPtrs& in, uint32_t n, int sh_degree,
 // Host code cannot hand that array to a kernel by name (in host code the name
 // is only a stand-in), so the first call on each device, with that device
 // current, looks its device address up with cudaGetSymbolAddress and keeps it.
+// The view sizes travel to the device as a kernel argument (copied by value
+// at launch), and a one-block kernel writes the view table and the block
+// prefix into the array, so no host buffer is read after the call returns.
 namespace {
 
 constexpr int kNoAllocMaxViews = 1024;
@@ -200,12 +207,48 @@ constexpr size_t kNoAllocBytes = kNoAllocPrefixOffset + sizeof(int) * (kNoAllocM
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
+// width and height of every view (each at most 16384), passed by value
+struct NoAllocViews {
+  uint16_t w[kNoAllocMaxViews];
+  uint16_t h[kNoAllocMaxViews];
+};
+
+// One block of kNoAllocMaxViews threads: thread v fills the view table entry of
+// view v (size and first pixel) and the block prefix (first loss block of v).
+__global__ void __launch_bounds__(kNoAllocMaxViews) noalloc_setup_kernel(const NoAllocViews views, int n_views,
+                                                                         ocgs::DevCam* __restrict__ cams,
+                                                                         int* __restrict__ prefix) {
+  __shared__ long long s_pix[kNoAllocMaxViews];
+  __shared__ int s_blk[kNoAllocMaxViews];
+  const int v = threadIdx.x;
+  const long long np = v < n_views ? (long long)views.w[v] * views.h[v] : 0;
+  s_pix[v] = np;
+  s_blk[v] = (int)((np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels);
+  __syncthreads();
+  // inclusive Hillis-Steele scan over the views
+  for (int o = 1; o < kNoAllocMaxViews; o <<= 1) {
+    const long long pp = v >= o ? s_pix[v - o] : 0;
+    const int bb = v >= o ? s_blk[v - o] : 0;
+    __syncthreads();
+    s_pix[v] += pp;
+    s_blk[v] += bb;
+    __syncthreads();
+  }
+  if (v < n_views) {
+    ocgs::DevCam d;
+    memset(&d, 0, sizeof(d));
+    d.W = views.w[v];
+    d.H = views.h[v];
+    d.pix_offset = s_pix[v] - np;
+    cams[v] = d;
+    prefix[v] = s_blk[v] - (int)((np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels);
+  }
+  if (v == n_views - 1) prefix[n_views] = s_blk[v];
+}
+
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
 unsigned char* g_noalloc_addr[kNoAllocMaxDevices];  // device address of the array, per device
-// host staging of the view table and prefix (reused under the mutex)
-ocgs::DevCam g_noalloc_cams[kNoAllocMaxViews];
-int g_noalloc_prefix[kNoAllocMaxViews + 1];
 
 }  // namespace
 
@@ -216,52 +259,38 @@ extern "C" ocgs_status ocgs_background_loss_noalloc(const float* alpha, const ui
   if (n_views < 1) return OCGS_ERR_ARG;
   if (n_views > kNoAllocMaxViews) return OCGS_ERR_CAPACITY;  // beyond the static view table
   if (!std::isfinite(gamma)) return OCGS_ERR_ARG;
+  NoAllocViews views;
   int64_t blocks = 0;
   for (int v = 0; v < n_views; ++v) {
     if (cams[v].width < 1 || cams[v].height < 1 || cams[v].width > 16384 || cams[v].height > 16384)
       return OCGS_ERR_ARG;
     const int64_t np = (int64_t)cams[v].width * cams[v].height;
     blocks += (np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels;
+    views.w[v] = (uint16_t)cams[v].width;
+    views.h[v] = (uint16_t)cams[v].height;
   }
   if (blocks > kNoAllocMaxBlocks) return OCGS_ERR_CAPACITY;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return OCGS_ERR_CUDA;
   if (dev < 0 || dev >= kNoAllocMaxDevices) return OCGS_ERR_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OCGS_ERR_CUDA;
-    g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return OCGS_ERR_CUDA;
+      g_noalloc_addr[dev] = static_cast<unsigned char*>(p);
+    }
+    base = g_noalloc_addr[dev];
   }
-  unsigned char* base = g_noalloc_addr[dev];
-  int64_t pix = 0;
-  int acc = 0;
-  for (int v = 0; v < n_views; ++v) {
-    ocgs::DevCam& d = g_noalloc_cams[v];
-    std::memset(&d, 0, sizeof(d));
-    d.W = cams[v].width;
-    d.H = cams[v].height;
-    d.pix_offset = pix;
-    g_noalloc_prefix[v] = acc;
-    const int64_t np = (int64_t)d.W * d.H;
-    acc += (int)((np + ocgs::kLossBlockPixels - 1) / ocgs::kLossBlockPixels);
-    pix += np;
-  }
-  g_noalloc_prefix[n_views] = acc;
   ocgs::DevCam* d_cams = reinterpret_cast<ocgs::DevCam*>(base + kNoAllocCamOffset);
   int* d_prefix = reinterpret_cast<int*>(base + kNoAllocPrefixOffset);
   double* d_partial = reinterpret_cast<double*>(base);
-  // copies from pageable host memory return once the data is staged, so the
-  // host tables may be refilled by the next call
-  if (cudaMemcpyAsync(d_cams, g_noalloc_cams, sizeof(ocgs::DevCam) * n_views, cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
-    return OCGS_ERR_CUDA;
-  if (cudaMemcpyAsync(d_prefix, g_noalloc_prefix, sizeof(int) * (n_views + 1), cudaMemcpyHostToDevice, s) !=
-      cudaSuccess)
-    return OCGS_ERR_CUDA;
-  if (ocgs::launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, acc, gamma, d_partial, loss, d_alpha,
-                                   s) != cudaSuccess)
+  noalloc_setup_kernel<<<1, kNoAllocMaxViews, 0, s>>>(views, n_views, d_cams, d_prefix);
+  if (ocgs::launched() != cudaSuccess) return OCGS_ERR_CUDA;
+  if (ocgs::launch_background_loss(alpha, mask, d_cams, n_views, d_prefix, (int)blocks, gamma, d_partial, loss,
+                                   d_alpha, s) != cudaSuccess)
     return OCGS_ERR_CUDA;
   return OCGS_OK;
 }

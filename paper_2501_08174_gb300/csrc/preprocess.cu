@@ -124,6 +124,29 @@ __device__ __forceinline__ Frame make_frame(float4 q) {
   return f;
 }
 
+// Sort key of the front-to-back order: the centre depth R_2 . X + t_z of the float32 camera
+// and centre, evaluated as accurately as in twice the precision and rounded once to float32
+// (the compensated dot product Dot2 of Ogita, Rump and Oishi, 2005): each product is split
+// exactly into p + e with e = fma(a, b, -p), the running sum is kept exact with Knuth's
+// TwoSum, and the collected errors are added before the one final rounding.  The key is
+// then the depth rounded to float32 (up to cases within about 1e-4 ulp of a rounding
+// midpoint), independent of how the float32 geometry below is contracted; positive for
+// every record that is not culled, so the bit pattern orders like the value.
+__device__ __forceinline__ uint32_t depth_key_of(const DevCam& cam, const float* X) {
+  float s = cam.t[2], c = 0.f;
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float p = __fmul_rn(cam.R[6 + j], X[j]);
+    const float e = __fmaf_rn(cam.R[6 + j], X[j], -p);  // R X = p + e exactly
+    const float t = __fadd_rn(s, p);
+    const float bp = __fsub_rn(t, s);
+    const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));  // s + p = t + err exactly
+    s = t;
+    c = __fadd_rn(c, __fadd_rn(err, e));
+  }
+  return __float_as_uint(__fadd_rn(s, c));
+}
+
 __device__ __forceinline__ void rot3(const float* R, const float* a, float* o) {
   o[0] = R[0] * a[0] + R[1] * a[1] + R[2] * a[2];
   o[1] = R[3] * a[0] + R[4] * a[1] + R[5] * a[2];
@@ -268,7 +291,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
       continue;
     }
     ntiles[idx] = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-    depth_key[idx] = __float_as_uint(G.p[2]);  // positive: the bit pattern orders like the value
+    depth_key[idx] = depth_key_of(cam, X);
     const float pz = G.p[2];
     const float e0 = G.a * G.d - G.b * G.c;
     const float e1 = G.V[2] * G.c - G.U[2] * G.d;
@@ -556,7 +579,7 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
       continue;
     }
     ntiles[idx] = (rc.z - rc.x + 1) * (rc.w - rc.y + 1);
-    depth_key[idx] = __float_as_uint(t[2]);
+    depth_key[idx] = depth_key_of(cam, X);
     float dirn[3], dlen, raw[3];
     view_colour<DEG>(cam, X, sh, dirn, &dlen, raw);
     const float4 g0 = make_float4(ccx, ccy, o, t[2]);

@@ -1,0 +1,386 @@
+// Backward tile rasterizer: the reverse-order adjoint of the front-to-back
+// compositing (the backpropagation through the rasterizer of Sec. 3.2).
+//
+// The backward walks each tile's list back to front from each pixel's last
+// blended entry, recovering the transmittance T_i = T_{i+1} / (1 - alpha_i)
+// from the stored final transmittance, so nothing per (pixel, Gaussian) is
+// stored between the passes.  Per-Gaussian gradients are summed over the
+// thread's pixels, reduced over the warp, gathered per batch in the warp's
+// shared memory and added to global memory with one vector atomic per 4
+// values, entry and warp.  The warp reduction of the 13 slots of a colour and
+// opacity loss goes through shared memory (each lane writes its sums, then
+// 26 lanes each add 16 of them and pair up with one shuffle); the 18 slots
+// with depth and normal cotangents use a halving transpose of shuffles.
+#include "raster_common.cuh"
+
+namespace ocgs {
+namespace {
+using namespace raster;
+
+#ifndef OCGS_BWD_WARPS
+#define OCGS_BWD_WARPS 16
+#endif
+#ifndef OCGS_BWD_WARPS_GEO
+#define OCGS_BWD_WARPS_GEO 12
+#endif
+
+// One halving step of a warp transpose-reduction: lanes with bit OFF clear keep
+// the first ceil(C/2) of their C values, the others keep the rest, and each
+// adds the partner's copy of what it keeps.  After the steps for OFF = 16..1
+// every lane holds the warp total of one slot: C + C/2 + ... shuffles in all
+// instead of 5 C for independent butterflies.
+template <int C, int OFF>
+__device__ __forceinline__ void halve(float* v, int lane, int& base, int& real) {
+  constexpr int KEEP = (C + 1) / 2;
+  const bool upper = (lane & OFF) != 0;
+#pragma unroll
+  for (int i = 0; i < KEEP; ++i) {
+    const float lo = v[i];
+    const float hi = (KEEP + i < C) ? v[KEEP + i] : 0.f;
+    const float got = __shfl_xor_sync(kFull, upper ? lo : hi, OFF);
+    v[i] = (upper ? hi : lo) + got;
+  }
+  if (upper) {
+    base += KEEP;
+    real -= KEEP;
+  } else if (real > KEEP) {
+    real = KEEP;
+  }
+}
+
+// Warp sum of the 18 gradient slots; returns the slot this lane holds (or -1).
+__device__ __forceinline__ int warp_reduce18(float* v, int lane) {
+  int base = 0, real = 18;
+  halve<18, 16>(v, lane, base, real);
+  halve<9, 8>(v, lane, base, real);
+  halve<5, 4>(v, lane, base, real);
+  halve<3, 2>(v, lane, base, real);
+  halve<2, 1>(v, lane, base, real);
+  return real >= 1 ? base : -1;
+}
+
+// Row of one lane in the reduction buffer of the 13-slot path: 13 float2 (the
+// two pixel lanes of the packed sums, not yet added).  13 is odd, so the
+// 16-lane phases of the 64-bit stores (lane L writes row L) and of the 64-bit
+// loads (lane L reads slot L & 15 of rows 16 (L >> 4) + i) hit distinct banks.
+constexpr int kRedRow = kGradSlotsRGB;
+// slots 13..15 of the last row are read (and ignored) by lanes 13..15 and 29..31
+constexpr int kRedSize = 32 * kRedRow + 3;
+
+// Slots accumulated with the opposite sign (flipped when the lanes are summed).
+__device__ __forceinline__ bool negated_slot(int q) {
+  return q == kGcx || q == kGcy || q == kGe0 || q == kGe1 || q == kGe2;
+}
+
+// GEO: a depth, depth2 or normal cotangent is given; without one the depth and
+// normal terms of the adjoint are zero and are not evaluated (13 slots instead
+// of 18).
+template <int TW, int TH, int PPT, int BATCH, bool GEO>
+__global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD_WARPS) / kBlockWarps)
+    raster_bwd_kernel(const RasterBwdArgs a) {
+  constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
+  constexpr int NG = GEO ? kGradSlots : kGradSlotsRGB;
+  constexpr int ROWS = BATCH > 32 ? BATCH / 32 : 1;  // gradient rows of a batch each lane flushes
+  using B = Batch<BATCH>;
+  __shared__ float4 s_g0[kBlockWarps][BATCH], s_g1[kBlockWarps][BATCH], s_g2[kBlockWarps][BATCH],
+      s_a0[kBlockWarps][BATCH];
+  __shared__ float2 s_a1[kBlockWarps][BATCH];
+  __shared__ uint32_t s_idx[kBlockWarps][BATCH];
+  __shared__ int s_q[kBlockWarps][BATCH];  // list position of each kept entry
+  __shared__ __align__(16) float s_grad[kBlockWarps][BATCH * kGradStride];  // per-batch gradient sums of each entry
+  __shared__ float s_rb[kBlockWarps][BATCH];
+  __shared__ __align__(16) float2 s_red[kBlockWarps][GEO ? 1 : kRedSize];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < ROWS; ++r) {
+    if (r * 32 + lane < BATCH) {  // a batch of 16 has rows for half the lanes
+      float* row = &s_grad[wib][(r * 32 + lane) * kGradStride];
+#pragma unroll
+      for (int q = 0; q < kGradStride; ++q) row[q] = 0.f;
+    }
+  }
+  // the slot this lane adds up in the 13-slot reduction, and its sign
+  const int red_slot = lane & 15;
+  const float red_sign = negated_slot(red_slot) ? -1.f : 1.f;
+  const uint32_t n_units = a.n_tiles * (uint32_t)WPT;
+  for (uint32_t it = 0;; ++it) {
+    // work unit: one warp's band of one tile; the warps run independently
+    uint32_t unit;
+    if (a.persistent_ctas) {
+      uint32_t u = 0;
+      if (lane == 0) u = atomicAdd(a.queue, 1u);
+      unit = __shfl_sync(kFull, u, 0);
+      if (unit >= n_units) break;
+    } else {
+      if (it > 0) break;
+      unit = blockIdx.x * kBlockWarps + wib;
+      if (unit >= n_units) break;
+    }
+    uint32_t tile = unit / WPT;
+    if (a.persistent_ctas && a.tile_order) tile = a.tile_order[tile];
+    const int tid = (int)(unit % WPT) * 32 + lane;  // thread of the tile
+    const int lx = tid % TW, ly0 = (tid / TW) * PPT;
+    const int v = view_of_tile(a.tile_prefix, a.n_views, (int)tile);
+    const DevCam& cam = a.cams[v];
+    const int local = (int)tile - cam.tile_offset;
+    const int px = (local % cam.tiles_x) * TW + lx;
+    const int py0 = (local / cam.tiles_x) * TH + ly0;
+    const float pxf = (float)px + 0.5f;
+    const uint2 rg1 = a.ranges[tile];
+    const uint32_t start = rg1.x;
+    // a two-pass list continues in the second segment after its first rg1.y - rg1.x entries
+    const uint32_t len1 = a.ranges2 ? rg1.y - rg1.x : 0xffffffffu;
+    const uint32_t start2 = a.ranges2 ? a.ranges2[tile].x : 0u;
+    // pixel k of this thread is lane (k & 1) of pair k / 2 (an odd PPT leaves an idle lane)
+    constexpr int NP = (PPT + 1) / 2;
+    float2 T[NP], gAT[NP], S[NP];
+    float2 gC0[NP], gC1[NP], gC2[NP], gD[NP], gN0[NP], gN1[NP], gN2[NP], gQ[NP];
+    uint32_t last[2 * NP];
+    uint32_t thread_last = 0;
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+      T[p] = bc2(1.f);
+      gAT[p] = bc2(0.f);
+      S[p] = bc2(0.f);  // sum over later blended entries of w * (gC.rgb + gD z + gN.n)
+      gC0[p] = gC1[p] = gC2[p] = gD[p] = gN0[p] = gN1[p] = gN2[p] = gQ[p] = bc2(0.f);
+    }
+#pragma unroll
+    for (int k = 0; k < 2 * NP; ++k) {
+      last[k] = 0u;
+      const int py = py0 + k;
+      const int p = k >> 1, i = k & 1;
+      if (k < PPT && px < cam.W && py < cam.H) {
+        const int64_t pix = cam.pix_offset + (int64_t)py * cam.W + px;
+        const float Tf = a.t_final[pix];
+        set_lane2(T[p], i, Tf);
+        last[k] = a.last[pix];
+        if (a.d_out.rgb) {
+          set_lane2(gC0[p], i, a.d_out.rgb[3 * pix]);
+          set_lane2(gC1[p], i, a.d_out.rgb[3 * pix + 1]);
+          set_lane2(gC2[p], i, a.d_out.rgb[3 * pix + 2]);
+        }
+        if (a.d_out.alpha) set_lane2(gAT[p], i, a.d_out.alpha[pix] * Tf);
+        if (GEO && a.d_out.depth) set_lane2(gD[p], i, a.d_out.depth[pix]);
+        if (GEO && a.d_out.depth2) set_lane2(gQ[p], i, a.d_out.depth2[pix]);
+        if (GEO && a.d_out.normal) {
+          set_lane2(gN0[p], i, a.d_out.normal[3 * pix]);
+          set_lane2(gN1[p], i, a.d_out.normal[3 * pix + 1]);
+          set_lane2(gN2[p], i, a.d_out.normal[3 * pix + 2]);
+        }
+        thread_last = max(thread_last, last[k]);
+      }
+    }
+    // entries at or beyond the warp's largest last index are idle for every lane
+    const int warp_last = (int)__reduce_max_sync(kFull, thread_last);
+    const float4 band = warp_band<TW, TH, PPT>(cam, local, (int)(unit % WPT));
+    for (int bend = warp_last; bend > 0; bend -= BATCH) {
+      const int bstart = max(0, bend - BATCH);
+      __syncwarp();  // the previous batch is consumed and flushed
+      // a batch of the list, ending at bend; keep (in order) the entries whose rows meet the band
+      int cnt = 0;
+#pragma unroll
+      for (int r = 0; r < B::kRounds; ++r) {
+        const int q = bstart + r * 32 + lane;
+        bool keep = false;
+        uint32_t idx = 0;
+        float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lane < B::kLanes && q < bend) {
+          idx = (uint32_t)q < len1 ? a.vals[start + q] : a.vals2[start2 + ((uint32_t)q - len1)];
+          a1 = a.rec.a1[idx];
+          keep = a1.w >= band.z && a1.z <= band.w;
+        }
+        const unsigned km = __ballot_sync(kFull, keep);
+        if (keep) {
+          const int slot = cnt + __popc(km & lt);
+          const float4 g0 = a.rec.g0[idx];
+          s_g0[wib][slot] = g0;
+          s_g1[wib][slot] = a.rec.g1[idx];
+          s_g2[wib][slot] = a.rec.g2[idx];
+          s_a0[wib][slot] = a.rec.a0[idx];
+          s_a1[wib][slot] = make_float2(a1.x, a1.y);
+          s_rb[wib][slot] = support_rho(g0.z);
+          s_idx[wib][slot] = idx;
+          s_q[wib][slot] = q;
+        }
+        cnt += __popc(km);
+      }
+      __syncwarp();
+      for (int j = cnt - 1; j >= 0; --j) {
+        const int jj = s_q[wib][j];
+#ifdef OCGS_COUNT
+        if (lane == 0) OCGS_DIAG(2, 1);
+#endif
+        // every entry of the walk lies before warp_last, so some lane has jj < its
+        // last index; the support test of all pixels runs as straight-line code
+        const float4 g0 = s_g0[wib][j], g1 = s_g1[wib][j], g2 = s_g2[wib][j];
+        const float rb = s_rb[wib][j];
+        const SplatColumn col = splat_column(g0, g1, g2, pxf);
+        SplatHead2 hd[NP];
+        bool any = false;
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const float2 py = make_float2((float)(py0 + 2 * p) + 0.5f, (float)(py0 + 2 * p + 1) + 0.5f);
+          hd[p] = splat_head2(g0, g1, g2, col, py, rb);
+          hd[p].pass[0] = hd[p].pass[0] && jj < (int)last[2 * p];
+          hd[p].pass[1] = hd[p].pass[1] && jj < (int)last[2 * p + 1];
+          any = any || hd[p].pass[0] || hd[p].pass[1];
+        }
+        if (!__any_sync(kFull, any)) continue;  // the support misses every pixel of the band
+        const float4 ap = s_a0[wib][j];
+        const float2 an = s_a1[wib][j];
+        const float2 dx = bc2(col.dx);
+        const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
+        const float2 nho = bc2(-0.5f * g0.z);  // dalpha/drho = -alpha/2 = -o G / 2
+        float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
+#pragma unroll
+        for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
+        bool contrib = false;
+        // no per-pair branch: a candidate that is not blended has alpha = 0 and
+        // Gc = 0, which makes its weight and every term of its adjoint exactly 0
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+          const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb);
+          contrib = contrib || e.ok[0] || e.ok[1];
+          // undo the entry: T before it, its weight, and dL/dalpha
+          const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
+          const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+          const float2 Ti = __fmul2_rn(T[p], inv);
+          const float2 w = __fmul2_rn(e.alpha, Ti);
+          float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
+          F = __ffma2_rn(gC1[p], bc2(ap.y), F);
+          F = __ffma2_rn(gC2[p], bc2(ap.z), F);
+          if (GEO) {
+            F = __ffma2_rn(gD[p], e.z, F);
+            F = __ffma2_rn(__fmul2_rn(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
+            F = __ffma2_rn(gN0[p], bc2(ap.w), F);
+            F = __ffma2_rn(gN1[p], bc2(an.x), F);
+            F = __ffma2_rn(gN2[p], bc2(an.y), F);
+          }
+          // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
+          const float2 ga = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
+          S[p] = __ffma2_rn(w, F, S[p]);
+          T[p] = make_float2(e.ok[0] ? Ti.x : T[p].x, e.ok[1] ? Ti.y : T[p].y);
+          acc[kGr] = __ffma2_rn(gC0[p], w, acc[kGr]);
+          acc[kGg] = __ffma2_rn(gC1[p], w, acc[kGg]);
+          acc[kGb] = __ffma2_rn(gC2[p], w, acc[kGb]);
+          if (GEO) {
+            acc[kGnx] = __ffma2_rn(gN0[p], w, acc[kGnx]);
+            acc[kGny] = __ffma2_rn(gN1[p], w, acc[kGny]);
+            acc[kGnz] = __ffma2_rn(gN2[p], w, acc[kGnz]);
+          }
+          // alpha = o G below the clamp: dalpha/do = G, dalpha/drho = -o G / 2
+          // (Gc is 0 at the clamp and for skipped candidates)
+          const float2 gop = __fmul2_rn(ga, e.Gc);
+          acc[kGo] = __fadd2_rn(acc[kGo], gop);
+          const float2 grho = __fmul2_rn(gop, nho);
+          // rho and depth came from the surfel's (u, v) where it won the min, from the
+          // screen-space filter elsewhere.  e.r and e.rho3 are 0 where the filter won,
+          // so the surfel terms below vanish there without a mask.
+          const float2 grf = make_float2(e.surf[0] ? 0.f : grho.x, e.surf[1] ? 0.f : grho.y);
+          float2 gzs = bc2(0.f);
+          if (GEO) {
+            // d/dz of w (gD z + gQ z^2)
+            const float2 gz = __fmul2_rn(__ffma2_rn(__fmul2_rn(bc2(2.f), gQ[p]), e.z, gD[p]), w);
+            gzs = make_float2(e.surf[0] ? gz.x : 0.f, e.surf[1] ? gz.y : 0.f);
+            acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
+            acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+          }
+          const float2 r2 = __fmul2_rn(e.r, e.r);
+          const float2 gs2 = __fmul2_rn(grho, bc2(2.f));
+          const float2 gun = __fmul2_rn(__fmul2_rn(gs2, hd[p].un), r2);
+          const float2 gvn = __fmul2_rn(__fmul2_rn(gs2, hd[p].vn), r2);
+          // -dL/dden = (2 grho rho3 + gz z) / den; the e slots and c slots below
+          // accumulate negated and are flipped when the lanes are summed
+          const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
+                                   : __fmul2_rn(__fmul2_rn(gs2, e.rho3), e.r);
+          const float2 gdxs = __ffma2_rn(ngden, ng2y, __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
+          const float2 gdys = __ffma2_rn(ngden, ng2z, __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
+          acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
+          acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
+          acc[kGA10] = __ffma2_rn(gvn, dx, acc[kGA10]);
+          acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
+          acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
+          acc[kGe1] = __ffma2_rn(ngden, dx, acc[kGe1]);
+          acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
+          const float2 gf4 = __fmul2_rn(grf, bc2(4.f));
+          acc[kGcx] = __fadd2_rn(acc[kGcx], __ffma2_rn(gf4, dx, gdxs));
+          acc[kGcy] = __fadd2_rn(acc[kGcy], __ffma2_rn(gf4, hd[p].dy, gdys));
+        }
+        if (!__any_sync(kFull, contrib)) continue;  // no pixel of the band blends it
+#ifdef OCGS_COUNT
+        if (lane == 0) OCGS_DIAG(3, 1);
+        OCGS_DIAG(4, contrib ? 1 : 0);
+#endif
+        if (GEO) {
+          float gr[kGradSlots];
+#pragma unroll
+          for (int q = 0; q < NG; ++q)
+            gr[q] = negated_slot(q) ? -__fadd_rn(acc[q].x, acc[q].y) : __fadd_rn(acc[q].x, acc[q].y);
+          const int slot = warp_reduce18(gr, lane);
+          if (slot >= 0) s_grad[wib][j * kGradStride + slot] = gr[0];  // one lane per slot
+        } else {
+          // through shared memory: lane L's row holds its 13 packed sums; lane L then adds
+          // slot L & 15 over the rows 16 (L >> 4) .. 16 (L >> 4) + 15, both pixel lanes
+          float2* red = s_red[wib];
+#pragma unroll
+          for (int q = 0; q < kGradSlotsRGB; ++q) red[lane * kRedRow + q] = acc[q];
+          __syncwarp();
+          // four independent partial sums keep the dependent chain short
+          const float2* col = red + (lane >> 4) * 16 * kRedRow + red_slot;
+          float2 s4[4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i) s4[i] = col[i * kRedRow];
+#pragma unroll
+          for (int i = 4; i < 16; ++i) s4[i & 3] = __fadd2_rn(s4[i & 3], col[i * kRedRow]);
+          const float2 sum = __fadd2_rn(__fadd2_rn(s4[0], s4[1]), __fadd2_rn(s4[2], s4[3]));
+          float tot = __fadd_rn(sum.x, sum.y);
+          tot = __fadd_rn(tot, __shfl_xor_sync(kFull, tot, 16));
+          if (lane < kGradSlotsRGB) s_grad[wib][j * kGradStride + lane] = tot * red_sign;
+          __syncwarp();  // the rows are read before the next entry writes them
+        }
+      }
+      // flush the batch: one vector atomic per 4 slots and entry for the warp
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < ROWS; ++r) {
+        const int e = r * 32 + lane;
+        if (e < cnt) {
+          float4* row = reinterpret_cast<float4*>(&s_grad[wib][e * kGradStride]);
+          float4* dst = reinterpret_cast<float4*>(a.grad_rec + (size_t)s_idx[wib][e] * kGradStride);
+#pragma unroll
+          for (int q = 0; q < kGradStride / 4; ++q) {
+            const float4 g4 = row[q];
+            if (g4.x != 0.f || g4.y != 0.f || g4.z != 0.f || g4.w != 0.f) {
+              atomicAdd(dst + q, g4);
+              row[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+template <int TW, int TH, int PPT, int BATCH>
+cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
+  const unsigned grid = warp_grid<TW, TH, PPT>(a.persistent_ctas, a.n_tiles);
+  if (grid == 0) return cudaSuccess;
+  if (a.d_out.depth || a.d_out.normal || a.d_out.depth2)
+    raster_bwd_kernel<TW, TH, PPT, BATCH, true><<<grid, kBlockWarps * 32, 0, s>>>(a);
+  else raster_bwd_kernel<TW, TH, PPT, BATCH, false><<<grid, kBlockWarps * 32, 0, s>>>(a);
+  return launched();
+}
+
+}  // namespace
+
+cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, int batch,
+                                   cudaStream_t s) {
+#define OCGS_BWD(W, H, K, BT) \
+  if (tile_w == W && tile_h == H && ppt == K && batch == BT) return bwd_dispatch<W, H, K, BT>(a, s);
+  OCGS_RASTER_SHAPES(OCGS_BWD)
+#undef OCGS_BWD
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ocgs

@@ -1,0 +1,178 @@
+// Definitions shared by the forward (raster_fwd.cu) and backward
+// (raster_bwd.cu) tile rasterizers: the warp's band of a tile, the evaluation
+// of one surfel at two pixel centres of a column, and the launch shapes.
+//
+// Both passes evaluate a (pixel, surfel) candidate with the same explicitly
+// rounded intrinsics, so that the backward replays every decision of the
+// forward (skip, clamp, stop, surfel/filter branch) bit for bit, and the value
+// at a pixel depends neither on the tile shape nor on how many pixels a
+// thread owns.
+#pragma once
+
+#include "common.cuh"
+
+namespace ocgs {
+namespace raster {
+
+constexpr unsigned kFull = 0xffffffffu;
+// Warps per CTA.  Each warp owns one band of full tile rows (32 threads x PPT
+// pixels) and walks its tile's list on its own: its own queue slot, its own
+// shared-memory batches, no CTA barrier.
+constexpr int kBlockWarps = 4;
+
+// Records a warp stages in shared memory per batch: 16, 32 or 64 (the
+// Gaussians-per-batch option).  32 lanes load one record each per staging
+// round; 64 takes two rounds, 16 loads with half the lanes.
+template <int BATCH>
+struct Batch {
+  static_assert(BATCH == 16 || BATCH == 32 || BATCH == 64, "batch size");
+  static constexpr int kRounds = BATCH > 32 ? BATCH / 32 : 1;
+  static constexpr int kLanes = BATCH < 32 ? BATCH : 32;
+};
+
+#ifdef OCGS_COUNT
+// diagnostic build only: warp iterations and evaluated (lane, pixel) pairs
+extern __device__ unsigned long long g_diag[8];
+#define OCGS_DIAG(slot, v) atomicAdd(&g_diag[slot], (unsigned long long)(v))
+#else
+#define OCGS_DIAG(slot, v)
+#endif
+
+// The band of a warp: its pixel rows of the tile (32 threads x PPT rows) and
+// the tile's columns, as pixel-centre bounds clipped to the image.
+template <int TW, int TH, int PPT>
+__device__ __forceinline__ float4 warp_band(const DevCam& cam, int local, int wt) {
+  constexpr int kRows = (32 / TW) * PPT;
+  const int x0 = (local % cam.tiles_x) * TW, y0 = (local / cam.tiles_x) * TH + ((wt * 32) / TW) * PPT;
+  return make_float4((float)x0 + 0.5f, (float)(min(x0 + TW, cam.W) - 1) + 0.5f, (float)y0 + 0.5f,
+                     (float)(min(y0 + kRows, cam.H) - 1) + 0.5f);
+}
+
+// CTAs of kBlockWarps independent warps: persistent_ctas counts tile-sized CTAs
+// (TW*TH/PPT threads), converted to the same number of warps
+template <int TW, int TH, int PPT>
+unsigned warp_grid(int persistent_ctas, uint32_t n_tiles) {
+  constexpr uint64_t WPT = TW * TH / PPT / 32;
+  const uint64_t warps = (persistent_ctas ? (uint64_t)persistent_ctas : (uint64_t)n_tiles) * WPT;
+  return (unsigned)((warps + kBlockWarps - 1) / kBlockWarps);
+}
+
+// ----------------------------------------------------------------------------- one surfel at two pixels
+// The ray-splat map of a record about its projected centre (see common.cuh):
+// for (dx, dy) = x - c, u = (A00 dx + A01 dy) / den, v = (A10 dx + A11 dy) / den,
+// den = e0 + e1 dx + e2 dy.  The terms that depend only on the pixel column
+// are computed once per entry and thread.
+struct SplatColumn {
+  float dx, ux, vx, ex, dx2;
+};
+
+__device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float4 g1, const float4 g2, float px) {
+  SplatColumn c;
+  c.dx = __fsub_rn(px, g0.x);
+  c.ux = __fmul_rn(g1.x, c.dx);
+  c.vx = __fmul_rn(g1.z, c.dx);
+  c.ex = __fmaf_rn(g2.y, c.dx, g2.x);
+  c.dx2 = __fmul_rn(c.dx, c.dx);
+  return c;
+}
+
+// Two pixels of one column (rows py.x and py.y) are evaluated together on the
+// packed FP32x2 pipes of sm_100+: every lane of __ffma2_rn / __fmul2_rn /
+// __fadd2_rn rounds as the scalar operation does, so a pair gives the two
+// scalar results bit for bit with half the issued instructions.
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+__device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
+__device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
+  if (i) v.y = x;
+  else v.x = x;
+}
+
+// rb: the record's support bound support_rho(o) <= 9.  Candidates with
+// rho > rb have o exp(-rho/2) < 1/255, so testing rb instead of 9 first only
+// skips work; every decision is the one the 9 cut and the 1/255 floor give.
+// The evaluation is split so that a thread runs the cheap support test of all
+// its pixels as straight-line code (head) before the rest (tail).
+struct SplatHead2 {
+  float2 dy, un, vn, den, rho2, q;
+  bool in3[2];   // the surfel term is within its support: u^2 + v^2 <= rb
+  bool pass[2];  // in3, or the screen filter term rho2 <= rb
+};
+
+// EWA: a projected 3D Gaussian (constant denominator, the screen filter already
+// folded into its covariance): the support test is the Mahalanobis term alone.
+// in3 needs no separate den != 0 test: with den = 0 the limit is 0, so only
+// q = 0 passes, and then rho3 = 0 * inf is NaN, the surfel branch is not taken
+// and every decision is the one the test would have given.
+template <bool EWA = false>
+__device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
+                                                  const SplatColumn& c, float2 py, float rb) {
+  SplatHead2 h;
+  h.dy = __fadd2_rn(py, bc2(-g0.y));
+  h.un = __ffma2_rn(bc2(g1.y), h.dy, bc2(c.ux));
+  h.vn = __ffma2_rn(bc2(g1.w), h.dy, bc2(c.vx));
+  h.den = __ffma2_rn(bc2(g2.z), h.dy, bc2(c.ex));
+  h.rho2 = __fmul2_rn(bc2(kInvSigmaF2), __ffma2_rn(h.dy, h.dy, bc2(c.dx2)));
+  h.q = __ffma2_rn(h.un, h.un, __fmul2_rn(h.vn, h.vn));
+  const float2 lim = __fmul2_rn(bc2(rb), __fmul2_rn(h.den, h.den));
+  h.in3[0] = h.q.x <= lim.x;
+  h.in3[1] = h.q.y <= lim.y;
+  h.pass[0] = h.in3[0] || (!EWA && h.rho2.x <= rb);
+  h.pass[1] = h.in3[1] || (!EWA && h.rho2.y <= rb);
+  return h;
+}
+
+struct SplatEval2 {
+  float2 r, rho3;   // 1 / den and the surfel rho (FINITE: zeroed where the filter term won)
+  float2 Gc;        // dalpha/do: G where the candidate blends below the 0.99 clamp, else 0
+  float2 alpha;     // the blended opacity min(0.99, o G), 0 where the candidate is skipped
+  float2 z;         // depth of the hit (surfel term) or of the centre (filter term)
+  bool surf[2];     // the surfel term won the min (else the screen filter)
+  bool ok[2];       // pass, rho <= rb and o G >= 1/255: blended unless the pixel stops
+};
+
+// FINITE (backward): r and rho3 are zeroed where the filter term won, so that
+// products the backward masks with zero stay finite (the forward reads z only).
+// A skipped candidate gets alpha = 0 (T (1 - 0) = T and w = 0 exactly) and
+// Gc = 0, which zeroes every term of its adjoint without further masks.
+template <bool FINITE, bool EWA = false>
+__device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
+  SplatEval2 e;
+  // where in3 is false the reciprocal is never used unmasked (surf is false)
+  const float2 r = EWA ? bc2(1.0f) : make_float2(__fdividef(1.0f, h.den.x), __fdividef(1.0f, h.den.y));
+  const float2 r3 = EWA ? h.q : __fmul2_rn(h.q, __fmul2_rn(r, r));
+  e.surf[0] = h.in3[0] && (EWA || r3.x <= h.rho2.x);
+  e.surf[1] = h.in3[1] && (EWA || r3.y <= h.rho2.y);
+  if (FINITE) {
+    e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
+    e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
+  } else {
+    e.r = r;
+    e.rho3 = r3;
+  }
+  const float2 rho = make_float2(e.surf[0] ? r3.x : h.rho2.x, e.surf[1] ? r3.y : h.rho2.y);
+  const float2 ex = __fmul2_rn(bc2(-0.5f), rho);
+  const float2 G = make_float2(__expf(ex.x), __expf(ex.y));
+  const float2 oG = __fmul2_rn(bc2(g0.z), G);
+  // min(0.99, o G) >= 1/255 exactly when o G >= 1/255
+  e.ok[0] = h.pass[0] && (rho.x <= rb) && (oG.x >= kAlphaMin);
+  e.ok[1] = h.pass[1] && (rho.y <= rb) && (oG.y >= kAlphaMin);
+  e.alpha = make_float2(e.ok[0] ? fminf(kAlphaMax, oG.x) : 0.0f, e.ok[1] ? fminf(kAlphaMax, oG.y) : 0.0f);
+  if (FINITE)
+    e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);
+  const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
+  e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);
+  return e;
+}
+
+}  // namespace raster
+
+// ----------------------------------------------------------------------------- launch shapes
+// The tile shapes and pixels per thread the rasterizers are built for, with
+// the batch sizes each shape offers (every shape has 32; the 16-wide shapes
+// also 16 and 64).
+#define OCGS_RASTER_SHAPES(X)                                                             \
+  X(16, 16, 1, 32) X(16, 16, 2, 32) X(16, 16, 4, 32) X(16, 8, 1, 32) X(16, 8, 2, 32)     \
+  X(16, 8, 4, 32) X(8, 8, 1, 32) X(8, 8, 2, 32) X(32, 8, 1, 32) X(32, 8, 2, 32)           \
+  X(16, 16, 2, 16) X(16, 16, 4, 16) X(16, 8, 4, 16) X(16, 16, 2, 64) X(16, 16, 4, 64) X(16, 8, 4, 64)
+
+}  // namespace ocgs

@@ -47,12 +47,21 @@ def look_at(position, target=(0.0, 0.0, 0.0), up=(0.0, 0.0, 1.0)) -> np.ndarray:
     return vm
 
 
+def _f32(x):
+    """The nearest float32 value, as float64: the library's camera is float32, so both
+    sides of a comparison see the same camera numbers."""
+    return np.asarray(x, np.float32).astype(np.float64)
+
+
 def make_camera(position, width: int, height: int, fov_x_deg: float = FOV_X_DEG,
-                near: float = NEAR, target=(0.0, 0.0, 0.0)) -> dict:
-    """Pinhole camera with a horizontal field of view and the principal point at the centre."""
-    fx = (width / 2.0) / math.tan(math.radians(fov_x_deg) / 2.0)
-    return dict(viewmat=look_at(position, target), fx=fx, fy=fx, cx=width / 2.0,
-                cy=height / 2.0, width=int(width), height=int(height), near=float(near))
+                near: float = NEAR, target=(0.0, 0.0, 0.0), f32: bool = True) -> dict:
+    """Pinhole camera with a horizontal field of view and the principal point at the centre.
+    With ``f32`` (the default) every number is float32-representable, as the library holds
+    it; without, the rotation is exactly orthonormal (for world-space checks of the oracle)."""
+    rnd = _f32 if f32 else (lambda x: np.asarray(x, np.float64))
+    fx = float(rnd((width / 2.0) / math.tan(math.radians(fov_x_deg) / 2.0)))
+    return dict(viewmat=rnd(look_at(position, target)), fx=fx, fy=fx, cx=float(rnd(width / 2.0)),
+                cy=float(rnd(height / 2.0)), width=int(width), height=int(height), near=float(rnd(near)))
 
 
 def hemisphere_positions(rng: np.random.Generator, n: int, radius: float) -> np.ndarray:
@@ -186,13 +195,15 @@ def config2(seed: int = 2, n: int = 100_000, width: int = 800, height: int = 800
 
 
 def config3(seed: int = 3, n_views: int = 100, width: int = 800, height: int = 800,
-            shell_counts=(60_000, 60_000, 60_000), n_interior: int = 120_000) -> dict:
+            shell_counts=(60_000, 60_000, 60_000), n_interior: int = 120_000,
+            shell_scale=(0.04, 0.06)) -> dict:
     """Occlusion pruning sweep: three dense tangent shells hide an interior cloud.
 
     Shell radii 1.00, 0.97, 0.94; shell surfels are tangent to the sphere
-    (normal radial), scales U(0.04, 0.06), opacity 0.95; the interior surfels
-    sit in r < 0.7 with the config-2 scale law.  Cameras sit on the upper
-    hemisphere of radius 3 and look at the origin.
+    (normal radial), scales U(shell_scale) (default U(0.04, 0.06)), opacity
+    0.95; the interior surfels sit in r < 0.7 with the config-2 scale law.
+    Cameras sit on the upper hemisphere of radius 3 and look at the origin.
+    A scaled-down scene keeps the shells closed with fewer, larger surfels.
     """
     rng = np.random.default_rng(seed)
     xyz, quat, scale, opac = [], [], [], []
@@ -201,7 +212,7 @@ def config3(seed: int = 3, n_views: int = 100, width: int = 800, height: int = 8
         d /= np.linalg.norm(d, axis=1, keepdims=True)
         xyz.append(d * r)
         quat.append(quats_with_normal(rng, d))
-        scale.append(rng.uniform(0.04, 0.06, size=(m, 2)))
+        scale.append(rng.uniform(shell_scale[0], shell_scale[1], size=(m, 2)))
         opac.append(np.full(m, 0.95))
     xyz.append(uniform_ball(rng, n_interior, 0.7))
     quat.append(random_quats(rng, n_interior))

@@ -70,7 +70,7 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
 
 
 def test_status_strings_and_version(lib):
-    assert lib.ocgs_abi_version() == 3
+    assert lib.ocgs_abi_version() == 4
     assert lib.ocgs_status_str(0) == b"OCGS_OK"
     assert lib.ocgs_status_str(5) == b"OCGS_ERR_NONFINITE"
     assert lib.ocgs_status_str(99) == b"OCGS_ERR_UNKNOWN"

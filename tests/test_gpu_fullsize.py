@@ -13,7 +13,8 @@ import torch
 
 import oracle
 import synthetic
-from _helpers import FWD_TOL, GRAD_TOL, KEYS, OUT_KEYS, forward_errors, grad_errors, to_device
+from _helpers import (FWD_TOL, GRAD_TOL, KEYS, OUT_KEYS, add_grads, forward_errors, grad_errors, oracle_adjoint,
+                      to_device, worst_element)
 
 pytestmark = pytest.mark.gpu
 
@@ -84,15 +85,15 @@ def test_c2_gradient_of_sampled_l1_plus_background_loss(rast, dev, c2):
     d_rgb = np.sign(c - target) * mask[px, None] / (3 * len(px))
     d_alpha = 0.5 * (1.0 - mask[px]) / P
     d_ref = dict(rgb=d_rgb, alpha=d_alpha, depth=np.zeros(len(px)), normal=np.zeros((len(px), 3)))
-    ref = oracle.render(sc["gaussians"], cam, pixels=px, d_out=d_ref)
+    ref, ref32 = oracle_adjoint(sc["gaussians"], cam, d_ref, pixels=px)
     full_rgb = torch.zeros(P, 3, device=dev)
     full_a = torch.zeros(P, device=dev)
     idx = torch.as_tensor(px, device=dev)
     full_rgb[idx] = torch.tensor(d_rgb, dtype=torch.float32, device=dev)
     full_a[idx] = torch.tensor(d_alpha, dtype=torch.float32, device=dev)
     grads = rast.render_backward(state, g, {"rgb": full_rgb, "alpha": full_a})
-    errs = grad_errors(grads, ref["grads"])
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(grads, ref, ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(grads, ref, k, ref32) for k in KEYS})
 
 
 def test_c2_gradient_against_central_differences(rast, dev, c2):
@@ -200,30 +201,27 @@ def test_c4_batched_forward_and_gradient_at_sampled_pixels(rast, dev):
     off = pixel_offsets(cams)
     P = off[-1]
     full = {k: torch.zeros((P, 3) if k in ("rgb", "normal") else (P,), device=dev) for k in OUT_KEYS}
-    grads_ref = {k: 0.0 for k in KEYS}
+    grads_ref, grads_ref32 = {}, {}
     rng = np.random.default_rng(40)
     worst = 0.0
     for v, cam in enumerate(cams):
-        px = _sample(cam, 40, 400 + v)
+        px = _sample(cam, 256, 400 + v)
         d = dict(rgb=rng.normal(size=(len(px), 3)), alpha=rng.normal(size=len(px)), depth=rng.normal(size=len(px)),
                  normal=rng.normal(size=(len(px), 3)))
-        ref = oracle.render(sc["gaussians"], cam, pixels=px, d_out=d)
-        if ref["fragile_grad"].any():  # give fragile pixels no cotangent on either side
-            keep = ~ref["fragile_grad"]
-            d = {k: np.where(keep.reshape((-1,) + (1,) * (x.ndim - 1)), x, 0.0) for k, x in d.items()}
-            ref = oracle.render(sc["gaussians"], cam, pixels=px, d_out=d)
-        ok = ~ref["fragile"]
-        errs = forward_errors(_gather(out, px + off[v]), ref, ok)
+        probe = oracle.render(sc["gaussians"], cam, pixels=px)
+        keep = ~probe["fragile_grad"]  # give fragile pixels no cotangent on either side
+        d = {k: np.where(keep.reshape((-1,) + (1,) * (x.ndim - 1)), x, 0.0) for k, x in d.items()}
+        errs = forward_errors(_gather(out, px + off[v]), probe, ~probe["fragile"])
         worst = max(worst, max(errs.values()))
+        ref, ref32 = oracle_adjoint(sc["gaussians"], cam, d, pixels=px)
         idx = torch.as_tensor(px + off[v], device=dev)
         for k in OUT_KEYS:
             full[k][idx] = torch.tensor(d[k], dtype=torch.float32, device=dev)
-        for k in KEYS:
-            grads_ref[k] = grads_ref[k] + ref["grads"][k]
+        grads_ref, grads_ref32 = add_grads(grads_ref, ref), add_grads(grads_ref32, ref32)
     assert worst <= FWD_TOL, worst
     grads = rast.render_backward(state, g, full)
-    errs = grad_errors(grads, grads_ref)
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(grads, grads_ref, grads_ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(grads, grads_ref, k, grads_ref32) for k in KEYS})
     a = out["alpha"]
     assert float(a.min()) >= 0.0 and float(a.max()) < 1.0
 
@@ -231,10 +229,10 @@ def test_c4_batched_forward_and_gradient_at_sampled_pixels(rast, dev):
 # ----------------------------------------------------------------------------- config 5: training iteration, 1M x 64 views
 def test_c5_training_iteration_at_sampled_pixels(rast, dev):
     """One full iteration at the config-5 size (1M surfels, 64 views 1600x1200) in the launch
-    configuration bench.py times: the batched forward at sampled pixels of four views against
-    the oracle; the gradient of a colour + opacity loss restricted to those samples against the
-    oracle adjoint (the backward instantiation without depth and normal cotangents, as in the
-    training step); the Adam update against the oracle applied to the GPU's own gradient at
+    configuration bench.py times: the batched forward at sampled pixels against the oracle
+    (128 pixels on each of eight views); the gradient of a colour + opacity loss restricted
+    to those samples against the oracle adjoint (the backward instantiation without depth
+    and normal cotangents, as in the training step); the Adam update against the oracle applied to the GPU's own gradient at
     sampled elements; the pruning of parameters and of both moments with one keep-set."""
     sc = synthetic.config5()
     cams = sc["cameras"]
@@ -248,32 +246,29 @@ def test_c5_training_iteration_at_sampled_pixels(rast, dev):
     out, state = rast.render(g, cams, score=score)
     full_rgb = torch.zeros(P, 3, device=dev)
     full_alpha = torch.zeros(P, device=dev)
-    grads_ref = {k: 0.0 for k in KEYS}
+    grads_ref, grads_ref32 = {}, {}
     rng = np.random.default_rng(50)
     worst = 0.0
-    for v in (0, 21, 42, 63):
+    for v in (0, 9, 18, 27, 36, 45, 54, 63):
         cam = cams[v]
-        px = _sample(cam, 24, 500 + v)
+        px = _sample(cam, 128, 500 + v)
         d = dict(rgb=rng.normal(size=(len(px), 3)), alpha=rng.normal(size=len(px)), depth=np.zeros(len(px)),
                  normal=np.zeros((len(px), 3)))
-        ref = oracle.render(g_np, cam, pixels=px, d_out=d)
-        if ref["fragile_grad"].any():  # no cotangent on either side at fragile pixels
-            keep = ~ref["fragile_grad"]
-            d = {k: np.where(keep.reshape((-1,) + (1,) * (x.ndim - 1)), x, 0.0) for k, x in d.items()}
-            ref = oracle.render(g_np, cam, pixels=px, d_out=d)
-        ok = ~ref["fragile"]
-        errs = forward_errors(_gather(out, px + off[v]), ref, ok)
+        probe = oracle.render(g_np, cam, pixels=px)
+        keep = ~probe["fragile_grad"]  # no cotangent on either side at fragile pixels
+        d = {k: np.where(keep.reshape((-1,) + (1,) * (x.ndim - 1)), x, 0.0) for k, x in d.items()}
+        errs = forward_errors(_gather(out, px + off[v]), probe, ~probe["fragile"])
         worst = max(worst, max(errs.values()))
+        ref, ref32 = oracle_adjoint(g_np, cam, d, pixels=px)
         idx = torch.as_tensor(px + off[v], device=dev)
         full_rgb[idx] = torch.tensor(d["rgb"], dtype=torch.float32, device=dev)
         full_alpha[idx] = torch.tensor(d["alpha"], dtype=torch.float32, device=dev)
-        for k in KEYS:
-            grads_ref[k] = grads_ref[k] + ref["grads"][k]
+        grads_ref, grads_ref32 = add_grads(grads_ref, ref), add_grads(grads_ref32, ref32)
     assert worst <= FWD_TOL, worst
     grads = rast.render_backward(state, g, {"rgb": full_rgb, "alpha": full_alpha})
     state.release()
-    errs = grad_errors(grads, grads_ref)
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(grads, grads_ref, grads_ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(grads, grads_ref, k, grads_ref32) for k in KEYS})
 
     lr = dict(xyz=1.6e-4, quat=1e-3, scale=5e-3, opacity=5e-2, sh=2.5e-3)
     params = {k: v.clone() for k, v in g.items()}

@@ -13,8 +13,8 @@ import torch
 
 import oracle
 import synthetic
-from _helpers import (FWD_TOL, GRAD_TOL, KEYS, OUT_KEYS, forward_errors, gpu_at, grad_errors, masked,
-                      to_device)
+from _helpers import (FWD_TOL, KEYS, OUT_KEYS, forward_errors, gpu_at, grad_errors, masked, oracle_adjoint,
+                      to_device, worst_element)
 
 pytestmark = pytest.mark.gpu
 
@@ -91,11 +91,11 @@ def test_backward_matches_oracle_adjoint(rast, dev, seed, n, w, h, deg):
     ok = ~probe["fragile_grad"]
     assert ok.mean() > 0.97
     d_out = {k: masked(v, ok) for k, v in d_out.items()}
-    ref = oracle.render(g_np, cam, d_out=d_out)
+    ref, ref32 = oracle_adjoint(g_np, cam, d_out)
     grads = rast.render_backward(state, g, {k: torch.tensor(v, dtype=torch.float32, device=dev)
                                             for k, v in d_out.items()})
-    errs = grad_errors(grads, ref["grads"])
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(grads, ref, ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(grads, ref, k, ref32) for k in KEYS})
 
 
 def test_backward_single_plane_cotangents(rast, dev):
@@ -111,12 +111,12 @@ def test_backward_single_plane_cotangents(rast, dev):
                 normal=rng.normal(size=(P, 3)))
     for key in OUT_KEYS:
         d = {k: (masked(v, ok) if k == key else np.zeros_like(v)) for k, v in full.items()}
-        ref = oracle.render(g_np, cam, d_out=d)
+        ref, ref32 = oracle_adjoint(g_np, cam, d)
         grads = rast.render_backward(state, g, {key: torch.tensor(d[key], dtype=torch.float32, device=dev)})
-        errs = grad_errors(grads, ref["grads"])
+        errs = grad_errors(grads, ref, ref32)
         # opacity-only and colour-only planes leave some parameter groups at exactly zero
-        errs = {k: e for k, e in errs.items() if np.abs(ref["grads"][k]).max() > 0}
-        assert max(errs.values()) <= GRAD_TOL, (key, errs)
+        errs = {k: e for k, e in errs.items() if np.abs(ref[k]).max() > 0}
+        assert max(errs.values()) <= 1.0, (key, errs)
 
 
 def test_tile_shapes_and_persistent_queue_give_identical_results(dev):
@@ -125,10 +125,13 @@ def test_tile_shapes_and_persistent_queue_give_identical_results(dev):
     g = to_device(sc["gaussians"], dev)
     cams = sc["cameras"]
     base = None
-    combos = [(t, k) for t in ((16, 16), (16, 8), (8, 8), (32, 8)) for k in (1, 2)] + [((16, 16), 4)]
-    for tile, ppt in combos:
+    combos = [(t, k, 32) for t in ((16, 16), (16, 8), (8, 8), (32, 8)) for k in (1, 2)] + [((16, 16), 4, 32)]
+    # Gaussians per batch where the shape offers it
+    combos += [((16, 16), 4, 16), ((16, 16), 4, 64), ((16, 16), 2, 16), ((16, 16), 2, 64), ((16, 8), 4, 16),
+               ((16, 8), 4, 64)]
+    for tile, ppt, batch in combos:
         for persistent in (False, True):
-            r = Rasterizer(dev, tile=tile, persistent=persistent, pixels_per_thread=ppt)
+            r = Rasterizer(dev, tile=tile, persistent=persistent, pixels_per_thread=ppt, batch=batch)
             score = torch.zeros(len(sc["gaussians"]["opacity"]), device=dev)
             out, _ = r.render(g, cams, score=score, keep_state=False)
             torch.cuda.synchronize()
@@ -138,8 +141,19 @@ def test_tile_shapes_and_persistent_queue_give_identical_results(dev):
                 base = cur
             else:
                 for k in base:
-                    assert torch.equal(base[k], cur[k]), (tile, ppt, persistent, k)
+                    assert torch.equal(base[k], cur[k]), (tile, ppt, batch, persistent, k)
             r.close()
+    # the two-pass split of persistent renders
+    for front in (0.0, 0.02, 0.3, 1.0):
+        r = Rasterizer(dev, tile=(16, 16), persistent=True, pixels_per_thread=4, front_fraction=front)
+        score = torch.zeros(len(sc["gaussians"]["opacity"]), device=dev)
+        out, _ = r.render(g, cams, score=score, keep_state=False)
+        torch.cuda.synchronize()
+        cur = {k: v.cpu() for k, v in out.items()}
+        cur["score"] = score.cpu()
+        for k in base:
+            assert torch.equal(base[k], cur[k]), (front, k)
+        r.close()
 
 
 def test_batched_views_equal_per_view_launches(rast, dev):
@@ -272,7 +286,8 @@ def test_autotune_picks_valid_options_and_caches_them(dev, tmp_path):
     before = {k: v.clone() for k, v in before.items()}
     cache = tmp_path / "tune.txt"
     res = r.autotune(g, sc["cameras"], cache_path=cache)
-    assert res["n_tried"] >= 10 and not res["from_cache"] and res["ms"] > 0
+    assert res["n_tried"] >= 14 and not res["from_cache"] and res["ms"] > 0
+    assert res["batch"] in (16, 32, 64) and 0.0 <= res["front_fraction"] <= 1.0
     after, _ = r.render(g, sc["cameras"], keep_state=False)
     torch.cuda.synchronize()
     for k in OUT_KEYS:  # options change the time, never the result
@@ -280,6 +295,10 @@ def test_autotune_picks_valid_options_and_caches_them(dev, tmp_path):
     r2 = Rasterizer(dev)
     res2 = r2.autotune(g, sc["cameras"], cache_path=cache)
     assert res2["from_cache"] and res2["tile"] == res["tile"] and res2["pixels_per_thread"] == res["pixels_per_thread"]
+    assert res2["batch"] == res["batch"] and res2["front_fraction"] == pytest.approx(res["front_fraction"])
+    assert r2.options() == dict(tile=res["tile"], persistent=res["persistent"],
+                                pixels_per_thread=res["pixels_per_thread"], front_fraction=res2["front_fraction"],
+                                batch=res["batch"])
     r.close()
     r2.close()
 
@@ -314,3 +333,46 @@ def test_captured_sweep_equals_eager_sweep_and_reports_overflow(dev):
         g["scale"].div_(3.0)
         graph.close()
         r.close()
+
+
+@pytest.mark.parametrize("opts", [dict(), dict(tile=(16, 16), persistent=True, pixels_per_thread=4)])
+def test_config3_geometry_keep_set_matches_oracle(dev, opts):
+    """Config 3's geometry scaled down (three closed tangent shells of 900 surfels around 400
+    interior surfels, 8 hemisphere views of 64x64).  Scores are compared within 1e-5 and the
+    keep-set at tau = 0.01 exactly (borderline scores listed) for every surfel whose score is
+    certain in float32: not itself at a fragile threshold at any pixel and with its largest
+    weight at a firm pixel; the others (listed, a few percent at most) keep their firm lower
+    bound.  The paper's rule (tau = 0) is checked the same way, and the interior hidden behind
+    the shells is pruned."""
+    from paper_2501_08174_gb300 import Rasterizer
+    sc = synthetic.config3(seed=33, n_views=8, width=64, height=64, shell_counts=(900, 900, 900),
+                           n_interior=400, shell_scale=(0.09, 0.12))
+    g_np = sc["gaussians"]
+    refs = [oracle.render(g_np, c) for c in sc["cameras"]]
+    ref = np.max([r["score"] for r in refs], axis=0)
+    firm = np.max([r["score_firm"] for r in refs], axis=0)
+    uncertain = np.any([r["at_edge"] for r in refs], axis=0) | (ref > firm)
+    assert sum(r["fragile"].sum() for r in refs) < 0.01 * sum(r["fragile"].size for r in refs)
+    assert uncertain.mean() < 0.03, int(uncertain.sum())
+    r = Rasterizer(dev, **opts)
+    g = to_device(g_np, dev)
+    score = r.accumulate_contribution(g, sc["cameras"])
+    s = score.cpu().numpy()
+    sure = ~uncertain
+    assert np.abs(s - ref)[sure].max() <= 1e-5
+    assert (s[uncertain] >= firm[uncertain] - 1e-5).all()
+    tau = 0.01
+    keep_ref, near_ref = oracle.keep_set(ref, tau)
+    kept, border, n_border = r.prune(g, score, tau)
+    keep_gpu = s > tau
+    near = np.abs(ref - tau) <= 1e-6
+    checked = sure & ~near
+    assert (keep_gpu[checked] == keep_ref[checked]).all(), np.nonzero(keep_gpu[checked] != keep_ref[checked])
+    np.testing.assert_array_equal(np.sort(border.cpu().numpy()), np.nonzero(np.abs(s - tau) <= 1e-6)[0])
+    kept_ref = oracle.prune(g_np, keep_gpu)
+    for k in KEYS:
+        np.testing.assert_array_equal(kept[k].cpu().numpy(), np.asarray(kept_ref[k], np.float32))
+    assert ((s > 0) == (ref > 0))[sure].all()          # the paper's "used in blending" rule
+    interior = slice(sc["n_shell"], None)
+    assert not keep_gpu[interior].any() and keep_ref[:sc["n_shell"]].mean() > 0.5
+    r.close()

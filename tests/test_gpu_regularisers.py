@@ -1,12 +1,13 @@
 """The 2DGS regularisers of Eq. 3 on the GPU against the FP64 oracle: the Q = sum w z^2
 plane of the forward, the backward with its cotangent, the depth distortion and the
 normal consistency with their adjoints, and the parameter gradients they produce.
+Both losses are also compared with the oracle's losses on the oracle's own planes.
 
 The regularisers are checked in two parts: their arithmetic on the GPU's own planes
 (FP64 sums of FP32 planes: 1e-6 relative on the losses; 1e-4 of the largest entry on the
 FP32 adjoints, whose normal-consistency part goes through central differences of the
 expected depth and a normalisation), and the planes themselves against the oracle
-(forward bar 1e-4).  Parameter gradients meet the gradient bar (1e-3 relative).
+(forward bar 1e-4).  Parameter gradients meet the element-wise gradient bar (_helpers.grad_bar).
 """
 import numpy as np
 import pytest
@@ -14,7 +15,7 @@ import torch
 
 import oracle
 import synthetic
-from _helpers import FWD_TOL, GRAD_TOL, KEYS, grad_errors, to_device
+from _helpers import FWD_TOL, KEYS, add_grads, grad_errors, oracle_adjoint, to_device, worst_element
 
 pytestmark = pytest.mark.gpu
 
@@ -69,13 +70,13 @@ def test_backward_with_a_depth2_cotangent(rast, scene):
     keep = ~ref0["fragile_grad"]
     d = dict(rgb=np.zeros((P, 3)), alpha=rng.normal(size=P) * keep, depth=np.zeros(P),
              normal=np.zeros((P, 3)), depth2=rng.normal(size=P) * keep)
-    ref = oracle.render(sc["gaussians"], cam, d_out=d)
+    ref, ref32 = oracle_adjoint(sc["gaussians"], cam, d)
     out, st = rast.render(g, [cam], depth2=True)
     grads = rast.render_backward(st, g, {k: torch.tensor(d[k], dtype=torch.float32, device=dev)
                                          for k in ("alpha", "depth2")})
     st.release()
-    errs = grad_errors(grads, ref["grads"])
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(grads, ref, ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(grads, ref, k, ref32) for k in KEYS})
 
 
 def test_depth_distortion_loss_adjoint_and_parameter_gradient(rast, scene):
@@ -97,7 +98,7 @@ def test_depth_distortion_loss_adjoint_and_parameter_gradient(rast, scene):
     pgrads = rast.render_backward(st, g, grads_img)
     st.release()
     torch.cuda.synchronize()
-    grads_ref = {k: 0.0 for k in KEYS}
+    grads_ref, grads_ref32 = {}, {}
     for v, cam in enumerate(cams):
         sl = slice(off[v], off[v + 1])
         # the kernel's arithmetic on its own planes
@@ -113,11 +114,10 @@ def test_depth_distortion_loss_adjoint_and_parameter_gradient(rast, scene):
         keep = ~ref["fragile_grad"]
         n = cam["width"] * cam["height"]
         d = dict(rgb=np.zeros((n, 3)), alpha=ra * keep, depth=rd * keep, normal=np.zeros((n, 3)), depth2=rq * keep)
-        gr = oracle.render(sc["gaussians"], cam, d_out=d)["grads"]
-        for k in KEYS:
-            grads_ref[k] = grads_ref[k] + gr[k]
-    errs = grad_errors(pgrads, grads_ref)
-    assert max(errs.values()) <= GRAD_TOL, errs
+        gr, gr32 = oracle_adjoint(sc["gaussians"], cam, d)
+        grads_ref, grads_ref32 = add_grads(grads_ref, gr), add_grads(grads_ref32, gr32)
+    errs = grad_errors(pgrads, grads_ref, grads_ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(pgrads, grads_ref, k, grads_ref32) for k in KEYS})
 
 
 def test_normal_consistency_loss_and_adjoint(rast, scene):
@@ -141,7 +141,7 @@ def test_normal_consistency_loss_and_adjoint(rast, scene):
     st.release()
     torch.cuda.synchronize()
     counted = 0
-    grads_ref = {k: 0.0 for k in KEYS}
+    grads_ref, grads_ref32 = {}, {}
     for v, cam in enumerate(cams):
         sl = slice(off[v], off[v + 1])
         a, dp, nr = _host(out["alpha"][sl]), _host(out["depth"][sl]), _host(out["normal"][sl])
@@ -150,13 +150,19 @@ def test_normal_consistency_loss_and_adjoint(rast, scene):
         assert float(loss[v]) == pytest.approx(l_own, rel=1e-5, abs=1e-9)
         for got, want in ((own["alpha"][sl], ga), (own["depth"][sl], gd), (own["normal"][sl], gn)):
             assert np.abs(_host(got) - want).max() <= 1e-4 * np.abs(want).max() + 1e-12
+        # the oracle's own loss on its planes: no pixel lies within the forward bar of a_min, so
+        # both sides count the same pixels; plane errors of 1e-4 relative move this loss by
+        # < 1e-4 relative on this scene, so the 1e-3 bar of the depth distortion applies
+        ref = refs[v]
+        assert np.abs(ref["alpha"] - 0.5).min() > FWD_TOL
+        l_ref = oracle.normal_consistency(ref["alpha"], ref["depth"], ref["normal"], cam, weight=0.05, a_min=0.5)[0]
+        assert float(loss[v]) == pytest.approx(l_ref, rel=1e-3, abs=1e-6)
         # the parameter gradient of these cotangents through the oracle's adjoint
         n = cam["width"] * cam["height"]
         d = dict(rgb=np.zeros((n, 3)), alpha=_host(gi["alpha"][sl]), depth=_host(gi["depth"][sl]),
                  normal=_host(gi["normal"][sl]).reshape(n, 3))
-        gr = oracle.render(sc["gaussians"], cam, d_out=d)["grads"]
-        for k in KEYS:
-            grads_ref[k] = grads_ref[k] + gr[k]
+        gr, gr32 = oracle_adjoint(sc["gaussians"], cam, d)
+        grads_ref, grads_ref32 = add_grads(grads_ref, gr), add_grads(grads_ref32, gr32)
     assert counted > 200                      # the scene has covered pixels to check
-    errs = grad_errors(pgrads, grads_ref)
-    assert max(errs.values()) <= GRAD_TOL, errs
+    errs = grad_errors(pgrads, grads_ref, grads_ref32)
+    assert max(errs.values()) <= 1.0, (errs, {k: worst_element(pgrads, grads_ref, k, grads_ref32) for k in KEYS})

@@ -291,7 +291,8 @@ def _brute_force(g, cam):
 @pytest.mark.parametrize("seed", [21, 22])
 def test_brute_force_tiny_scene(seed):
     sc = synthetic.small_scene(seed, 8, 16, 16, degree=1, scale_range=(0.2, 0.6))
-    g, cam = sc["gaussians"], sc["cameras"][0]
+    g = sc["gaussians"]
+    cam = synthetic.make_camera((0.3, -3.0, 0.4), 16, 16, f32=False)  # orthonormal, for the world-space solve
     g = {k: (np.asarray(v, np.float64) if k != "sh_degree" else v) for k, v in g.items()}
     r = oracle.render(g, cam, prefilter=False)
     bf = _brute_force(g, cam)
@@ -606,6 +607,42 @@ def test_depth_distortion_equals_brute_force_pairs():
     ld, ga, gd, gq = oracle.depth_distortion(np.array(A), np.array(D), np.array(Q), weight=1.0)
     assert ld == pytest.approx(np.mean(ref), rel=1e-12)
     np.testing.assert_allclose(gq, 2 * np.array(A) / 6, rtol=1e-12)   # d/dQ of the mean of 2 (A Q - D^2)
+
+
+def test_depth_distortion_pairs_brute_force_against_the_planes():
+    """The brute-force pair sums over each pixel's blended entries: the squared reading equals
+    2 (A Q - D^2) of the rendered planes at every pixel (which pins the Q plane and the closed
+    form), and the printed |z_i - z_j| form of two stacked surfels is 2 w1 w2 |z1 - z2|."""
+    sc = synthetic.small_scene(41, 250, 24, 20, degree=1, scale_range=(0.05, 0.3))
+    r = oracle.render(sc["gaussians"], sc["cameras"][0], pair_powers=(1, 2))
+    closed = 2.0 * (r["alpha"] * r["depth2"] - r["depth"] ** 2)
+    np.testing.assert_allclose(r["distortion_pairs_2"], closed, rtol=1e-9, atol=1e-12)
+    assert (r["n_blended"] >= 2).sum() > 50 and r["distortion_pairs_1"].max() > 0
+    cam = cam65()
+    o1, o2 = 0.6, 0.7
+    g = surfels([[0, 0, 0], [0, 0.5, 0]], [Q_FACE] * 2, [[0.1, 0.1]] * 2, [o1, o2], [[0.5, 0.5, 0.5]] * 2)
+    two = oracle.render(g, cam, pix(cam, 32, 32), pair_powers=(1, 2))
+    w1, w2 = o1, (1 - o1) * o2
+    assert two["distortion_pairs_1"][0] == pytest.approx(2 * w1 * w2 * 0.5, abs=1e-12)
+    assert two["distortion_pairs_2"][0] == pytest.approx(2 * w1 * w2 * 0.25, abs=1e-12)
+
+
+def test_prune_keeps_the_flagged_surfels_in_order():
+    """A hand case: five surfels, keep-set {score > 0.01} of the scores below keeps rows 1 and 3
+    (score 0.01 itself is not kept), each array sliced the same way, order preserved."""
+    g = dict(xyz=np.arange(15.0).reshape(5, 3), quat=np.arange(20.0).reshape(5, 4),
+             scale=np.arange(10.0).reshape(5, 2), opacity=np.array([0.1, 0.2, 0.3, 0.4, 0.5]),
+             sh=np.arange(15.0).reshape(5, 1, 3), sh_degree=0)
+    keep, near = oracle.keep_set(np.array([0.0, 0.5, 0.01, 0.02, 0.0099995]), 0.01)
+    assert keep.tolist() == [False, True, False, True, False]
+    assert near.tolist() == [2, 4]
+    out = oracle.prune(g, keep)
+    assert out["xyz"].tolist() == [[3.0, 4.0, 5.0], [9.0, 10.0, 11.0]]
+    assert out["quat"].tolist() == [[4.0, 5.0, 6.0, 7.0], [12.0, 13.0, 14.0, 15.0]]
+    assert out["scale"].tolist() == [[2.0, 3.0], [6.0, 7.0]]
+    assert out["opacity"].tolist() == [0.2, 0.4]
+    assert out["sh"].tolist() == [[[3.0, 4.0, 5.0]], [[9.0, 10.0, 11.0]]]
+    assert out["sh_degree"] == 0
 
 
 def _plane_images(cam, n, p0, a=0.8):

@@ -96,3 +96,23 @@ def test_noalloc_rejects_requests_beyond_its_limits(setup):
     assert call(_cams(((16384, 16384),) * 2)) == _lib.ERR_CAPACITY   # 2 x 65536 blocks > 65536
     assert call(_cams(((4, 4),) * 1025)) == _lib.ERR_CAPACITY         # more than 1024 views
     assert call(_cams(((0, 4),))) == _lib.ERR_ARG
+
+
+def test_noalloc_full_view_table_matches_context_entry_point(setup):
+    """1024 views (the table's limit) of ragged sizes: every view's loss, the block prefix the
+    device-side set-up builds and the adjoint agree with the context entry point."""
+    dev, rast, lib, _lib = setup
+    rng = np.random.default_rng(4)
+    sizes = [(int(w), int(h)) for w, h in rng.integers(1, 90, size=(1024, 2))]
+    sizes[7] = (4097, 1)  # a view that needs two loss blocks
+    cams = _cams(sizes)
+    P = sum(w * h for w, h in sizes)
+    alpha = torch.tensor(rng.uniform(0, 1, P).astype(np.float32), device=dev)
+    mask = torch.tensor((rng.uniform(0, 1, P) < 0.4).astype(np.uint8), device=dev)
+    d_ref = torch.zeros(P, device=dev)
+    ref = rast.background_loss(alpha, mask, cams, gamma=0.5, d_alpha=d_ref)
+    d_new = torch.zeros(P, device=dev)
+    got = _noalloc(lib, _lib, alpha, mask, cams, 0.5, d_new)
+    torch.cuda.synchronize()
+    np.testing.assert_allclose(got.cpu().numpy(), ref.cpu().numpy(), rtol=1e-12, atol=0)
+    np.testing.assert_allclose(d_new.cpu().numpy(), d_ref.cpu().numpy(), rtol=0, atol=1e-7)
