@@ -86,6 +86,9 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-per-view", action="store_true")
     p.add_argument("--cpu-sample", type=int, default=1536, help="pixels of the oracle's timed sample")
+    p.add_argument("--prune-record", choices=("fused", "graph"), default="fused",
+                   help="fused: the contribution record rides on the step's forward; graph: the step renders "
+                        "without it and the pruning sweep over the same views runs as the captured CUDA graph")
     a = p.parse_args()
     if a.n is None:
         a.n = 1_000_000 if a.workload == "c5" else 500_000
@@ -335,12 +338,13 @@ def run_reference(a, rank: int, world: int):
 class TrainingStep:
     """One training step through the library (all arithmetic in libocgs kernels)."""
 
-    def __init__(self, rast, g, cams, target, mask, per_view: bool, adam: bool = False):
+    def __init__(self, rast, g, cams, target, mask, per_view: bool, adam: bool = False, graph=None):
         import torch
         from paper_2501_08174_gb300 import pixel_offsets
         self.rast, self.g, self.cams, self.target, self.mask = rast, g, cams, target, mask
         self.per_view = per_view
         self.adam = adam
+        self.graph = graph  # the pruning sweep as a captured graph (the forward then keeps no record)
         self.t = 0
         if adam:
             self.m = {k: torch.zeros_like(v) for k, v in g.items()}
@@ -355,13 +359,13 @@ class TrainingStep:
             self.d_depth2 = torch.zeros(P, device=dev)
             self.d_normal = torch.zeros(P, 3, device=dev)
         self.grads = {k: torch.zeros_like(v) for k, v in g.items()}
-        self.score = torch.zeros(g["opacity"].shape[0], device=dev)
+        self.score = graph.score if graph is not None else torch.zeros(g["opacity"].shape[0], device=dev)
         self.loss = torch.zeros(2, len(cams), dtype=torch.float64, device=dev)
         self.kept = 0
 
     def _views(self, cams, lo, hi):
         r = self.rast
-        out, st = r.render(self.g, cams, score=self.score, depth2=self.adam)
+        out, st = r.render(self.g, cams, score=None if self.graph is not None else self.score, depth2=self.adam)
         tgt = self.target[lo:hi]
         msk = self.mask[lo:hi]
         d_rgb, d_alpha = self.d_rgb[lo:hi], self.d_alpha[lo:hi]
@@ -382,7 +386,8 @@ class TrainingStep:
         return l1, lb
 
     def __call__(self):
-        self.score.zero_()
+        if self.graph is None:
+            self.score.zero_()
         self.d_rgb.zero_()
         self.d_alpha.zero_()
         if self.adam:
@@ -400,6 +405,8 @@ class TrainingStep:
             l1, lb = self._views(self.cams, 0, self.off[-1])
             self.loss[0].copy_(l1)
             self.loss[1].copy_(lb)
+        if self.graph is not None:
+            self.graph.launch()  # zeroes the score and sweeps every view
         if self.adam:
             self.t += 1
             self.rast.adam_step(self.g, self.grads, self.m, self.v, ADAM_LR, step=self.t)
@@ -544,7 +551,8 @@ def run_ours(a, rank: int, world: int, local: int):
 
     # batched step, with the library's stage timers on
     adam = a.workload == "c5"
-    step = TrainingStep(rast, g, cams, target, mask, per_view=False, adam=adam)
+    graph = rast.contribution_graph(g, cams) if a.prune_record == "graph" else None
+    step = TrainingStep(rast, g, cams, target, mask, per_view=False, adam=adam, graph=graph)
     for _ in range(a.warmup):
         step()
     rast.profile(True)
@@ -634,6 +642,8 @@ def run_ours(a, rank: int, world: int, local: int):
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_name(a), "mode": "batched (one pass over all views)",
+                           "prune_record": ("fused into the step's forward" if a.prune_record == "fused" else
+                                            "captured CUDA-graph sweep over the step's views"),
                            "n_gaussians": N, "n_views": len(cams), "pixels_per_gpu": P,
                            "resolutions": [f"{c['width']}x{c['height']}" for c in cams],
                            "tile": f"{opts['tile'][0]}x{opts['tile'][1]}",

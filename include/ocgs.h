@@ -484,7 +484,8 @@ typedef struct {
  * the context's front_fraction and 32 Gaussians per batch; (2) for a
  * persistent choice, front_fraction in {0, 0.05, 0.1, 0.2}; (3) 16 or 64
  * Gaussians per batch where the chosen shape offers them.  Each candidate runs
- * once untimed and twice timed (CUDA events on the context stream).
+ * once untimed and twice timed (CUDA events on the context stream); one whose
+ * pair count exceeds a render's capacity (OCGS_ERR_CAPACITY) is skipped.
  * cache_path (host string or NULL) names a text file of earlier choices keyed
  * by GPU, SM count, SH degree, views and power-of-two buckets of Gaussians and
  * pixels; a hit skips the timing, a miss appends a line.  Synchronises;

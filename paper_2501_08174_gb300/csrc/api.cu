@@ -563,8 +563,10 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
       CK(cudaMemsetAsync(st->ranges2, 0, sizeof(uint2) * n_t, s));
       {
         StageTimer t(ctx, OCGS_STAGE_BINNING);
+        uint32_t* open_ids;
+        CK(tmp.alloc(&open_ids, n_t));
         CK(launch_duplicate_open(cand, counts, ctx->d_scalar + 5, n_back, n_cand, bin, st->d_cams, N, tw, th, open,
-                                 P, K2, qkey, qval, s));
+                                 P, n_t, open_ids, K2, qkey, qval, s));
       }
       bool qalt = false;
       {
@@ -1377,7 +1379,9 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   ocgs_status status = OCGS_OK;
-  // ms of one render + backward with options o (once untimed, twice timed), or < 0
+  // ms of one render + backward with options o (once untimed, twice timed), or < 0.  A
+  // candidate whose pair count exceeds the capacity of one render (small tiles in one pass)
+  // is infeasible for this workload and skipped.
   auto time_options = [&](const ocgs_options& o) -> double {
     if (status != OCGS_OK || ocgs_set_options(ctx, &o) != OCGS_OK) return -1.0;
     for (int rep = 0; rep < 3 && status == OCGS_OK; ++rep) {
@@ -1387,6 +1391,10 @@ extern "C" ocgs_status ocgs_autotune(ocgs_ctx* ctx, const ocgs_gaussians* g, con
       if (status == OCGS_ERR_NONFINITE) status = OCGS_OK;
       if (status == OCGS_OK) status = ocgs_render_backward(ctx, st, g, &d_out, &dp);
       if (st) ocgs_state_release(ctx, st);
+    }
+    if (status == OCGS_ERR_CAPACITY) {
+      status = OCGS_OK;
+      return -1.0;
     }
     if (status != OCGS_OK) return -1.0;
     cudaEventRecord(e1, s);

@@ -382,11 +382,12 @@ cudaError_t launch_open_count(const uint32_t* cand, uint32_t n, const uint32_t* 
                               const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
                               const uint32_t* open_prefix, uint64_t* counts, cudaStream_t s);
 // the (open tile, record) pairs of the candidates, in depth order, from the scan of those counts
+// (open_ids: scratch of n_tiles ids, filled with the compacted open tiles first)
 cudaError_t launch_duplicate_open(const uint32_t* cand, const uint64_t* offsets, const uint64_t* total,
                                   uint32_t n_rec, const uint32_t* n_cand, const float4* bin, const DevCam* cams,
                                   int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open,
-                                  const uint32_t* open_prefix, uint32_t n_pairs, uint32_t* keys, uint32_t* vals,
-                                  cudaStream_t s);
+                                  const uint32_t* open_prefix, uint32_t n_tiles, uint32_t* open_ids, uint32_t n_pairs,
+                                  uint32_t* keys, uint32_t* vals, cudaStream_t s);
 // the second pass's queue: tiles with a non-empty ranges2 first (longest first);
 // n_again (zeroed by the caller) counts them
 cudaError_t launch_second_queue(const uint2* ranges2, uint32_t n_tiles, uint32_t* work_key, uint32_t* ids,

@@ -217,21 +217,22 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
         const float rb = s_rb[wib][j];
         const SplatColumn col = splat_column(g0, g1, g2, pxf);
         SplatHead2 hd[NP];
+        bool live[2 * NP];
         bool any = false;
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
           const float2 py = make_float2((float)(py0 + 2 * p) + 0.5f, (float)(py0 + 2 * p + 1) + 0.5f);
-          hd[p] = splat_head2(g0, g1, g2, col, py, rb);
-          hd[p].pass[0] = hd[p].pass[0] && jj < (int)last[2 * p];
-          hd[p].pass[1] = hd[p].pass[1] && jj < (int)last[2 * p + 1];
-          any = any || hd[p].pass[0] || hd[p].pass[1];
+          hd[p] = splat_head2(g0, g1, g2, col, py);
+          live[2 * p] = jj < (int)last[2 * p];
+          live[2 * p + 1] = jj < (int)last[2 * p + 1];
+          any = any || may_blend(hd[p], rb, live[2 * p], live[2 * p + 1]);
         }
         if (!__any_sync(kFull, any)) continue;  // the support misses every pixel of the band
         const float4 ap = s_a0[wib][j];
         const float2 an = s_a1[wib][j];
         const float2 dx = bc2(col.dx);
         const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
-        const float2 nho = bc2(-0.5f * g0.z);  // dalpha/drho = -alpha/2 = -o G / 2
+        const float2 no = bc2(-g0.z);  // 2 dalpha/drho = -alpha = -o G
         float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
 #pragma unroll
         for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
@@ -240,7 +241,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
         // Gc = 0, which makes its weight and every term of its adjoint exactly 0
 #pragma unroll
         for (int p = 0; p < NP; ++p) {
-          const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb);
+          const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb, live[2 * p], live[2 * p + 1]);
           contrib = contrib || e.ok[0] || e.ok[1];
           // undo the entry: T before it, its weight, and dL/dalpha
           const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
@@ -270,14 +271,14 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
             acc[kGnz] = __ffma2_rn(gN2[p], w, acc[kGnz]);
           }
           // alpha = o G below the clamp: dalpha/do = G, dalpha/drho = -o G / 2
-          // (Gc is 0 at the clamp and for skipped candidates)
+          // (Gc is 0 at the clamp and for skipped candidates); gs2 = 2 dL/drho
           const float2 gop = __fmul2_rn(ga, e.Gc);
           acc[kGo] = __fadd2_rn(acc[kGo], gop);
-          const float2 grho = __fmul2_rn(gop, nho);
+          const float2 gs2 = __fmul2_rn(gop, no);
           // rho and depth came from the surfel's (u, v) where it won the min, from the
           // screen-space filter elsewhere.  e.r and e.rho3 are 0 where the filter won,
           // so the surfel terms below vanish there without a mask.
-          const float2 grf = make_float2(e.surf[0] ? 0.f : grho.x, e.surf[1] ? 0.f : grho.y);
+          const float2 gf2 = make_float2(e.surf[0] ? 0.f : gs2.x, e.surf[1] ? 0.f : gs2.y);
           float2 gzs = bc2(0.f);
           if (GEO) {
             // d/dz of w (gD z + gQ z^2)
@@ -286,14 +287,14 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
             acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
             acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
           }
-          const float2 r2 = __fmul2_rn(e.r, e.r);
-          const float2 gs2 = __fmul2_rn(grho, bc2(2.f));
-          const float2 gun = __fmul2_rn(__fmul2_rn(gs2, hd[p].un), r2);
-          const float2 gvn = __fmul2_rn(__fmul2_rn(gs2, hd[p].vn), r2);
+          // 2 grho / den^2, shared by the u, v and den terms (rho3 = q / den^2)
+          const float2 t = __fmul2_rn(gs2, __fmul2_rn(e.r, e.r));
+          const float2 gun = __fmul2_rn(t, hd[p].un);
+          const float2 gvn = __fmul2_rn(t, hd[p].vn);
           // -dL/dden = (2 grho rho3 + gz z) / den; the e slots and c slots below
           // accumulate negated and are flipped when the lanes are summed
           const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
-                                   : __fmul2_rn(__fmul2_rn(gs2, e.rho3), e.r);
+                                   : __fmul2_rn(t, __fmul2_rn(hd[p].q, e.r));
           const float2 gdxs = __ffma2_rn(ngden, ng2y, __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
           const float2 gdys = __ffma2_rn(ngden, ng2z, __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
           acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
           acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
           acc[kGe1] = __ffma2_rn(ngden, dx, acc[kGe1]);
           acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
-          const float2 gf4 = __fmul2_rn(grf, bc2(4.f));
+          const float2 gf4 = __fmul2_rn(gf2, bc2(2.f));  // d rho2 / d(c) = -4 (x - c) with rho2 = 2 |x - c|^2
           acc[kGcx] = __fadd2_rn(acc[kGcx], __ffma2_rn(gf4, dx, gdxs));
           acc[kGcy] = __fadd2_rn(acc[kGcy], __ffma2_rn(gf4, hd[p].dy, gdys));
         }

@@ -94,18 +94,10 @@ __device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
 // its pixels as straight-line code (head) before the rest (tail).
 struct SplatHead2 {
   float2 dy, un, vn, den, rho2, q;
-  bool in3[2];   // the surfel term is within its support: u^2 + v^2 <= rb
-  bool pass[2];  // in3, or the screen filter term rho2 <= rb
 };
 
-// EWA: a projected 3D Gaussian (constant denominator, the screen filter already
-// folded into its covariance): the support test is the Mahalanobis term alone.
-// in3 needs no separate den != 0 test: with den = 0 the limit is 0, so only
-// q = 0 passes, and then rho3 = 0 * inf is NaN, the surfel branch is not taken
-// and every decision is the one the test would have given.
-template <bool EWA = false>
 __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
-                                                  const SplatColumn& c, float2 py, float rb) {
+                                                  const SplatColumn& c, float2 py) {
   SplatHead2 h;
   h.dy = __fadd2_rn(py, bc2(-g0.y));
   h.un = __ffma2_rn(bc2(g1.y), h.dy, bc2(c.ux));
@@ -113,12 +105,17 @@ __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 
   h.den = __ffma2_rn(bc2(g2.z), h.dy, bc2(c.ex));
   h.rho2 = __fmul2_rn(bc2(kInvSigmaF2), __ffma2_rn(h.dy, h.dy, bc2(c.dx2)));
   h.q = __ffma2_rn(h.un, h.un, __fmul2_rn(h.vn, h.vn));
-  const float2 lim = __fmul2_rn(bc2(rb), __fmul2_rn(h.den, h.den));
-  h.in3[0] = h.q.x <= lim.x;
-  h.in3[1] = h.q.y <= lim.y;
-  h.pass[0] = h.in3[0] || (!EWA && h.rho2.x <= rb);
-  h.pass[1] = h.in3[1] || (!EWA && h.rho2.y <= rb);
   return h;
+}
+
+// A cheap superset of the pixels a candidate can blend: the surfel term within its
+// support (u^2 + v^2 <= rb, tested as q <= rb den^2 with a relative margin that
+// covers the rounding of rho3 = q / den^2) or the filter term within it.  Only used
+// to skip an entry no pixel of the band can blend; the blend decision itself is
+// taken in splat_tail2.
+__device__ __forceinline__ bool may_blend(const SplatHead2& h, float rb, bool live0, bool live1) {
+  const float2 lim = __fmul2_rn(bc2(__fmul_rn(rb, 1.0001f)), __fmul2_rn(h.den, h.den));
+  return (live0 && (h.q.x <= lim.x || h.rho2.x <= rb)) || (live1 && (h.q.y <= lim.y || h.rho2.y <= rb));
 }
 
 struct SplatEval2 {
@@ -127,21 +124,26 @@ struct SplatEval2 {
   float2 alpha;     // the blended opacity min(0.99, o G), 0 where the candidate is skipped
   float2 z;         // depth of the hit (surfel term) or of the centre (filter term)
   bool surf[2];     // the surfel term won the min (else the screen filter)
-  bool ok[2];       // pass, rho <= rb and o G >= 1/255: blended unless the pixel stops
+  bool ok[2];       // live, rho <= rb and o G >= 1/255: blended unless the pixel stops
 };
 
+// rho = min(rho3, rho2), rho3 = (u^2 + v^2) = q / den^2: the surfel term wins where
+// rho3 <= rho2 (with den = 0, rho3 is +inf or NaN and the filter term wins).
+// live[i]: the pixel still composites (forward) or lies before its last blended
+// entry (backward); EWA: a projected 3D Gaussian, rho = q (constant denominator,
+// the screen filter already folded into its covariance), blended only where q <= rb.
 // FINITE (backward): r and rho3 are zeroed where the filter term won, so that
 // products the backward masks with zero stay finite (the forward reads z only).
 // A skipped candidate gets alpha = 0 (T (1 - 0) = T and w = 0 exactly) and
 // Gc = 0, which zeroes every term of its adjoint without further masks.
 template <bool FINITE, bool EWA = false>
-__device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb) {
+__device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb,
+                                                  bool live0, bool live1) {
   SplatEval2 e;
-  // where in3 is false the reciprocal is never used unmasked (surf is false)
   const float2 r = EWA ? bc2(1.0f) : make_float2(__fdividef(1.0f, h.den.x), __fdividef(1.0f, h.den.y));
   const float2 r3 = EWA ? h.q : __fmul2_rn(h.q, __fmul2_rn(r, r));
-  e.surf[0] = h.in3[0] && (EWA || r3.x <= h.rho2.x);
-  e.surf[1] = h.in3[1] && (EWA || r3.y <= h.rho2.y);
+  e.surf[0] = EWA || r3.x <= h.rho2.x;
+  e.surf[1] = EWA || r3.y <= h.rho2.y;
   if (FINITE) {
     e.r = make_float2(e.surf[0] ? r.x : 0.0f, e.surf[1] ? r.y : 0.0f);
     e.rho3 = make_float2(e.surf[0] ? r3.x : 0.0f, e.surf[1] ? r3.y : 0.0f);
@@ -154,8 +156,8 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
   const float2 G = make_float2(__expf(ex.x), __expf(ex.y));
   const float2 oG = __fmul2_rn(bc2(g0.z), G);
   // min(0.99, o G) >= 1/255 exactly when o G >= 1/255
-  e.ok[0] = h.pass[0] && (rho.x <= rb) && (oG.x >= kAlphaMin);
-  e.ok[1] = h.pass[1] && (rho.y <= rb) && (oG.y >= kAlphaMin);
+  e.ok[0] = live0 && (rho.x <= rb) && (oG.x >= kAlphaMin);
+  e.ok[1] = live1 && (rho.y <= rb) && (oG.y >= kAlphaMin);
   e.alpha = make_float2(e.ok[0] ? fminf(kAlphaMax, oG.x) : 0.0f, e.ok[1] ? fminf(kAlphaMax, oG.y) : 0.0f);
   if (FINITE)
     e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);

