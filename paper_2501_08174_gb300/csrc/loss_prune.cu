@@ -12,6 +12,23 @@ namespace {
 
 constexpr int kLossThreads = 256;
 
+// Float32 arithmetic with the rounding error kept (FP64 is slow on this part):
+// Knuth's TwoSum gives s + err = a + b exactly; compensated summation adds each
+// term to hi and collects the rounding errors in lo, so hi + lo carries about
+// twice the float precision (the per-thread sums reach the FP64 block
+// reduction as (double)hi + (double)lo).
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+__device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
+  float err;
+  hi = two_sum(hi, x, err);
+  lo = __fadd_rn(lo, err);
+}
+
 // Each block reduces kLossBlockPixels pixels of one view in FP64, in a fixed
 // order, and writes one partial sum; a second pass adds the partials of a view
 // in block order, so the loss is bitwise reproducible.
@@ -27,13 +44,14 @@ __global__ void __launch_bounds__(kLossThreads) bg_loss_partial_kernel(
   const int64_t lo = (int64_t)(b - block_prefix[v]) * kLossBlockPixels;
   const int64_t hi = (lo + kLossBlockPixels < npix) ? lo + kLossBlockPixels : npix;
   const float g = gamma / (float)npix;
-  double acc = 0.0;
+  float ahi = 0.f, alo = 0.f;
   for (int64_t k = lo + threadIdx.x; k < hi; k += kLossThreads) {
     const int64_t p = cam.pix_offset + k;
     const float bg = mask[p] ? 0.f : 1.f;
-    acc += (double)alpha[p] * (double)bg;
+    comp_add(ahi, alo, alpha[p] * bg);  // alpha (1 - M) is exact
     if (d_alpha) d_alpha[p] += g * bg;
   }
+  double acc = (double)ahi + (double)alo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
@@ -45,12 +63,12 @@ __global__ void __launch_bounds__(kLossThreads) bg_loss_partial_kernel(
   }
 }
 
-// Masked L1 (Eq. 2, L1 part): |I M - R M| summed in FP64 per block, with the
-// adjoint weight * sign(R - I) * M / (3 h w) added into d_rgb.  The difference
-// of the two FP32 values is taken in FP64, where it is exact unless their
-// exponents differ by more than 28 (then within 2^-53 relative), so the loss
-// differs from the exact one by the FP64 summation order alone; its sign is
-// the sign of the exact difference.
+// Masked L1 (Eq. 2, L1 part): |I M - R M| summed per block, with the adjoint
+// weight * sign(R - I) * M / (3 h w) added into d_rgb.  Each difference is
+// taken exactly as a float pair (TwoSum: R - I = d + e, |e| <= ulp(d) / 2, so
+// |R - I| = |d| + sign(d) e) and summed with compensation, so the loss differs
+// from the exact one by rounding far below float precision; the sign of d is
+// the sign of the exact difference (d = 0 only when R = I).
 __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ block_prefix, float weight,
@@ -63,17 +81,20 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
   const int64_t lo = (int64_t)(b - block_prefix[v]) * kLossBlockPixels;
   const int64_t hi = (lo + kLossBlockPixels < npix) ? lo + kLossBlockPixels : npix;
   const float g = weight / (3.0f * (float)npix);
-  double acc = 0.0;
+  float ahi = 0.f, alo = 0.f;
   for (int64_t k = lo + threadIdx.x; k < hi; k += kLossThreads) {
     const int64_t p = cam.pix_offset + k;
     if (!mask[p]) continue;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-      const double d = (double)rgb[3 * p + c] - (double)target[3 * p + c];
-      acc += fabs(d);
-      if (d_rgb) d_rgb[3 * p + c] += d > 0.0 ? g : (d < 0.0 ? -g : 0.f);
+      float e;
+      const float d = two_sum(rgb[3 * p + c], -target[3 * p + c], e);
+      comp_add(ahi, alo, fabsf(d));
+      alo = __fadd_rn(alo, d > 0.f ? e : -e);
+      if (d_rgb) d_rgb[3 * p + c] += d > 0.f ? g : (d < 0.f ? -g : 0.f);
     }
   }
+  double acc = (double)ahi + (double)alo;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;

@@ -261,7 +261,9 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
           // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
           const float2 ga = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
           S[p] = __ffma2_rn(w, F, S[p]);
-          T[p] = make_float2(e.ok[0] ? Ti.x : T[p].x, e.ok[1] ? Ti.y : T[p].y);
+          // a skipped candidate has alpha = 0, and the fast reciprocal of 1 - 0 is exactly 1
+          // on this GPU (checked at 1, 2 and 0.5), so T passes through it unchanged
+          T[p] = Ti;
           acc[kGr] = __ffma2_rn(gC0[p], w, acc[kGr]);
           acc[kGg] = __ffma2_rn(gC1[p], w, acc[kGg]);
           acc[kGb] = __ffma2_rn(gC2[p], w, acc[kGb]);

@@ -575,8 +575,8 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ra
   return launched();
 }
 
-cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key,
-                              uint32_t* tile_ids, cudaStream_t s, const uint2* ranges2) {
+cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key, uint32_t* tile_ids,
+                              cudaStream_t s, const uint2* ranges2) {
   if (n_tiles == 0) return cudaSuccess;
   tile_work_kernel<<<(n_tiles + 255) / 256, 256, 0, s>>>(ranges, ranges2, n_tiles, work_key, tile_ids);
   return launched();
