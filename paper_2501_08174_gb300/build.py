@@ -37,8 +37,16 @@ def _headers_mtime() -> float:
     return max(os.path.getmtime(h) for h in hs)
 
 
+def _obj_dir(extra: list[str]) -> str:
+    """Objects live in a directory named for the extra flags, so a build with other flags
+    (a diagnostic build, say) never reuses them."""
+    import hashlib
+    tag = hashlib.sha256(" ".join(extra).encode()).hexdigest()[:12] if extra else "default"
+    return os.path.join(BUILD, tag)
+
+
 def _compile(src: str, extra: list[str], verbose: bool) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+    obj = os.path.join(_obj_dir(extra), os.path.basename(src)[:-3] + ".o")
     if os.path.exists(obj) and os.path.getmtime(obj) >= max(os.path.getmtime(src), _headers_mtime()):
         return obj
     cmd = [nvcc(), *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
@@ -54,18 +62,23 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
 
 def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compile and link libocgs.so; return its path."""
-    os.makedirs(BUILD, exist_ok=True)
-    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra or [])
+    os.makedirs(_obj_dir(extra), exist_ok=True)
+    srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra, verbose), srcs))
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
+    # relink when an object is newer or the library was linked from another flag set
+    stamp = LIB + ".flags"
+    same_flags = os.path.exists(stamp) and open(stamp).read() == " ".join(extra)
+    if not os.path.exists(LIB) or not same_flags or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        with open(stamp, "w") as f:
+            f.write(" ".join(extra))
     return LIB
 
 

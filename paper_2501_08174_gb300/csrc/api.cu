@@ -896,8 +896,7 @@ ocgs_status ocgs_render_backward(ocgs_ctx* ctx, const ocgs_fwd_state* st, const 
   GaussOut go{d_params->xyz, d_params->quat, d_params->scale, d_params->opacity, d_params->sh};
   {
     StageTimer t(ctx, OCGS_STAGE_PREPROCESS_BWD);
-    CK(launch_preprocess_backward(gptrs(g), st->N, st->deg, st->d_cams, st->V, grad_rec, st->ntiles, st->rec.a0, go,
-                                  s));
+    CK(launch_preprocess_backward(gptrs(g), st->N, st->deg, st->d_cams, st->V, grad_rec, st->ntiles, go, s));
   }
   return OCGS_OK;
 }

@@ -321,11 +321,9 @@ cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, cons
 cudaError_t launch_preprocess_ewa(const GaussPtrs& g, int64_t n, int sh_degree, const DevCam* cams, int n_views,
                                   int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles, float4* bin,
                                   uint32_t* depth_key, int* status, cudaStream_t s);
-// chain rule from the record gradients to the parameters (rec_a0: the records' colours,
-// whose sign gives the colour clamp of the SH gradient)
 cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
                                        const DevCam* cams, int n_views, const float* grad_rec,
-                                       const int32_t* ntiles, const float4* rec_a0, GaussOut out, cudaStream_t s);
+                                       const int32_t* ntiles, GaussOut out, cudaStream_t s);
 
 // stable LSD radix sort of (key, value) 32-bit pairs on key bits [0, n_bits)
 // in ping-pong buffers; returns in *result_in_alt whether the sorted data ended

@@ -190,20 +190,15 @@ __device__ __forceinline__ void view_geom(const DevCam& cam, const float* X, con
   G.d = cam.fy * (G.V[1] - G.V[2] * G.pyn);
 }
 
-// Unit direction from the camera centre to the Gaussian centre (the SH argument) and the distance.
-__device__ __forceinline__ void view_dir(const DevCam& cam, const float* X, float* dirn, float* dlen) {
+template <int DEG>
+__device__ __forceinline__ void view_colour(const DevCam& cam, const float* X, const float* sh,
+                                            float* dirn, float* dlen, float* raw) {
+  constexpr int K = (DEG + 1) * (DEG + 1);
   float dv[3] = {X[0] - cam.campos[0], X[1] - cam.campos[1], X[2] - cam.campos[2]};
   const float len = sqrtf(dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2]);
   const float il = 1.0f / len;
   dirn[0] = dv[0] * il; dirn[1] = dv[1] * il; dirn[2] = dv[2] * il;
   *dlen = len;
-}
-
-template <int DEG>
-__device__ __forceinline__ void view_colour(const DevCam& cam, const float* X, const float* sh,
-                                            float* dirn, float* dlen, float* raw) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  view_dir(cam, X, dirn, dlen);
   float Y[K];
   sh_basis<DEG>(dirn[0], dirn[1], dirn[2], Y);
   float r0 = 0.5f, r1 = 0.5f, r2 = 0.5f;
@@ -340,6 +335,9 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
   float gX[3] = {0.f, 0.f, 0.f};
   float gtu[3] = {0.f, 0.f, 0.f}, gtv[3] = {0.f, 0.f, 0.f}, gtw[3] = {0.f, 0.f, 0.f};
   float gsu = 0.f, gsv = 0.f, go = 0.f;
+  float gsh[3 * K];
+#pragma unroll
+  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
 
   // the next view's tile count and record gradient are requested before the
   // current view is processed, so their memory latency overlaps its arithmetic
@@ -430,11 +428,15 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
     view_colour<DEG>(cam, X, sh, dirn, &dlen, raw);
     const float graw[3] = {raw[0] > 0.f ? grgb[0] : 0.f, raw[1] > 0.f ? grgb[1] : 0.f,
                            raw[2] > 0.f ? grgb[2] : 0.f};
-    // the coefficients' own gradient is preprocess_bwd_sh_kernel's; here only the
-    // direction's: beta_k = dL/dY_k
-    float beta[K];
+    float Y[K], beta[K];
+    sh_basis<DEG>(dirn[0], dirn[1], dirn[2], Y);
 #pragma unroll
-    for (int k = 0; k < K; ++k) beta[k] = graw[0] * sh[3 * k] + graw[1] * sh[3 * k + 1] + graw[2] * sh[3 * k + 2];
+    for (int k = 0; k < K; ++k) {
+      gsh[3 * k + 0] += graw[0] * Y[k];
+      gsh[3 * k + 1] += graw[1] * Y[k];
+      gsh[3 * k + 2] += graw[2] * Y[k];
+      beta[k] = graw[0] * sh[3 * k] + graw[1] * sh[3 * k + 1] + graw[2] * sh[3 * k + 2];
+    }
     if (DEG > 0) {
       const float3 gdn = sh_basis_vjp<DEG>(dirn[0], dirn[1], dirn[2], beta);
       const float dp = gdn.x * dirn[0] + gdn.y * dirn[1] + gdn.z * dirn[2];
@@ -469,46 +471,8 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
   out.scale[2 * i + 0] += gsu;
   out.scale[2 * i + 1] += gsv;
   out.opacity[i] += go;
-}
-
-// Gradient of the SH coefficients, one thread per Gaussian: dL/dc_kc = sum over views of
-// graw_c Y_k(dir), graw_c the colour cotangent where the colour is not clamped at 0.  The
-// record's stored colour max(raw, 0) is > 0 exactly where raw > 0, so this needs neither
-// the coefficients nor the geometric chain rule and runs apart from preprocess_bwd_kernel
-// (which would otherwise hold 48 more accumulators); the views are summed in the same order.
-template <int DEG>
-__global__ void __launch_bounds__(128) preprocess_bwd_sh_kernel(const float* __restrict__ xyz, int64_t n,
-                                                                const DevCam* __restrict__ cams, int n_views,
-                                                                const float* __restrict__ grad_rec,
-                                                                const int32_t* __restrict__ ntiles,
-                                                                const float4* __restrict__ a0,
-                                                                float* __restrict__ out_sh) {
-  constexpr int K = (DEG + 1) * (DEG + 1);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  const float X[3] = {xyz[3 * i], xyz[3 * i + 1], xyz[3 * i + 2]};
-  float gsh[3 * K];
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
-  for (int v = 0; v < n_views; ++v) {
-    const int64_t idx = (int64_t)v * n + i;
-    if (ntiles[idx] == 0) continue;
-    const float4 col = a0[idx];
-    const float4 gc = reinterpret_cast<const float4*>(grad_rec + idx * kGradStride)[kGr / 4];
-    const float graw[3] = {col.x > 0.f ? gc.x : 0.f, col.y > 0.f ? gc.y : 0.f, col.z > 0.f ? gc.z : 0.f};
-    float dirn[3], dlen;
-    view_dir(cams[v], X, dirn, &dlen);
-    float Y[K];
-    sh_basis<DEG>(dirn[0], dirn[1], dirn[2], Y);
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      gsh[3 * k + 0] += graw[0] * Y[k];
-      gsh[3 * k + 1] += graw[1] * Y[k];
-      gsh[3 * k + 2] += graw[2] * Y[k];
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) out_sh[3 * K * i + k] += gsh[k];
+  for (int k = 0; k < 3 * K; ++k) out.sh[(int64_t)3 * K * i + k] += gsh[k];
 }
 
 // EWA projection of 3D Gaussians, for the 3DGS variant of the pruning record
@@ -652,22 +616,16 @@ cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, cons
 
 cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_degree,
                                        const DevCam* cams, int n_views, const float* grad_rec,
-                                       const int32_t* ntiles, const float4* rec_a0, GaussOut out, cudaStream_t s) {
+                                       const int32_t* ntiles, GaussOut out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   const int bs = 128;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
-#define OCGS_PBWD(D)                                                                                            \
-  preprocess_bwd_kernel<D><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out);                     \
-  if (cudaError_t e = launched(); e != cudaSuccess) return e;                                                    \
-  preprocess_bwd_sh_kernel<D><<<grid, bs, 0, s>>>(g.xyz, n, cams, n_views, grad_rec, ntiles, rec_a0, out.sh);  \
-  break;
   switch (sh_degree) {
-    case 0: OCGS_PBWD(0)
-    case 1: OCGS_PBWD(1)
-    case 2: OCGS_PBWD(2)
-    default: OCGS_PBWD(3)
+    case 0: preprocess_bwd_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
+    case 1: preprocess_bwd_kernel<1><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
+    case 2: preprocess_bwd_kernel<2><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
+    default: preprocess_bwd_kernel<3><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
   }
-#undef OCGS_PBWD
   return launched();
 }
 

@@ -17,6 +17,10 @@ namespace ocgs {
 namespace {
 using namespace raster;
 
+#ifdef OCGS_COUNT
+__device__ unsigned long long g_diag[8];
+#endif
+
 #ifndef OCGS_BWD_WARPS
 #define OCGS_BWD_WARPS 16
 #endif
@@ -199,7 +203,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
           s_g2[wib][slot] = a.rec.g2[idx];
           s_a0[wib][slot] = a.rec.a0[idx];
           s_a1[wib][slot] = make_float2(a1.x, a1.y);
-          s_rb[wib][slot] = support_rho(g0.z);
+          s_rb[wib][slot] = blend_rho(g0.z);
           s_idx[wib][slot] = idx;
           s_q[wib][slot] = q;
         }
@@ -228,6 +232,9 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
           any = any || may_blend(hd[p], rb, live[2 * p], live[2 * p + 1]);
         }
         if (!__any_sync(kFull, any)) continue;  // the support misses every pixel of the band
+#ifdef OCGS_COUNT
+        if (lane == 0) OCGS_DIAG(5, 1);  // entries evaluated in full
+#endif
         const float4 ap = s_a0[wib][j];
         const float2 an = s_a1[wib][j];
         const float2 dx = bc2(col.dx);
@@ -376,6 +383,17 @@ cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
 }
 
 }  // namespace
+
+#ifdef OCGS_COUNT
+extern "C" int ocgs_diag_read_bwd(unsigned long long* out, int reset) {
+  cudaMemcpyFromSymbol(out, g_diag, sizeof(g_diag));
+  if (reset) {
+    unsigned long long z[8] = {0};
+    cudaMemcpyToSymbol(g_diag, z, sizeof(z));
+  }
+  return 0;
+}
+#endif
 
 cudaError_t launch_raster_backward(const RasterBwdArgs& a, int tile_w, int tile_h, int ppt, int batch,
                                    cudaStream_t s) {

@@ -31,8 +31,8 @@ struct Batch {
 };
 
 #ifdef OCGS_COUNT
-// diagnostic build only: warp iterations and evaluated (lane, pixel) pairs
-extern __device__ unsigned long long g_diag[8];
+// diagnostic build only: counters of warp iterations and evaluated (lane, pixel) pairs,
+// one array per translation unit (g_diag, defined by each rasterizer file)
 #define OCGS_DIAG(slot, v) atomicAdd(&g_diag[slot], (unsigned long long)(v))
 #else
 #define OCGS_DIAG(slot, v)
@@ -87,11 +87,17 @@ __device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
   else v.x = x;
 }
 
-// rb: the record's support bound support_rho(o) <= 9.  Candidates with
-// rho > rb have o exp(-rho/2) < 1/255, so testing rb instead of 9 first only
-// skips work; every decision is the one the 9 cut and the 1/255 floor give.
-// The evaluation is split so that a thread runs the cheap support test of all
-// its pixels as straight-line code (head) before the rest (tail).
+// rb: the record's blend bound in rho.  A candidate is blended only where rho <= 9
+// (the 3-sigma cut) and alpha = o exp(-rho/2) >= 1/255, i.e. rho <= 2 ln(255 o); both
+// tests are the one comparison rho <= min(9, 2 ln(255 o)), computed once per record.
+// Evaluated in float32 it can differ from the alpha test only where alpha is within a
+// few ulps of 1/255.
+__device__ __forceinline__ float blend_rho(float o) {
+  return fminf(kRhoCut, __fmul_rn(2.0f, __logf(__fmul_rn(255.0f, o))));
+}
+
+// The evaluation is split so that a thread computes the cheap terms of all its pixels
+// as straight-line code (head) before the rest (tail).
 struct SplatHead2 {
   float2 dy, un, vn, den, rho2, q;
 };
@@ -108,8 +114,8 @@ __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 
   return h;
 }
 
-// A cheap superset of the pixels a candidate can blend: the surfel term within its
-// support (u^2 + v^2 <= rb, tested as q <= rb den^2 with a relative margin that
+// A cheap superset of the pixels a candidate can blend: the surfel term within the
+// blend bound (u^2 + v^2 <= rb, tested as q <= rb den^2 with a relative margin that
 // covers the rounding of rho3 = q / den^2) or the filter term within it.  Only used
 // to skip an entry no pixel of the band can blend; the blend decision itself is
 // taken in splat_tail2.
@@ -134,7 +140,7 @@ struct SplatEval2 {
   float2 alpha;     // the blended opacity min(0.99, o G), 0 where the candidate is skipped
   float2 z;         // depth of the hit (surfel term) or of the centre (filter term)
   bool surf[2];     // the surfel term won the min (else the screen filter)
-  bool ok[2];       // live, rho <= rb and o G >= 1/255: blended unless the pixel stops
+  bool ok[2];       // live and rho <= rb (within 3 sigma, alpha >= 1/255): blended unless the pixel stops
 };
 
 // rho = min(rho3, rho2), rho3 = (u^2 + v^2) = q / den^2: the surfel term wins where
@@ -165,9 +171,8 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
   const float2 ex = __fmul2_rn(bc2(kNegHalfLog2e), rho);
   const float2 G = make_float2(exp2_approx(ex.x), exp2_approx(ex.y));
   const float2 oG = __fmul2_rn(bc2(g0.z), G);
-  // min(0.99, o G) >= 1/255 exactly when o G >= 1/255
-  e.ok[0] = live0 && (rho.x <= rb) && (oG.x >= kAlphaMin);
-  e.ok[1] = live1 && (rho.y <= rb) && (oG.y >= kAlphaMin);
+  e.ok[0] = live0 && (rho.x <= rb);
+  e.ok[1] = live1 && (rho.y <= rb);
   e.alpha = make_float2(e.ok[0] ? fminf(kAlphaMax, oG.x) : 0.0f, e.ok[1] ? fminf(kAlphaMax, oG.y) : 0.0f);
   if (FINITE)
     e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);

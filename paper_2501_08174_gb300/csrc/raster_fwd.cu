@@ -17,13 +17,12 @@
 #include "raster_common.cuh"
 
 namespace ocgs {
+namespace {
+using namespace raster;
 
 #ifdef OCGS_COUNT
 __device__ unsigned long long g_diag[8];
 #endif
-
-namespace {
-using namespace raster;
 
 // Resident warps per SM the compiler is asked to fit (caps registers per
 // thread): 20 leaves 96 registers, enough for the image planes without spills
@@ -150,7 +149,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             s_a0[wib][slot] = a.rec.a0[idx];
             s_a1[wib][slot] = make_float2(a1.x, a1.y);
           }
-          s_rb[wib][slot] = support_rho(g0.z);
+          s_rb[wib][slot] = blend_rho(g0.z);
           s_pos[wib][slot] = kk;
           if (SCORE) s_gid[wib][slot] = (uint32_t)((int64_t)idx - gbase);
         }
@@ -195,7 +194,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             const uint32_t l0 = last[k0], l1 = last[k1];
             if (e.ok[0]) last[k0] = pos;
             if (e.ok[1]) last[k1] = pos;
-            if (Tn.x < kTEps || Tn.y < kTEps) {
+            if (fminf(Tn.x, Tn.y) < kTEps) {
               // rare: an entry that would take T below kTEps ends the pixel unblended
               if (Tn.x < kTEps) { done[k0] = true; w.x = 0.f; Tn.x = T[p].x; last[k0] = l0; }
               if (Tn.y < kTEps) { done[k1] = true; w.y = 0.f; Tn.y = T[p].y; last[k1] = l1; }
