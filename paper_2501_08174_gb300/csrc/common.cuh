@@ -234,6 +234,21 @@ __device__ __forceinline__ uint32_t work_code(uint32_t len) {
   return e * 16u + m;
 }
 
+#ifndef OCGS_QUEUE_DROP
+#define OCGS_QUEUE_DROP 4
+#endif
+// an empty tile (code 0) must stay behind every non-empty one (codes >= 16)
+static_assert(OCGS_QUEUE_DROP >= 0 && OCGS_QUEUE_DROP <= 4, "queue key bits");
+// Radix key of a tile in a persistent queue: heaviest first.  The low
+// OCGS_QUEUE_DROP bits of the code are dropped (4: whole octaves of the pair
+// count), so that the tiles of one weight class keep their id order (view by
+// view, row by row) and neighbouring tiles, which share records, run close
+// together in time.  On 500k surfels x 16 views this halved the backward's
+// DRAM reads (3.53 -> 1.92 GB per launch) against the exact 8-bit code.
+__device__ __forceinline__ uint32_t queue_key(uint32_t len) {
+  return 255u - (work_code(len) & ~((1u << OCGS_QUEUE_DROP) - 1u));
+}
+
 // Tile runs of one row of a record's candidate rectangle: the union of the
 // runs of the two intervals, as at most two disjoint runs in increasing order.
 struct RowRuns {
@@ -360,11 +375,11 @@ cudaError_t launch_tile_ranges(const uint32_t* keys, uint32_t n_pairs, uint2* ra
                                const uint32_t* d_n = nullptr);
 // n32 = min(*total, cap); raises kStatusCapacity when *total > cap
 cudaError_t launch_clamp_count(const uint64_t* total, uint32_t cap, uint32_t* n32, int* status, cudaStream_t s);
-// Work keys of the persistent queue: heaviest tiles first over all views (ranges2: an
-// optional second segment of each tile's list, counted with the first), sorted with one
-// 8-bit radix pass.  A view-by-view order (the views' tiles share no records) kept no
-// more of the records in L2 on a 4-view case and left SMs idle at the end of each launch,
-// each view's heavy tiles starting late (backward active warps 15.6 -> 14.6 per SM).
+// Work keys of the persistent queue: heaviest tiles first over all views, by octave
+// of the pair count (queue_key; ranges2: an optional second segment of each tile's
+// list, counted with the first), sorted with one 8-bit radix pass.  A strict
+// view-by-view order left SMs idle at the end of each launch, each view's heavy tiles
+// starting late (backward active warps 15.6 -> 14.6 per SM on a 4-view case).
 cudaError_t launch_tile_order(const uint2* ranges, uint32_t n_tiles, uint32_t* work_key, uint32_t* tile_ids,
                               cudaStream_t s, const uint2* ranges2 = nullptr);
 

@@ -7,10 +7,16 @@
 // stored between the passes.  Per-Gaussian gradients are summed over the
 // thread's pixels, reduced over the warp, gathered per batch in the warp's
 // shared memory and added to global memory with one vector atomic per 4
-// values, entry and warp.  The warp reduction of the 13 slots of a colour and
+// values, entry and warp.  The warp reduction of the 15 sums of a colour and
 // opacity loss goes through shared memory (each lane writes its sums, then
-// 26 lanes each add 16 of them and pair up with one shuffle); the 18 slots
+// 30 lanes each add 16 of them and pair up with one shuffle); the 20 sums
 // with depth and normal cotangents use a halving transpose of shuffles.
+//
+// Terms that are linear in per-entry or per-column constants are summed before
+// they are multiplied: a thread sums the pixel terms of its column and scales
+// the sums by the column offset dx once per entry, and the centre gradient's
+// share through (u, v, den) is formed from the warp totals of the u, v and den
+// terms when the batch is flushed.
 #include "raster_common.cuh"
 
 namespace ocgs {
@@ -52,29 +58,38 @@ __device__ __forceinline__ void halve(float* v, int lane, int& base, int& real) 
   }
 }
 
-// Warp sum of the 18 gradient slots; returns the slot this lane holds (or -1).
-__device__ __forceinline__ int warp_reduce18(float* v, int lane) {
-  int base = 0, real = 18;
-  halve<18, 16>(v, lane, base, real);
-  halve<9, 8>(v, lane, base, real);
+// Warp sum of the 20 sums; returns the one this lane holds (or -1).
+__device__ __forceinline__ int warp_reduce20(float* v, int lane) {
+  int base = 0, real = 20;
+  halve<20, 16>(v, lane, base, real);
+  halve<10, 8>(v, lane, base, real);
   halve<5, 4>(v, lane, base, real);
   halve<3, 2>(v, lane, base, real);
   halve<2, 1>(v, lane, base, real);
   return real >= 1 ? base : -1;
 }
 
-// Row of one lane in the reduction buffer of the 13-slot path: 13 float2 (the
-// two pixel lanes of the packed sums, not yet added).  13 is odd, so the
+// Two sums beside the gradient slots, kept in the row's padding until the
+// flush: the totals of the u and v terms, 2 dL/drho (u, v) / den^2, from
+// which the flush forms the centre gradient's share through (u, v, den).
+constexpr int kSumU = 18, kSumV = 19;
+static_assert(kSumV < kGradStride && kGradSlots <= kSumU, "sums in the row padding");
+
+// Sums of the 15-sum path in the order of the reduction buffer: the 13 slots,
+// then the u and v totals.
+constexpr int kRedSums = kGradSlotsRGB + 2;
+__device__ __forceinline__ int red_target(int q) { return q < kGradSlotsRGB ? q : kSumU + (q - kGradSlotsRGB); }
+
+// Row of one lane in the reduction buffer of the 15-sum path: 15 float2 (the
+// two pixel lanes of the packed sums, not yet added).  15 is odd, so the
 // 16-lane phases of the 64-bit stores (lane L writes row L) and of the 64-bit
-// loads (lane L reads slot L & 15 of rows 16 (L >> 4) + i) hit distinct banks.
-constexpr int kRedRow = kGradSlotsRGB;
-// slots 13..15 of the last row are read (and ignored) by lanes 13..15 and 29..31
-constexpr int kRedSize = 32 * kRedRow + 3;
+// loads (lane L reads sum L & 15 of rows 16 (L >> 4) + i) hit distinct banks.
+constexpr int kRedRow = kRedSums;
+// sum 15 of the last row is read (and ignored) by lanes 15 and 31
+constexpr int kRedSize = 32 * kRedRow + 1;
 
 // Slots accumulated with the opposite sign (flipped when the lanes are summed).
-__device__ __forceinline__ bool negated_slot(int q) {
-  return q == kGcx || q == kGcy || q == kGe0 || q == kGe1 || q == kGe2;
-}
+__device__ __forceinline__ bool negated_slot(int q) { return q == kGe0 || q == kGe1 || q == kGe2; }
 
 // GEO: a depth, depth2 or normal cotangent is given; without one the depth and
 // normal terms of the adjoint are zero and are not evaluated (13 slots instead
@@ -104,9 +119,10 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
       for (int q = 0; q < kGradStride; ++q) row[q] = 0.f;
     }
   }
-  // the slot this lane adds up in the 13-slot reduction, and its sign
+  // the sum this lane adds up in the 15-sum reduction, its sign and its place in the row
   const int red_slot = lane & 15;
   const float red_sign = negated_slot(red_slot) ? -1.f : 1.f;
+  const int red_dst = red_target(red_slot);
   const uint32_t n_units = a.n_tiles * (uint32_t)WPT;
   for (uint32_t it = 0;; ++it) {
     // work unit: one warp's band of one tile; the warps run independently
@@ -237,104 +253,115 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
 #endif
         const float4 ap = s_a0[wib][j];
         const float2 an = s_a1[wib][j];
-        const float2 dx = bc2(col.dx);
-        const float2 ng2y = bc2(-g2.y), ng2z = bc2(-g2.z);
         const float2 no = bc2(-g0.z);  // 2 dalpha/drho = -alpha = -o G
-        float2 acc[kGradSlots];  // this thread's sums (first NG used), one lane per pixel of a pair
+        // this thread's sums (one lane per pixel of a pair): the slots of the
+        // record gradient, and the u and v totals in kSumU, kSumV.  The dx-scaled
+        // slots (A00, A10, e1, and the filter term of cx) hold their pixel sums
+        // until the column offset is applied after the pairs.
+        float2 acc[kGradStride];
 #pragma unroll
-        for (int q = 0; q < NG; ++q) acc[q] = bc2(0.f);
+        for (int q = 0; q < kGradStride; ++q) acc[q] = bc2(0.f);
         bool contrib = false;
         // no per-pair branch: a candidate that is not blended has alpha = 0 and
         // Gc = 0, which makes its weight and every term of its adjoint exactly 0
+        auto pairs = [&](auto clamp) {
+          constexpr bool CLAMP = decltype(clamp)::value;
 #pragma unroll
-        for (int p = 0; p < NP; ++p) {
-          const SplatEval2 e = splat_tail2<true>(g0, g2, hd[p], rb, live[2 * p], live[2 * p + 1]);
-          contrib = contrib || e.ok[0] || e.ok[1];
-          // undo the entry: T before it, its weight, and dL/dalpha
-          const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
-          const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
-          const float2 Ti = __fmul2_rn(T[p], inv);
-          const float2 w = __fmul2_rn(e.alpha, Ti);
-          float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
-          F = __ffma2_rn(gC1[p], bc2(ap.y), F);
-          F = __ffma2_rn(gC2[p], bc2(ap.z), F);
-          if (GEO) {
-            F = __ffma2_rn(gD[p], e.z, F);
-            F = __ffma2_rn(__fmul2_rn(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
-            F = __ffma2_rn(gN0[p], bc2(ap.w), F);
-            F = __ffma2_rn(gN1[p], bc2(an.x), F);
-            F = __ffma2_rn(gN2[p], bc2(an.y), F);
+          for (int p = 0; p < NP; ++p) {
+            const SplatEval2 e = splat_tail2<true, false, CLAMP>(g0, g2, hd[p], rb, live[2 * p], live[2 * p + 1]);
+            contrib = contrib || e.ok[0] || e.ok[1];
+            // undo the entry: T before it, its weight, and dL/dalpha
+            const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
+            const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
+            const float2 Ti = __fmul2_rn(T[p], inv);
+            const float2 w = __fmul2_rn(e.alpha, Ti);
+            float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
+            F = __ffma2_rn(gC1[p], bc2(ap.y), F);
+            F = __ffma2_rn(gC2[p], bc2(ap.z), F);
+            if (GEO) {
+              F = __ffma2_rn(gD[p], e.z, F);
+              F = __ffma2_rn(__fmul2_rn(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
+              F = __ffma2_rn(gN0[p], bc2(ap.w), F);
+              F = __ffma2_rn(gN1[p], bc2(an.x), F);
+              F = __ffma2_rn(gN2[p], bc2(an.y), F);
+            }
+            // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
+            const float2 ga = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
+            S[p] = __ffma2_rn(w, F, S[p]);
+            // a skipped candidate has alpha = 0, and the fast reciprocal of 1 - 0 is exactly 1
+            // on this GPU (checked at 1, 2 and 0.5), so T passes through it unchanged
+            T[p] = Ti;
+            acc[kGr] = __ffma2_rn(gC0[p], w, acc[kGr]);
+            acc[kGg] = __ffma2_rn(gC1[p], w, acc[kGg]);
+            acc[kGb] = __ffma2_rn(gC2[p], w, acc[kGb]);
+            if (GEO) {
+              acc[kGnx] = __ffma2_rn(gN0[p], w, acc[kGnx]);
+              acc[kGny] = __ffma2_rn(gN1[p], w, acc[kGny]);
+              acc[kGnz] = __ffma2_rn(gN2[p], w, acc[kGnz]);
+            }
+            // alpha = o G below the clamp: dalpha/do = G, dalpha/drho = -o G / 2
+            // (Gc is 0 at the clamp and for skipped candidates); gs2 = 2 dL/drho
+            const float2 gop = __fmul2_rn(ga, e.Gc);
+            acc[kGo] = __fadd2_rn(acc[kGo], gop);
+            const float2 gs2 = __fmul2_rn(gop, no);
+            // rho and depth came from the surfel's (u, v) where it won the min, from the
+            // screen-space filter elsewhere.  e.r and e.rho3 are 0 where the filter won,
+            // so the surfel terms below vanish there without a mask.
+            const float2 gf2 = make_float2(e.surf[0] ? 0.f : gs2.x, e.surf[1] ? 0.f : gs2.y);
+            float2 gzs = bc2(0.f);
+            if (GEO) {
+              // d/dz of w (gD z + gQ z^2)
+              const float2 gz = __fmul2_rn(__ffma2_rn(__fmul2_rn(bc2(2.f), gQ[p]), e.z, gD[p]), w);
+              gzs = make_float2(e.surf[0] ? gz.x : 0.f, e.surf[1] ? gz.y : 0.f);
+              acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
+              acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+            }
+            // 2 grho / den^2, shared by the u, v and den terms (rho3 = q / den^2)
+            const float2 t = __fmul2_rn(gs2, __fmul2_rn(e.r, e.r));
+            const float2 gun = __fmul2_rn(t, hd[p].un);
+            const float2 gvn = __fmul2_rn(t, hd[p].vn);
+            // -dL/dden = (2 grho rho3 + gz z) / den; the e slots accumulate negated and
+            // are flipped when the lanes are summed
+            const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
+                                     : __fmul2_rn(t, __fmul2_rn(hd[p].q, e.r));
+            acc[kSumU] = __fadd2_rn(acc[kSumU], gun);
+            acc[kSumV] = __fadd2_rn(acc[kSumV], gvn);
+            acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
+            acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
+            acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
+            acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
+            // the filter term: d rho2 / d(c) = -4 (x - c) with rho2 = 2 |x - c|^2 (the
+            // factor -2 and dx are applied later)
+            acc[kGcx] = __fadd2_rn(acc[kGcx], gf2);
+            acc[kGcy] = __ffma2_rn(gf2, hd[p].dy, acc[kGcy]);
           }
-          // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
-          const float2 ga = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
-          S[p] = __ffma2_rn(w, F, S[p]);
-          // a skipped candidate has alpha = 0, and the fast reciprocal of 1 - 0 is exactly 1
-          // on this GPU (checked at 1, 2 and 0.5), so T passes through it unchanged
-          T[p] = Ti;
-          acc[kGr] = __ffma2_rn(gC0[p], w, acc[kGr]);
-          acc[kGg] = __ffma2_rn(gC1[p], w, acc[kGg]);
-          acc[kGb] = __ffma2_rn(gC2[p], w, acc[kGb]);
-          if (GEO) {
-            acc[kGnx] = __ffma2_rn(gN0[p], w, acc[kGnx]);
-            acc[kGny] = __ffma2_rn(gN1[p], w, acc[kGny]);
-            acc[kGnz] = __ffma2_rn(gN2[p], w, acc[kGnz]);
-          }
-          // alpha = o G below the clamp: dalpha/do = G, dalpha/drho = -o G / 2
-          // (Gc is 0 at the clamp and for skipped candidates); gs2 = 2 dL/drho
-          const float2 gop = __fmul2_rn(ga, e.Gc);
-          acc[kGo] = __fadd2_rn(acc[kGo], gop);
-          const float2 gs2 = __fmul2_rn(gop, no);
-          // rho and depth came from the surfel's (u, v) where it won the min, from the
-          // screen-space filter elsewhere.  e.r and e.rho3 are 0 where the filter won,
-          // so the surfel terms below vanish there without a mask.
-          const float2 gf2 = make_float2(e.surf[0] ? 0.f : gs2.x, e.surf[1] ? 0.f : gs2.y);
-          float2 gzs = bc2(0.f);
-          if (GEO) {
-            // d/dz of w (gD z + gQ z^2)
-            const float2 gz = __fmul2_rn(__ffma2_rn(__fmul2_rn(bc2(2.f), gQ[p]), e.z, gD[p]), w);
-            gzs = make_float2(e.surf[0] ? gz.x : 0.f, e.surf[1] ? gz.y : 0.f);
-            acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
-            acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
-          }
-          // 2 grho / den^2, shared by the u, v and den terms (rho3 = q / den^2)
-          const float2 t = __fmul2_rn(gs2, __fmul2_rn(e.r, e.r));
-          const float2 gun = __fmul2_rn(t, hd[p].un);
-          const float2 gvn = __fmul2_rn(t, hd[p].vn);
-          // -dL/dden = (2 grho rho3 + gz z) / den; the e slots and c slots below
-          // accumulate negated and are flipped when the lanes are summed
-          const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
-                                   : __fmul2_rn(t, __fmul2_rn(hd[p].q, e.r));
-          const float2 gdxs = __ffma2_rn(ngden, ng2y, __ffma2_rn(gvn, bc2(g1.z), __fmul2_rn(gun, bc2(g1.x))));
-          const float2 gdys = __ffma2_rn(ngden, ng2z, __ffma2_rn(gvn, bc2(g1.w), __fmul2_rn(gun, bc2(g1.y))));
-          acc[kGA00] = __ffma2_rn(gun, dx, acc[kGA00]);
-          acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
-          acc[kGA10] = __ffma2_rn(gvn, dx, acc[kGA10]);
-          acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
-          acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
-          acc[kGe1] = __ffma2_rn(ngden, dx, acc[kGe1]);
-          acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
-          const float2 gf4 = __fmul2_rn(gf2, bc2(2.f));  // d rho2 / d(c) = -4 (x - c) with rho2 = 2 |x - c|^2
-          acc[kGcx] = __fadd2_rn(acc[kGcx], __ffma2_rn(gf4, dx, gdxs));
-          acc[kGcy] = __fadd2_rn(acc[kGcy], __ffma2_rn(gf4, hd[p].dy, gdys));
-        }
+        };
+        if (g0.z < kNoClampO) pairs(std::false_type{});
+        else pairs(std::true_type{});
         if (!__any_sync(kFull, contrib)) continue;  // no pixel of the band blends it
 #ifdef OCGS_COUNT
         if (lane == 0) OCGS_DIAG(3, 1);
         OCGS_DIAG(4, contrib ? 1 : 0);
 #endif
+        // the column offset of this thread's pixels
+        const float2 dx = bc2(col.dx);
+        acc[kGA00] = __fmul2_rn(acc[kSumU], dx);
+        acc[kGA10] = __fmul2_rn(acc[kSumV], dx);
+        acc[kGe1] = __fmul2_rn(acc[kGe0], dx);
+        acc[kGcx] = __fmul2_rn(acc[kGcx], dx);
         if (GEO) {
-          float gr[kGradSlots];
+          float gr[kGradStride];
 #pragma unroll
-          for (int q = 0; q < NG; ++q)
+          for (int q = 0; q < kGradStride; ++q)
             gr[q] = negated_slot(q) ? -__fadd_rn(acc[q].x, acc[q].y) : __fadd_rn(acc[q].x, acc[q].y);
-          const int slot = warp_reduce18(gr, lane);
+          const int slot = warp_reduce20(gr, lane);
           if (slot >= 0) s_grad[wib][j * kGradStride + slot] = gr[0];  // one lane per slot
         } else {
-          // through shared memory: lane L's row holds its 13 packed sums; lane L then adds
-          // slot L & 15 over the rows 16 (L >> 4) .. 16 (L >> 4) + 15, both pixel lanes
+          // through shared memory: lane L's row holds its 15 packed sums; lane L then adds
+          // sum L & 15 over the rows 16 (L >> 4) .. 16 (L >> 4) + 15, both pixel lanes
           float2* red = s_red[wib];
 #pragma unroll
-          for (int q = 0; q < kGradSlotsRGB; ++q) red[lane * kRedRow + q] = acc[q];
+          for (int q = 0; q < kRedSums; ++q) red[lane * kRedRow + q] = acc[red_target(q)];
           __syncwarp();
           // four independent partial sums keep the dependent chain short
           const float2* col = red + (lane >> 4) * 16 * kRedRow + red_slot;
@@ -346,17 +373,28 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
           const float2 sum = __fadd2_rn(__fadd2_rn(s4[0], s4[1]), __fadd2_rn(s4[2], s4[3]));
           float tot = __fadd_rn(sum.x, sum.y);
           tot = __fadd_rn(tot, __shfl_xor_sync(kFull, tot, 16));
-          if (lane < kGradSlotsRGB) s_grad[wib][j * kGradStride + lane] = tot * red_sign;
+          if (lane < kRedSums) s_grad[wib][j * kGradStride + red_dst] = tot * red_sign;
           __syncwarp();  // the rows are read before the next entry writes them
         }
       }
-      // flush the batch: one vector atomic per 4 slots and entry for the warp
+      // flush the batch: complete the centre gradient, then one vector atomic per
+      // 4 slots and entry for the warp
       __syncwarp();
 #pragma unroll
       for (int r = 0; r < ROWS; ++r) {
         const int e = r * 32 + lane;
         if (e < cnt) {
-          float4* row = reinterpret_cast<float4*>(&s_grad[wib][e * kGradStride]);
+          float* rs = &s_grad[wib][e * kGradStride];
+          // dL/dc = -2 x the filter sums, minus the totals of dL/du, dL/dv and dL/dden times
+          // the coefficients with which x - c enters u, v and den (g1.x, g1.z, g2.y for the
+          // x offset; g1.y, g1.w, g2.z for y); the e0 slot holds the dL/dden total
+          const float4 g1 = s_g1[wib][e], g2 = s_g2[wib][e];
+          const float su = rs[kSumU], sv = rs[kSumV], se = rs[kGe0];
+          rs[kGcx] = -2.f * rs[kGcx] - g2.y * se - g1.z * sv - g1.x * su;
+          rs[kGcy] = -2.f * rs[kGcy] - g2.z * se - g1.w * sv - g1.y * su;
+          rs[kSumU] = 0.f;
+          rs[kSumV] = 0.f;
+          float4* row = reinterpret_cast<float4*>(rs);
           float4* dst = reinterpret_cast<float4*>(a.grad_rec + (size_t)s_idx[wib][e] * kGradStride);
 #pragma unroll
           for (int q = 0; q < kGradStride / 4; ++q) {

@@ -480,7 +480,7 @@ __global__ void tile_work_kernel(const uint2* __restrict__ ranges, const uint2* 
   const uint2 r = ranges[t];
   uint32_t len = r.y - r.x;
   if (ranges2) len += ranges2[t].y - ranges2[t].x;
-  work_key[t] = 255u - work_code(len);
+  work_key[t] = queue_key(len);
   ids[t] = t;
 }
 
@@ -864,7 +864,7 @@ __global__ void second_queue_kernel(const uint2* __restrict__ ranges2, uint32_t 
   const uint2 r2 = ranges2[t];
   const uint32_t len = r2.y - r2.x;
   if (len) atomicAdd(n_again, 1u);
-  work_key[t] = 255u - work_code(len);
+  work_key[t] = queue_key(len);
   ids[t] = t;
 }
 
