@@ -33,6 +33,12 @@ __device__ unsigned long long g_diag[8];
 #ifndef OCGS_BWD_WARPS_GEO
 #define OCGS_BWD_WARPS_GEO 12
 #endif
+// warps per CTA of the backward (the resident-warp targets are multiples of it)
+#ifndef OCGS_BWD_BLOCK_WARPS
+#define OCGS_BWD_BLOCK_WARPS 4
+#endif
+constexpr int kBW = OCGS_BWD_BLOCK_WARPS;
+static_assert(OCGS_BWD_WARPS % kBW == 0 && OCGS_BWD_WARPS_GEO % kBW == 0, "resident warps per CTA");
 
 // One halving step of a warp transpose-reduction: lanes with bit OFF clear keep
 // the first ceil(C/2) of their C values, the others keep the rest, and each
@@ -95,20 +101,19 @@ __device__ __forceinline__ bool negated_slot(int q) { return q == kGe0 || q == k
 // normal terms of the adjoint are zero and are not evaluated (13 slots instead
 // of 18).
 template <int TW, int TH, int PPT, int BATCH, bool GEO>
-__global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD_WARPS) / kBlockWarps)
+__global__ void __launch_bounds__(kBW * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD_WARPS) / kBW)
     raster_bwd_kernel(const RasterBwdArgs a) {
   constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
-  constexpr int NG = GEO ? kGradSlots : kGradSlotsRGB;
   constexpr int ROWS = BATCH > 32 ? BATCH / 32 : 1;  // gradient rows of a batch each lane flushes
   using B = Batch<BATCH>;
-  __shared__ float4 s_g0[kBlockWarps][BATCH], s_g1[kBlockWarps][BATCH], s_g2[kBlockWarps][BATCH],
-      s_a0[kBlockWarps][BATCH];
-  __shared__ float2 s_a1[kBlockWarps][BATCH];
-  __shared__ uint32_t s_idx[kBlockWarps][BATCH];
-  __shared__ int s_q[kBlockWarps][BATCH];  // list position of each kept entry
-  __shared__ __align__(16) float s_grad[kBlockWarps][BATCH * kGradStride];  // per-batch gradient sums of each entry
-  __shared__ float s_rb[kBlockWarps][BATCH];
-  __shared__ __align__(16) float2 s_red[kBlockWarps][GEO ? 1 : kRedSize];
+  __shared__ float4 s_g0[kBW][BATCH], s_g1[kBW][BATCH], s_g2[kBW][BATCH],
+      s_a0[kBW][BATCH];
+  __shared__ float2 s_a1[kBW][BATCH];
+  __shared__ uint32_t s_idx[kBW][BATCH];
+  __shared__ int s_q[kBW][BATCH];  // list position of each kept entry
+  __shared__ __align__(16) float s_grad[kBW][BATCH * kGradStride];  // per-batch gradient sums of each entry
+  __shared__ float s_rb[kBW][BATCH];
+  __shared__ __align__(16) float2 s_red[kBW][GEO ? 1 : kRedSize];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
 #pragma unroll
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
       if (unit >= n_units) break;
     } else {
       if (it > 0) break;
-      unit = blockIdx.x * kBlockWarps + wib;
+      unit = blockIdx.x * kBW + wib;
       if (unit >= n_units) break;
     }
     uint32_t tile = unit / WPT;
@@ -412,11 +417,11 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (GEO ? OCGS_BWD_WARPS_GEO : 
 
 template <int TW, int TH, int PPT, int BATCH>
 cudaError_t bwd_dispatch(const RasterBwdArgs& a, cudaStream_t s) {
-  const unsigned grid = warp_grid<TW, TH, PPT>(a.persistent_ctas, a.n_tiles);
+  const unsigned grid = warp_grid<TW, TH, PPT, kBW>(a.persistent_ctas, a.n_tiles);
   if (grid == 0) return cudaSuccess;
   if (a.d_out.depth || a.d_out.normal || a.d_out.depth2)
-    raster_bwd_kernel<TW, TH, PPT, BATCH, true><<<grid, kBlockWarps * 32, 0, s>>>(a);
-  else raster_bwd_kernel<TW, TH, PPT, BATCH, false><<<grid, kBlockWarps * 32, 0, s>>>(a);
+    raster_bwd_kernel<TW, TH, PPT, BATCH, true><<<grid, kBW * 32, 0, s>>>(a);
+  else raster_bwd_kernel<TW, TH, PPT, BATCH, false><<<grid, kBW * 32, 0, s>>>(a);
   return launched();
 }
 

@@ -50,13 +50,13 @@ __device__ __forceinline__ float4 warp_band(const DevCam& cam, int local, int wt
                      (float)(min(y0 + kRows, cam.H) - 1) + 0.5f);
 }
 
-// CTAs of kBlockWarps independent warps: persistent_ctas counts tile-sized CTAs
+// CTAs of BW independent warps: persistent_ctas counts tile-sized CTAs
 // (TW*TH/PPT threads), converted to the same number of warps
-template <int TW, int TH, int PPT>
+template <int TW, int TH, int PPT, int BW = kBlockWarps>
 unsigned warp_grid(int persistent_ctas, uint32_t n_tiles) {
   constexpr uint64_t WPT = TW * TH / PPT / 32;
   const uint64_t warps = (persistent_ctas ? (uint64_t)persistent_ctas : (uint64_t)n_tiles) * WPT;
-  return (unsigned)((warps + kBlockWarps - 1) / kBlockWarps);
+  return (unsigned)((warps + BW - 1) / BW);
 }
 
 // ----------------------------------------------------------------------------- one surfel at two pixels
@@ -145,12 +145,6 @@ struct SplatEval2 {
   bool ok[2];       // live and rho <= rb (within 3 sigma, alpha >= 1/255): blended unless the pixel stops
 };
 
-// Opacity below which the 0.99 clamp of alpha never applies: G = exp(-rho/2) <= 1
-// for rho >= 0 (the base-2 exponential's relative error is about 2^-22), so o G <
-// 0.989 (1 + 2^-20) < 0.99.  A record below it takes the clamp-free path, whose
-// alpha = o (ok ? G : 0) equals the clamped form bit for bit there.
-constexpr float kNoClampO = 0.989f;
-
 // rho = min(rho3, rho2), rho3 = (u^2 + v^2) = q / den^2: the surfel term wins where
 // rho3 <= rho2 (with den = 0, rho3 is +inf or NaN and the filter term wins).
 // live[i]: the pixel still composites (forward) or lies before its last blended
@@ -160,7 +154,8 @@ constexpr float kNoClampO = 0.989f;
 // products the backward masks with zero stay finite (the forward reads z only).
 // A skipped candidate gets alpha = 0 (T (1 - 0) = T and w = 0 exactly) and
 // Gc = 0, which zeroes every term of its adjoint without further masks.
-// CLAMP = false: the record's o < kNoClampO (alpha never reaches the clamp).
+// CLAMP = false: the record's o < kNoClampO (alpha never reaches the clamp; see
+// kNoClampO).
 template <bool FINITE, bool EWA = false, bool CLAMP = true>
 __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb,
                                                   bool live0, bool live1) {
@@ -187,8 +182,13 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
     if (FINITE)
       e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);
   } else {
+#ifdef OCGS_NOCLAMP_SELECT
+    e.alpha = make_float2(e.ok[0] ? oG.x : 0.0f, e.ok[1] ? oG.y : 0.0f);
+    if (FINITE) e.Gc = make_float2(e.ok[0] ? G.x : 0.0f, e.ok[1] ? G.y : 0.0f);
+#else
     e.Gc = make_float2(e.ok[0] ? G.x : 0.0f, e.ok[1] ? G.y : 0.0f);
     e.alpha = __fmul2_rn(bc2(g0.z), e.Gc);  // o G where blended, o 0 = 0 elsewhere
+#endif
   }
   const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
   e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);
