@@ -400,7 +400,6 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
 
     RasterArgs ra{};
     ra.ewa = ewa ? 1 : 0;
-    ra.no_clamp = !ewa && !(status & kStatusOpaque);  // status: read back after the projection
     ra.cams = st->d_cams;
     ra.tile_prefix = st->d_tile_prefix;
     ra.n_views = V;
@@ -506,7 +505,6 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     }
     RasterArgs ra{};
     ra.ewa = ewa ? 1 : 0;
-    ra.no_clamp = !ewa && !(status & kStatusOpaque);  // status: read back after the projection
     ra.cams = st->d_cams;
     ra.tile_prefix = st->d_tile_prefix;
     ra.n_views = V;

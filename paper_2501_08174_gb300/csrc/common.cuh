@@ -28,8 +28,8 @@ constexpr float kAlphaMin = 1.0f / 255.0f;  // skip below this opacity
 constexpr float kAlphaMax = 0.99f;          // opacity clamp
 // Opacity below which the 0.99 clamp of alpha never applies: G = exp(-rho/2) <= 1
 // for rho >= 0 (the base-2 exponential's relative error is about 2^-22), so o G <
-// 0.989 (1 + 2^-20) < 0.99.  A record below it may take a clamp-free path, whose
-// alpha = o (blended ? G : 0) equals the clamped form bit for bit there.
+// 0.989 (1 + 2^-20) < 0.99.  The backward takes a clamp-free path for such a
+// record, whose alpha = o (blended ? G : 0) equals the clamped form bit for bit.
 constexpr float kNoClampO = 0.989f;
 constexpr float kTEps = 1e-4f;              // stop when T (1 - alpha) would fall below this
 constexpr float kInvSigmaF2 = 2.0f;         // 1 / sigma_f^2 of the screen low-pass filter (sigma_f^2 = 1/2 px^2)
@@ -38,8 +38,6 @@ constexpr float kInvSigmaF2 = 2.0f;         // 1 / sigma_f^2 of the screen low-p
 constexpr int kStatusNonFinite = 1;
 constexpr int kStatusCapacity = 2;
 constexpr int kStatusTimeout = 4;
-// informational, not an error: a Gaussian has o >= kNoClampO, so the alpha clamp may apply
-constexpr int kStatusOpaque = 8;
 
 struct DevCam {
   float R[9];        // world->camera rotation, row-major
@@ -447,9 +445,6 @@ struct RasterArgs {
   uint32_t* open;
   uint8_t* done;
   const uint2* prior;
-  // every record has o < kNoClampO (no kStatusOpaque from the projection): the
-  // clamp-free instantiation may run
-  int no_clamp;
 };
 // ppt: pixels per thread (vertically adjacent): 1 or 2, and 4 for 16-wide tiles;
 // batch: records a warp stages per batch (32; also 16 and 64 for the 16-wide

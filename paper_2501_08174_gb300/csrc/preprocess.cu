@@ -240,12 +240,6 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
   const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   if (!finite) atomicOr(status, kStatusNonFinite);
   const bool bad = !finite || !(qn2 > 0.f) || !(s.x > 0.f) || !(s.y > 0.f) || !(o >= kAlphaMin);
-  {
-    // one atomic per warp for the Gaussians whose alpha may reach the clamp
-    const bool opaque = !bad && o >= kNoClampO;
-    const unsigned m = __ballot_sync(__activemask(), opaque);
-    if (opaque && (threadIdx.x & 31) == __ffs(m) - 1) atomicOr(status, kStatusOpaque);
-  }
   const Frame f = make_frame(q);
   // support bound in rho: the 3-sigma cut, tightened where o exp(-rho/2) < 1/255 anyway
   const float rho_b = bad ? 0.f : support_rho(o);

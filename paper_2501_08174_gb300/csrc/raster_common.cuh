@@ -154,8 +154,8 @@ struct SplatEval2 {
 // products the backward masks with zero stay finite (the forward reads z only).
 // A skipped candidate gets alpha = 0 (T (1 - 0) = T and w = 0 exactly) and
 // Gc = 0, which zeroes every term of its adjoint without further masks.
-// CLAMP = false: the record's o < kNoClampO (alpha never reaches the clamp; see
-// kNoClampO).
+// CLAMP = false (backward): the record's o < kNoClampO, so alpha never reaches
+// the clamp (see kNoClampO).
 template <bool FINITE, bool EWA = false, bool CLAMP = true>
 __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 g2, const SplatHead2& h, float rb,
                                                   bool live0, bool live1) {
@@ -182,13 +182,8 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
     if (FINITE)
       e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);
   } else {
-#ifdef OCGS_NOCLAMP_SELECT
-    e.alpha = make_float2(e.ok[0] ? oG.x : 0.0f, e.ok[1] ? oG.y : 0.0f);
-    if (FINITE) e.Gc = make_float2(e.ok[0] ? G.x : 0.0f, e.ok[1] ? G.y : 0.0f);
-#else
     e.Gc = make_float2(e.ok[0] ? G.x : 0.0f, e.ok[1] ? G.y : 0.0f);
     e.alpha = __fmul2_rn(bc2(g0.z), e.Gc);  // o G where blended, o 0 = 0 elsewhere
-#endif
   }
   const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
   e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);

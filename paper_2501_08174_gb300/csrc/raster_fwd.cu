@@ -36,8 +36,7 @@ __device__ unsigned long long g_diag[8];
 
 // Q2: also accumulate Q = sum w z^2 (the depth distortion's third plane)
 // EWA: the records are projected 3D Gaussians (the 3DGS variant of Appendix B)
-// CLAMP = false: every record has o < kNoClampO, so alpha never reaches the clamp
-template <int TW, int TH, int PPT, int BATCH, bool IMG, bool SCORE, bool Q2, bool EWA, bool CLAMP = true>
+template <int TW, int TH, int PPT, int BATCH, bool IMG, bool SCORE, bool Q2, bool EWA>
 __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OCGS_FWD_WARPS) / kBlockWarps)
     raster_fwd_kernel(const RasterArgs a) {
   constexpr int WPT = TW * TH / PPT / 32;  // warps per tile: each owns a band of full tile rows
@@ -189,7 +188,7 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             const int k0 = 2 * p, k1 = 2 * p + 1;
             const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
             const SplatHead2 h = splat_head2(g0, g1, g2, col, py);
-            const SplatEval2 e = splat_tail2<false, EWA, CLAMP>(g0, g2, h, rb, !done[k0], !done[k1]);
+            const SplatEval2 e = splat_tail2<false, EWA>(g0, g2, h, rb, !done[k0], !done[k1]);
             float2 Tn = __fmul2_rn(T[p], __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
             float2 w = __fmul2_rn(e.alpha, T[p]);
             const uint32_t l0 = last[k0], l1 = last[k1];
@@ -213,6 +212,9 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             }
             T[p] = Tn;
             if (SCORE) wmax = fmaxf(wmax, fmaxf(w.x, w.y));
+#ifdef OCGS_COUNT
+            OCGS_DIAG(2, (w.x > 0.f ? 1 : 0) + (w.y > 0.f ? 1 : 0));  // (pixel, entry) blends
+#endif
           }
           if (stopped) {  // done only changes when a pixel stops
             alldone = true;
@@ -281,12 +283,6 @@ cudaError_t fwd_dispatch(const RasterArgs& a, bool img, cudaStream_t s) {
     if (img && score) raster_fwd_kernel<TW, TH, PPT, BATCH, true, true, false, true><<<grid, NT, 0, s>>>(a);
     else if (img) raster_fwd_kernel<TW, TH, PPT, BATCH, true, false, false, true><<<grid, NT, 0, s>>>(a);
     else if (score) raster_fwd_kernel<TW, TH, PPT, BATCH, false, true, false, true><<<grid, NT, 0, s>>>(a);
-    else return cudaSuccess;
-  } else if (a.no_clamp && !q2) {
-    // the projection saw no Gaussian with o >= kNoClampO: the clamp-free instantiations
-    if (img && score) raster_fwd_kernel<TW, TH, PPT, BATCH, true, true, false, false, false><<<grid, NT, 0, s>>>(a);
-    else if (img) raster_fwd_kernel<TW, TH, PPT, BATCH, true, false, false, false, false><<<grid, NT, 0, s>>>(a);
-    else if (score) raster_fwd_kernel<TW, TH, PPT, BATCH, false, true, false, false, false><<<grid, NT, 0, s>>>(a);
     else return cudaSuccess;
   } else if (img && score && q2) raster_fwd_kernel<TW, TH, PPT, BATCH, true, true, true, false><<<grid, NT, 0, s>>>(a);
   else if (img && q2) raster_fwd_kernel<TW, TH, PPT, BATCH, true, false, true, false><<<grid, NT, 0, s>>>(a);

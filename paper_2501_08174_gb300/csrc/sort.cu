@@ -209,11 +209,7 @@ __global__ void __launch_bounds__(kBlock) radix_scatter_kernel(const uint32_t* _
   for (int j = 0; j < kItems; ++j) {
     const uint32_t k = wbase + j * 32 + lane;
     const uint32_t d = k < n ? ((key[j] >> shift) & mask) : (uint32_t)R;
-#ifdef OCGS_MATCH_PEERS
-    const unsigned peers = __match_any_sync(kFull, d);
-#else
     const unsigned peers = digit_peers(d, bits);
-#endif
     const int leader = __ffs(peers) - 1;
     uint32_t before = 0;
     if (lane == leader) before = whist[warp][d];
