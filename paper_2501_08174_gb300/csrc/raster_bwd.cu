@@ -282,39 +282,39 @@ __global__ void __launch_bounds__(kBW * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD
             OCGS_DIAG(6, (e.ok[0] ? 1 : 0) + (e.ok[1] ? 1 : 0));  // (pixel, entry) blends
 #endif
             // undo the entry: T before it, its weight, and dL/dalpha
-            const float2 om = __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
+            const float2 om = pfma(e.alpha, bc2(-1.f), bc2(1.f));  // 1 - alpha
             const float2 inv = make_float2(__fdividef(1.f, om.x), __fdividef(1.f, om.y));
-            const float2 Ti = __fmul2_rn(T[p], inv);
-            const float2 w = __fmul2_rn(e.alpha, Ti);
-            float2 F = __fmul2_rn(gC0[p], bc2(ap.x));
-            F = __ffma2_rn(gC1[p], bc2(ap.y), F);
-            F = __ffma2_rn(gC2[p], bc2(ap.z), F);
+            const float2 Ti = pmul(T[p], inv);
+            const float2 w = pmul(e.alpha, Ti);
+            float2 F = pmul(gC0[p], bc2(ap.x));
+            F = pfma(gC1[p], bc2(ap.y), F);
+            F = pfma(gC2[p], bc2(ap.z), F);
             if (GEO) {
-              F = __ffma2_rn(gD[p], e.z, F);
-              F = __ffma2_rn(__fmul2_rn(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
-              F = __ffma2_rn(gN0[p], bc2(ap.w), F);
-              F = __ffma2_rn(gN1[p], bc2(an.x), F);
-              F = __ffma2_rn(gN2[p], bc2(an.y), F);
+              F = pfma(gD[p], e.z, F);
+              F = pfma(pmul(gQ[p], e.z), e.z, F);  // d(sum w z^2)/dw = z^2
+              F = pfma(gN0[p], bc2(ap.w), F);
+              F = pfma(gN1[p], bc2(an.x), F);
+              F = pfma(gN2[p], bc2(an.y), F);
             }
             // dL/dalpha = T_i F + (gAT - S) / (1 - alpha)
-            const float2 ga = __ffma2_rn(Ti, F, __fmul2_rn(__ffma2_rn(S[p], bc2(-1.f), gAT[p]), inv));
-            S[p] = __ffma2_rn(w, F, S[p]);
+            const float2 ga = pfma(Ti, F, pmul(pfma(S[p], bc2(-1.f), gAT[p]), inv));
+            S[p] = pfma(w, F, S[p]);
             // a skipped candidate has alpha = 0, and the fast reciprocal of 1 - 0 is exactly 1
             // on this GPU (checked at 1, 2 and 0.5), so T passes through it unchanged
             T[p] = Ti;
-            acc[kGr] = __ffma2_rn(gC0[p], w, acc[kGr]);
-            acc[kGg] = __ffma2_rn(gC1[p], w, acc[kGg]);
-            acc[kGb] = __ffma2_rn(gC2[p], w, acc[kGb]);
+            acc[kGr] = pfma(gC0[p], w, acc[kGr]);
+            acc[kGg] = pfma(gC1[p], w, acc[kGg]);
+            acc[kGb] = pfma(gC2[p], w, acc[kGb]);
             if (GEO) {
-              acc[kGnx] = __ffma2_rn(gN0[p], w, acc[kGnx]);
-              acc[kGny] = __ffma2_rn(gN1[p], w, acc[kGny]);
-              acc[kGnz] = __ffma2_rn(gN2[p], w, acc[kGnz]);
+              acc[kGnx] = pfma(gN0[p], w, acc[kGnx]);
+              acc[kGny] = pfma(gN1[p], w, acc[kGny]);
+              acc[kGnz] = pfma(gN2[p], w, acc[kGnz]);
             }
             // alpha = o G below the clamp: dalpha/do = G, dalpha/drho = -o G / 2
             // (Gc is 0 at the clamp and for skipped candidates); gs2 = 2 dL/drho
-            const float2 gop = __fmul2_rn(ga, e.Gc);
-            acc[kGo] = __fadd2_rn(acc[kGo], gop);
-            const float2 gs2 = __fmul2_rn(gop, no);
+            const float2 gop = pmul(ga, e.Gc);
+            acc[kGo] = padd(acc[kGo], gop);
+            const float2 gs2 = pmul(gop, no);
             // rho and depth came from the surfel's (u, v) where it won the min, from the
             // screen-space filter elsewhere.  e.r and e.rho3 are 0 where the filter won,
             // so the surfel terms below vanish there without a mask.
@@ -322,29 +322,29 @@ __global__ void __launch_bounds__(kBW * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD
             float2 gzs = bc2(0.f);
             if (GEO) {
               // d/dz of w (gD z + gQ z^2)
-              const float2 gz = __fmul2_rn(__ffma2_rn(__fmul2_rn(bc2(2.f), gQ[p]), e.z, gD[p]), w);
+              const float2 gz = pmul(pfma(pmul(bc2(2.f), gQ[p]), e.z, gD[p]), w);
               gzs = make_float2(e.surf[0] ? gz.x : 0.f, e.surf[1] ? gz.y : 0.f);
-              acc[kGzc] = __fadd2_rn(acc[kGzc], __ffma2_rn(gzs, bc2(-1.f), gz));
-              acc[kGzD] = __ffma2_rn(gzs, e.r, acc[kGzD]);
+              acc[kGzc] = padd(acc[kGzc], pfma(gzs, bc2(-1.f), gz));
+              acc[kGzD] = pfma(gzs, e.r, acc[kGzD]);
             }
             // 2 grho / den^2, shared by the u, v and den terms (rho3 = q / den^2)
-            const float2 t = __fmul2_rn(gs2, __fmul2_rn(e.r, e.r));
-            const float2 gun = __fmul2_rn(t, hd[p].un);
-            const float2 gvn = __fmul2_rn(t, hd[p].vn);
+            const float2 t = pmul(gs2, pmul(e.r, e.r));
+            const float2 gun = pmul(t, hd[p].un);
+            const float2 gvn = pmul(t, hd[p].vn);
             // -dL/dden = (2 grho rho3 + gz z) / den; the e slots accumulate negated and
             // are flipped when the lanes are summed
-            const float2 ngden = GEO ? __fmul2_rn(__ffma2_rn(gs2, e.rho3, __fmul2_rn(gzs, e.z)), e.r)
-                                     : __fmul2_rn(t, __fmul2_rn(hd[p].q, e.r));
-            acc[kSumU] = __fadd2_rn(acc[kSumU], gun);
-            acc[kSumV] = __fadd2_rn(acc[kSumV], gvn);
-            acc[kGA01] = __ffma2_rn(gun, hd[p].dy, acc[kGA01]);
-            acc[kGA11] = __ffma2_rn(gvn, hd[p].dy, acc[kGA11]);
-            acc[kGe0] = __fadd2_rn(acc[kGe0], ngden);
-            acc[kGe2] = __ffma2_rn(ngden, hd[p].dy, acc[kGe2]);
+            const float2 ngden = GEO ? pmul(pfma(gs2, e.rho3, pmul(gzs, e.z)), e.r)
+                                     : pmul(t, pmul(hd[p].q, e.r));
+            acc[kSumU] = padd(acc[kSumU], gun);
+            acc[kSumV] = padd(acc[kSumV], gvn);
+            acc[kGA01] = pfma(gun, hd[p].dy, acc[kGA01]);
+            acc[kGA11] = pfma(gvn, hd[p].dy, acc[kGA11]);
+            acc[kGe0] = padd(acc[kGe0], ngden);
+            acc[kGe2] = pfma(ngden, hd[p].dy, acc[kGe2]);
             // the filter term: d rho2 / d(c) = -4 (x - c) with rho2 = 2 |x - c|^2 (the
             // factor -2 and dx are applied later)
-            acc[kGcx] = __fadd2_rn(acc[kGcx], gf2);
-            acc[kGcy] = __ffma2_rn(gf2, hd[p].dy, acc[kGcy]);
+            acc[kGcx] = padd(acc[kGcx], gf2);
+            acc[kGcy] = pfma(gf2, hd[p].dy, acc[kGcy]);
           }
         };
         if (g0.z < kNoClampO) pairs(std::false_type{});
@@ -356,10 +356,10 @@ __global__ void __launch_bounds__(kBW * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD
 #endif
         // the column offset of this thread's pixels
         const float2 dx = bc2(col.dx);
-        acc[kGA00] = __fmul2_rn(acc[kSumU], dx);
-        acc[kGA10] = __fmul2_rn(acc[kSumV], dx);
-        acc[kGe1] = __fmul2_rn(acc[kGe0], dx);
-        acc[kGcx] = __fmul2_rn(acc[kGcx], dx);
+        acc[kGA00] = pmul(acc[kSumU], dx);
+        acc[kGA10] = pmul(acc[kSumV], dx);
+        acc[kGe1] = pmul(acc[kGe0], dx);
+        acc[kGcx] = pmul(acc[kGcx], dx);
         if (GEO) {
           float gr[kGradStride];
 #pragma unroll
@@ -380,8 +380,8 @@ __global__ void __launch_bounds__(kBW * 32, (GEO ? OCGS_BWD_WARPS_GEO : OCGS_BWD
 #pragma unroll
           for (int i = 0; i < 4; ++i) s4[i] = col[i * kRedRow];
 #pragma unroll
-          for (int i = 4; i < 16; ++i) s4[i & 3] = __fadd2_rn(s4[i & 3], col[i * kRedRow]);
-          const float2 sum = __fadd2_rn(__fadd2_rn(s4[0], s4[1]), __fadd2_rn(s4[2], s4[3]));
+          for (int i = 4; i < 16; ++i) s4[i & 3] = padd(s4[i & 3], col[i * kRedRow]);
+          const float2 sum = padd(padd(s4[0], s4[1]), padd(s4[2], s4[3]));
           float tot = __fadd_rn(sum.x, sum.y);
           tot = __fadd_rn(tot, __shfl_xor_sync(kFull, tot, 16));
           if (lane < kRedSums) s_grad[wib][j * kGradStride + red_dst] = tot * red_sign;

@@ -78,10 +78,27 @@ __device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float
   return c;
 }
 
-// Two pixels of one column (rows py.x and py.y) are evaluated together on the
-// packed FP32x2 pipes of sm_100+: every lane of __ffma2_rn / __fmul2_rn /
-// __fadd2_rn rounds as the scalar operation does, so a pair gives the two
-// scalar results bit for bit with half the issued instructions.
+// Two pixels of one column (rows py.x and py.y) are evaluated together as a
+// pair.  pfma / pmul / padd round each lane as the scalar operation does, so a
+// pair gives the two scalar results bit for bit whether it runs on the packed
+// FP32x2 instructions of sm_100+ (__ffma2_rn, ...) or as two scalar ones
+// (-DOCGS_SCALAR_PAIRS: measured 9-10 % slower in both rasterizers on 500k
+// surfels x 16 views).
+#ifdef OCGS_SCALAR_PAIRS
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+#else
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#endif
 __device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
 __device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
 __device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
@@ -107,12 +124,12 @@ struct SplatHead2 {
 __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 g1, const float4 g2,
                                                   const SplatColumn& c, float2 py) {
   SplatHead2 h;
-  h.dy = __fadd2_rn(py, bc2(-g0.y));
-  h.un = __ffma2_rn(bc2(g1.y), h.dy, bc2(c.ux));
-  h.vn = __ffma2_rn(bc2(g1.w), h.dy, bc2(c.vx));
-  h.den = __ffma2_rn(bc2(g2.z), h.dy, bc2(c.ex));
-  h.rho2 = __fmul2_rn(bc2(kInvSigmaF2), __ffma2_rn(h.dy, h.dy, bc2(c.dx2)));
-  h.q = __ffma2_rn(h.un, h.un, __fmul2_rn(h.vn, h.vn));
+  h.dy = padd(py, bc2(-g0.y));
+  h.un = pfma(bc2(g1.y), h.dy, bc2(c.ux));
+  h.vn = pfma(bc2(g1.w), h.dy, bc2(c.vx));
+  h.den = pfma(bc2(g2.z), h.dy, bc2(c.ex));
+  h.rho2 = pmul(bc2(kInvSigmaF2), pfma(h.dy, h.dy, bc2(c.dx2)));
+  h.q = pfma(h.un, h.un, pmul(h.vn, h.vn));
   return h;
 }
 
@@ -122,7 +139,7 @@ __device__ __forceinline__ SplatHead2 splat_head2(const float4 g0, const float4 
 // to skip an entry no pixel of the band can blend; the blend decision itself is
 // taken in splat_tail2.
 __device__ __forceinline__ bool may_blend(const SplatHead2& h, float rb, bool live0, bool live1) {
-  const float2 lim = __fmul2_rn(bc2(__fmul_rn(rb, 1.0001f)), __fmul2_rn(h.den, h.den));
+  const float2 lim = pmul(bc2(__fmul_rn(rb, 1.0001f)), pmul(h.den, h.den));
   return (live0 && (h.q.x <= lim.x || h.rho2.x <= rb)) || (live1 && (h.q.y <= lim.y || h.rho2.y <= rb));
 }
 
@@ -161,7 +178,7 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
                                                   bool live0, bool live1) {
   SplatEval2 e;
   const float2 r = EWA ? bc2(1.0f) : make_float2(__fdividef(1.0f, h.den.x), __fdividef(1.0f, h.den.y));
-  const float2 r3 = EWA ? h.q : __fmul2_rn(h.q, __fmul2_rn(r, r));
+  const float2 r3 = EWA ? h.q : pmul(h.q, pmul(r, r));
   e.surf[0] = EWA || r3.x <= h.rho2.x;
   e.surf[1] = EWA || r3.y <= h.rho2.y;
   if (FINITE) {
@@ -172,9 +189,9 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
     e.rho3 = r3;
   }
   const float2 rho = make_float2(e.surf[0] ? r3.x : h.rho2.x, e.surf[1] ? r3.y : h.rho2.y);
-  const float2 ex = __fmul2_rn(bc2(kNegHalfLog2e), rho);
+  const float2 ex = pmul(bc2(kNegHalfLog2e), rho);
   const float2 G = make_float2(exp2_approx(ex.x), exp2_approx(ex.y));
-  const float2 oG = __fmul2_rn(bc2(g0.z), G);
+  const float2 oG = pmul(bc2(g0.z), G);
   e.ok[0] = live0 && (rho.x <= rb);
   e.ok[1] = live1 && (rho.y <= rb);
   if (CLAMP) {
@@ -183,9 +200,9 @@ __device__ __forceinline__ SplatEval2 splat_tail2(const float4 g0, const float4 
       e.Gc = make_float2(e.ok[0] && oG.x < kAlphaMax ? G.x : 0.0f, e.ok[1] && oG.y < kAlphaMax ? G.y : 0.0f);
   } else {
     e.Gc = make_float2(e.ok[0] ? G.x : 0.0f, e.ok[1] ? G.y : 0.0f);
-    e.alpha = __fmul2_rn(bc2(g0.z), e.Gc);  // o G where blended, o 0 = 0 elsewhere
+    e.alpha = pmul(bc2(g0.z), e.Gc);  // o G where blended, o 0 = 0 elsewhere
   }
-  const float2 zs = __fmul2_rn(bc2(g2.w), e.r);
+  const float2 zs = pmul(bc2(g2.w), e.r);
   e.z = make_float2(e.surf[0] ? zs.x : g0.w, e.surf[1] ? zs.y : g0.w);
   return e;
 }

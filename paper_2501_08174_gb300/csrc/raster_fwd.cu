@@ -189,8 +189,8 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
             const float2 py = make_float2((float)(py0 + k0) + 0.5f, (float)(py0 + k1) + 0.5f);
             const SplatHead2 h = splat_head2(g0, g1, g2, col, py);
             const SplatEval2 e = splat_tail2<false, EWA>(g0, g2, h, rb, !done[k0], !done[k1]);
-            float2 Tn = __fmul2_rn(T[p], __ffma2_rn(e.alpha, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
-            float2 w = __fmul2_rn(e.alpha, T[p]);
+            float2 Tn = pmul(T[p], pfma(e.alpha, bc2(-1.f), bc2(1.f)));  // T (1 - alpha)
+            float2 w = pmul(e.alpha, T[p]);
             const uint32_t l0 = last[k0], l1 = last[k1];
             if (e.ok[0]) last[k0] = pos;
             if (e.ok[1]) last[k1] = pos;
@@ -201,14 +201,14 @@ __global__ void __launch_bounds__(kBlockWarps * 32, (Q2 ? OCGS_FWD_WARPS_Q2 : OC
               stopped = true;
             }
             if (IMG) {
-              c0[p] = __ffma2_rn(w, bc2(ap.x), c0[p]);
-              c1[p] = __ffma2_rn(w, bc2(ap.y), c1[p]);
-              c2[p] = __ffma2_rn(w, bc2(ap.z), c2[p]);
-              dep[p] = __ffma2_rn(w, e.z, dep[p]);
-              if (Q2) qz[p] = __ffma2_rn(__fmul2_rn(w, e.z), e.z, qz[p]);
-              n0[p] = __ffma2_rn(w, bc2(ap.w), n0[p]);
-              n1[p] = __ffma2_rn(w, bc2(an.x), n1[p]);
-              n2[p] = __ffma2_rn(w, bc2(an.y), n2[p]);
+              c0[p] = pfma(w, bc2(ap.x), c0[p]);
+              c1[p] = pfma(w, bc2(ap.y), c1[p]);
+              c2[p] = pfma(w, bc2(ap.z), c2[p]);
+              dep[p] = pfma(w, e.z, dep[p]);
+              if (Q2) qz[p] = pfma(pmul(w, e.z), e.z, qz[p]);
+              n0[p] = pfma(w, bc2(ap.w), n0[p]);
+              n1[p] = pfma(w, bc2(an.x), n1[p]);
+              n2[p] = pfma(w, bc2(an.y), n2[p]);
             }
             T[p] = Tn;
             if (SCORE) wmax = fmaxf(wmax, fmaxf(w.x, w.y));
