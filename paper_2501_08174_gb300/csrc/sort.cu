@@ -276,30 +276,80 @@ __global__ void iota_kernel(uint32_t* v, uint32_t n) {
 }
 
 constexpr int kThreads = 256;
-constexpr int kSmallRows = 16;  // a lane handles a record with at most this many candidate rows alone
+// a record with at most this many candidate rows is a small one: its row runs are
+// kept in shared memory and its tiles written in the warp-flat list
+constexpr int kSmallRows = 16;
 
 __device__ __forceinline__ int row_count(const RowRuns& rr) {
   return max(0, rr.a1 - rr.a0 + 1) + max(0, rr.b1 - rr.b0 + 1);
 }
 
-// Exact tile count of each record: one thread per record, one closed-form
-// coverage computation per candidate tile row.
+// What a lane knows of its record for the rows of that record that other lanes
+// of its warp evaluate: the support conic, the candidate tile rectangle and the view.
+struct RowOwner {
+  SupportConic k;
+  int4 rc;
+  int tile_offset, tiles_x, W, H;
+};
+
+// The candidate tile rows of the warp's 32 records, flattened over the lanes:
+// f(ri, ty) runs once for every row ty of record ri, 32 rows at a time, so
+// records with many rows no longer leave the lanes of small ones idle.
+// nrows: the rows of this lane's record (0 for none); s_own[lane] must hold it.
+template <class F>
+__device__ __forceinline__ void for_warp_rows(int nrows, int lane, int* s_incl, const RowOwner* s_own, F f) {
+  const int incl = warp_inclusive_scan<int>(nrows, lane);
+  s_incl[lane] = incl;
+  const int total = __shfl_sync(kFull, incl, 31);
+  __syncwarp();
+  for (int q0 = 0; q0 < total; q0 += 32) {
+    const int q = q0 + lane;
+    if (q < total) {
+      int lo = 0, hi = 31;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (s_incl[mid] > q) hi = mid; else lo = mid + 1;
+      }
+      const int excl = lo > 0 ? s_incl[lo - 1] : 0;
+      f(lo, s_own[lo].rc.y + (q - excl));
+    }
+  }
+  __syncwarp();
+}
+
+// Exact tile count of each record: one closed-form coverage computation per
+// candidate tile row, the rows of a warp's 32 records spread over its lanes.
 __global__ void __launch_bounds__(kThreads) tile_count_kernel(const float4* __restrict__ bin,
                                                               const DevCam* __restrict__ cams, int64_t n_gauss,
                                                               uint32_t n_rec, int tw, int th,
                                                               int32_t* __restrict__ ntiles,
                                                               uint32_t* __restrict__ depth_key) {
+  __shared__ RowOwner s_own[kThreads / 32][32];
+  __shared__ int s_incl[kThreads / 32][32], s_cnt[kThreads / 32][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t r = blockIdx.x * kThreads + threadIdx.x;
-  if (r >= n_rec) return;
-  const BinView b = load_bin(bin, r);
-  int cnt = 0;
-  if (b.rc.z >= b.rc.x) {
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, b.rc));
+  int nrows = 0;
+  if (r < n_rec) {
+    const BinView b = load_bin(bin, r);
+    if (b.rc.z >= b.rc.x) {
+      const DevCam& cam = cams[r / (uint64_t)n_gauss];
+      s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
+                                   cam.W, cam.H};
+      nrows = b.rc.w - b.rc.y + 1;
+    }
   }
-  ntiles[r] = cnt;
-  if (cnt == 0) depth_key[r] = 0xffffffffu;
+  s_cnt[warp][lane] = 0;
+  // the rows of the warp's records, spread over the lanes
+  for_warp_rows(nrows, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
+    const RowOwner& o = s_own[warp][ri];
+    const int c = row_count(row_runs(o.k, ty, tw, th, o.W, o.H, o.rc));
+    if (c) atomicAdd(&s_cnt[warp][ri], c);
+  });
+  if (r < n_rec) {
+    const int cnt = s_cnt[warp][lane];
+    ntiles[r] = cnt;
+    if (cnt == 0) depth_key[r] = 0xffffffffu;
+  }
 }
 
 __device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowbase, uint32_t r, uint64_t pos,
@@ -315,13 +365,15 @@ __device__ __forceinline__ uint64_t write_runs(const RowRuns& rr, uint32_t rowba
 // The (tile, record) pairs, written in depth order: entry i of the depth
 // order (record order[i]) writes its tiles from offsets[i] on, rows in order
 // and tiles left to right, so the runs of consecutive entries are adjacent and
-// a warp's stores are contiguous.  A lane computes the row runs of its entry
-// when it spans few rows; the warp then writes all those entries' tiles as one
-// flat list, 32 consecutive slots per step.  The rows of an entry with many
-// rows are shared out over the warp, with a warp scan of the row counts.
-constexpr int kWarpsPerBlock = kThreads / 32;
+// a warp's stores are contiguous.  The row runs of the entries that span few
+// rows are computed with those rows spread over the warp; the warp then writes
+// all those entries' tiles as one flat list, 32 consecutive slots per step.  The
+// rows of an entry with many rows are shared out over the warp, with a warp scan
+// of the row counts.
+constexpr int kDupThreads = 128;
+constexpr int kWarpsPerBlock = kDupThreads / 32;
 
-__global__ void __launch_bounds__(kThreads) duplicate_kernel(
+__global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
     uint32_t n_rec, const float4* __restrict__ bin, const DevCam* __restrict__ cams, int64_t n_gauss, int tw, int th,
     uint32_t n_pairs, uint32_t* __restrict__ keys, uint32_t* __restrict__ vals) {
@@ -331,8 +383,9 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
   __shared__ uint32_t s_tilesx[kWarpsPerBlock][32];
   __shared__ uint32_t s_pos[kWarpsPerBlock][32];
   __shared__ uint32_t s_rec[kWarpsPerBlock][32];
+  __shared__ RowOwner s_own[kWarpsPerBlock][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
+  const uint32_t i = blockIdx.x * kDupThreads + threadIdx.x;
   uint32_t r = 0;
   int cnt = 0;
   BinView bv;
@@ -353,16 +406,19 @@ __global__ void __launch_bounds__(kThreads) duplicate_kernel(
   const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const SupportConic k = support_conic(bv.g0, bv.g1, bv.g2, bv.rb);
-    for (int ty = rc.y; ty <= rc.w; ++ty) {
-      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      s_runs[warp][ty - rc.y][lane] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
-    }
+    s_own[warp][lane] = RowOwner{support_conic(bv.g0, bv.g1, bv.g2, bv.rb), rc, cam.tile_offset, cam.tiles_x, cam.W,
+                                 cam.H};
     s_rowbase[warp][lane] = (uint32_t)(cam.tile_offset + rc.y * cam.tiles_x);
     s_tilesx[warp][lane] = (uint32_t)cam.tiles_x;
     s_pos[warp][lane] = (uint32_t)o;
     s_rec[warp][lane] = r;
   }
+  // the row runs of the small entries, the rows spread over the warp
+  for_warp_rows(small ? rc.w - rc.y + 1 : 0, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
+    const RowOwner& ow = s_own[warp][ri];
+    const RowRuns rr = row_runs(ow.k, ty, tw, th, ow.W, ow.H, ow.rc);
+    s_runs[warp][ty - ow.rc.y][ri] = make_short4((short)rr.a0, (short)rr.a1, (short)rr.b0, (short)rr.b1);
+  });
   // flat walk over the small entries' tiles
   const int scnt = small ? cnt : 0;
   int incl = scnt;
@@ -561,9 +617,8 @@ cudaError_t launch_duplicate(const uint32_t* order, const uint64_t* offsets, con
                              const float4* bin, const DevCam* cams, int64_t n_gauss, int tile_w, int tile_h,
                              uint32_t n_pairs, uint32_t* keys, uint32_t* vals, cudaStream_t s) {
   if (n_pairs == 0 || n_rec == 0) return cudaSuccess;
-  duplicate_kernel<<<(n_rec + kThreads - 1) / kThreads, kThreads, 0, s>>>(order, offsets, total, n_rec, bin, cams,
-                                                                          n_gauss, tile_w, tile_h, n_pairs, keys,
-                                                                          vals);
+  duplicate_kernel<<<(n_rec + kDupThreads - 1) / kDupThreads, kDupThreads, 0, s>>>(
+      order, offsets, total, n_rec, bin, cams, n_gauss, tile_w, tile_h, n_pairs, keys, vals);
   return launched();
 }
 
@@ -622,23 +677,40 @@ __device__ __forceinline__ int open_in(const uint32_t* __restrict__ P, uint32_t 
   return x1 < x0 ? 0 : (int)(P[rowbase + (uint32_t)x1 + 1u] - P[rowbase + (uint32_t)x0]);
 }
 
+constexpr int kFlatWarps = kThreads / 32;
+
 __global__ void __launch_bounds__(kThreads) tile_count_sorted_kernel(const uint32_t* __restrict__ order, uint32_t n,
                                                                      const float4* __restrict__ bin,
                                                                      const DevCam* __restrict__ cams, int64_t n_gauss,
                                                                      int tw, int th, int32_t* __restrict__ ntiles,
                                                                      uint64_t* __restrict__ counts) {
+  __shared__ RowOwner s_own[kFlatWarps][32];
+  __shared__ int s_incl[kFlatWarps][32], s_cnt[kFlatWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t i = blockIdx.x * kThreads + threadIdx.x;
-  if (i >= n) return;
-  const uint32_t r = order[i];
-  const BinView b = load_bin(bin, r);
-  int cnt = 0;
-  if (b.rc.z >= b.rc.x) {
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) cnt += row_count(row_runs(k, ty, tw, th, cam.W, cam.H, b.rc));
+  uint32_t r = 0;
+  int nrows = 0;
+  if (i < n) {
+    r = order[i];
+    const BinView b = load_bin(bin, r);
+    if (b.rc.z >= b.rc.x) {
+      const DevCam& cam = cams[r / (uint64_t)n_gauss];
+      s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
+                                   cam.W, cam.H};
+      nrows = b.rc.w - b.rc.y + 1;
+    }
   }
-  ntiles[r] = cnt;
-  counts[i] = (uint64_t)cnt;
+  s_cnt[warp][lane] = 0;
+  for_warp_rows(nrows, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
+    const RowOwner& o = s_own[warp][ri];
+    const int c = row_count(row_runs(o.k, ty, tw, th, o.W, o.H, o.rc));
+    if (c) atomicAdd(&s_cnt[warp][ri], c);
+  });
+  if (i < n) {
+    const int cnt = s_cnt[warp][lane];
+    ntiles[r] = cnt;
+    counts[i] = (uint64_t)cnt;
+  }
 }
 
 // number of entries of an ascending array below key (one thread)
@@ -689,21 +761,29 @@ __global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __
                                                               const DevCam* __restrict__ cams, int64_t n_gauss,
                                                               int tw, int th, const uint32_t* __restrict__ P,
                                                               uint64_t* __restrict__ counts) {
+  __shared__ RowOwner s_own[kFlatWarps][32];
+  __shared__ int s_incl[kFlatWarps][32], s_cnt[kFlatWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t c = blockIdx.x * kThreads + threadIdx.x;
-  if (c >= n) return;
-  int cnt = 0;
-  if (c < *n_cand) {
+  const uint32_t nc = min(n, *n_cand);
+  int nrows = 0;
+  if (c < nc) {
     const uint32_t r = cand[c];
     const BinView b = load_bin(bin, r);
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-    for (int ty = b.rc.y; ty <= b.rc.w; ++ty) {
-      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, b.rc);
-      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
-      cnt += open_in(P, rowbase, rr.a0, rr.a1) + open_in(P, rowbase, rr.b0, rr.b1);
-    }
+    s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
+                                 cam.W, cam.H};
+    nrows = max(0, b.rc.w - b.rc.y + 1);
   }
-  counts[c] = (uint64_t)cnt;
+  s_cnt[warp][lane] = 0;
+  for_warp_rows(nrows, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
+    const RowOwner& o = s_own[warp][ri];
+    const RowRuns rr = row_runs(o.k, ty, tw, th, o.W, o.H, o.rc);
+    const uint32_t rowbase = (uint32_t)(o.tile_offset + ty * o.tiles_x);
+    const int cnt = open_in(P, rowbase, rr.a0, rr.a1) + open_in(P, rowbase, rr.b0, rr.b1);
+    if (cnt) atomicAdd(&s_cnt[warp][ri], cnt);
+  });
+  if (c < n) counts[c] = (uint64_t)s_cnt[warp][lane];
 }
 
 // The open tiles, compacted in ascending id: open_ids[P[t]] = t for every open tile t.
@@ -730,10 +810,11 @@ constexpr int kOpenWarps = kOpenThreads / 32;
 
 // step 4, the second-pass pairs in depth order: candidate i writes its open
 // tiles from offsets[i] on (rows in order, tiles left to right), each run's open
-// tiles being a slice of open_ids.  As in the first pass's duplication, a lane
-// finds the slices of its candidate when it spans few rows and the warp writes
-// all those candidates' tiles as one flat list, 32 consecutive slots per step;
-// the rows of a taller candidate are shared out over the warp.
+// tiles being a slice of open_ids.  As in the first pass's duplication, the
+// slices of the candidates that span few rows are found with their rows spread
+// over the warp, and the warp writes all those candidates' tiles as one flat
+// list, 32 consecutive slots per step; the rows of a taller candidate are
+// shared out over the warp.
 __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
     uint32_t n_rec, const uint32_t* __restrict__ n_cand, const float4* __restrict__ bin,
@@ -744,6 +825,7 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
   __shared__ int s_incl[kOpenWarps][32];
   __shared__ uint32_t s_pos[kOpenWarps][32];
   __shared__ uint32_t s_rec[kOpenWarps][32];
+  __shared__ RowOwner s_own[kOpenWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t i = blockIdx.x * kOpenThreads + threadIdx.x;
   n_rec = min(n_rec, *n_cand);
@@ -765,18 +847,22 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
   if (small) {
     const BinView b = load_bin(bin, r);
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
-    for (int ty = rc.y; ty <= rc.w; ++ty) {
-      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
-      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
-      const OpenSlice sa = open_slice(P, rowbase, rr.a0, rr.a1), sb = open_slice(P, rowbase, rr.b0, rr.b1);
-      s_sa[warp][ty - rc.y][lane] = sa.start;
-      s_sb[warp][ty - rc.y][lane] = sb.start;
-      s_cnt[warp][ty - rc.y][lane] = (uint32_t)sa.count | ((uint32_t)sb.count << 16);
-    }
+    s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), rc, cam.tile_offset, cam.tiles_x, cam.W,
+                                 cam.H};
     s_pos[warp][lane] = (uint32_t)o;
     s_rec[warp][lane] = r;
   }
+  // the open-tile slices of the small candidates' rows, the rows spread over the warp
+  for_warp_rows(small ? rc.w - rc.y + 1 : 0, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
+    const RowOwner& ow = s_own[warp][ri];
+    const RowRuns rr = row_runs(ow.k, ty, tw, th, ow.W, ow.H, ow.rc);
+    const uint32_t rowbase = (uint32_t)(ow.tile_offset + ty * ow.tiles_x);
+    const OpenSlice sa = open_slice(P, rowbase, rr.a0, rr.a1), sb = open_slice(P, rowbase, rr.b0, rr.b1);
+    const int row = ty - ow.rc.y;
+    s_sa[warp][row][ri] = sa.start;
+    s_sb[warp][row][ri] = sb.start;
+    s_cnt[warp][row][ri] = (uint32_t)sa.count | ((uint32_t)sb.count << 16);
+  });
   // flat walk over the small candidates' open tiles
   const int scnt = small ? cnt : 0;
   int incl = scnt;
