@@ -226,6 +226,34 @@ def candidate_mask(T: torch.Tensor, scale: torch.Tensor, cam: dict, xs: torch.Te
 
 
 # ----------------------------------------------------------------------------- compositing
+def front_to_back(rho, opacity):
+    """Front-to-back compositing weights of Sec. 4.3 from each candidate's rho
+    (columns already in depth order, rows are pixels): alpha = min(0.99, o exp(-rho/2)),
+    a candidate with rho > 9 or alpha < 1/255 is skipped, and a pixel stops at the first
+    candidate that would take its transmittance T (1 - alpha) below 1e-4 (that one is not
+    blended).  Returns the weights w = alpha T_before of the blended candidates, the
+    final transmittance and the decisions that a float32 evaluation may take the other
+    way (the rho cut, the 1/255 floor, the stop)."""
+    alpha_raw = opacity[None] * torch.exp(-0.5 * rho)
+    alpha = alpha_raw.clamp(max=ALPHA_MAX)
+    valid = ((rho <= RHO_CUT) & (alpha >= ALPHA_MIN)).detach()
+    a = torch.where(valid, alpha, torch.zeros_like(alpha))
+    one_minus = 1.0 - a
+    t_incl = torch.cumprod(one_minus, dim=1)
+    blended = (valid & (t_incl.detach() >= T_EPS))
+    t_excl = torch.cat([torch.ones(rho.shape[0], 1, dtype=DT), t_incl[:, :-1]], dim=1)
+    w = torch.where(blended, a * t_excl, torch.zeros_like(a))
+    t_final = torch.where(blended, one_minus, torch.ones_like(a)).prod(1)
+    with torch.no_grad():
+        e = FRAGILE_REL
+        a_at_cut = (opacity * math.exp(-0.5 * RHO_CUT)).clamp(max=ALPHA_MAX)
+        f_cut = ((rho - RHO_CUT).abs() <= e * RHO_CUT) & (a_at_cut[None] >= ALPHA_MIN * (1 - e))
+        f_amin = ((alpha_raw - ALPHA_MIN).abs() <= e * ALPHA_MIN) & (rho <= RHO_CUT * (1 + e))
+        f_stop = valid & ((t_incl - T_EPS).abs() <= e * T_EPS)
+    return dict(w=w, t_final=t_final, blended=blended, alpha_raw=alpha_raw, n_blended=blended.sum(1),
+                at_edge=f_cut | f_amin | f_stop)
+
+
 def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
     """Front-to-back compositing of the candidates (columns, already in depth order)
     for the pixel centres (xs, ys) (rows).  Returns per-pixel outputs and the
@@ -254,32 +282,20 @@ def composite(T, z_c, normal, rgb, opacity, xs, ys, rgb_raw=None):
     cy = row1[:, 2] / row2[:, 2]
     rho2 = ((xs[:, None] - cx[None]) ** 2 + (ys[:, None] - cy[None]) ** 2) / SIGMA_F2
     rho = torch.minimum(rho3, rho2)
-    alpha_raw = opacity[None] * torch.exp(-0.5 * rho)
-    alpha = alpha_raw.clamp(max=ALPHA_MAX)
-    valid = ((rho <= RHO_CUT) & (alpha >= ALPHA_MIN)).detach()
     use_hit = (rho3 <= rho2).detach()
     z_hit = row2[None, :, 0] * u + row2[None, :, 1] * v + row2[None, :, 2]
     z = torch.where(use_hit, z_hit, z_c[None].expand(B, n))
-    a = torch.where(valid, alpha, torch.zeros_like(alpha))
-    one_minus = 1.0 - a
-    t_incl = torch.cumprod(one_minus, dim=1)
-    blended = (valid & (t_incl.detach() >= T_EPS))
-    ones = torch.ones(B, 1, dtype=DT)
-    t_excl = torch.cat([ones, t_incl[:, :-1]], dim=1)
-    w = torch.where(blended, a * t_excl, torch.zeros_like(a))
+    fb = front_to_back(rho, opacity)
+    w, blended, alpha_raw = fb["w"], fb["blended"], fb["alpha_raw"]
     out = dict(
         rgb=w @ rgb, alpha=w.sum(1), depth=(w * z).sum(1), depth2=(w * z * z).sum(1), normal=w @ normal,
-        t_final=torch.where(blended, one_minus, torch.ones_like(a)).prod(1),
-        n_blended=blended.sum(1), w=w, z=z)
-    # decisions that a float32 evaluation may take the other way
+        t_final=fb["t_final"], n_blended=fb["n_blended"], w=w, z=z)
+    # decisions that a float32 evaluation may take the other way (besides those of the
+    # compositing): the surfel/filter switch, and for gradients the clamp
     with torch.no_grad():
         e = FRAGILE_REL
-        a_at_cut = (opacity * math.exp(-0.5 * RHO_CUT)).clamp(max=ALPHA_MAX)
-        f_cut = ((rho - RHO_CUT).abs() <= e * RHO_CUT) & (a_at_cut[None] >= ALPHA_MIN * (1 - e))
-        f_amin = ((alpha_raw - ALPHA_MIN).abs() <= e * ALPHA_MIN) & (rho <= RHO_CUT * (1 + e))
-        f_stop = valid & ((t_incl - T_EPS).abs() <= e * T_EPS)
         f_branch = blended & ((rho3 - rho2).abs() <= e * torch.maximum(rho3.clamp(max=1e30), rho2))
-        at_edge = f_cut | f_amin | f_stop | f_branch
+        at_edge = fb["at_edge"] | f_branch
         fragile = at_edge.any(1)
         f_clamp = blended & ((alpha_raw - ALPHA_MAX).abs() <= e)
         f_grad = f_clamp
@@ -652,27 +668,16 @@ def render_3d(g: dict, cam: dict, pixels: Optional[np.ndarray] = None, chunk: in
         dx = xs_all[s:e, None] - ctr[None, :, 0]
         dy = ys_all[s:e, None] - ctr[None, :, 1]
         rho = C[None, :, 0, 0] * dx * dx + 2.0 * C[None, :, 0, 1] * dx * dy + C[None, :, 1, 1] * dy * dy
-        a_raw = o[None] * torch.exp(-0.5 * rho)
-        alpha = a_raw.clamp(max=ALPHA_MAX)
-        valid = (rho <= RHO_CUT) & (alpha >= ALPHA_MIN)
-        a = torch.where(valid, alpha, torch.zeros_like(alpha))
-        t_incl = torch.cumprod(1.0 - a, dim=1)
-        blended = valid & (t_incl >= T_EPS)
-        t_excl = torch.cat([torch.ones(e - s, 1, dtype=DT), t_incl[:, :-1]], dim=1)
-        w = torch.where(blended, a * t_excl, torch.zeros_like(a))
+        fb = front_to_back(rho, o)
+        w = fb["w"]
         res["rgb"][s:e] = (w @ rgb).numpy()
         res["alpha"][s:e] = w.sum(1).numpy()
         res["depth"][s:e] = (w @ z).numpy()
-        res["t_final"][s:e] = torch.where(blended, 1.0 - a, torch.ones_like(a)).prod(1).numpy()
-        res["n_blended"][s:e] = blended.sum(1).numpy()
+        res["t_final"][s:e] = fb["t_final"].numpy()
+        res["n_blended"][s:e] = fb["n_blended"].numpy()
         if len(order):
             score[order] = torch.maximum(score[order], w.max(0).values)
-        f = FRAGILE_REL
-        a_cut = (o * math.exp(-0.5 * RHO_CUT)).clamp(max=ALPHA_MAX)
-        fragile = (((rho - RHO_CUT).abs() <= f * RHO_CUT) & (a_cut[None] >= ALPHA_MIN * (1 - f))) | \
-                  (((a_raw - ALPHA_MIN).abs() <= f * ALPHA_MIN) & (rho <= RHO_CUT * (1 + f))) | \
-                  (valid & ((t_incl - T_EPS).abs() <= f * T_EPS))
-        res["fragile"][s:e] = fragile.any(1).numpy()
+        res["fragile"][s:e] = fb["at_edge"].any(1).numpy()
     res["score"] = score.numpy()
     return res
 
