@@ -810,10 +810,9 @@ constexpr int kOpenWarps = kOpenThreads / 32;
 
 // step 4, the second-pass pairs in depth order: candidate i writes its open
 // tiles from offsets[i] on (rows in order, tiles left to right), each run's open
-// tiles being a slice of open_ids.  As in the first pass's duplication, the
-// slices of the candidates that span few rows are found with their rows spread
-// over the warp, and the warp writes all those candidates' tiles as one flat
-// list, 32 consecutive slots per step; the rows of a taller candidate are
+// tiles being a slice of open_ids.  A lane finds the slices of its candidate
+// when it spans few rows and the warp writes all those candidates' tiles as one
+// flat list, 32 consecutive slots per step; the rows of a taller candidate are
 // shared out over the warp.
 __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
     const uint32_t* __restrict__ order, const uint64_t* __restrict__ offsets, const uint64_t* __restrict__ total,
@@ -825,7 +824,6 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
   __shared__ int s_incl[kOpenWarps][32];
   __shared__ uint32_t s_pos[kOpenWarps][32];
   __shared__ uint32_t s_rec[kOpenWarps][32];
-  __shared__ RowOwner s_own[kOpenWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t i = blockIdx.x * kOpenThreads + threadIdx.x;
   n_rec = min(n_rec, *n_cand);
@@ -845,24 +843,22 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
   }
   const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
+    // a lane finds its candidate's slices (the rows spread over the warp measured slower
+    // here, the candidates behind the front spanning few rows)
     const BinView b = load_bin(bin, r);
     const DevCam& cam = cams[r / (uint64_t)n_gauss];
-    s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), rc, cam.tile_offset, cam.tiles_x, cam.W,
-                                 cam.H};
+    const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
+    for (int ty = rc.y; ty <= rc.w; ++ty) {
+      const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
+      const uint32_t rowbase = (uint32_t)(cam.tile_offset + ty * cam.tiles_x);
+      const OpenSlice sa = open_slice(P, rowbase, rr.a0, rr.a1), sb = open_slice(P, rowbase, rr.b0, rr.b1);
+      s_sa[warp][ty - rc.y][lane] = sa.start;
+      s_sb[warp][ty - rc.y][lane] = sb.start;
+      s_cnt[warp][ty - rc.y][lane] = (uint32_t)sa.count | ((uint32_t)sb.count << 16);
+    }
     s_pos[warp][lane] = (uint32_t)o;
     s_rec[warp][lane] = r;
   }
-  // the open-tile slices of the small candidates' rows, the rows spread over the warp
-  for_warp_rows(small ? rc.w - rc.y + 1 : 0, lane, s_incl[warp], s_own[warp], [&](int ri, int ty) {
-    const RowOwner& ow = s_own[warp][ri];
-    const RowRuns rr = row_runs(ow.k, ty, tw, th, ow.W, ow.H, ow.rc);
-    const uint32_t rowbase = (uint32_t)(ow.tile_offset + ty * ow.tiles_x);
-    const OpenSlice sa = open_slice(P, rowbase, rr.a0, rr.a1), sb = open_slice(P, rowbase, rr.b0, rr.b1);
-    const int row = ty - ow.rc.y;
-    s_sa[warp][row][ri] = sa.start;
-    s_sb[warp][row][ri] = sb.start;
-    s_cnt[warp][row][ri] = (uint32_t)sa.count | ((uint32_t)sb.count << 16);
-  });
   // flat walk over the small candidates' open tiles
   const int scnt = small ? cnt : 0;
   int incl = scnt;
