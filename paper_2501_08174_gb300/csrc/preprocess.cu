@@ -214,6 +214,97 @@ __device__ __forceinline__ void view_colour(const DevCam& cam, const float* X, c
 __device__ __forceinline__ float project_x(const DevCam& cam, float X, float Z) { return cam.fx * X / Z + cam.cx; }
 __device__ __forceinline__ float project_y(const DevCam& cam, float Y, float Z) { return cam.fy * Y / Z + cam.cy; }
 
+// ----------------------------------------------------------------------------- SH staging
+// A block's SH coefficients (NF = 3K floats per Gaussian, NF x 4 bytes apart) are
+// one contiguous span of the array: they are moved between global and shared
+// memory with coalesced loads and stores, and each thread reads or writes its own
+// NF floats in shared memory.  When NF is a multiple of 4 the rows are float4 rows
+// whose stride in float4 is odd (conflict-free 16-byte accesses by 8 threads per
+// phase); otherwise float rows of odd stride.
+constexpr int kPreThreads = 128;
+
+template <int NF>
+struct ShRows {
+  static constexpr bool kVec = NF % 4 == 0;
+  static constexpr int kStride = kVec ? 4 * ((NF / 4) | 1) : (NF | 1);  // floats per row
+  static constexpr int kFloats = kPreThreads * kStride;
+  // position in shared memory of float f of the block's span
+  __device__ static __forceinline__ int at(int f) { return (f / NF) * kStride + f % NF; }
+};
+
+// loads the block's span of src into its rows (all threads; ends with a barrier)
+template <int NF>
+__device__ __forceinline__ void sh_rows_load(const float* __restrict__ src, int64_t n, float* rows) {
+  using L = ShRows<NF>;
+  const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
+  const int total = (int)min((int64_t)kPreThreads, n - i0) * NF;
+  const float* base = src + i0 * NF;
+  if (L::kVec && (reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+    for (int j = threadIdx.x; 4 * j < total; j += kPreThreads)  // total is a multiple of 4 here
+      *reinterpret_cast<float4*>(rows + L::at(4 * j)) = reinterpret_cast<const float4*>(base)[j];
+  } else {
+    for (int f = threadIdx.x; f < total; f += kPreThreads) rows[L::at(f)] = base[f];
+  }
+  __syncthreads();
+}
+
+// this thread's row
+template <int NF>
+__device__ __forceinline__ void sh_row_read(const float* rows, float* v) {
+  using L = ShRows<NF>;
+  const float* r = rows + threadIdx.x * L::kStride;
+  if constexpr (L::kVec) {
+#pragma unroll
+    for (int m = 0; m < NF / 4; ++m) {
+      const float4 a = reinterpret_cast<const float4*>(r)[m];
+      v[4 * m] = a.x;
+      v[4 * m + 1] = a.y;
+      v[4 * m + 2] = a.z;
+      v[4 * m + 3] = a.w;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) v[k] = r[k];
+  }
+}
+
+template <int NF>
+__device__ __forceinline__ void sh_row_write(float* rows, const float* v) {
+  using L = ShRows<NF>;
+  float* r = rows + threadIdx.x * L::kStride;
+  if constexpr (L::kVec) {
+#pragma unroll
+    for (int m = 0; m < NF / 4; ++m)
+      reinterpret_cast<float4*>(r)[m] = make_float4(v[4 * m], v[4 * m + 1], v[4 * m + 2], v[4 * m + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NF; ++k) r[k] = v[k];
+  }
+}
+
+// adds the block's rows to its span of dst (all threads; starts with a barrier)
+template <int NF>
+__device__ __forceinline__ void sh_rows_add(float* __restrict__ dst, int64_t n, const float* rows) {
+  using L = ShRows<NF>;
+  __syncthreads();
+  const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
+  const int total = (int)min((int64_t)kPreThreads, n - i0) * NF;
+  float* base = dst + i0 * NF;
+  if (L::kVec && (reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+    for (int j = threadIdx.x; 4 * j < total; j += kPreThreads) {
+      float4 v = reinterpret_cast<float4*>(base)[j];
+      const float4 a = *reinterpret_cast<const float4*>(rows + L::at(4 * j));
+      v.x += a.x;
+      v.y += a.y;
+      v.z += a.z;
+      v.w += a.w;
+      reinterpret_cast<float4*>(base)[j] = v;
+    }
+  } else {
+    for (int f = threadIdx.x; f < total; f += kPreThreads) base[f] += rows[L::at(f)];
+  }
+}
+
 template <int DEG>
 __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
                                                          const DevCam* __restrict__ cams, int n_views,
@@ -223,6 +314,8 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
                                                          uint32_t* __restrict__ depth_key,
                                                          int* __restrict__ status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
+  __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
+  sh_rows_load<3 * K>(g.sh, n, s_rows);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
@@ -230,13 +323,11 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
   const float2 s = reinterpret_cast<const float2*>(g.scale)[i];
   const float o = g.opacity[i];
   float sh[3 * K];
+  sh_row_read<3 * K>(s_rows, sh);
   bool finite = finitef(X[0]) && finitef(X[1]) && finitef(X[2]) && finitef(q.x) && finitef(q.y) &&
                 finitef(q.z) && finitef(q.w) && finitef(s.x) && finitef(s.y) && finitef(o);
 #pragma unroll
-  for (int k = 0; k < 3 * K; ++k) {
-    sh[k] = g.sh[(int64_t)3 * K * i + k];
-    finite = finite && finitef(sh[k]);
-  }
+  for (int k = 0; k < 3 * K; ++k) finite = finite && finitef(sh[k]);
   const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
   if (!finite) atomicOr(status, kStatusNonFinite);
   const bool bad = !finite || !(qn2 > 0.f) || !(s.x > 0.f) || !(s.y > 0.f) || !(o >= kAlphaMin);
@@ -322,14 +413,18 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
                                                              const int32_t* __restrict__ ntiles,
                                                              GaussOut out) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
+  sh_rows_load<3 * K>(g.sh, n, s_rows);
+  // every thread reaches the block's final exchange of SH gradients: a thread past
+  // the end recomputes the last Gaussian and writes nothing
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = i0 < n;
+  const int64_t i = active ? i0 : n - 1;
   float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
   const float4 q = reinterpret_cast<const float4*>(g.quat)[i];
   const float2 s = reinterpret_cast<const float2*>(g.scale)[i];
   float sh[3 * K];
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) sh[k] = g.sh[(int64_t)3 * K * i + k];
+  sh_row_read<3 * K>(s_rows, sh);
   const Frame f = make_frame(q);
 
   float gX[3] = {0.f, 0.f, 0.f};
@@ -461,18 +556,22 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
                           x * G20 + y * G21);
   const float dotq = gw * w + gx * x + gy * y + gz * z;
   const float in = f.inv_norm;
-  out.xyz[3 * i + 0] += gX[0];
-  out.xyz[3 * i + 1] += gX[1];
-  out.xyz[3 * i + 2] += gX[2];
-  out.quat[4 * i + 0] += (gw - w * dotq) * in;
-  out.quat[4 * i + 1] += (gx - x * dotq) * in;
-  out.quat[4 * i + 2] += (gy - y * dotq) * in;
-  out.quat[4 * i + 3] += (gz - z * dotq) * in;
-  out.scale[2 * i + 0] += gsu;
-  out.scale[2 * i + 1] += gsv;
-  out.opacity[i] += go;
-#pragma unroll
-  for (int k = 0; k < 3 * K; ++k) out.sh[(int64_t)3 * K * i + k] += gsh[k];
+  if (active) {
+    out.xyz[3 * i + 0] += gX[0];
+    out.xyz[3 * i + 1] += gX[1];
+    out.xyz[3 * i + 2] += gX[2];
+    out.quat[4 * i + 0] += (gw - w * dotq) * in;
+    out.quat[4 * i + 1] += (gx - x * dotq) * in;
+    out.quat[4 * i + 2] += (gy - y * dotq) * in;
+    out.quat[4 * i + 3] += (gz - z * dotq) * in;
+    out.scale[2 * i + 0] += gsu;
+    out.scale[2 * i + 1] += gsv;
+    out.opacity[i] += go;
+  }
+  // the SH gradients leave through this thread's row (only it has read that row) and
+  // are added to the output with coalesced accesses
+  sh_row_write<3 * K>(s_rows, gsh);
+  sh_rows_add<3 * K>(out.sh, n, s_rows);
 }
 
 // EWA projection of 3D Gaussians, for the 3DGS variant of the pruning record
@@ -493,6 +592,8 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
                                                              uint32_t* __restrict__ depth_key,
                                                              int* __restrict__ status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
+  __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
+  sh_rows_load<3 * K>(g.sh, n, s_rows);
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
@@ -504,7 +605,7 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
                 finitef(q.z) && finitef(q.w) && finitef(s3[0]) && finitef(s3[1]) && finitef(s3[2]) && finitef(o);
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) {
-    sh[k] = g.sh[(int64_t)3 * K * i + k];
+    sh[k] = s_rows[threadIdx.x * ShRows<3 * K>::kStride + k];
     finite = finite && finitef(sh[k]);
   }
   const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
@@ -603,7 +704,7 @@ cudaError_t launch_preprocess(const GaussPtrs& g, int64_t n, int sh_degree, cons
                               int n_views, int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles,
                               float4* bin, uint32_t* depth_key, int* status, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int bs = 128;
+  const int bs = kPreThreads;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   switch (sh_degree) {
     case 0: preprocess_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
@@ -618,7 +719,7 @@ cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_deg
                                        const DevCam* cams, int n_views, const float* grad_rec,
                                        const int32_t* ntiles, GaussOut out, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int bs = 128;
+  const int bs = kPreThreads;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   switch (sh_degree) {
     case 0: preprocess_bwd_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, grad_rec, ntiles, out); break;
@@ -636,7 +737,7 @@ cudaError_t launch_preprocess_ewa(const GaussPtrs& g, int64_t n, int sh_degree, 
                                   int tile_w, int tile_h, RecPtrs rec, int32_t* ntiles, float4* bin,
                                   uint32_t* depth_key, int* status, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
-  const int bs = 128;
+  const int bs = kPreThreads;
   const unsigned grid = (unsigned)((n + bs - 1) / bs);
   switch (sh_degree) {
     case 0: preprocess_ewa_kernel<0><<<grid, bs, 0, s>>>(g, n, cams, n_views, tile_w, tile_h, rec, ntiles, bin, depth_key, status); break;
