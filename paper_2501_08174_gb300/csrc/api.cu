@@ -337,8 +337,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     bool alt = false;
     {
       StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
-      CK(launch_iota(order, VN, s));
-      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s, nullptr, true));
     }
     uint32_t* sorted = alt ? order_alt : order;
     {
@@ -429,8 +428,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
     bool alt = false;
     {
       StageTimer t(ctx, OCGS_STAGE_DEPTH_SORT);
-      CK(launch_iota(order, VN, s));
-      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s));
+      CK(radix_sort_pairs(dkey, order, dkey_alt, order_alt, VN, 32, scratch, &alt, s, nullptr, true));
     }
     uint32_t* sorted = alt ? order_alt : order;
     const uint32_t* skeys = alt ? dkey_alt : dkey;
@@ -676,9 +674,8 @@ ocgs_status enqueue_sweep_chunk(ocgs_ctx* ctx, const ocgs_gaussians* g, int V, c
   CK(launch_preprocess(gptrs(g), N, g->sh_degree, d_cams, V, tw, th, w.rec, w.ntiles, w.bin, w.dkey, ctx->d_status,
                        s));
   CK(launch_tile_count(w.bin, d_cams, N, VN, tw, th, w.ntiles, w.dkey, s));
-  CK(launch_iota(w.order, VN, s));
   bool alt = false;
-  CK(radix_sort_pairs(w.dkey, w.order, w.dkey_alt, w.order_alt, VN, 32, w.scratch, &alt, s));
+  CK(radix_sort_pairs(w.dkey, w.order, w.dkey_alt, w.order_alt, VN, 32, w.scratch, &alt, s, nullptr, true));
   uint32_t* sorted = alt ? w.order_alt : w.order;
   CK(launch_gather_counts(sorted, w.ntiles, w.counts, VN, s));
   CK(scan_exclusive_u64(w.counts, w.counts, VN, w.total, w.scratch, s));

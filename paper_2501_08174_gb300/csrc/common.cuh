@@ -350,10 +350,11 @@ cudaError_t launch_preprocess_backward(const GaussPtrs& g, int64_t n, int sh_deg
 // in the alternate buffers.  scratch must hold radix_scratch_bytes(n) bytes.
 size_t radix_scratch_bytes(uint32_t n);
 // d_n (optional): device-side item count, read by the kernels and clamped to n
-// (n sizes the launch: a capacity)
+// (n sizes the launch: a capacity).  index_vals: the values are 0, 1, ..., n - 1 (the
+// first pass generates them instead of reading vals, which need not be initialised)
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              uint32_t n, int n_bits, void* scratch, bool* result_in_alt,
-                             cudaStream_t s, const uint32_t* d_n = nullptr);
+                             cudaStream_t s, const uint32_t* d_n = nullptr, bool index_vals = false);
 
 // exclusive scan of n uint64 values (in may equal out); the total is written to *d_total.
 size_t scan_scratch_bytes(uint32_t n);
@@ -480,6 +481,42 @@ cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, cons
                                    int n_views, const int* block_prefix, int n_blocks, float gamma,
                                    double* partial, double* loss, float* d_alpha, cudaStream_t s);
 constexpr int kLossBlockPixels = 4096;
+
+// Per-view totals of per-block FP64 partial sums: one CTA of kViewSumThreads per
+// view (blockIdx.x = view) adds NV values per block, partial[NV b + k] for the
+// view's blocks [b0, b1), in a fixed order (each thread a strided run of blocks,
+// then each warp's xor tree, then the warps in order), so the totals are the
+// same from run to run.  The result is valid in thread 0.
+constexpr int kViewSumThreads = 128;
+template <int NV>
+__device__ __forceinline__ void view_block_sums(const double* __restrict__ partial, int b0, int b1, double* out) {
+  __shared__ double s_w[kViewSumThreads / 32][NV];
+  double t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) t[k] = 0.0;
+  for (int b = b0 + (int)threadIdx.x; b < b1; b += kViewSumThreads) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) t[k] += partial[(int64_t)NV * b + k];
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_xor_sync(0xffffffffu, t[k], o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_w[threadIdx.x >> 5][k] = t[k];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (int w = 0; w < kViewSumThreads / 32; ++w) a += s_w[w][k];
+      out[k] = a;
+    }
+  }
+}
 cudaError_t launch_masked_l1(const float* rgb, const float* target, const uint8_t* mask, const DevCam* cams,
                              int n_views, const int* block_prefix, int n_blocks, float weight, double* partial,
                              double* loss, float* d_rgb, cudaStream_t s);

@@ -106,13 +106,15 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
   }
 }
 
-__global__ void bg_loss_final_kernel(const double* __restrict__ partial, const int* __restrict__ block_prefix,
-                                     const DevCam* __restrict__ cams, int n_views, double* __restrict__ loss) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_views) return;
-  double t = 0.0;
-  for (int b = block_prefix[v]; b < block_prefix[v + 1]; ++b) t += partial[b];
-  loss[v] = t / ((double)cams[v].W * (double)cams[v].H);
+// one CTA per view
+__global__ void __launch_bounds__(kViewSumThreads) bg_loss_final_kernel(const double* __restrict__ partial,
+                                                                       const int* __restrict__ block_prefix,
+                                                                       const DevCam* __restrict__ cams,
+                                                                       double* __restrict__ loss) {
+  const int v = blockIdx.x;
+  double t;
+  view_block_sums<1>(partial, block_prefix[v], block_prefix[v + 1], &t);
+  if (threadIdx.x == 0) loss[v] = t / ((double)cams[v].W * (double)cams[v].H);
 }
 
 __global__ void scale_kernel(double* __restrict__ x, int n, double f) {
@@ -162,7 +164,7 @@ cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, cons
     cudaError_t e = launched();
     if (e != cudaSuccess) return e;
   }
-  bg_loss_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  bg_loss_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, block_prefix, cams, loss);
   return launched();
 }
 
@@ -176,7 +178,7 @@ cudaError_t launch_masked_l1(const float* rgb, const float* target, const uint8_
     if (e != cudaSuccess) return e;
   }
   // the final pass divides by h*w; the L1 mean is over 3*h*w values
-  bg_loss_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  bg_loss_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, block_prefix, cams, loss);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
   scale_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(loss, n_views, 1.0 / 3.0);

@@ -171,13 +171,15 @@ __global__ void __launch_bounds__(kRegThreads) normal_consistency_gather_kernel(
   }
 }
 
-__global__ void reg_final_kernel(const double* __restrict__ partial, const int* __restrict__ block_prefix,
-                                 const DevCam* __restrict__ cams, int n_views, double* __restrict__ loss) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_views) return;
-  double t = 0.0;
-  for (int b = block_prefix[v]; b < block_prefix[v + 1]; ++b) t += partial[b];
-  loss[v] = t / ((double)cams[v].W * (double)cams[v].H);
+// one CTA per view
+__global__ void __launch_bounds__(kViewSumThreads) reg_final_kernel(const double* __restrict__ partial,
+                                                                   const int* __restrict__ block_prefix,
+                                                                   const DevCam* __restrict__ cams,
+                                                                   double* __restrict__ loss) {
+  const int v = blockIdx.x;
+  double t;
+  view_block_sums<1>(partial, block_prefix[v], block_prefix[v + 1], &t);
+  if (threadIdx.x == 0) loss[v] = t / ((double)cams[v].W * (double)cams[v].H);
 }
 
 }  // namespace
@@ -192,7 +194,7 @@ cudaError_t launch_depth_distortion(const float* alpha, const float* depth, cons
     cudaError_t e = launched();
     if (e != cudaSuccess) return e;
   }
-  reg_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  reg_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, block_prefix, cams, loss);
   return launched();
 }
 
@@ -213,7 +215,7 @@ cudaError_t launch_normal_consistency(const float* alpha, const float* depth, co
       if (e != cudaSuccess) return e;
     }
   }
-  reg_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, cams, n_views, loss);
+  reg_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, block_prefix, cams, loss);
   return launched();
 }
 

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kBlock) radix_upsweep_kernel(const uint32_t* _
 // with a running per-warp count of every digit.  The block then orders its
 // whole chunk by digit in shared memory and writes it out in digit runs, so
 // the global stores are coalesced.
+// vals_in NULL: the values are the items' indices
 __global__ void __launch_bounds__(kBlock) radix_scatter_kernel(const uint32_t* __restrict__ keys_in,
                                                                const uint32_t* __restrict__ vals_in,
                                                                uint32_t* __restrict__ keys_out,
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(kBlock) radix_scatter_kernel(const uint32_t* _
     const uint32_t k = wbase + j * 32 + lane;
     const bool valid = k < n;
     key[j] = valid ? keys_in[k] : 0u;
-    val[j] = valid ? vals_in[k] : 0u;
+    val[j] = valid ? (vals_in ? vals_in[k] : k) : 0u;  // no values: the item's index
   }
 #pragma unroll
   for (int j = 0; j < kItems; ++j) {
@@ -563,9 +564,15 @@ size_t radix_scratch_bytes(uint32_t n) {
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                              uint32_t n, int n_bits, void* scratch, bool* result_in_alt, cudaStream_t s,
-                             const uint32_t* d_n) {
+                             const uint32_t* d_n, bool index_vals) {
   *result_in_alt = false;
-  if (n <= 1 || n_bits <= 0) return cudaSuccess;
+  if (n <= 1 || n_bits <= 0) {
+    if (index_vals && n > 0) {  // nothing to sort: the values are the indices
+      launch_iota(vals, n, s);
+      return launched();
+    }
+    return cudaSuccess;
+  }
   const uint32_t nb = (n + kChunk - 1) / kChunk;
   const int passes = (n_bits + 7) / 8;
   const int digit = (n_bits + passes - 1) / passes;  // balanced digit width <= 8
@@ -582,7 +589,8 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt,
     if (e != cudaSuccess) return e;
     e = scan_exclusive<uint32_t>(counts, counts, (mask + 1) * nb, nullptr, scan_scratch, s);
     if (e != cudaSuccess) return e;
-    radix_scatter_kernel<<<nb, kBlock, 0, s>>>(kin, vin, kout, vout, n, shift, mask, counts, nb, d_n);
+    radix_scatter_kernel<<<nb, kBlock, 0, s>>>(kin, p == 0 && index_vals ? nullptr : vin, kout, vout, n, shift,
+                                               mask, counts, nb, d_n);
     e = launched();
     if (e != cudaSuccess) return e;
     uint32_t* t = kin; kin = kout; kout = t;
@@ -713,15 +721,24 @@ __global__ void __launch_bounds__(kThreads) tile_count_sorted_kernel(const uint3
   }
 }
 
-// number of entries of an ascending array below key (one thread)
+// number of entries of an ascending array below key: a 32-way search by one warp
+// (each round probes 32 evenly spaced entries of the bracket [lo, hi] that holds
+// the answer and keeps the stretch between the last probe below key and the next)
 __global__ void count_below_kernel(const uint32_t* __restrict__ sorted_keys, uint32_t n, uint32_t key,
                                    uint32_t* __restrict__ out) {
+  const uint32_t lane = threadIdx.x;
   uint32_t lo = 0, hi = n;
-  while (lo < hi) {
-    const uint32_t mid = lo + (hi - lo) / 2u;
-    if (sorted_keys[mid] < key) lo = mid + 1u; else hi = mid;
+  while (hi - lo > 32u) {
+    const uint32_t step = (hi - lo + 31u) / 32u;
+    const uint32_t pos = lo + lane * step;
+    const int c = __popc(__ballot_sync(kFull, pos < hi && sorted_keys[pos] < key));
+    const uint32_t nhi = min(hi, lo + (uint32_t)c * step);
+    lo = c > 0 ? lo + (uint32_t)(c - 1) * step + 1u : lo;
+    hi = nhi;
   }
-  *out = lo;
+  const uint32_t pos = lo + lane;
+  const int c = __popc(__ballot_sync(kFull, pos < hi && sorted_keys[pos] < key));
+  if (lane == 0) *out = lo + (uint32_t)c;
 }
 
 // Second pass, step 1: flag the entries (records behind the front, in depth
@@ -963,7 +980,7 @@ cudaError_t launch_tile_count_sorted(const uint32_t* order, uint32_t n, const fl
 
 cudaError_t launch_count_below(const uint32_t* sorted_keys, uint32_t n, uint32_t key, uint32_t* out,
                                cudaStream_t s) {
-  count_below_kernel<<<1, 1, 0, s>>>(sorted_keys, n, key, out);
+  count_below_kernel<<<1, 32, 0, s>>>(sorted_keys, n, key, out);
   return launched();
 }
 

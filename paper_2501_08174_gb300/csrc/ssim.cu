@@ -222,19 +222,18 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_grad_kernel(
 }
 
 // out[v]: k = 0 -> mean over all values, 1 -> mean over mask values (NaN if none)
-__global__ void ssim_final_kernel(const double* __restrict__ partial, const int* __restrict__ prefix,
-                                  const DevCam* __restrict__ cams, int n_views, double* __restrict__ ssim,
-                                  double* __restrict__ ssim_masked) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_views) return;
-  double a = 0.0, m = 0.0, n = 0.0;
-  for (int b = prefix[v]; b < prefix[v + 1]; ++b) {
-    a += partial[3 * b];
-    m += partial[3 * b + 1];
-    n += partial[3 * b + 2];
-  }
-  ssim[v] = a / (3.0 * (double)cams[v].W * (double)cams[v].H);
-  if (ssim_masked) ssim_masked[v] = n > 0.0 ? m / n : __longlong_as_double(0x7ff8000000000000ll);
+// one CTA per view
+__global__ void __launch_bounds__(kViewSumThreads) ssim_final_kernel(const double* __restrict__ partial,
+                                                                    const int* __restrict__ prefix,
+                                                                    const DevCam* __restrict__ cams,
+                                                                    double* __restrict__ ssim,
+                                                                    double* __restrict__ ssim_masked) {
+  const int v = blockIdx.x;
+  double t[3];
+  view_block_sums<3>(partial, prefix[v], prefix[v + 1], t);
+  if (threadIdx.x != 0) return;
+  ssim[v] = t[0] / (3.0 * (double)cams[v].W * (double)cams[v].H);
+  if (ssim_masked) ssim_masked[v] = t[2] > 0.0 ? t[1] / t[2] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
 // partial[2 b]: sum of squared masked differences, partial[2 b + 1]: mask values
@@ -279,15 +278,15 @@ __global__ void __launch_bounds__(256) psnr_partial_kernel(const float* __restri
   }
 }
 
-__global__ void psnr_final_kernel(const double* __restrict__ partial, const int* __restrict__ block_prefix,
-                                  int n_views, double max_i, double* __restrict__ psnr) {
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_views) return;
-  double se = 0.0, n = 0.0;
-  for (int b = block_prefix[v]; b < block_prefix[v + 1]; ++b) {
-    se += partial[2 * b];
-    n += partial[2 * b + 1];
-  }
+// one CTA per view
+__global__ void __launch_bounds__(kViewSumThreads) psnr_final_kernel(const double* __restrict__ partial,
+                                                                    const int* __restrict__ block_prefix,
+                                                                    double max_i, double* __restrict__ psnr) {
+  const int v = blockIdx.x;
+  double t[2];
+  view_block_sums<2>(partial, block_prefix[v], block_prefix[v + 1], t);
+  if (threadIdx.x != 0) return;
+  const double se = t[0], n = t[1];
   if (n == 0.0) psnr[v] = __longlong_as_double(0x7ff8000000000000ll);
   else if (se == 0.0) psnr[v] = __longlong_as_double(0x7ff0000000000000ll);
   else psnr[v] = 20.0 * log10(max_i / sqrt(se / n));
@@ -317,7 +316,7 @@ cudaError_t launch_ssim(const float* rgb, const float* target, const uint8_t* ma
                                                      partial, d_rgb ? gmap : nullptr);
   cudaError_t e = launched();
   if (e != cudaSuccess) return e;
-  ssim_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, tile_prefix, cams, n_views, ssim, ssim_masked);
+  ssim_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, tile_prefix, cams, ssim, ssim_masked);
   e = launched();
   if (e != cudaSuccess || !d_rgb) return e;
   ssim_grad_kernel<<<n_tiles, kThreadsSsim, 0, s>>>(rgb, target, mask, cams, n_views, tile_prefix, w, p_total, gmap,
@@ -333,7 +332,7 @@ cudaError_t launch_masked_psnr(const float* rgb, const float* target, const uint
     cudaError_t e = launched();
     if (e != cudaSuccess) return e;
   }
-  psnr_final_kernel<<<(n_views + 127) / 128, 128, 0, s>>>(partial, block_prefix, n_views, max_i, psnr);
+  psnr_final_kernel<<<n_views, kViewSumThreads, 0, s>>>(partial, block_prefix, max_i, psnr);
   return launched();
 }
 
