@@ -222,6 +222,8 @@ __device__ __forceinline__ float project_y(const DevCam& cam, float Y, float Z) 
 // whose stride in float4 is odd (conflict-free 16-byte accesses by 8 threads per
 // phase); otherwise float rows of odd stride.
 constexpr int kPreThreads = 128;
+// views whose cameras the backward projection keeps in shared memory (more are read from global)
+constexpr int kSmemCams = 64;
 
 template <int NF>
 struct ShRows {
@@ -414,7 +416,16 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
                                                              GaussOut out) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
-  sh_rows_load<3 * K>(g.sh, n, s_rows);
+  // the views' cameras in shared memory (short-latency reads in the view loop)
+  __shared__ DevCam s_cams[kSmemCams];
+  const bool cams_in_smem = n_views <= kSmemCams;
+  if (cams_in_smem) {
+    const int words = n_views * (int)(sizeof(DevCam) / sizeof(int));
+    for (int w = threadIdx.x; w < words; w += blockDim.x)
+      reinterpret_cast<int*>(s_cams)[w] = reinterpret_cast<const int*>(cams)[w];
+  }
+  const DevCam* vcams = cams_in_smem ? s_cams : cams;
+  sh_rows_load<3 * K>(g.sh, n, s_rows);  // its barrier also publishes s_cams
   // every thread reaches the block's final exchange of SH gradients: a thread past
   // the end recomputes the last Gaussian and writes nothing
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -434,17 +445,20 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
 #pragma unroll
   for (int k = 0; k < 3 * K; ++k) gsh[k] = 0.f;
 
-  // the next view's tile count and record gradient are requested before the
-  // current view is processed, so their memory latency overlaps its arithmetic
+  // the tile counts and record gradients of the next two views are requested before
+  // the current view is processed, so their memory latency overlaps its arithmetic
   constexpr int NQ = kGradStride / 4;
-  int nt_next = 0;
-  float4 g_next[NQ];
-  if (n_views > 0) {
-    nt_next = ntiles[i];
-    const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + i * kGradStride);
+  int nt_next = 0, nt_next2 = 0;
+  float4 g_next[NQ], g_next2[NQ];
+  auto request = [&](int v, int& nt, float4* gv) {
+    const int64_t idx = (int64_t)v * n + i;
+    nt = ntiles[idx];
+    const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + idx * kGradStride);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) g_next[q] = gr4[q];
-  }
+    for (int q = 0; q < NQ; ++q) gv[q] = gr4[q];
+  };
+  if (n_views > 0) request(0, nt_next, g_next);
+  if (n_views > 1) request(1, nt_next2, g_next2);
   for (int v = 0; v < n_views; ++v) {
     const int nt = nt_next;
     float gq[kGradStride];
@@ -454,16 +468,12 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
       gq[4 * q + 1] = g_next[q].y;
       gq[4 * q + 2] = g_next[q].z;
       gq[4 * q + 3] = g_next[q].w;
+      g_next[q] = g_next2[q];
     }
-    if (v + 1 < n_views) {
-      const int64_t idx1 = (int64_t)(v + 1) * n + i;
-      nt_next = ntiles[idx1];
-      const float4* gr4 = reinterpret_cast<const float4*>(grad_rec + idx1 * kGradStride);
-#pragma unroll
-      for (int q = 0; q < NQ; ++q) g_next[q] = gr4[q];
-    }
+    nt_next = nt_next2;
+    if (v + 2 < n_views) request(v + 2, nt_next2, g_next2);
     if (nt == 0) continue;
-    const DevCam& cam = cams[v];
+    const DevCam& cam = vcams[v];
     const float g_cx = gq[kGcx], g_cy = gq[kGcy], g_o = gq[kGo], g_zc = gq[kGzc];
     const float gA00 = gq[kGA00], gA01 = gq[kGA01], gA10 = gq[kGA10], gA11 = gq[kGA11];
     float ge0 = gq[kGe0];
