@@ -311,6 +311,12 @@ __device__ __forceinline__ BinView load_bin(const float4* __restrict__ bin, uint
   return v;
 }
 
+// view of a (view, Gaussian) record index r = v N + i (record indices fit 32 bits, so
+// a 32-bit division does)
+__device__ __forceinline__ int view_of_record(uint32_t r, int64_t n_gauss) {
+  return (int)(r / (uint32_t)n_gauss);
+}
+
 // first global tile id -> view, by binary search over V+1 prefix offsets
 __device__ __forceinline__ int view_of_tile(const int* tile_prefix, int n_views, int tile) {
   int lo = 0, hi = n_views - 1;

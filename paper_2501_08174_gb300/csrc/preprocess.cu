@@ -222,8 +222,18 @@ __device__ __forceinline__ float project_y(const DevCam& cam, float Y, float Z) 
 // whose stride in float4 is odd (conflict-free 16-byte accesses by 8 threads per
 // phase); otherwise float rows of odd stride.
 constexpr int kPreThreads = 128;
-// views whose cameras the backward projection keeps in shared memory (more are read from global)
+// views whose cameras the projection kernels keep in shared memory (more are read from global)
 constexpr int kSmemCams = 64;
+
+// Copies the views' cameras to s_cams when they fit (the caller's next block barrier
+// publishes them) and returns where the view loop reads them from.
+__device__ __forceinline__ const DevCam* stage_cams(const DevCam* __restrict__ cams, int n_views, DevCam* s_cams) {
+  if (n_views > kSmemCams) return cams;
+  const int words = n_views * (int)(sizeof(DevCam) / sizeof(int));
+  for (int w = threadIdx.x; w < words; w += blockDim.x)
+    reinterpret_cast<int*>(s_cams)[w] = reinterpret_cast<const int*>(cams)[w];
+  return s_cams;
+}
 
 template <int NF>
 struct ShRows {
@@ -317,7 +327,9 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
                                                          int* __restrict__ status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
-  sh_rows_load<3 * K>(g.sh, n, s_rows);
+  __shared__ DevCam s_cams[kSmemCams];
+  const DevCam* vcams = stage_cams(cams, n_views, s_cams);
+  sh_rows_load<3 * K>(g.sh, n, s_rows);  // its barrier also publishes s_cams
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
@@ -340,7 +352,7 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
   const float rf = sqrtf(0.5f * fmaxf(rho_b, 0.f));
 
   for (int v = 0; v < n_views; ++v) {
-    const DevCam& cam = cams[v];
+    const DevCam& cam = vcams[v];
     const int64_t idx = (int64_t)v * n + i;
     bool culled = bad;
     ViewGeom G;
@@ -418,13 +430,7 @@ __global__ void __launch_bounds__(128) preprocess_bwd_kernel(GaussPtrs g, int64_
   __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
   // the views' cameras in shared memory (short-latency reads in the view loop)
   __shared__ DevCam s_cams[kSmemCams];
-  const bool cams_in_smem = n_views <= kSmemCams;
-  if (cams_in_smem) {
-    const int words = n_views * (int)(sizeof(DevCam) / sizeof(int));
-    for (int w = threadIdx.x; w < words; w += blockDim.x)
-      reinterpret_cast<int*>(s_cams)[w] = reinterpret_cast<const int*>(cams)[w];
-  }
-  const DevCam* vcams = cams_in_smem ? s_cams : cams;
+  const DevCam* vcams = stage_cams(cams, n_views, s_cams);
   sh_rows_load<3 * K>(g.sh, n, s_rows);  // its barrier also publishes s_cams
   // every thread reaches the block's final exchange of SH gradients: a thread past
   // the end recomputes the last Gaussian and writes nothing
@@ -603,7 +609,9 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
                                                              int* __restrict__ status) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   __shared__ __align__(16) float s_rows[ShRows<3 * K>::kFloats];
-  sh_rows_load<3 * K>(g.sh, n, s_rows);
+  __shared__ DevCam s_cams[kSmemCams];
+  const DevCam* vcams = stage_cams(cams, n_views, s_cams);
+  sh_rows_load<3 * K>(g.sh, n, s_rows);  // its barrier also publishes s_cams
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float X[3] = {g.xyz[3 * i], g.xyz[3 * i + 1], g.xyz[3 * i + 2]};
@@ -633,7 +641,7 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
   const float rho_b = bad ? 0.f : support_rho(o);
 
   for (int v = 0; v < n_views; ++v) {
-    const DevCam& cam = cams[v];
+    const DevCam& cam = vcams[v];
     const int64_t idx = (int64_t)v * n + i;
     float t[3];
     rot3(cam.R, X, t);

@@ -333,7 +333,7 @@ __global__ void __launch_bounds__(kThreads) tile_count_kernel(const float4* __re
   if (r < n_rec) {
     const BinView b = load_bin(bin, r);
     if (b.rc.z >= b.rc.x) {
-      const DevCam& cam = cams[r / (uint64_t)n_gauss];
+      const DevCam& cam = cams[view_of_record(r, n_gauss)];
       s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
                                    cam.W, cam.H};
       nrows = b.rc.w - b.rc.y + 1;
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
   const int4 rc = bv.rc;
   const bool small = cnt > 0 && (rc.w - rc.y + 1) <= kSmallRows;
   if (small) {
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(r, n_gauss)];
     s_own[warp][lane] = RowOwner{support_conic(bv.g0, bv.g1, bv.g2, bv.rb), rc, cam.tile_offset, cam.tiles_x, cam.W,
                                  cam.H};
     s_rowbase[warp][lane] = (uint32_t)(cam.tile_offset + rc.y * cam.tiles_x);
@@ -467,7 +467,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(
     const int bcnt = __shfl_sync(kFull, cnt, src);
     const BinView bb = load_bin(bin, rr);
     const int4 bc = bb.rc;
-    const DevCam& cam = cams[rr / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(rr, n_gauss)];
     const SupportConic k = support_conic(bb.g0, bb.g1, bb.g2, bb.rb);
     const uint64_t stop = min(oo + (uint64_t)bcnt, (uint64_t)n_pairs);
     uint64_t base = oo;
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kThreads) tile_count_sorted_kernel(const uint3
     r = order[i];
     const BinView b = load_bin(bin, r);
     if (b.rc.z >= b.rc.x) {
-      const DevCam& cam = cams[r / (uint64_t)n_gauss];
+      const DevCam& cam = cams[view_of_record(r, n_gauss)];
       s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
                                    cam.W, cam.H};
       nrows = b.rc.w - b.rc.y + 1;
@@ -755,7 +755,7 @@ __global__ void __launch_bounds__(kThreads) open_candidate_kernel(const uint32_t
   const int4 rc = bin_rect(bin[3 * (size_t)r + 2]);
   int cand = 0;
   if (rc.z >= rc.x) {
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(r, n_gauss)];
     const uint32_t base = (uint32_t)(cam.tile_offset + rc.y * cam.tiles_x);
     for (int ty = rc.y; ty <= rc.w; ++ty)
       cand += open_in(P, base + (uint32_t)((ty - rc.y) * cam.tiles_x), rc.x, rc.z);
@@ -787,7 +787,7 @@ __global__ void __launch_bounds__(kThreads) open_count_kernel(const uint32_t* __
   if (c < nc) {
     const uint32_t r = cand[c];
     const BinView b = load_bin(bin, r);
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(r, n_gauss)];
     s_own[warp][lane] = RowOwner{support_conic(b.g0, b.g1, b.g2, b.rb), b.rc, cam.tile_offset, cam.tiles_x,
                                  cam.W, cam.H};
     nrows = max(0, b.rc.w - b.rc.y + 1);
@@ -863,7 +863,7 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
     // a lane finds its candidate's slices (the rows spread over the warp measured slower
     // here, the candidates behind the front spanning few rows)
     const BinView b = load_bin(bin, r);
-    const DevCam& cam = cams[r / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(r, n_gauss)];
     const SupportConic k = support_conic(b.g0, b.g1, b.g2, b.rb);
     for (int ty = rc.y; ty <= rc.w; ++ty) {
       const RowRuns rr = row_runs(k, ty, tw, th, cam.W, cam.H, rc);
@@ -923,7 +923,7 @@ __global__ void __launch_bounds__(kOpenThreads) duplicate_open_kernel(
     const int bcnt = __shfl_sync(kFull, cnt, src);
     const BinView bb = load_bin(bin, rr);
     const int4 bc = bb.rc;
-    const DevCam& cam = cams[rr / (uint64_t)n_gauss];
+    const DevCam& cam = cams[view_of_record(rr, n_gauss)];
     const SupportConic k = support_conic(bb.g0, bb.g1, bb.g2, bb.rb);
     const uint64_t stop = min(oo + (uint64_t)bcnt, (uint64_t)n_pairs);
     uint64_t base = oo;
