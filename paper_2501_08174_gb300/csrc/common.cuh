@@ -134,13 +134,19 @@ __device__ __forceinline__ SupportConic support_conic(const float4 g0, const flo
   k.a = __fsub_rn(__fmaf_rn(g1.x, g1.x, __fmul_rn(g1.z, g1.z)), __fmul_rn(rt, __fmul_rn(g2.y, g2.y)));
   k.b = __fsub_rn(__fmaf_rn(g1.x, g1.y, __fmul_rn(g1.z, g1.w)), __fmul_rn(rt, __fmul_rn(g2.y, g2.z)));
   k.c = __fsub_rn(__fmaf_rn(g1.y, g1.y, __fmul_rn(g1.w, g1.w)), __fmul_rn(rt, __fmul_rn(g2.z, g2.z)));
-  const float d = -__fmul_rn(rt, __fmul_rn(g2.x, g2.y));
-  const float e = -__fmul_rn(rt, __fmul_rn(g2.x, g2.z));
-  const float f = -__fmul_rn(rt, __fmul_rn(g2.x, g2.x));
-  k.det = __fsub_rn(__fmul_rn(k.a, k.c), __fmul_rn(k.b, k.b));
-  k.mx = __fdividef(__fsub_rn(__fmul_rn(k.b, e), __fmul_rn(k.c, d)), k.det);
-  k.my = __fdividef(__fsub_rn(__fmul_rn(k.b, d), __fmul_rn(k.a, e)), k.det);
-  k.kappa = -__fmaf_rn(e, k.my, __fmaf_rn(d, k.mx, f));
+  // With p = (A00, A10) and q = (A01, A11), the columns of the map, and w = e1 q - e2 p,
+  // Lagrange's identity gives det = a c - b^2 = (A00 A11 - A01 A10)^2 - rt |w|^2, the
+  // centre m = rt e0 (q.w, -p.w) / det and kappa = rt e0 (e0 + e1 mx + e2 my).  These
+  // forms keep their accuracy for a thin ellipse (an almost edge-on surfel), where the
+  // product form a c - b^2 cancels to a few correct digits and shrinks the support.
+  const float D = __fmaf_rn(g1.x, g1.w, -__fmul_rn(g1.y, g1.z));
+  const float wx = __fmaf_rn(g2.y, g1.y, -__fmul_rn(g2.z, g1.x));
+  const float wy = __fmaf_rn(g2.y, g1.w, -__fmul_rn(g2.z, g1.z));
+  k.det = __fsub_rn(__fmul_rn(D, D), __fmul_rn(rt, __fmaf_rn(wx, wx, __fmul_rn(wy, wy))));
+  const float s = __fmul_rn(rt, g2.x);
+  k.mx = __fdividef(__fmul_rn(s, __fmaf_rn(g1.y, wx, __fmul_rn(g1.w, wy))), k.det);
+  k.my = -__fdividef(__fmul_rn(s, __fmaf_rn(g1.x, wx, __fmul_rn(g1.z, wy))), k.det);
+  k.kappa = __fmul_rn(s, __fmaf_rn(g2.z, k.my, __fmaf_rn(g2.y, k.mx, g2.x)));
   k.ellipse = k.a > 0.f && k.det > 0.f && k.kappa > 0.f && isfinite(k.mx) && isfinite(k.my) &&
               isfinite(k.kappa) && isfinite(k.det);
   k.umax = k.vmax = k.vstar = 0.f;
