@@ -86,6 +86,7 @@ SIGNATURES = {
     "ocgs_destroy": (C.c_int, [C.c_void_p]),
     "ocgs_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "ocgs_set_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
+    "ocgs_set_coverage": (C.c_int, [C.c_void_p, C.c_int32]),
     "ocgs_get_options": (C.c_int, [C.c_void_p, C.POINTER(Options)]),
     "ocgs_get_stats": (C.c_int, [C.c_void_p, C.POINTER(Stats)]),
     "ocgs_sync": (C.c_int, [C.c_void_p]),

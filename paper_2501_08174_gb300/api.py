@@ -206,6 +206,12 @@ class Rasterizer:
         self.front_fraction = float(front_fraction)
         self.batch = int(batch)
 
+    def set_coverage(self, rect: bool) -> None:
+        """Tile coverage of the binning (see ocgs_set_coverage): False, the default, keeps the
+        pairs whose support reaches the tile; True bins every tile of each record's screen
+        rectangle with no support test, which must render the same bits, only slower."""
+        self._call("ocgs_set_coverage", self._ctx, int(bool(rect)))
+
     def options(self) -> dict:
         """The context's launch options, as ``set_options`` takes them."""
         return dict(tile=self.tile, persistent=self.persistent, pixels_per_thread=self.pixels_per_thread,

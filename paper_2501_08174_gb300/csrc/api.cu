@@ -26,6 +26,7 @@ struct ocgs_ctx {
   cudaStream_t stream = nullptr;
   cudaMemPool_t pool = nullptr;
   ocgs_options opts{16, 16, 0, 2, 0.f, 32};
+  int cover_rect = 0;  // ocgs_set_coverage
   ocgs_stats stats{};
   std::string err;
   int* d_status = nullptr;
@@ -173,7 +174,7 @@ struct CamPlan {
   int64_t tiles = 0;
 };
 
-CamPlan plan_cameras(const ocgs_camera* cams, int V, int tw, int th) {
+CamPlan plan_cameras(const ocgs_camera* cams, int V, int tw, int th, int cover_rect) {
   CamPlan pl;
   pl.cams.resize(V);
   pl.tile_prefix.resize(V + 1);
@@ -195,6 +196,7 @@ CamPlan plan_cameras(const ocgs_camera* cams, int V, int tw, int th) {
     d.tiles_x = (c.width + tw - 1) / tw;
     d.tiles_y = (c.height + th - 1) / th;
     d.tile_offset = (int)tiles;
+    d.cover_rect = cover_rect;
     d.pix_offset = pix;
     pl.tile_prefix[v] = (int)tiles;
     tiles += (int64_t)d.tiles_x * d.tiles_y;
@@ -275,7 +277,7 @@ ocgs_status forward_pass(ocgs_ctx* ctx, const ocgs_gaussians* g, const ocgs_came
                          bool ewa = false) {
   const int tw = ctx->opts.tile_w, th = ctx->opts.tile_h;
   const int64_t N = g->n;
-  CamPlan pl = plan_cameras(cams, V, tw, th);
+  CamPlan pl = plan_cameras(cams, V, tw, th, ctx->cover_rect);
   if ((uint64_t)N * (uint64_t)V >= 0xffffffffull)
     return set_err(ctx, OCGS_ERR_CAPACITY, "n_views * n exceeds 2^32 - 1 records");
   if (pl.tiles >= (int64_t)INT32_MAX) return set_err(ctx, OCGS_ERR_CAPACITY, "too many tiles");
@@ -787,6 +789,12 @@ ocgs_status ocgs_set_options(ocgs_ctx* ctx, const ocgs_options* o) {
   ctx->opts = *o;
   ctx->opts.pixels_per_thread = ppt;
   ctx->opts.batch = batch;
+  return OCGS_OK;
+}
+
+ocgs_status ocgs_set_coverage(ocgs_ctx* ctx, int32_t rect) {
+  if (!ctx || (rect != 0 && rect != 1)) return OCGS_ERR_ARG;
+  ctx->cover_rect = rect;
   return OCGS_OK;
 }
 
@@ -1478,7 +1486,7 @@ extern "C" ocgs_status ocgs_contribution_graph_create(ocgs_ctx* ctx, const ocgs_
     r = forward_pass(ctx, g, cams + v0, nv, nullptr, nullptr, &st, false);
     if (r != OCGS_OK && r != OCGS_ERR_NONFINITE) return r;
     kmax = std::max<uint64_t>(kmax, (uint64_t)ctx->stats.n_pairs);
-    plans.push_back(plan_cameras(cams + v0, nv, tw, th));
+    plans.push_back(plan_cameras(cams + v0, nv, tw, th, ctx->cover_rect));
     tiles_max = std::max<int64_t>(tiles_max, plans.back().tiles);
   }
   const double capd = (double)kmax * (double)headroom + 4096.0;

@@ -48,7 +48,7 @@ struct DevCam {
   int W, H;
   int tiles_x, tiles_y;
   int tile_offset;   // first global tile id of this view
-  int pad0;
+  int cover_rect;    // 1: the binning takes every tile of a record's screen rectangle (no support test)
   long long pix_offset;  // first pixel of this view in the concatenated images
 };
 

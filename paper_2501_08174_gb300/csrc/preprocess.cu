@@ -408,13 +408,16 @@ __global__ void __launch_bounds__(128) preprocess_kernel(GaussPtrs g, int64_t n,
     rec.g0[idx] = g0;
     rec.g1[idx] = g1;
     rec.g2[idx] = make_float4(e0, e1, e2, pz * e0);
-    bin[3 * idx] = make_float4(g0.x, g0.y, rho_b, g1.x);
+    // the support bound the binning and the rasterizers' row test see; unbounded (every
+    // tile and row of the screen rectangle) when the view checks the support test
+    const float rb_bin = cam.cover_rect ? INFINITY : rho_b;
+    bin[3 * idx] = make_float4(g0.x, g0.y, rb_bin, g1.x);
     bin[3 * idx + 1] = make_float4(g1.y, g1.z, g1.w, e0);
     bin[3 * idx + 2] = make_float4(e1, e2, __uint_as_float(pack_i16x2(rc.x, rc.y)),
                                    __uint_as_float(pack_i16x2(rc.z, rc.w)));
     rec.a0[idx] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), G.n[0]);
     const float4 g2 = make_float4(e0, e1, e2, pz * e0);
-    const float2 rows = support_rows(g0, g1, g2, rho_b);
+    const float2 rows = support_rows(g0, g1, g2, rb_bin);
     rec.a1[idx] = make_float4(G.n[1], G.n[2], rows.x, rows.y);
   }
 }
@@ -707,9 +710,10 @@ __global__ void __launch_bounds__(128) preprocess_ewa_kernel(GaussPtrs g, int64_
     rec.g1[idx] = g1;
     rec.g2[idx] = make_float4(1.f, 0.f, 0.f, t[2]);
     rec.a0[idx] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 0.f);
-    const float2 rows = support_rows(g0, g1, make_float4(1.f, 0.f, 0.f, t[2]), rho_b);
+    const float rb_bin = cam.cover_rect ? INFINITY : rho_b;  // as in the surfel projection
+    const float2 rows = support_rows(g0, g1, make_float4(1.f, 0.f, 0.f, t[2]), rb_bin);
     rec.a1[idx] = make_float4(0.f, 0.f, rows.x, rows.y);
-    bin[3 * idx] = make_float4(g0.x, g0.y, rho_b, g1.x);
+    bin[3 * idx] = make_float4(g0.x, g0.y, rb_bin, g1.x);
     bin[3 * idx + 1] = make_float4(g1.y, g1.z, g1.w, 1.f);
     bin[3 * idx + 2] = make_float4(0.f, 0.f, __uint_as_float(pack_i16x2(rc.x, rc.y)),
                                    __uint_as_float(pack_i16x2(rc.z, rc.w)));

@@ -65,3 +65,67 @@ def test_thin_support_tip_is_binned(dev, tile):
     assert ok[tip].all()
     errs = forward_errors(gpu, ref, ok)
     assert max(errs.values()) <= FWD_TOL, errs
+
+
+@pytest.fixture(scope="module")
+def c4(dev):
+    sc = synthetic.config4()
+    return sc["gaussians"], sc["cameras"]
+
+
+def _render_both(dev, render, n):
+    """render(rast, score) under the exact coverage, then with every tile of each record's
+    screen rectangle: (outputs, score, pairs) of each."""
+    from paper_2501_08174_gb300 import Rasterizer
+    r = Rasterizer(dev, tile=(16, 16), persistent=True, pixels_per_thread=4)
+    res = []
+    for rect in (False, True):
+        r.set_coverage(rect)
+        score = torch.zeros(n, device=dev)
+        out = render(r, score)
+        torch.cuda.synchronize()
+        res.append(({k: v.cpu() for k, v in out.items()}, score.cpu(), r.stats()["n_pairs"]))
+    r.close()
+    return res
+
+
+@pytest.mark.parametrize("front", [0.1, 0.0])
+def test_support_test_drops_no_blend(dev, c4, front):
+    """On the 500k-surfel, 16-view scene, binning every tile of each record's screen rectangle
+    and staging every record for every band (no support test) renders the same bits and the
+    same contribution record as the exact coverage: the support test drops only pairs that
+    blend no pixel.  One pass and two passes."""
+    g_np, cams = c4
+    g = to_device(g_np, dev)
+
+    def render(r, score):
+        r.set_options(tile=(16, 16), persistent=True, pixels_per_thread=4, front_fraction=front)
+        out, st = r.render(g, cams, score=score)
+        st.release()
+        return out
+
+    (a, sa, ka), (b, sb, kb) = _render_both(dev, render, g_np["opacity"].shape[0])
+    assert kb > 1.5 * ka, (ka, kb)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(sa, sb)
+
+
+def test_support_test_drops_no_blend_3d(dev, c4):
+    """The same for the 3DGS variant (Appendix B): projected 3D Gaussians, whose support
+    conic is the covariance's."""
+    g_np, cams = c4
+    rng = np.random.default_rng(44)
+    n = g_np["opacity"].shape[0]
+    third = np.exp(rng.uniform(np.log(0.01), np.log(0.1), size=(n, 1)))
+    g3 = dict(g_np, scale=np.concatenate([np.asarray(g_np["scale"], np.float64), third], 1))
+    g = {k: torch.tensor(np.asarray(g3[k], np.float32), device=dev) for k in ("xyz", "quat", "scale", "opacity", "sh")}
+
+    def render(r, score):
+        return r.render_3d(g, cams, score=score)
+
+    (a, sa, ka), (b, sb, kb) = _render_both(dev, render, n)
+    assert kb > ka, (ka, kb)
+    for k in ("rgb", "alpha", "depth"):
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(sa, sb)
