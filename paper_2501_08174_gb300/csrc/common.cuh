@@ -494,6 +494,65 @@ cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, cons
                                    double* partial, double* loss, float* d_alpha, cudaStream_t s);
 constexpr int kLossBlockPixels = 4096;
 
+// Float32 sums with the rounding error kept (FP64 runs at a small fraction of the
+// FP32 rate on this part): Knuth's TwoSum gives s + err = a + b exactly, and a
+// compensated sum adds each term to hi and collects the rounding errors in lo, so
+// hi + lo carries about twice the float precision.  The loss kernels accumulate
+// per thread this way and reduce the pairs to one FP64 partial per block.
+__device__ __forceinline__ float two_sum(float a, float b, float& err) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return s;
+}
+struct CompSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    float err;
+    hi = two_sum(hi, x, err);
+    lo = __fadd_rn(lo, err);
+  }
+  // a term known as a float pair x + y (y far below x)
+  __device__ __forceinline__ void add(float x, float y) {
+    add(x);
+    lo = __fadd_rn(lo, y);
+  }
+};
+
+// Block totals of NV compensated sums per thread, in a fixed order: each warp's
+// shuffle tree merges the pairs with two_sum, then thread 0 adds the warps' pairs
+// in order in FP64.  Every thread of the NT-thread block calls it; out is written
+// by thread 0.
+template <int NT, int NV>
+__device__ __forceinline__ void block_comp_sums(CompSum (&c)[NV], double* out) {
+  static_assert(NT % 32 == 0, "whole warps");
+  __shared__ float2 s_w[NT / 32][NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h = __shfl_down_sync(0xffffffffu, c[k].hi, o);
+      const float l = __shfl_down_sync(0xffffffffu, c[k].lo, o);
+      float err;
+      c[k].hi = two_sum(c[k].hi, h, err);
+      c[k].lo = __fadd_rn(__fadd_rn(c[k].lo, l), err);
+    }
+  }
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) s_w[threadIdx.x >> 5][k] = make_float2(c[k].hi, c[k].lo);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < NT / 32; ++w) t += (double)s_w[w][k].x + (double)s_w[w][k].y;
+      out[k] = t;
+    }
+  }
+}
+
 // Per-view totals of per-block FP64 partial sums: one CTA of kViewSumThreads per
 // view (blockIdx.x = view) adds NV values per block, partial[NV b + k] for the
 // view's blocks [b0, b1), in a fixed order (each thread a strided run of blocks,

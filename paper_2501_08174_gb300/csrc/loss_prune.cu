@@ -12,31 +12,14 @@ namespace {
 
 constexpr int kLossThreads = 256;
 
-// Float32 arithmetic with the rounding error kept (FP64 is slow on this part):
-// Knuth's TwoSum gives s + err = a + b exactly; compensated summation adds each
-// term to hi and collects the rounding errors in lo, so hi + lo carries about
-// twice the float precision (the per-thread sums reach the FP64 block
-// reduction as (double)hi + (double)lo).
-__device__ __forceinline__ float two_sum(float a, float b, float& err) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-  return s;
-}
-__device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
-  float err;
-  hi = two_sum(hi, x, err);
-  lo = __fadd_rn(lo, err);
-}
-
-// Each block reduces kLossBlockPixels pixels of one view in FP64, in a fixed
-// order, and writes one partial sum; a second pass adds the partials of a view
-// in block order, so the loss is bitwise reproducible.
+// Each block reduces kLossBlockPixels pixels of one view, in a fixed order
+// (compensated float32 sums per thread, merged into one FP64 partial per block),
+// and a second pass adds the partials of a view in block order, so the loss is
+// bitwise reproducible.
 __global__ void __launch_bounds__(kLossThreads) bg_loss_partial_kernel(
     const float* __restrict__ alpha, const uint8_t* __restrict__ mask, const DevCam* __restrict__ cams,
     int n_views, const int* __restrict__ block_prefix, float gamma, double* __restrict__ partial,
     float* __restrict__ d_alpha) {
-  __shared__ double warp_part[kLossThreads / 32];
   const int b = blockIdx.x;
   const int v = view_of_tile(block_prefix, n_views, b);
   const DevCam& cam = cams[v];
@@ -44,23 +27,14 @@ __global__ void __launch_bounds__(kLossThreads) bg_loss_partial_kernel(
   const int64_t lo = (int64_t)(b - block_prefix[v]) * kLossBlockPixels;
   const int64_t hi = (lo + kLossBlockPixels < npix) ? lo + kLossBlockPixels : npix;
   const float g = gamma / (float)npix;
-  float ahi = 0.f, alo = 0.f;
+  CompSum acc[1];
   for (int64_t k = lo + threadIdx.x; k < hi; k += kLossThreads) {
     const int64_t p = cam.pix_offset + k;
     const float bg = mask[p] ? 0.f : 1.f;
-    comp_add(ahi, alo, alpha[p] * bg);  // alpha (1 - M) is exact
+    acc[0].add(alpha[p] * bg);  // alpha (1 - M) is exact
     if (d_alpha) d_alpha[p] += g * bg;
   }
-  double acc = (double)ahi + (double)alo;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kLossThreads / 32; ++w) t += warp_part[w];
-    partial[b] = t;
-  }
+  block_comp_sums<kLossThreads, 1>(acc, partial + b);
 }
 
 // Masked L1 (Eq. 2, L1 part): |I M - R M| summed per block, with the adjoint
@@ -73,7 +47,6 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ block_prefix, float weight,
     double* __restrict__ partial, float* __restrict__ d_rgb) {
-  __shared__ double warp_part[kLossThreads / 32];
   const int b = blockIdx.x;
   const int v = view_of_tile(block_prefix, n_views, b);
   const DevCam& cam = cams[v];
@@ -81,7 +54,7 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
   const int64_t lo = (int64_t)(b - block_prefix[v]) * kLossBlockPixels;
   const int64_t hi = (lo + kLossBlockPixels < npix) ? lo + kLossBlockPixels : npix;
   const float g = weight / (3.0f * (float)npix);
-  float ahi = 0.f, alo = 0.f;
+  CompSum acc[1];
   for (int64_t k = lo + threadIdx.x; k < hi; k += kLossThreads) {
     const int64_t p = cam.pix_offset + k;
     if (!mask[p]) continue;
@@ -89,21 +62,11 @@ __global__ void __launch_bounds__(kLossThreads) l1_partial_kernel(
     for (int c = 0; c < 3; ++c) {
       float e;
       const float d = two_sum(rgb[3 * p + c], -target[3 * p + c], e);
-      comp_add(ahi, alo, fabsf(d));
-      alo = __fadd_rn(alo, d > 0.f ? e : -e);
+      acc[0].add(fabsf(d), d > 0.f ? e : -e);
       if (d_rgb) d_rgb[3 * p + c] += d > 0.f ? g : (d < 0.f ? -g : 0.f);
     }
   }
-  double acc = (double)ahi + (double)alo;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) warp_part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kLossThreads / 32; ++w) t += warp_part[w];
-    partial[b] = t;
-  }
+  block_comp_sums<kLossThreads, 1>(acc, partial + b);
 }
 
 // one CTA per view

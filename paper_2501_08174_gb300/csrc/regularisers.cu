@@ -33,17 +33,11 @@ __device__ __forceinline__ Block loss_block(const int* block_prefix, int n_views
   return b;
 }
 
-__device__ __forceinline__ void block_sum(double acc, double* out) {
-  __shared__ double part[kRegThreads / 32];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-  if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = acc;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kRegThreads / 32; ++w) t += part[w];
-    *out = t;
-  }
+// a * b exactly, as the float pair p + e (FMA: e = a b - p)
+__device__ __forceinline__ float two_prod(float a, float b, float& e) {
+  const float p = __fmul_rn(a, b);
+  e = __fmaf_rn(a, b, -p);
+  return p;
 }
 
 __global__ void __launch_bounds__(kRegThreads) depth_distortion_kernel(
@@ -54,18 +48,24 @@ __global__ void __launch_bounds__(kRegThreads) depth_distortion_kernel(
   const Block b = loss_block(block_prefix, n_views, cams);
   const DevCam& cam = cams[b.v];
   const float k = weight / ((float)cam.W * (float)cam.H);
-  double acc = 0.0;
+  CompSum acc[1];
   for (int64_t i = b.lo + threadIdx.x; i < b.hi; i += kRegThreads) {
     const int64_t p = cam.pix_offset + i;
     const float A = alpha[p], D = depth[p], Q = depth2[p];
-    acc += 2.0 * ((double)A * (double)Q - (double)D * (double)D);
+    // A Q - D^2 from the exact products, so that its cancellation (the blended depths
+    // close together) costs no accuracy: (aq + ea) - (dd + ed), the leading difference
+    // kept exactly by two_sum
+    float ea, ed, es;
+    const float aq = two_prod(A, Q, ea), dd = two_prod(D, D, ed);
+    const float s0 = two_sum(aq, -dd, es);
+    acc[0].add(2.f * s0, 2.f * __fadd_rn(es, __fsub_rn(ea, ed)));
     if (d_alpha) {
       d_alpha[p] += k * 2.f * Q;
       d_depth[p] += k * -4.f * D;
       d_depth2[p] += k * 2.f * A;
     }
   }
-  block_sum(acc, partial + blockIdx.x);
+  block_comp_sums<kRegThreads, 1>(acc, partial + blockIdx.x);
 }
 
 struct Pt {
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(kRegThreads) normal_consistency_kernel(
   const Block b = loss_block(block_prefix, n_views, cams);
   const DevCam& cam = cams[b.v];
   const float k = weight / ((float)cam.W * (float)cam.H);
-  double acc = 0.0;
+  CompSum acc[1];
   for (int64_t i = b.lo + threadIdx.x; i < b.hi; i += kRegThreads) {
     const int64_t p = cam.pix_offset + i;
     const int x = (int)(i % cam.W), y = (int)(i / cam.W);
@@ -121,7 +121,9 @@ __global__ void __launch_bounds__(kRegThreads) normal_consistency_kernel(
         const float3 N = make_float3(s * ch.x, s * ch.y, s * ch.z);
         const float3 Nr = make_float3(normal[3 * p], normal[3 * p + 1], normal[3 * p + 2]);
         const float A = alpha[p];
-        acc += (double)A - (double)dot3(N, Nr);
+        float e;
+        const float t = two_sum(A, -dot3(N, Nr), e);  // A - N . N_r exactly
+        acc[0].add(t, e);
         if (gmap) {
           d_alpha[p] += k;
           d_normal[3 * p] -= k * N.x;
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(kRegThreads) normal_consistency_kernel(
       for (int j = 0; j < 6; ++j) gmap[6 * p + j] = g6[j];
     }
   }
-  block_sum(acc, partial + blockIdx.x);
+  block_comp_sums<kRegThreads, 1>(acc, partial + blockIdx.x);
 }
 
 // point gradient of pixel q: it is the x+1 point of q - x, the x-1 point of

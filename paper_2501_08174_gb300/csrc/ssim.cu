@@ -64,13 +64,14 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
     int64_t p_total, double* __restrict__ partial, float* __restrict__ gmap) {
   __shared__ float2 sx[kP][kP + 1];               // (masked target x1, masked render x2) of one channel
   __shared__ __align__(16) float h[5][kP][kT];    // row-windowed x1, x2, x1^2, x2^2, x1 x2
-  __shared__ double red[3][kThreadsSsim / 32];
+  __shared__ int s_cnt[kThreadsSsim / 32];
   int v, x0, y0;
   tile_origin(prefix, n_views, cams, &v, &x0, &y0);
   const DevCam& cam = cams[v];
   const int tid = threadIdx.x;
   const int col = tid % kT, r0 = (tid / kT) * kSeg;  // second pass: 4 rows of one column
-  double sum_all = 0.0, sum_m = 0.0, cnt = 0.0;
+  CompSum sums[2];  // S over all values, S over the mask values
+  int cnt = 0;      // mask values
   for (int c = 0; c < 3; ++c) {
     if (c > 0) __syncthreads();  // the previous channel's second pass is done with sx and h
     for (int i = tid; i < kP * kP; i += kThreadsSsim) {
@@ -129,10 +130,10 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
       const float d1 = mu1 * mu1 + mu2 * mu2 + kC1, d2 = v11 + v22 + kC2;
       const float inv = 1.f / (d1 * d2);
       const float S = n1 * n2 * inv;
-      sum_all += (double)S;
+      sums[0].add(S);
       if (m) {
-        sum_m += (double)S;
-        cnt += 1.0;
+        sums[1].add(S);
+        ++cnt;
       }
       if (gmap) {
         // partial derivatives at fixed (mu, sigma), then through sigma22 = E[x2^2] - mu2^2
@@ -146,23 +147,14 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
       }
     }
   }
-  // block sums (fixed order: warp shuffles, then warps in order)
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    sum_all += __shfl_down_sync(0xffffffffu, sum_all, o);
-    sum_m += __shfl_down_sync(0xffffffffu, sum_m, o);
-    cnt += __shfl_down_sync(0xffffffffu, cnt, o);
-  }
-  if ((tid & 31) == 0) {
-    red[0][tid >> 5] = sum_all;
-    red[1][tid >> 5] = sum_m;
-    red[2][tid >> 5] = cnt;
-  }
-  __syncthreads();
-  if (tid < 3) {
-    double t = 0.0;
-    for (int w = 0; w < kThreadsSsim / 32; ++w) t += red[tid][w];
-    partial[3 * blockIdx.x + tid] = t;
+  // block sums in a fixed order; the barrier inside block_comp_sums publishes s_cnt
+  const int wc = __reduce_add_sync(0xffffffffu, cnt);
+  if ((tid & 31) == 0) s_cnt[tid >> 5] = wc;
+  block_comp_sums<kThreadsSsim, 2>(sums, partial + 3 * blockIdx.x);
+  if (tid == 0) {
+    int t = 0;
+    for (int w = 0; w < kThreadsSsim / 32; ++w) t += s_cnt[w];
+    partial[3 * blockIdx.x + 2] = (double)t;
   }
 }
 
