@@ -80,9 +80,9 @@ __device__ __forceinline__ Pt surface_point(const float* __restrict__ alpha, con
   r.P = make_float3(0.f, 0.f, 0.f);
   if (x < 0 || x >= cam.W || y < 0 || y >= cam.H) return r;
   const int64_t p = cam.pix_offset + (int64_t)y * cam.W + x;
-  const float A = alpha[p];
+  const float A = alpha[p], D = depth[p];  // both loads issued before the test
   if (!(A > a_min)) return r;
-  const float d = depth[p] / A;
+  const float d = D / A;
   r.P = make_float3(d * (((float)x + 0.5f - cam.cx) / cam.fx), d * (((float)y + 0.5f - cam.cy) / cam.fy), d);
   r.ok = true;
   return r;

@@ -26,6 +26,8 @@ constexpr int kSeg = 4;              // outputs per thread along a row (first pa
 constexpr int kThreadsSsim = 256;
 constexpr int kTaps = 2 * kR + 1;
 constexpr int kRowItems = kP * (kT / kSeg);  // row segments of one plane (336)
+constexpr int kPatchLoads = (kP * kP + kThreadsSsim - 1) / kThreadsSsim;  // patch values per thread (7)
+constexpr int kLoadGroup = 4;        // patch values a thread of the statistics pass loads at once
 constexpr float kC1 = 0.0001f;       // (0.01)^2
 constexpr float kC2 = 0.0009f;       // (0.03)^2
 
@@ -58,7 +60,7 @@ __device__ __forceinline__ void taps4(const float (&in)[kSeg + 2 * kR], const Wi
 // partial[3 b + k]: k = 0 sum of S over the tile's values, 1 sum over its mask
 // values, 2 number of mask values.  gmap (or NULL): planes [9][P_total], plane
 // 3 c + j holds, for channel c, j = 0 dS/dE[x2], 1 dS/dE[x2^2], 2 dS/dE[x1 x2].
-__global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
+__global__ void __launch_bounds__(kThreadsSsim, 4) ssim_stats_kernel(
     const float* __restrict__ rgb, const float* __restrict__ target, const uint8_t* __restrict__ mask,
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ prefix, const Window win,
     int64_t p_total, double* __restrict__ partial, float* __restrict__ gmap) {
@@ -74,15 +76,32 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_stats_kernel(
   int cnt = 0;      // mask values
   for (int c = 0; c < 3; ++c) {
     if (c > 0) __syncthreads();  // the previous channel's second pass is done with sx and h
-    for (int i = tid; i < kP * kP; i += kThreadsSsim) {
-      const int py = i / kP, px = i % kP;
-      const int gy = y0 - kR + py, gx = x0 - kR + px;
-      float2 q = make_float2(0.f, 0.f);
-      if (gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W) {
-        const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-        if (mask[p]) q = make_float2(target[3 * p + c], rgb[3 * p + c]);
+    // the patch in groups of kLoadGroup values per thread, each group's loads issued
+    // before the first is used (the memory latency is paid per group, not per value)
+#pragma unroll
+    for (int j0 = 0; j0 < kPatchLoads; j0 += kLoadGroup) {
+      float lt[kLoadGroup], lr[kLoadGroup];
+      bool lm[kLoadGroup];
+#pragma unroll
+      for (int u = 0; u < kLoadGroup; ++u) {
+        const int i = tid + (j0 + u) * kThreadsSsim;
+        const int py = i / kP, px = i % kP;
+        const int gy = y0 - kR + py, gx = x0 - kR + px;
+        lt[u] = lr[u] = 0.f;
+        lm[u] = false;
+        if (j0 + u < kPatchLoads && i < kP * kP && gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W) {
+          const int64_t q = cam.pix_offset + (int64_t)gy * cam.W + gx;
+          lm[u] = mask[q] != 0;
+          lt[u] = target[3 * q + c];
+          lr[u] = rgb[3 * q + c];
+        }
       }
-      sx[py][px] = q;
+#pragma unroll
+      for (int u = 0; u < kLoadGroup; ++u) {
+        const int i = tid + (j0 + u) * kThreadsSsim;
+        if (j0 + u < kPatchLoads && i < kP * kP)
+          sx[i / kP][i % kP] = lm[u] ? make_float2(lt[u], lr[u]) : make_float2(0.f, 0.f);
+      }
     }
     __syncthreads();
     for (int i = tid; i < kRowItems; i += kThreadsSsim) {
@@ -173,14 +192,24 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_grad_kernel(
   const float coef = -weight / (3.f * (float)cam.W * (float)cam.H);
   for (int c = 0; c < 3; ++c) {
     if (c > 0) __syncthreads();
-    for (int i = tid; i < 3 * kP * kP; i += kThreadsSsim) {
-      const int j = i / (kP * kP), rem = i % (kP * kP);
-      const int py = rem / kP, px = rem % kP;
-      const int gy = y0 - kR + py, gx = x0 - kR + px;
-      float val = 0.f;
-      if (gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W)
-        val = gmap[(3 * c + j) * p_total + cam.pix_offset + (int64_t)gy * cam.W + gx];
-      sg[j][py][px] = val;
+    // each plane's patch in one group: its loads in flight together, then the stores
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      float lv[kPatchLoads];
+#pragma unroll
+      for (int k = 0; k < kPatchLoads; ++k) {
+        const int i = tid + k * kThreadsSsim;
+        const int py = i / kP, px = i % kP;
+        const int gy = y0 - kR + py, gx = x0 - kR + px;
+        lv[k] = 0.f;
+        if (i < kP * kP && gy >= 0 && gy < cam.H && gx >= 0 && gx < cam.W)
+          lv[k] = gmap[(3 * c + j) * p_total + cam.pix_offset + (int64_t)gy * cam.W + gx];
+      }
+#pragma unroll
+      for (int k = 0; k < kPatchLoads; ++k) {
+        const int i = tid + k * kThreadsSsim;
+        if (i < kP * kP) sg[j][i / kP][i % kP] = lv[k];
+      }
     }
     __syncthreads();
     for (int i = tid; i < 3 * kRowItems; i += kThreadsSsim) {
@@ -201,14 +230,27 @@ __global__ void __launch_bounds__(kThreadsSsim) ssim_grad_kernel(
       for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = h[j][r0 + t][col];
       taps4(in, win, g[j]);
     }
+    // x2 = R M: no gradient where M = 0 (the loads of the 4 outputs are issued together)
+    bool om[kSeg];
+    float o1[kSeg], o2[kSeg], od[kSeg];
 #pragma unroll
     for (int k = 0; k < kSeg; ++k) {
       const int gx = x0 + col, gy = y0 + r0 + k;
-      if (gx >= cam.W || gy >= cam.H) continue;
-      const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
-      if (!mask[p]) continue;  // x2 = R M: no gradient where M = 0
-      const float x1 = target[3 * p + c], x2 = rgb[3 * p + c];
-      d_rgb[3 * p + c] += coef * (g[0][k] + 2.f * x2 * g[1][k] + x1 * g[2][k]);
+      om[k] = false;
+      o1[k] = o2[k] = od[k] = 0.f;
+      if (gx < cam.W && gy < cam.H) {
+        const int64_t p = cam.pix_offset + (int64_t)gy * cam.W + gx;
+        om[k] = mask[p] != 0;
+        o1[k] = target[3 * p + c];
+        o2[k] = rgb[3 * p + c];
+        od[k] = d_rgb[3 * p + c];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kSeg; ++k) {
+      if (!om[k]) continue;
+      const int64_t p = cam.pix_offset + (int64_t)(y0 + r0 + k) * cam.W + (x0 + col);
+      d_rgb[3 * p + c] = od[k] + coef * (g[0][k] + 2.f * o2[k] * g[1][k] + o1[k] * g[2][k]);
     }
   }
 }
