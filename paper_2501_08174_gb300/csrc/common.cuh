@@ -494,6 +494,28 @@ cudaError_t launch_background_loss(const float* alpha, const uint8_t* mask, cons
                                    double* partial, double* loss, float* d_alpha, cudaStream_t s);
 constexpr int kLossBlockPixels = 4096;
 
+// Packed FP32x2 arithmetic: pfma / pmul / padd round each lane as the scalar
+// operation does, so a pair gives two scalar results bit for bit whether it runs
+// on the packed instructions of sm_100+ (__ffma2_rn, ...) or, with
+// -DOCGS_SCALAR_PAIRS, as two scalar ones (measured 9-10 % slower in both
+// rasterizers on 500k surfels x 16 views).
+#ifdef OCGS_SCALAR_PAIRS
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
+}
+#else
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+#endif
+__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+
 // Float32 sums with the rounding error kept (FP64 runs at a small fraction of the
 // FP32 rate on this part): Knuth's TwoSum gives s + err = a + b exactly, and a
 // compensated sum adds each term to hi and collects the rounding errors in lo, so

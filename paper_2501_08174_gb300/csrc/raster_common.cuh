@@ -79,27 +79,9 @@ __device__ __forceinline__ SplatColumn splat_column(const float4 g0, const float
 }
 
 // Two pixels of one column (rows py.x and py.y) are evaluated together as a
-// pair.  pfma / pmul / padd round each lane as the scalar operation does, so a
-// pair gives the two scalar results bit for bit whether it runs on the packed
-// FP32x2 instructions of sm_100+ (__ffma2_rn, ...) or as two scalar ones
-// (-DOCGS_SCALAR_PAIRS: measured 9-10 % slower in both rasterizers on 500k
-// surfels x 16 views).
-#ifdef OCGS_SCALAR_PAIRS
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
-  return make_float2(__fmaf_rn(a.x, b.x, c.x), __fmaf_rn(a.y, b.y, c.y));
-}
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
-  return make_float2(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y));
-}
-__device__ __forceinline__ float2 padd(float2 a, float2 b) {
-  return make_float2(__fadd_rn(a.x, b.x), __fadd_rn(a.y, b.y));
-}
-#else
-__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
-__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
-__device__ __forceinline__ float2 padd(float2 a, float2 b) { return __fadd2_rn(a, b); }
-#endif
-__device__ __forceinline__ float2 bc2(float x) { return make_float2(x, x); }
+// pair with the packed FP32x2 helpers pfma / pmul / padd of common.cuh (each
+// lane rounded as the scalar operation), so a pair gives the two scalar results
+// bit for bit.
 __device__ __forceinline__ float lane2(float2 v, int i) { return i ? v.y : v.x; }
 __device__ __forceinline__ void set_lane2(float2& v, int i, float x) {
   if (i) v.y = x;

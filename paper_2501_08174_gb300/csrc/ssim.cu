@@ -6,7 +6,9 @@
 // a 42x42 patch (its 32x32 output tile plus a 5-pixel halo) of one channel of
 // both masked images in shared memory and applies the 11 taps along rows, then
 // columns, each thread producing 4 neighbouring outputs from one 14-value
-// window so that a staged value is read once per 4 outputs.
+// window so that a staged value is read once per 4 outputs.  The statistics
+// pass filters (x1, x2) and (x1^2, x2^2) as packed FP32x2 pairs, one packed FMA
+// per tap for two planes (each lane rounded as the scalar tap).
 // The adjoint of the mean SSIM needs, at every pixel q,
 //     sum_p dS(p)/dE[x2](p) G(p-q) + 2 x2(q) sum_p dS(p)/dE[x2^2](p) G(p-q)
 //                                 +   x1(q) sum_p dS(p)/dE[x1 x2](p) G(p-q),
@@ -57,6 +59,18 @@ __device__ __forceinline__ void taps4(const float (&in)[kSeg + 2 * kR], const Wi
   }
 }
 
+// the same window over pairs of planes, one packed FP32x2 FMA per tap (each lane
+// rounded as taps4 rounds it)
+__device__ __forceinline__ void taps4x2(const float2 (&in)[kSeg + 2 * kR], const Window& win, float2 (&out)[kSeg]) {
+#pragma unroll
+  for (int k = 0; k < kSeg; ++k) {
+    float2 acc = bc2(0.f);
+#pragma unroll
+    for (int t = 0; t < kTaps; ++t) acc = pfma(bc2(win.w[t]), in[k + t], acc);
+    out[k] = acc;
+  }
+}
+
 // partial[3 b + k]: k = 0 sum of S over the tile's values, 1 sum over its mask
 // values, 2 number of mask values.  gmap (or NULL): planes [9][P_total], plane
 // 3 c + j holds, for channel c, j = 0 dS/dE[x2], 1 dS/dE[x2^2], 2 dS/dE[x1 x2].
@@ -65,7 +79,9 @@ __global__ void __launch_bounds__(kThreadsSsim, 4) ssim_stats_kernel(
     const DevCam* __restrict__ cams, int n_views, const int* __restrict__ prefix, const Window win,
     int64_t p_total, double* __restrict__ partial, float* __restrict__ gmap) {
   __shared__ float2 sx[kP][kP + 1];               // (masked target x1, masked render x2) of one channel
-  __shared__ __align__(16) float h[5][kP][kT];    // row-windowed x1, x2, x1^2, x2^2, x1 x2
+  // row-windowed (x1, x2), (x1^2, x2^2) as packed pairs, and x1 x2
+  __shared__ __align__(16) float2 h01[kP][kT], h23[kP][kT];
+  __shared__ __align__(16) float h4[kP][kT];
   __shared__ int s_cnt[kThreadsSsim / 32];
   int v, x0, y0;
   tile_origin(prefix, n_views, cams, &v, &x0, &y0);
@@ -106,36 +122,50 @@ __global__ void __launch_bounds__(kThreadsSsim, 4) ssim_stats_kernel(
     __syncthreads();
     for (int i = tid; i < kRowItems; i += kThreadsSsim) {
       const int r = i / (kT / kSeg), x = (i % (kT / kSeg)) * kSeg;
-      float a[kSeg + 2 * kR], b[kSeg + 2 * kR], aa[kSeg + 2 * kR], bb[kSeg + 2 * kR], ab[kSeg + 2 * kR];
+      float2 in2[kSeg + 2 * kR], sq2[kSeg + 2 * kR];
+      float x12[kSeg + 2 * kR];
 #pragma unroll
       for (int t = 0; t < kSeg + 2 * kR; ++t) {
         const float2 q = sx[r][x + t];
-        a[t] = q.x;
-        b[t] = q.y;
-        aa[t] = q.x * q.x;
-        bb[t] = q.y * q.y;
-        ab[t] = q.x * q.y;
+        in2[t] = q;
+        sq2[t] = pmul(q, q);
+        x12[t] = __fmul_rn(q.x, q.y);
       }
+      float2 o2[kSeg];
       float o[kSeg];
-      taps4(a, win, o);
-      *reinterpret_cast<float4*>(&h[0][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
-      taps4(b, win, o);
-      *reinterpret_cast<float4*>(&h[1][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
-      taps4(aa, win, o);
-      *reinterpret_cast<float4*>(&h[2][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
-      taps4(bb, win, o);
-      *reinterpret_cast<float4*>(&h[3][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
-      taps4(ab, win, o);
-      *reinterpret_cast<float4*>(&h[4][r][x]) = make_float4(o[0], o[1], o[2], o[3]);
+      taps4x2(in2, win, o2);
+      *reinterpret_cast<float4*>(&h01[r][x]) = make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y);
+      *reinterpret_cast<float4*>(&h01[r][x + 2]) = make_float4(o2[2].x, o2[2].y, o2[3].x, o2[3].y);
+      taps4x2(sq2, win, o2);
+      *reinterpret_cast<float4*>(&h23[r][x]) = make_float4(o2[0].x, o2[0].y, o2[1].x, o2[1].y);
+      *reinterpret_cast<float4*>(&h23[r][x + 2]) = make_float4(o2[2].x, o2[2].y, o2[3].x, o2[3].y);
+      taps4(x12, win, o);
+      *reinterpret_cast<float4*>(&h4[r][x]) = make_float4(o[0], o[1], o[2], o[3]);
     }
     __syncthreads();
-    float st[5][kSeg];
+    float st[5][kSeg];  // windowed x1, x2, x1^2, x2^2, x1 x2
+    {
+      float2 in2[kSeg + 2 * kR], o2[kSeg];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in2[t] = h01[r0 + t][col];
+      taps4x2(in2, win, o2);
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k) {
+        st[0][k] = o2[k].x;
+        st[1][k] = o2[k].y;
+      }
+#pragma unroll
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in2[t] = h23[r0 + t][col];
+      taps4x2(in2, win, o2);
+#pragma unroll
+      for (int k = 0; k < kSeg; ++k) {
+        st[2][k] = o2[k].x;
+        st[3][k] = o2[k].y;
+      }
       float in[kSeg + 2 * kR];
 #pragma unroll
-      for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = h[q][r0 + t][col];
-      taps4(in, win, st[q]);
+      for (int t = 0; t < kSeg + 2 * kR; ++t) in[t] = h4[r0 + t][col];
+      taps4(in, win, st[4]);
     }
 #pragma unroll
     for (int k = 0; k < kSeg; ++k) {
