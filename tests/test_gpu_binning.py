@@ -129,3 +129,23 @@ def test_support_test_drops_no_blend_3d(dev, c4):
     for k in ("rgb", "alpha", "depth"):
         assert torch.equal(a[k], b[k]), k
     assert torch.equal(sa, sb)
+
+
+def test_support_test_drops_no_blend_1m_64views(dev):
+    """The same check on the 1M-surfel, 64-view scene (1600x1200 views; 40 % of the surfels on
+    tangent shells, many seen almost edge-on), in two passes with the Q plane as the training
+    iteration renders it."""
+    sc = synthetic.config5()
+    g_np, cams = sc["gaussians"], sc["cameras"]
+    g = to_device(g_np, dev)
+
+    def render(r, score):
+        out, st = r.render(g, cams, score=score, depth2=True)
+        st.release()
+        return out
+
+    (a, sa, ka), (b, sb, kb) = _render_both(dev, render, g_np["opacity"].shape[0])
+    assert kb > ka, (ka, kb)
+    for k in a:
+        assert torch.equal(a[k], b[k]), k
+    assert torch.equal(sa, sb)
